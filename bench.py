@@ -1,0 +1,319 @@
+"""Benchmark: betweenness centrality GTEPS of MFBC on one GB300 (or N, one process per GPU).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl mfbc|reference] [--workload rmat22]
+
+One step = one whole MFBC pass (Algorithm 3: every batch of MFBF + MFBr +
+lambda accumulation) over the workload's full source list on the
+device-resident graph.  Default workload: unweighted undirected R-MAT scale 22
+(edge factor 16, a,b,c,d = .57,.19,.19,.05, seeded relabelling), 16384 sources
+sampled among vertices of degree >= 1.  GTEPS = sources * m / seconds with m
+the number of undirected edges.
+
+Printed JSON line (rank 0):
+  value       device-resident throughput over K timed steps (CUDA events on the
+              launching stream, barrier + synchronize on both sides, max over ranks);
+  e2e         the same metric through the C ABI with HOST buffers: graph upload
+              and construction (mfbc_graph_create from pinned host CSR),
+              mfbc_bc with host sources, lambda copied back to the host;
+  roofline    the dominant kernel's algorithmic bytes per launch (device-counted
+              in an untimed pass) over its average launch time (CUDA events
+              recorded by the library on the launching stream during the timed
+              steps), against the measured HBM copy bandwidth;
+  cpu_baseline  the CPU oracle (plain C Brandes) on a bounded sample of the
+              same workload on all host cores, rank 0 only.
+Multi-GPU (torchrun): each rank runs its own sample of sources (weak scaling)
+and lambda is summed across ranks with one all-reduce per step.
+The state (n x n_b x 8 bytes and more) is far larger than the 129 MB L2, so no
+explicit L2 flush is done between steps.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    "rmat22": dict(kind="rmat", scale=22, ef=16, nsrc=16384,
+                   desc="R-MAT scale 22, edge factor 16, undirected, unweighted, 16384 sampled sources"),
+    "er20k32": dict(kind="er", n=1 << 20, k=32, nsrc=16384,
+                    desc="Erdos-Renyi n=2^20, k=32, undirected, unweighted, 16384 sampled sources"),
+    "rmat16w": dict(kind="rmat16w", nsrc=4096,
+                    desc="R-MAT scale 16, edge factor 16, directed, weights U[1,255], 4096 sources, n_b=512"),
+}
+
+
+def make_workload(name, rank=0):
+    import graphgen as gg
+    w = WORKLOADS[name]
+    if w["kind"] == "rmat":
+        g = gg.rmat(w["scale"], w["ef"], seed=1)
+    elif w["kind"] == "er":
+        g = gg.erdos_renyi(w["n"], w["k"], seed=1)
+    else:
+        g = gg.rmat(16, 16, directed=True, weights=(1, 255), seed=1)
+    srcs = gg.sample_sources(g, w["nsrc"], seed=2 + rank)
+    return g, srcs
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{device_index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(g, srcs, budget_s=15.0):
+    """The oracle as it stands, on all host cores, on a bounded sample of sources."""
+    import oracle
+    nth = oracle.default_threads()
+    k = max(nth, 1)
+    t0 = time.perf_counter()
+    oracle.bc(g, srcs[:k], nthreads=nth)
+    dt = time.perf_counter() - t0
+    per_src = dt / k
+    k2 = int(min(len(srcs), max(k, (budget_s / max(per_src, 1e-6)) // nth * nth)))
+    if k2 > k:
+        t0 = time.perf_counter()
+        oracle.bc(g, srcs[:k2], nthreads=nth)
+        dt = time.perf_counter() - t0
+        k = k2
+    return {"value": k * g.m / dt / 1e9, "unit": "GTEPS", "cores": nth, "kind": "oracle",
+            "sample": f"first {k} of the {len(srcs)} sources, {dt:.1f} s"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    g, srcs = make_workload(args.workload)
+    import oracle
+    nth = oracle.default_threads()
+    per_step = max(nth, args.ref_sources)
+    for _ in range(args.warmup):
+        oracle.bc(g, srcs[:nth], nthreads=nth)
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        sl = srcs[(i * per_step) % len(srcs):][:per_step]
+        oracle.bc(g, sl, nthreads=nth)
+    dt = time.perf_counter() - t0
+    val = args.steps * per_step * g.m / dt / 1e9
+    line = {"impl": "reference", "metric": "BC GTEPS", "value": val, "unit": "GTEPS", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config_of(args, g, len(srcs), None),
+            "cpu_baseline": {"value": val, "unit": "GTEPS", "cores": nth, "kind": "oracle",
+                             "sample": f"{per_step} sources per step of the {len(srcs)}-source workload"},
+            "e2e": {"value": val, "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def config_of(args, g, nsrc, n_b):
+    return {"workload": WORKLOADS[args.workload]["desc"], "name": args.workload, "n": g.n, "nnz": g.nnz,
+            "m": g.m, "sources": nsrc, "n_b": n_b, "parallelism": f"sources sharded x{args.gpus}",
+            "l2": "state much larger than L2 (no flush)"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="mfbc", choices=["mfbc", "reference"])
+    ap.add_argument("--workload", default="rmat22", choices=sorted(WORKLOADS))
+    ap.add_argument("--n-b", type=int, default=0)
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--ref-sources", type=int, default=64)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--sources", type=int, default=0, help="use only the first N sources (probing)")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import paper_1609_07008_gb300 as mfbc
+    from paper_1609_07008_gb300 import build as mbuild
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if rank == 0:
+        mbuild.build()
+    if dist:
+        dist.barrier()
+    mfbc.load()
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+
+    g, srcs = make_workload(args.workload, rank)
+    if args.sources:
+        srcs = srcs[:args.sources]
+    nb_req = args.n_b or (512 if args.workload == "rmat16w" else 0)
+    G = mfbc.Graph.from_csr(g)
+    d_src = torch.from_numpy(srcs).to(dev)
+    lam = torch.empty(g.n, dtype=torch.float64, device=dev)
+
+    def step(profile=False):
+        out = G.bc(d_src, n_b=nb_req, out=lam, profile=profile)
+        if dist:
+            dist.all_reduce(lam)
+        return out
+
+    def barrier_sync():
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # untimed pass that counts algorithmic bytes per kernel on the device
+    _, prof_bytes = G.bc(d_src, n_b=nb_req, out=lam, count_bytes=True)
+    for _ in range(args.warmup):
+        step()
+    clocks = ClockSampler(local)
+    barrier_sync()
+    clocks.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    kstats = {}
+    ev0.record(stream)
+    for _ in range(args.steps):
+        _, prof = step(profile=True)
+        for k, v in prof["kernels"].items():
+            a = kstats.setdefault(k, {"launches": 0, "ms": 0.0})
+            a["launches"] += v["launches"]
+            a["ms"] += v["ms"]
+    ev1.record(stream)
+    barrier_sync()
+    clk = clocks.stop()
+    t = ev0.elapsed_time(ev1) / 1e3
+    if dist:
+        tt = torch.tensor([t], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t = float(tt.item())
+    units = args.steps * len(srcs) * g.m * world
+    value = units / t / 1e9
+
+    # end to end through the host-buffer C ABI
+    rp = torch.from_numpy(g.rowptr).pin_memory().numpy()
+    cl = torch.from_numpy(g.col).pin_memory().numpy()
+    hs = torch.from_numpy(srcs).pin_memory().numpy()
+    hl = torch.empty(g.n, dtype=torch.float64).pin_memory().numpy()
+    h2d = rp.nbytes + cl.nbytes + hs.nbytes
+    G.close()
+    del G
+    torch.cuda.empty_cache()
+    barrier_sync()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        with mfbc.Graph(rp, cl, None, directed=g.directed) as Ge:
+            Ge.bc(hs, n_b=nb_req, out=hl)
+        if dist:
+            x = torch.from_numpy(hl).to(dev)
+            dist.all_reduce(x)
+            hl[:] = x.cpu().numpy()
+    barrier_sync()
+    te = time.perf_counter() - t0
+    if dist:
+        tt = torch.tensor([te], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        te = float(tt.item())
+    e2e = args.e2e_steps * len(srcs) * g.m * world / te / 1e9
+
+    if rank == 0:
+        peak, peak_kind = load_peaks()
+        dom = max(kstats.items(), key=lambda kv: kv[1]["ms"])[0]
+        kb = prof_bytes["kernels"].get(dom, {})
+        per_launch_bytes = kb.get("bytes", 0.0) / max(kb.get("launches", 1), 1)
+        avg_ms = kstats[dom]["ms"] / kstats[dom]["launches"]
+        achieved = per_launch_bytes / (avg_ms / 1e3) / 1e9 if avg_ms > 0 else 0.0
+        launches = sum(v["launches"] for v in kstats.values())
+        line = {
+            "metric": "BC GTEPS", "value": value, "unit": "GTEPS", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_of(args, g, len(srcs), prof_bytes["n_b"]),
+            "clocks": clk,
+            "e2e": {"value": e2e, "unit": "GTEPS", "h2d_bytes_per_step": int(h2d),
+                    "d2h_bytes_per_step": int(hl.nbytes)},
+            "gpu_launches": int(launches),
+            "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
+                         "peak_kind": f"{peak_kind} copy bandwidth", "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "bytes_per_launch": per_launch_bytes, "avg_launch_ms": avg_ms},
+            "kernels_ms_share": {k: round(v["ms"] / sum(x["ms"] for x in kstats.values()), 4)
+                                 for k, v in sorted(kstats.items(), key=lambda kv: -kv[1]["ms"])},
+        }
+        if world == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(g, srcs)
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

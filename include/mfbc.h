@@ -1,0 +1,178 @@
+/*
+ * mfbc.h -- C ABI of the MFBC library (Maximal Frontier Betweenness
+ * Centrality; Solomonik, Besta, Vella, Hoefler, SC17, arXiv:1609.07008).
+ *
+ * The library computes, on one GPU, the two sparse passes of the paper and
+ * the centrality update that joins them:
+ *   MFBF  (Sec. 4.1, Algorithm 1): distances tau(s,v) and shortest-path
+ *         multiplicities sigma_bar(s,v) for a batch of n_b sources, as a
+ *         repeated generalised product of a sparse n x n_b frontier with the
+ *         adjacency matrix over the multpath monoid;
+ *   MFBr  (Sec. 4.2, Algorithm 2): partial centrality factors
+ *         zeta(s,v) = delta(s,v) / sigma_bar(s,v), propagated backwards from
+ *         the leaves of the shortest-path DAG over the centpath monoid;
+ *   MFBC  (Sec. 4.3, Algorithm 3): lambda(v) += sum_s zeta(s,v) sigma_bar(s,v)
+ *         over batches of sources.
+ *
+ * Conventions shared by every call
+ *  - Graphs are CSR over the adjacency matrix A of Sec. 2.1: row v lists the
+ *    arcs v -> col[k] with integer weight w[k] >= 1 (w == NULL: every arc
+ *    weighs 1).  Vertex ids are 0..n-1.  Rows must be sorted by column with
+ *    no duplicate arcs and no self-loops.
+ *  - Distances are int32 with INT32_MAX meaning "unreachable" (the infinity
+ *    of Sec. 2.1); path multiplicities and centralities are IEEE FP64.
+ *    Multiplicities are exact integers while below 2^53.
+ *  - Every call returns an mfbc_status; nothing aborts or throws.  On error
+ *    the outputs are unspecified and mfbc_last_error() describes the cause.
+ *  - "host" pointers are ordinary CPU memory (pinned memory makes copies
+ *    faster); "device" pointers are CUDA global memory of the current device.
+ *    The caller owns every buffer it passes; the library never keeps a
+ *    pointer to caller memory after a call returns.
+ *  - Calls on one graph handle must not overlap (the handle caches scratch
+ *    memory); distinct handles are independent.
+ */
+#ifndef MFBC_H
+#define MFBC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  MFBC_OK = 0,
+  MFBC_ERR_INVALID = 1,        /* bad argument or malformed graph */
+  MFBC_ERR_OOM = 2,            /* device or host allocation failed */
+  MFBC_ERR_CUDA = 3,           /* a CUDA runtime call failed */
+  MFBC_ERR_OVERFLOW = 4,       /* (n-1) * max weight could overflow int32 distances */
+  MFBC_ERR_NO_CONVERGENCE = 5, /* an MFBF/MFBr loop exceeded its iteration bound */
+  MFBC_ERR_TIMEOUT = 6         /* reserved: a bounded device-side wait gave up */
+} mfbc_status;
+
+/* mfbc_graph_create flags */
+#define MFBC_DIRECTED   0u
+#define MFBC_UNDIRECTED 1u     /* A is symmetric with symmetric weights (checked) */
+
+/* bits written to *mfbc_options.warn_out */
+#define MFBC_WARN_SIGMA_INEXACT 1u  /* some sigma_bar >= 2^53: FP64 counts may be rounded */
+
+/* mfbc_options.path */
+#define MFBC_PATH_AUTO    0    /* level-synchronous kernels for unit weights, general otherwise */
+#define MFBC_PATH_GENERAL 1    /* force the general (any integer weight) kernels */
+#define MFBC_PATH_LEVEL   2    /* require the unit-weight level kernels (INVALID if weighted) */
+
+typedef struct mfbc_graph mfbc_graph;   /* opaque, device resident */
+
+/* Per-kernel statistics, filled when mfbc_options.profile is non-NULL.
+ * ms is the sum of CUDA-event durations of the kernel's launches; bytes is
+ * the algorithmic (compulsory) DRAM traffic of those launches under the
+ * model documented beside each kernel. */
+#define MFBC_MAX_KSTATS 24
+typedef struct {
+  char name[40];
+  uint64_t launches;
+  double ms;
+  double bytes;
+} mfbc_kernel_stat;
+
+typedef struct {
+  int32_t nkernels;
+  mfbc_kernel_stat k[MFBC_MAX_KSTATS];
+  uint64_t batches;
+  uint64_t fwd_iters;          /* MFBF products over all batches */
+  uint64_t bwd_iters;          /* MFBr products over all batches */
+  int32_t n_b;                 /* batch width used */
+  int32_t path;                /* MFBC_PATH_GENERAL or MFBC_PATH_LEVEL */
+} mfbc_profile;
+
+typedef struct {
+  int32_t n_b;                 /* sources per batch; 0 = largest that fits; rounded up to 32 */
+  int32_t path;                /* MFBC_PATH_* */
+  void* stream;                /* cudaStream_t to run on; NULL = legacy default stream */
+  void* workspace;             /* optional caller-owned device scratch, 256-byte aligned */
+  uint64_t workspace_bytes;    /* its size; see mfbc_workspace_size */
+  uint32_t* warn_out;          /* optional host pointer, receives MFBC_WARN_* bits */
+  mfbc_profile* profile;       /* optional host pointer; enables per-kernel event timing */
+  uint32_t flags;              /* MFBC_OPT_* bits */
+} mfbc_options;                /* zero-initialised = all defaults */
+
+/* mfbc_options.flags */
+#define MFBC_OPT_COUNT_BYTES 1u  /* with profile: count algorithmic bytes on the device (slower) */
+
+/* Build a device-resident graph from HOST CSR arrays (Sec. 2.1: A(i,j) = w(i,j)
+ * for (i,j) in E; the paper's Tensor::write of the input, Sec. 6.1).
+ *   n       vertices (0 <= n < 2^31);  nnz = rowptr[n] arcs
+ *   rowptr  int64[n+1], col int32[nnz], w int32[nnz] or NULL (unweighted)
+ *   flags   MFBC_DIRECTED or MFBC_UNDIRECTED
+ *   stream  cudaStream_t or NULL; the call is complete on return
+ * The arrays are copied; the transposed adjacency needed by MFBr (A^T in
+ * Algorithm 2) is built for directed graphs.  Returns INVALID for unsorted
+ * or out-of-range columns, duplicates, self-loops, weights < 1, or an
+ * asymmetric UNDIRECTED graph; OVERFLOW if (n-1)*max_w + max_w >= 2^31-1. */
+mfbc_status mfbc_graph_create(int32_t n, int64_t nnz, const int64_t* rowptr, const int32_t* col,
+                              const int32_t* w, uint32_t flags, void* stream, mfbc_graph** out);
+
+/* Same as mfbc_graph_create, from DEVICE arrays (copied; caller keeps ownership). */
+mfbc_status mfbc_graph_create_device(int32_t n, int64_t nnz, const int64_t* rowptr,
+                                     const int32_t* col, const int32_t* w, uint32_t flags,
+                                     void* stream, mfbc_graph** out);
+
+/* Release the graph and any scratch cached on it.  NULL is ignored. */
+void mfbc_graph_destroy(mfbc_graph* g);
+
+/* n, nnz, flags and whether the graph has unit weights (out pointers may be NULL). */
+mfbc_status mfbc_graph_info(const mfbc_graph* g, int32_t* n, int64_t* nnz, uint32_t* flags,
+                            int32_t* unit_weights);
+
+/* Betweenness centrality over a source list (Algorithm 3, Theorem 1):
+ *   lambda_out[v] = sum over i < nsrc, v != sources[i], of
+ *                   sum_t sigma(sources[i],t,v) / sigma_bar(sources[i],t)
+ * (ordered pairs, Sec. 2.4; unreachable t contribute 0).  Sources may repeat
+ * and are counted once per occurrence (lambda is linear in the list); with
+ * every vertex listed once this is exact BC, otherwise the unscaled sum over
+ * the sample.  HOST pointers: sources int32[nsrc], lambda_out double[n].
+ * Sources are processed in batches of options->n_b (Algorithm 3's loop); a
+ * short last batch is padded with inactive columns (Theorem 1's padding). */
+mfbc_status mfbc_bc(const mfbc_graph* g, const int32_t* sources, int32_t nsrc,
+                    double* lambda_out, const mfbc_options* opt);
+
+/* mfbc_bc with DEVICE sources int32[nsrc] and DEVICE lambda_out double[n]
+ * (overwritten).  Work is queued on opt->stream; the call returns once the
+ * result is complete on that stream. */
+mfbc_status mfbc_bc_device(const mfbc_graph* g, const int32_t* sources, int32_t nsrc,
+                           double* lambda_out, const mfbc_options* opt);
+
+/* MFBF alone (Algorithm 1, Lemma 1): for each i < nsrc,
+ *   dist_out [i*n + v] = tau(sources[i], v)        (INT32_MAX if unreachable)
+ *   sigma_out[i*n + v] = sigma_bar(sources[i], v)  (0 if unreachable; sigma_bar(s,s) = 1)
+ * HOST pointers; sigma_out may be NULL. */
+mfbc_status mfbc_sssp_batch(const mfbc_graph* g, const int32_t* sources, int32_t nsrc,
+                            int32_t* dist_out, double* sigma_out, const mfbc_options* opt);
+
+/* mfbc_sssp_batch with DEVICE sources, dist_out and sigma_out (sigma_out may be NULL). */
+mfbc_status mfbc_sssp_batch_device(const mfbc_graph* g, const int32_t* sources, int32_t nsrc,
+                                   int32_t* dist_out, double* sigma_out,
+                                   const mfbc_options* opt);
+
+/* Device scratch (bytes) that mfbc_bc* (mode 0) or mfbc_sssp_batch* (mode 1)
+ * needs for nsrc sources under *opt (n_b, path).  A caller that passes its
+ * own opt->workspace of at least this size makes the call allocate nothing
+ * on the device. */
+mfbc_status mfbc_workspace_size(const mfbc_graph* g, int32_t nsrc, int32_t mode,
+                                const mfbc_options* opt, uint64_t* bytes);
+
+const char* mfbc_status_string(mfbc_status s);
+
+/* Detail of the last error on the calling thread ("" if none). */
+const char* mfbc_last_error(void);
+
+/* Library version string. */
+const char* mfbc_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MFBC_H */

@@ -1,0 +1,483 @@
+// C ABI of the MFBC library: argument checks, choice of kernel family and
+// batch width, scratch management, and the batch loop of Algorithm 3.
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+#include <string>
+
+#include "internal.cuh"
+
+using namespace mfbc;
+
+struct mfbc_graph {
+  DevGraph g;
+  void* ws = nullptr;              // cached scratch (cudaMalloc), grown on demand
+  size_t ws_bytes = 0;
+  uint32_t* h_ctr = nullptr;       // pinned counter mirror
+  uint32_t flags = 0;
+  std::mutex mu;
+};
+
+static thread_local std::string t_err;
+
+static mfbc_status fail(mfbc_status s, const std::string& msg) {
+  t_err = msg;
+  return s;
+}
+
+extern "C" const char* mfbc_status_string(mfbc_status s) {
+  switch (s) {
+    case MFBC_OK: return "ok";
+    case MFBC_ERR_INVALID: return "invalid argument";
+    case MFBC_ERR_OOM: return "out of memory";
+    case MFBC_ERR_CUDA: return "CUDA error";
+    case MFBC_ERR_OVERFLOW: return "distance overflow";
+    case MFBC_ERR_NO_CONVERGENCE: return "no convergence";
+    case MFBC_ERR_TIMEOUT: return "device wait timed out";
+  }
+  return "unknown status";
+}
+
+extern "C" const char* mfbc_last_error(void) { return t_err.c_str(); }
+
+extern "C" const char* mfbc_version(void) { return "mfbc-gb300 0.1 (sm_103a)"; }
+
+// ------------------------------------------------------------------ graphs
+static mfbc_status create_common(int32_t n, int64_t nnz, const int64_t* rowptr, const int32_t* col,
+                                 const int32_t* w, uint32_t flags, void* stream, mfbc_graph** out) {
+  auto* G = new (std::nothrow) mfbc_graph();
+  if (!G) return fail(MFBC_ERR_OOM, "host allocation of the graph handle failed");
+  std::string err;
+  mfbc_status s = graph_build(n, nnz, rowptr, col, w, flags, (cudaStream_t)stream, &G->g, &err);
+  if (s == MFBC_OK) {
+    cudaError_t e = cudaMallocHost((void**)&G->h_ctr, 64);
+    if (e != cudaSuccess) { s = MFBC_ERR_OOM; err = "cudaMallocHost of the counter mirror failed"; }
+  }
+  if (s != MFBC_OK) {
+    graph_free(&G->g);
+    if (G->h_ctr) cudaFreeHost(G->h_ctr);
+    delete G;
+    cudaGetLastError();
+    return fail(s, err);
+  }
+  G->flags = flags;
+  *out = G;
+  t_err.clear();
+  return MFBC_OK;
+}
+
+static mfbc_status check_create_args(int32_t n, int64_t nnz, const void* rowptr, const void* col,
+                                     uint32_t flags, mfbc_graph** out) {
+  if (!out) return fail(MFBC_ERR_INVALID, "out must not be NULL");
+  *out = nullptr;
+  if (n < 0) return fail(MFBC_ERR_INVALID, "n must be >= 0");
+  if (nnz < 0) return fail(MFBC_ERR_INVALID, "nnz must be >= 0");
+  if (!rowptr) return fail(MFBC_ERR_INVALID, "rowptr must not be NULL");
+  if (nnz > 0 && !col) return fail(MFBC_ERR_INVALID, "col must not be NULL when nnz > 0");
+  if (flags & ~1u) return fail(MFBC_ERR_INVALID, "unknown flag bits");
+  return MFBC_OK;
+}
+
+extern "C" mfbc_status mfbc_graph_create(int32_t n, int64_t nnz, const int64_t* rowptr, const int32_t* col,
+                                         const int32_t* w, uint32_t flags, void* stream, mfbc_graph** out) {
+  mfbc_status s = check_create_args(n, nnz, rowptr, col, flags, out);
+  if (s) return s;
+  if (rowptr[0] != 0 || rowptr[n] != nnz) return fail(MFBC_ERR_INVALID, "rowptr[0] must be 0 and rowptr[n] == nnz");
+  return create_common(n, nnz, rowptr, col, w, flags, stream, out);
+}
+
+extern "C" mfbc_status mfbc_graph_create_device(int32_t n, int64_t nnz, const int64_t* rowptr,
+                                                const int32_t* col, const int32_t* w, uint32_t flags,
+                                                void* stream, mfbc_graph** out) {
+  mfbc_status s = check_create_args(n, nnz, rowptr, col, flags, out);
+  if (s) return s;
+  // stage through the host: construction also needs the row pointers there
+  std::vector<int64_t> rp((size_t)n + 1);
+  std::vector<int32_t> c((size_t)nnz), ww(w ? (size_t)nnz : 0);
+  cudaStream_t st = (cudaStream_t)stream;
+  if (cudaMemcpyAsync(rp.data(), rowptr, sizeof(int64_t) * rp.size(), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      (nnz && cudaMemcpyAsync(c.data(), col, sizeof(int32_t) * c.size(), cudaMemcpyDeviceToHost, st) != cudaSuccess) ||
+      (w && nnz && cudaMemcpyAsync(ww.data(), w, sizeof(int32_t) * ww.size(), cudaMemcpyDeviceToHost, st) != cudaSuccess) ||
+      cudaStreamSynchronize(st) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(MFBC_ERR_CUDA, "copying the device graph arrays failed");
+  }
+  if (rp[0] != 0 || rp[(size_t)n] != nnz) return fail(MFBC_ERR_INVALID, "rowptr[0] must be 0 and rowptr[n] == nnz");
+  return create_common(n, nnz, rp.data(), c.data(), w ? ww.data() : nullptr, flags, stream, out);
+}
+
+extern "C" void mfbc_graph_destroy(mfbc_graph* G) {
+  if (!G) return;
+  graph_free(&G->g);
+  if (G->ws) cudaFree(G->ws);
+  if (G->h_ctr) cudaFreeHost(G->h_ctr);
+  delete G;
+}
+
+extern "C" mfbc_status mfbc_graph_info(const mfbc_graph* G, int32_t* n, int64_t* nnz, uint32_t* flags,
+                                       int32_t* unit) {
+  if (!G) return fail(MFBC_ERR_INVALID, "graph must not be NULL");
+  if (n) *n = G->g.n;
+  if (nnz) *nnz = G->g.nnz;
+  if (flags) *flags = G->flags;
+  if (unit) *unit = G->g.unit ? 1 : 0;
+  return MFBC_OK;
+}
+
+// ------------------------------------------------------------------ planning
+struct Plan {
+  int path = MFBC_PATH_GENERAL;
+  int nb = 32;
+  int Lcap = 0;
+  int64_t list_cap = 0;
+  size_t state_bytes = 0;          // kernel-family state
+  size_t extra_bytes = 0;          // lambda, device sources, sssp staging
+  size_t total = 0;
+};
+
+static inline size_t al256(size_t b) { return (b + 255) & ~size_t(255); }
+
+static size_t extras(const DevGraph& g, int32_t nsrc, int mode, int nb, bool host_io) {
+  size_t b = 0;
+  if (mode == 0) b += al256(sizeof(double) * (size_t)std::max(g.n, 1));        // device lambda
+  if (host_io) b += al256(sizeof(int32_t) * (size_t)std::max(nsrc, 1));        // device sources
+  if (mode == 1 && host_io) b += al256((sizeof(int32_t) + sizeof(double)) * (size_t)nb * std::max(g.n, 1));
+  return b;
+}
+
+static void level_caps(const DevGraph& g, int nb, int* Lcap, int64_t* list_cap) {
+  (void)nb;
+  const int64_t n = g.n;
+  *Lcap = (int)std::min<int64_t>(n + 2, 64);
+  *list_cap = n * std::min<int64_t>(*Lcap, 24) + 64;
+}
+
+static size_t plan_bytes(const DevGraph& g, int path, int nb, int32_t nsrc, int mode, bool host_io,
+                         Plan* p) {
+  p->path = path;
+  p->nb = nb;
+  if (path == MFBC_PATH_LEVEL) {
+    level_caps(g, nb, &p->Lcap, &p->list_cap);
+    p->state_bytes = level_bytes(g, nb, p->Lcap, p->list_cap);
+  } else {
+    p->state_bytes = general_bytes(g.n, nb);
+  }
+  p->extra_bytes = extras(g, nsrc, mode, nb, host_io);
+  p->total = p->state_bytes + p->extra_bytes;
+  return p->total;
+}
+
+static mfbc_status make_plan(const mfbc_graph* G, int32_t nsrc, int mode, const mfbc_options* opt,
+                             bool host_io, Plan* p) {
+  const DevGraph& g = G->g;
+  int path = opt ? opt->path : MFBC_PATH_AUTO;
+  if (path == MFBC_PATH_AUTO) path = g.unit ? MFBC_PATH_LEVEL : MFBC_PATH_GENERAL;
+  else if (path == MFBC_PATH_LEVEL && !g.unit)
+    return fail(MFBC_ERR_INVALID, "MFBC_PATH_LEVEL needs unit weights");
+  else if (path != MFBC_PATH_GENERAL && path != MFBC_PATH_LEVEL)
+    return fail(MFBC_ERR_INVALID, "unknown path");
+  const int maxnb = path == MFBC_PATH_LEVEL ? 1024 : 4096;
+  int req = opt ? opt->n_b : 0;
+  if (req < 0) return fail(MFBC_ERR_INVALID, "n_b must be >= 0");
+  if (req > 0) {
+    int nb = (req + 31) / 32 * 32;
+    if (nb > maxnb) return fail(MFBC_ERR_INVALID, "n_b too large for this path (max " + std::to_string(maxnb) + ")");
+    plan_bytes(g, path, nb, nsrc, mode, host_io, p);
+    return MFBC_OK;
+  }
+  // auto: widest batch (<= number of sources) whose scratch fits the budget
+  size_t budget;
+  if (opt && opt->workspace) budget = opt->workspace_bytes;
+  else {
+    size_t fr = 0, tot = 0;
+    if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) { cudaGetLastError(); return fail(MFBC_ERR_CUDA, "cudaMemGetInfo failed"); }
+    budget = (size_t)(0.80 * (double)(fr + G->ws_bytes));
+  }
+  int nb = std::min(maxnb, std::max(32, (nsrc + 31) / 32 * 32));
+  while (true) {
+    plan_bytes(g, path, nb, nsrc, mode, host_io, p);
+    if (p->total <= budget || nb == 32) break;
+    nb -= 32;
+  }
+  return MFBC_OK;
+}
+
+extern "C" mfbc_status mfbc_workspace_size(const mfbc_graph* G, int32_t nsrc, int32_t mode,
+                                           const mfbc_options* opt, uint64_t* bytes) {
+  if (!G || !bytes) return fail(MFBC_ERR_INVALID, "graph and bytes must not be NULL");
+  if (nsrc < 0 || (mode != 0 && mode != 1)) return fail(MFBC_ERR_INVALID, "bad nsrc or mode");
+  Plan p;
+  mfbc_options o = opt ? *opt : mfbc_options{};
+  o.workspace = nullptr;
+  mfbc_status s = make_plan(G, nsrc, mode, &o, true, &p);
+  if (s) return s;
+  *bytes = p.total;
+  return MFBC_OK;
+}
+
+// ------------------------------------------------------------------ runner
+namespace {
+
+struct Run {
+  mfbc_graph* G;
+  const mfbc_options* opt;
+  cudaStream_t st;
+  Profiler prof;
+  std::string err;
+  Plan plan;
+  char* ws = nullptr;
+  size_t ws_bytes = 0;
+};
+
+mfbc_status get_workspace(Run& R) {
+  const mfbc_options* opt = R.opt;
+  if (opt && opt->workspace) {
+    if ((uintptr_t)opt->workspace & 255u) return fail(MFBC_ERR_INVALID, "workspace must be 256-byte aligned");
+    if (opt->workspace_bytes < R.plan.total)
+      return fail(MFBC_ERR_INVALID, "workspace too small: need " + std::to_string(R.plan.total) + " bytes");
+    R.ws = (char*)opt->workspace;
+    R.ws_bytes = opt->workspace_bytes;
+    return MFBC_OK;
+  }
+  mfbc_graph* G = R.G;
+  if (G->ws_bytes < R.plan.total) {
+    if (G->ws) { cudaStreamSynchronize(R.st); cudaFree(G->ws); G->ws = nullptr; G->ws_bytes = 0; }
+    cudaError_t e = cudaMalloc(&G->ws, R.plan.total);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(MFBC_ERR_OOM, "cudaMalloc of " + std::to_string(R.plan.total) + " scratch bytes failed");
+    }
+    G->ws_bytes = R.plan.total;
+  }
+  R.ws = (char*)G->ws;
+  R.ws_bytes = G->ws_bytes;
+  return MFBC_OK;
+}
+
+void finish_profile(Run& R, mfbc_profile* out, int64_t batches, int64_t fi, int64_t bi, Counters* ctr) {
+  if (!out) return;
+  R.prof.drain();
+  unsigned long long bytes[K_NUM];
+  if (cudaMemcpy(bytes, ctr->bytes, sizeof(bytes), cudaMemcpyDeviceToHost) != cudaSuccess) {
+    cudaGetLastError();
+    memset(bytes, 0, sizeof(bytes));
+  }
+  out->nkernels = 0;
+  for (int i = 0; i < K_NUM && out->nkernels < MFBC_MAX_KSTATS; i++) {
+    KStat& k = R.prof.k[i];
+    if (!k.launches) continue;
+    mfbc_kernel_stat& o = out->k[out->nkernels++];
+    memset(o.name, 0, sizeof(o.name));
+    strncpy(o.name, k.name, sizeof(o.name) - 1);
+    o.launches = k.launches;
+    o.ms = k.ms;
+    o.bytes = k.bytes + (double)bytes[i];
+  }
+  out->batches = (uint64_t)batches;
+  out->fwd_iters = (uint64_t)fi;
+  out->bwd_iters = (uint64_t)bi;
+  out->n_b = R.plan.nb;
+  out->path = R.plan.path;
+}
+
+// mode 0: lambda (d_lambda device, n doubles, overwritten); mode 1: sssp rows.
+mfbc_status run(mfbc_graph* G, const int32_t* d_src, int32_t nsrc, int mode, double* d_lambda,
+                int32_t* dist_out, double* sigma_out, bool out_on_host, Run& R, char* extra) {
+  const DevGraph& g = G->g;
+  const Plan& P = R.plan;
+  const int nb = P.nb;
+  int64_t batches = 0, fi = 0, bi = 0;
+  RunCtx rc{&g, R.st, &R.prof, G->h_ctr, &R.err};
+  Carver c(R.ws, R.ws_bytes);
+  GeneralState gs;
+  LevelState ls;
+  Counters* ctr;
+  if (P.path == MFBC_PATH_LEVEL) { level_carve(c, g, nb, P.Lcap, P.list_cap, ls); ctr = ls.ctr; }
+  else { general_carve(c, g.n, nb, gs); ctr = gs.ctr; }
+  int32_t* stage_d = nullptr;
+  double* stage_s = nullptr;
+  if (mode == 1 && out_on_host) {
+    stage_d = (int32_t*)extra;
+    stage_s = (double*)(extra + al256(sizeof(int32_t) * (size_t)nb * std::max(g.n, 1)));
+  }
+  MFBC_CUDA_TRY(cudaMemsetAsync(ctr, 0, sizeof(Counters), R.st), &R.err);
+  if (mode == 0 && g.n) MFBC_CUDA_TRY(cudaMemsetAsync(d_lambda, 0, sizeof(double) * (size_t)g.n, R.st), &R.err);
+  if (P.path == MFBC_PATH_LEVEL && g.n) {
+    // masks start clean; each batch returns them to zero
+    MFBC_CUDA_TRY(cudaMemsetAsync(ls.V, 0, sizeof(uint32_t) * (size_t)g.n * ls.W, R.st), &R.err);
+    MFBC_CUDA_TRY(cudaMemsetAsync(ls.F, 0, sizeof(uint32_t) * (size_t)ls.Lcap * g.n * ls.W, R.st), &R.err);
+    MFBC_CUDA_TRY(cudaMemsetAsync(ls.member, 0, sizeof(uint32_t) * (size_t)ls.Lcap * ls.mw, R.st), &R.err);
+    if (g.items_out.nhub)
+      MFBC_CUDA_TRY(cudaMemsetAsync(ls.zacc, 0, sizeof(double) * (size_t)g.items_out.nhub * nb, R.st), &R.err);
+  }
+  uint32_t warn = 0;
+  for (int32_t b0 = 0; b0 < nsrc; b0 += nb) {
+    const int na = std::min(nb, nsrc - b0);
+    batches++;
+    mfbc_status s;
+    bool fallback = false;
+    if (P.path == MFBC_PATH_LEVEL) {
+      int levels = -1;
+      bool exceeded = false;
+      s = level_batch(rc, ls, d_src + b0, na, mode == 0 ? d_lambda : nullptr, mode == 0, &levels, &exceeded,
+                      &fi, &bi);
+      if (s == MFBC_OK) {
+        if (mode == 1) {
+          int32_t* dd = out_on_host ? stage_d : dist_out + (size_t)b0 * g.n;
+          double* ds = sigma_out ? (out_on_host ? stage_s : sigma_out + (size_t)b0 * g.n) : nullptr;
+          level_output(rc, ls, levels, na, dd, ds);
+          // exactness check reads the staged per-source rows
+          if (ds) check_sigma_exact(ds, (size_t)na * g.n, ls.ctr, R.st);
+        }
+        level_reset(rc, ls, levels);
+      } else if (exceeded) {
+        fallback = true;
+      }
+    }
+    if (P.path == MFBC_PATH_GENERAL || fallback) {
+      // general kernels; when falling back from the level path, run this batch
+      // in sub-batches that fit the scratch already held
+      GeneralState* gp = &gs;
+      GeneralState fb;
+      int nbg = nb;
+      if (fallback) {
+        Carver c2(R.ws, P.state_bytes);
+        nbg = nb;
+        while (nbg > 32 && general_bytes(g.n, nbg) > P.state_bytes) nbg -= 32;
+        if (general_bytes(g.n, nbg) > P.state_bytes)
+          return fail(MFBC_ERR_OOM, "level capacity exceeded and the general path does not fit the scratch");
+        general_carve(c2, g.n, nbg, fb);
+        gp = &fb;
+        // the level state is overwritten: start its masks again afterwards
+        MFBC_CUDA_TRY(cudaMemsetAsync(fb.ctr, 0, sizeof(Counters), R.st), &R.err);
+      }
+      for (int sb = 0; sb < na; sb += nbg) {
+        const int nsa = std::min(nbg, na - sb);
+        s = general_batch(rc, *gp, d_src + b0 + sb, nsa, mode == 0 ? d_lambda : nullptr, &fi, &bi);
+        if (s) break;
+        if (mode == 1) {
+          int32_t* dd = out_on_host ? stage_d + (size_t)sb * g.n : dist_out + (size_t)(b0 + sb) * g.n;
+          double* ds = sigma_out ? (out_on_host ? stage_s + (size_t)sb * g.n : sigma_out + (size_t)(b0 + sb) * g.n)
+                                 : nullptr;
+          general_output(rc, *gp, nsa, dd, ds);
+        }
+        MFBC_CUDA_TRY(cudaMemcpyAsync(G->h_ctr, &gp->ctr->flags, sizeof(uint32_t), cudaMemcpyDeviceToHost, R.st), &R.err);
+        MFBC_CUDA_TRY(cudaStreamSynchronize(R.st), &R.err);
+        if (G->h_ctr[0] & 2u) warn |= MFBC_WARN_SIGMA_INEXACT;
+      }
+      if (fallback && s == MFBC_OK) {
+        // restore the level masks for the next batch
+        Carver c3(R.ws, R.ws_bytes);
+        level_carve(c3, g, nb, P.Lcap, P.list_cap, ls);
+        MFBC_CUDA_TRY(cudaMemsetAsync(ls.V, 0, sizeof(uint32_t) * (size_t)g.n * ls.W, R.st), &R.err);
+        MFBC_CUDA_TRY(cudaMemsetAsync(ls.F, 0, sizeof(uint32_t) * (size_t)ls.Lcap * g.n * ls.W, R.st), &R.err);
+        MFBC_CUDA_TRY(cudaMemsetAsync(ls.member, 0, sizeof(uint32_t) * (size_t)ls.Lcap * ls.mw, R.st), &R.err);
+        if (g.items_out.nhub)
+          MFBC_CUDA_TRY(cudaMemsetAsync(ls.zacc, 0, sizeof(double) * (size_t)g.items_out.nhub * nb, R.st), &R.err);
+        MFBC_CUDA_TRY(cudaMemsetAsync(ls.ctr, 0, sizeof(Counters), R.st), &R.err);
+      }
+    }
+    if (s) return fail(s, R.err.empty() ? std::string(mfbc_status_string(s)) : R.err);
+    if (mode == 1 && out_on_host) {
+      MFBC_CUDA_TRY(cudaMemcpyAsync(dist_out + (size_t)b0 * g.n, stage_d, sizeof(int32_t) * (size_t)na * g.n,
+                                    cudaMemcpyDeviceToHost, R.st), &R.err);
+      if (sigma_out)
+        MFBC_CUDA_TRY(cudaMemcpyAsync(sigma_out + (size_t)b0 * g.n, stage_s, sizeof(double) * (size_t)na * g.n,
+                                      cudaMemcpyDeviceToHost, R.st), &R.err);
+    }
+  }
+  MFBC_CUDA_TRY(cudaMemcpyAsync(G->h_ctr, &ctr->flags, sizeof(uint32_t), cudaMemcpyDeviceToHost, R.st), &R.err);
+  MFBC_CUDA_TRY(cudaStreamSynchronize(R.st), &R.err);
+  if (G->h_ctr[0] & 2u) warn |= MFBC_WARN_SIGMA_INEXACT;
+  MFBC_CUDA_TRY(cudaGetLastError(), &R.err);
+  if (R.opt && R.opt->warn_out) *R.opt->warn_out = warn;
+  if (R.opt && R.opt->profile) finish_profile(R, R.opt->profile, batches, fi, bi, ctr);
+  return MFBC_OK;
+}
+
+mfbc_status entry(const mfbc_graph* Gc, const int32_t* sources, int32_t nsrc, int mode, double* lambda_out,
+                  int32_t* dist_out, double* sigma_out, const mfbc_options* opt, bool host_io) {
+  if (!Gc) return fail(MFBC_ERR_INVALID, "graph must not be NULL");
+  if (nsrc < 0) return fail(MFBC_ERR_INVALID, "nsrc must be >= 0");
+  if (nsrc > 0 && !sources) return fail(MFBC_ERR_INVALID, "sources must not be NULL");
+  if (mode == 0 && Gc->g.n > 0 && !lambda_out) return fail(MFBC_ERR_INVALID, "lambda_out must not be NULL");
+  if (mode == 1 && nsrc > 0 && Gc->g.n > 0 && !dist_out) return fail(MFBC_ERR_INVALID, "dist_out must not be NULL");
+  mfbc_graph* G = const_cast<mfbc_graph*>(Gc);
+  std::lock_guard<std::mutex> lock(G->mu);
+  const int32_t n = G->g.n;
+  if (host_io && nsrc > 0) {
+    for (int32_t i = 0; i < nsrc; i++)
+      if (sources[i] < 0 || sources[i] >= n) return fail(MFBC_ERR_INVALID, "source id out of range");
+  }
+  if (opt && opt->warn_out) *opt->warn_out = 0;
+  t_err.clear();
+  Run R;
+  R.G = G;
+  R.opt = opt;
+  R.st = opt ? (cudaStream_t)opt->stream : nullptr;
+  mfbc_status s = make_plan(G, nsrc, mode, opt, host_io, &R.plan);
+  if (s) return s;
+  s = get_workspace(R);
+  if (s) return s;
+  R.prof.on = opt && opt->profile;
+  R.prof.count_bytes = R.prof.on && (opt->flags & MFBC_OPT_COUNT_BYTES);
+  R.prof.stream = R.st;
+  char* extra = R.ws + R.plan.state_bytes;
+  double* d_lambda = lambda_out;
+  const int32_t* d_src = sources;
+  if (mode == 0 && host_io) { d_lambda = (double*)extra; extra += al256(sizeof(double) * (size_t)std::max(n, 1)); }
+  else if (mode == 0) extra += al256(sizeof(double) * (size_t)std::max(n, 1));
+  if (host_io) {
+    int32_t* ds = (int32_t*)extra;
+    extra += al256(sizeof(int32_t) * (size_t)std::max(nsrc, 1));
+    if (nsrc) {
+      cudaError_t e = cudaMemcpyAsync(ds, sources, sizeof(int32_t) * (size_t)nsrc, cudaMemcpyHostToDevice, R.st);
+      if (e != cudaSuccess) { cudaGetLastError(); return fail(MFBC_ERR_CUDA, "copying sources failed"); }
+    }
+    d_src = ds;
+  } else if (nsrc > 0) {
+    // device sources: validate the range on the host copy
+    std::vector<int32_t> hs((size_t)nsrc);
+    if (cudaMemcpyAsync(hs.data(), sources, sizeof(int32_t) * (size_t)nsrc, cudaMemcpyDeviceToHost, R.st) != cudaSuccess ||
+        cudaStreamSynchronize(R.st) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(MFBC_ERR_CUDA, "reading device sources failed");
+    }
+    for (int32_t v : hs) if (v < 0 || v >= n) return fail(MFBC_ERR_INVALID, "source id out of range");
+  }
+  s = run(G, d_src, nsrc, mode, d_lambda, dist_out, sigma_out, host_io, R, extra);
+  if (s == MFBC_OK && mode == 0 && host_io && n > 0) {
+    cudaError_t e = cudaMemcpyAsync(lambda_out, d_lambda, sizeof(double) * (size_t)n, cudaMemcpyDeviceToHost, R.st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(R.st);
+    if (e != cudaSuccess) { cudaGetLastError(); s = fail(MFBC_ERR_CUDA, std::string("copying lambda failed: ") + cudaGetErrorString(e)); }
+  }
+  R.prof.release();
+  if (s == MFBC_OK) t_err.clear();
+  else {
+    if (!R.err.empty() && t_err.empty()) t_err = R.err;
+    cudaGetLastError();
+  }
+  return s;
+}
+
+}  // namespace
+
+extern "C" mfbc_status mfbc_bc(const mfbc_graph* g, const int32_t* sources, int32_t nsrc, double* lambda_out,
+                               const mfbc_options* opt) {
+  return entry(g, sources, nsrc, 0, lambda_out, nullptr, nullptr, opt, true);
+}
+
+extern "C" mfbc_status mfbc_bc_device(const mfbc_graph* g, const int32_t* sources, int32_t nsrc,
+                                      double* lambda_out, const mfbc_options* opt) {
+  return entry(g, sources, nsrc, 0, lambda_out, nullptr, nullptr, opt, false);
+}
+
+extern "C" mfbc_status mfbc_sssp_batch(const mfbc_graph* g, const int32_t* sources, int32_t nsrc,
+                                       int32_t* dist_out, double* sigma_out, const mfbc_options* opt) {
+  return entry(g, sources, nsrc, 1, nullptr, dist_out, sigma_out, opt, true);
+}
+
+extern "C" mfbc_status mfbc_sssp_batch_device(const mfbc_graph* g, const int32_t* sources, int32_t nsrc,
+                                              int32_t* dist_out, double* sigma_out, const mfbc_options* opt) {
+  return entry(g, sources, nsrc, 1, nullptr, dist_out, sigma_out, opt, false);
+}

@@ -1,0 +1,505 @@
+// General path: MFBF (Algorithm 1) and MFBr (Algorithm 2) for any integer
+// weights >= 1, as sparse-frontier "push" products over the vertex-major
+// batch state.
+//
+// One warp owns one (frontier vertex u, 32-column word) pair; lane l is batch
+// column 32*word + l.  The warp walks u's arc list once, broadcasting 32 arcs
+// at a time by shuffle, and every lane whose column is in the frontier
+// applies the monoid action to its own column of the target row.  The 32
+// lanes of a warp therefore always touch one contiguous 128-byte (int32) or
+// 256-byte (FP64) segment of the target vertex's row.
+//
+// MFBF iteration i (Algorithm 1, with the readings of the seed and of the
+// frontier filter listed in the design notes):
+//   relax_min  product weight:  cw(s,v) = min over frontier (s,u), arcs u->v,
+//              of tau_i(s,u) + A(u,v)      [the (+) of the multpath monoid,
+//              Sec. 4.1.1, applied to f(a,w) = (a.w + w, a.m), Sec. 4.1.2];
+//              candidates heavier than the current T(s,v).w cannot survive the
+//              filter and are not offered;
+//   relax_tie  product multiplicity: cm(s,v) = sum of frontier multiplicities
+//              over the arcs that attain cw(s,v) (ties summed);
+//   accumulate T := T (+) product; the new frontier keeps every product entry
+//              whose weight equals the accumulated weight, carrying the
+//              product's multiplicity (the increment).
+// MFBr (Algorithm 2):
+//   counters_leaves  Z(s,v).c = number of successors u of v on shortest paths
+//              (arcs v->u with tau(s,u) = tau(s,v) + A(v,u)); leaves (c = 0)
+//              form the first frontier with value 1/sigma_bar(s,v);
+//   propagate  push over A^T: each frontier (s,u) adds its value to Z(s,v).p of
+//              every predecessor v (the Brandes action g(a,w) = (a.w - w, a.p,
+//              a.c) keeps exactly those v with tau(s,v) = tau(s,u) - A(v,u)) and
+//              decrements Z(s,v).c; the lane that takes a counter to zero
+//              enqueues (s,v) -- exactly once, so no retirement pass is needed;
+//   next_frontier  value of a new frontier entry: Z(s,v).p + 1/sigma_bar(s,v).
+// lambda (Algorithm 3): lambda(v) += sum_j zeta(src_j, v) * sigma_bar(src_j, v)
+//   over active columns with src_j != v.
+#include "internal.cuh"
+
+namespace mfbc {
+
+size_t general_bytes(int32_t n, int nb) {
+  Carver c(nullptr, 0);
+  GeneralState s;
+  general_carve(c, n, nb, s);
+  return c.off;
+}
+
+void general_carve(Carver& c, int32_t n, int nb, GeneralState& s) {
+  size_t cells = (size_t)n * nb;
+  s.nb = nb;
+  s.W = nb / 32;
+  s.dist = c.take<int32_t>(cells);
+  s.sig = c.take<double>(cells);
+  s.cw = c.take<int32_t>(cells);
+  s.cm = c.take<double>(cells);
+  s.fm = c.take<double>(cells);
+  s.fmask = c.take<uint32_t>((size_t)n * s.W);
+  s.tmask = c.take<uint32_t>((size_t)n * s.W);
+  s.vflag = c.take<uint32_t>((size_t)n);
+  s.listA = c.take<int32_t>((size_t)n);
+  s.listB = c.take<int32_t>((size_t)n);
+  s.src = c.take<int32_t>((size_t)nb);
+  s.ctr = c.take<Counters>(1);
+}
+
+// ---------------------------------------------------------------- kernels
+__device__ __forceinline__ void enqueue_once(uint32_t* vflag, int32_t* list, uint32_t* count,
+                                             int32_t v) {
+  if (*((volatile uint32_t*)&vflag[v]) == 0 && atomicExch(&vflag[v], 1u) == 0u)
+    list[atomicAdd(count, 1u)] = v;
+}
+
+// Seed (Algorithm 1 start, read as T(s,s) = (0,1), frontier {(s,s)}).
+__global__ void k_gp_seed(const int32_t* __restrict__ src, int nb, int W, int32_t* dist, double* sig,
+                          double* fm, uint32_t* fmask, uint32_t* vflag, int32_t* list,
+                          uint32_t* count) {
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= nb) return;
+  int32_t s = src[j];
+  if (s < 0) return;
+  size_t idx = (size_t)s * nb + j;
+  dist[idx] = 0;
+  sig[idx] = 1.0;
+  fm[idx] = 1.0;
+  atomicOr(&fmask[(size_t)s * W + (j >> 5)], 1u << (j & 31));
+  enqueue_once(vflag, list, count, s);
+}
+
+__global__ void k_clear_flags(const int32_t* __restrict__ list, uint32_t count, uint32_t* vflag) {
+  uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < count) vflag[list[i]] = 0;
+}
+
+// MFBF product, phase 1: minimum candidate weight per (s, v).
+__global__ void __launch_bounds__(256) k_gp_relax_min(
+    const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col, const int32_t* __restrict__ wt,
+    const int32_t* __restrict__ flist, uint32_t fcount, int W, int nb,
+    const uint32_t* __restrict__ fmask, const int32_t* __restrict__ dist, int32_t* cw, uint32_t* tmask,
+    uint32_t* vflag, int32_t* tlist, uint32_t* tcount, unsigned long long* bytes) {
+  uint64_t gw = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (gw >= (uint64_t)fcount * W) return;
+  const unsigned lane = lane_id();
+  const int word = (int)(gw % W);
+  const int32_t u = flist[gw / W];
+  const uint32_t m = fmask[(size_t)u * W + word];
+  if (!m) return;
+  const int j = word * 32 + lane;
+  const bool active = (m >> lane) & 1u;
+  const int32_t du = active ? dist[(size_t)u * nb + j] : 0;
+  const int64_t beg = rowptr[u], end = rowptr[u + 1];
+  unsigned long long nb_bytes = 0;
+  for (int64_t k0 = beg; k0 < end; k0 += 32) {
+    const int64_t k = k0 + lane;
+    const int32_t myv = k < end ? col[k] : 0;
+    const int32_t myw = k < end ? (wt ? wt[k] : 1) : 0;
+    const int cnt = (int)(end - k0 < 32 ? end - k0 : 32);
+    for (int t = 0; t < cnt; t++) {
+      const int32_t v = __shfl_sync(0xffffffffu, myv, t);
+      const int32_t w = __shfl_sync(0xffffffffu, myw, t);
+      bool touch = false;
+      if (active) {
+        const size_t idx = (size_t)v * nb + j;
+        const int32_t cand = du + w;
+        if (cand <= dist[idx]) {
+          if (cand < cw[idx]) atomicMin(&cw[idx], cand);
+          touch = true;
+        }
+      }
+      const uint32_t tb = __ballot_sync(0xffffffffu, touch);
+      if (tb && lane == 0) {
+        atomicOr(&tmask[(size_t)v * W + word], tb);
+        enqueue_once(vflag, tlist, tcount, v);
+      }
+      if (bytes) nb_bytes += 4ull * __popc(m) + 8ull * __popc(tb);
+    }
+  }
+  if (bytes && lane == 0) atomicAdd(bytes, nb_bytes + 8ull * (end - beg) / W + 4ull * __popc(m));
+}
+
+// MFBF product, phase 2: sum the frontier multiplicities that attain the minimum.
+__global__ void __launch_bounds__(256) k_gp_relax_tie(
+    const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col, const int32_t* __restrict__ wt,
+    const int32_t* __restrict__ flist, uint32_t fcount, int W, int nb,
+    const uint32_t* __restrict__ fmask, const int32_t* __restrict__ dist, const double* __restrict__ fm,
+    const int32_t* __restrict__ cw, double* cm, unsigned long long* bytes) {
+  uint64_t gw = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (gw >= (uint64_t)fcount * W) return;
+  const unsigned lane = lane_id();
+  const int word = (int)(gw % W);
+  const int32_t u = flist[gw / W];
+  const uint32_t m = fmask[(size_t)u * W + word];
+  if (!m) return;
+  const int j = word * 32 + lane;
+  const bool active = (m >> lane) & 1u;
+  const int32_t du = active ? dist[(size_t)u * nb + j] : 0;
+  const double mu = active ? fm[(size_t)u * nb + j] : 0.0;
+  const int64_t beg = rowptr[u], end = rowptr[u + 1];
+  unsigned long long nb_bytes = 0;
+  for (int64_t k0 = beg; k0 < end; k0 += 32) {
+    const int64_t k = k0 + lane;
+    const int32_t myv = k < end ? col[k] : 0;
+    const int32_t myw = k < end ? (wt ? wt[k] : 1) : 0;
+    const int cnt = (int)(end - k0 < 32 ? end - k0 : 32);
+    for (int t = 0; t < cnt; t++) {
+      const int32_t v = __shfl_sync(0xffffffffu, myv, t);
+      const int32_t w = __shfl_sync(0xffffffffu, myw, t);
+      bool hit = false;
+      if (active) {
+        const size_t idx = (size_t)v * nb + j;
+        if (du + w == cw[idx]) { atomicAdd(&cm[idx], mu); hit = true; }
+      }
+      if (bytes) nb_bytes += 4ull * __popc(m) + 16ull * __popc(__ballot_sync(0xffffffffu, hit));
+    }
+  }
+  if (bytes && lane == 0) atomicAdd(bytes, nb_bytes + 8ull * (end - beg) / W + 12ull * __popc(m));
+}
+
+__global__ void k_clear_mask_rows(const int32_t* __restrict__ list, uint32_t count, int W, uint32_t* mask) {
+  uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (uint64_t)count * W) return;
+  mask[(size_t)list[i / W] * W + (i % W)] = 0u;
+}
+
+// T := T (+) product, frontier filter, compaction of the next frontier.
+__global__ void __launch_bounds__(256) k_gp_accumulate(
+    const int32_t* __restrict__ tlist, const uint32_t* tcount_p, int W, int nb, int32_t* dist,
+    double* sig, int32_t* cw, double* cm, double* fm, uint32_t* fmask, uint32_t* tmask, uint32_t* vflag,
+    int32_t* nlist, uint32_t* ncount, unsigned long long* bytes) {
+  const uint32_t tcount = *tcount_p;
+  const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  for (uint64_t gw = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; gw < tcount; gw += nw) {
+  const unsigned lane = lane_id();
+  const int32_t v = tlist[gw];
+  bool any = false;
+  unsigned long long nbytes = 0;
+  for (int word = 0; word < W; word++) {
+    const size_t mi = (size_t)v * W + word;
+    const uint32_t t = tmask[mi];
+    if (!t) continue;
+    const bool on = (t >> lane) & 1u;
+    bool keep = false;
+    if (on) {
+      const size_t idx = (size_t)v * nb + word * 32 + lane;
+      const int32_t c = cw[idx], d = dist[idx];
+      const double mm = cm[idx];
+      if (c < d) { dist[idx] = c; sig[idx] = mm; keep = true; }
+      else if (c == d) { sig[idx] += mm; keep = true; }
+      if (keep) fm[idx] = mm;
+      cw[idx] = INF;
+      cm[idx] = 0.0;
+    }
+    const uint32_t kb = __ballot_sync(0xffffffffu, keep);
+    if (lane == 0) { fmask[mi] = kb; tmask[mi] = 0u; }
+    any |= (kb != 0u);
+    nbytes += 8ull + 48ull * __popc(t);
+  }
+  if (lane == 0) {
+    vflag[v] = 0u;
+    if (any) nlist[atomicAdd(ncount, 1u)] = v;
+    if (bytes) atomicAdd(bytes, nbytes + 8ull);
+  }
+  }
+}
+
+// Algorithm 2 initialisation: successor counters and the leaf frontier.
+__global__ void __launch_bounds__(256) k_gp_counters(
+    int32_t n, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+    const int32_t* __restrict__ wt, int W, int nb, const int32_t* __restrict__ src,
+    const int32_t* __restrict__ dist, const double* __restrict__ sig, int32_t* cnt, double* zp, double* fv,
+    uint32_t* fmask, int32_t* flist, uint32_t* fcount, unsigned long long* bytes) {
+  uint64_t gw = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (gw >= (uint64_t)n) return;
+  const unsigned lane = lane_id();
+  const int32_t v = (int32_t)gw;
+  const int64_t beg = rowptr[v], end = rowptr[v + 1];
+  bool any = false;
+  unsigned long long nbytes = 0;
+  for (int word = 0; word < W; word++) {
+    const int j = word * 32 + lane;
+    const size_t idx = (size_t)v * nb + j;
+    const double sv = sig[idx];
+    const bool reach = (src[j] >= 0) && (sv > 0.0);
+    const uint32_t rb = __ballot_sync(0xffffffffu, reach);
+    if (!rb) continue;
+    const int32_t dv = reach ? dist[idx] : 0;
+    int32_t c = 0;
+    for (int64_t k0 = beg; k0 < end; k0 += 32) {
+      const int64_t k = k0 + lane;
+      const int32_t myu = k < end ? col[k] : 0;
+      const int32_t myw = k < end ? (wt ? wt[k] : 1) : 0;
+      const int cntk = (int)(end - k0 < 32 ? end - k0 : 32);
+      for (int t = 0; t < cntk; t++) {
+        const int32_t u = __shfl_sync(0xffffffffu, myu, t);
+        const int32_t w = __shfl_sync(0xffffffffu, myw, t);
+        if (reach && dist[(size_t)u * nb + j] == dv + w) c++;
+      }
+    }
+    if (reach) {
+      cnt[idx] = c;
+      zp[idx] = 0.0;
+      if (c == 0) fv[idx] = 1.0 / sv;
+    }
+    const uint32_t lb = __ballot_sync(0xffffffffu, reach && c == 0);
+    if (lane == 0) fmask[(size_t)v * W + word] = lb;
+    any |= (lb != 0u);
+    nbytes += 4ull * __popc(rb) * (end - beg) + 24ull * __popc(rb);
+  }
+  if (lane == 0) {
+    if (any) flist[atomicAdd(fcount, 1u)] = v;
+    if (bytes) atomicAdd(bytes, nbytes + 8ull * (end - beg));
+  }
+}
+
+// MFBr product over A^T with counter decrement and exactly-once enqueue.
+__global__ void __launch_bounds__(256) k_gp_propagate(
+    const int64_t* __restrict__ rowptr_t, const int32_t* __restrict__ col_t,
+    const int32_t* __restrict__ wt_t, const int32_t* __restrict__ flist, uint32_t fcount, int W, int nb,
+    const uint32_t* __restrict__ fmask, const int32_t* __restrict__ dist, const double* __restrict__ fv,
+    double* zp, int32_t* cnt, uint32_t* tmask, uint32_t* vflag, int32_t* tlist, uint32_t* tcount,
+    unsigned long long* bytes) {
+  uint64_t gw = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (gw >= (uint64_t)fcount * W) return;
+  const unsigned lane = lane_id();
+  const int word = (int)(gw % W);
+  const int32_t u = flist[gw / W];
+  const uint32_t m = fmask[(size_t)u * W + word];
+  if (!m) return;
+  const int j = word * 32 + lane;
+  const bool active = (m >> lane) & 1u;
+  const int32_t du = active ? dist[(size_t)u * nb + j] : 0;
+  const double val = active ? fv[(size_t)u * nb + j] : 0.0;
+  const int64_t beg = rowptr_t[u], end = rowptr_t[u + 1];
+  unsigned long long nb_bytes = 0;
+  for (int64_t k0 = beg; k0 < end; k0 += 32) {
+    const int64_t k = k0 + lane;
+    const int32_t myv = k < end ? col_t[k] : 0;
+    const int32_t myw = k < end ? (wt_t ? wt_t[k] : 1) : 0;
+    const int cntk = (int)(end - k0 < 32 ? end - k0 : 32);
+    for (int t = 0; t < cntk; t++) {
+      const int32_t v = __shfl_sync(0xffffffffu, myv, t);
+      const int32_t w = __shfl_sync(0xffffffffu, myw, t);
+      bool ready = false, hit = false;
+      if (active) {
+        const size_t idx = (size_t)v * nb + j;
+        if (dist[idx] == du - w) {
+          atomicAdd(&zp[idx], val);
+          ready = (atomicSub(&cnt[idx], 1) == 1);
+          hit = true;
+        }
+      }
+      const uint32_t rb = __ballot_sync(0xffffffffu, ready);
+      if (rb && lane == 0) {
+        atomicOr(&tmask[(size_t)v * W + word], rb);
+        enqueue_once(vflag, tlist, tcount, v);
+      }
+      if (bytes) nb_bytes += 4ull * __popc(m) + 24ull * __popc(__ballot_sync(0xffffffffu, hit));
+    }
+  }
+  if (bytes && lane == 0) atomicAdd(bytes, nb_bytes + 8ull * (end - beg) / W + 16ull * __popc(m));
+}
+
+// New MFBr frontier entries: value Z.p + 1/sigma_bar.
+__global__ void __launch_bounds__(256) k_gp_next_frontier(
+    const int32_t* __restrict__ tlist, const uint32_t* tcount_p, int W, int nb,
+    const double* __restrict__ sig, const double* __restrict__ zp, double* fv, uint32_t* fmask,
+    uint32_t* tmask, uint32_t* vflag, int32_t* nlist, uint32_t* ncount, unsigned long long* bytes) {
+  const uint32_t tcount = *tcount_p;
+  const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  for (uint64_t gw = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; gw < tcount; gw += nw) {
+  const unsigned lane = lane_id();
+  const int32_t v = tlist[gw];
+  unsigned long long nbytes = 0;
+  for (int word = 0; word < W; word++) {
+    const size_t mi = (size_t)v * W + word;
+    const uint32_t r = tmask[mi];
+    if (!r) continue;
+    if ((r >> lane) & 1u) {
+      const size_t idx = (size_t)v * nb + word * 32 + lane;
+      fv[idx] = zp[idx] + 1.0 / sig[idx];
+    }
+    if (lane == 0) { fmask[mi] = r; tmask[mi] = 0u; }
+    nbytes += 8ull + 24ull * __popc(r);
+  }
+  if (lane == 0) {
+    vflag[v] = 0u;
+    nlist[atomicAdd(ncount, 1u)] = v;
+    if (bytes) atomicAdd(bytes, nbytes);
+  }
+  }
+}
+
+// Algorithm 3 accumulation, one warp per vertex, no atomics.
+__global__ void __launch_bounds__(256) k_gp_lambda(int32_t n, int W, int nb, const int32_t* __restrict__ src,
+                                                   const double* __restrict__ zp,
+                                                   const double* __restrict__ sig, double* lambda) {
+  uint64_t gw = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (gw >= (uint64_t)n) return;
+  const unsigned lane = lane_id();
+  const int32_t v = (int32_t)gw;
+  double acc = 0.0;
+  for (int word = 0; word < W; word++) {
+    const int j = word * 32 + lane;
+    const size_t idx = (size_t)v * nb + j;
+    const int32_t s = src[j];
+    const double sg = sig[idx];
+    if (s >= 0 && s != v && sg > 0.0) acc += zp[idx] * sg;
+  }
+  for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) lambda[v] += acc;
+}
+
+// ------------------------------------------------------------------ driver
+static inline unsigned warp_blocks(uint64_t warps) { return (unsigned)((warps + 7) / 8); }
+// grid for kernels whose item count is only known on the device (grid-stride)
+static inline unsigned stride_blocks(uint64_t max_warps) {
+  uint64_t b = (max_warps + 7) / 8;
+  return (unsigned)(b < 1 ? 1 : (b > 152 * 16 ? 152 * 16 : b));
+}
+
+static mfbc_status read_counts(RunCtx& rc, Counters* ctr) {
+  MFBC_CUDA_TRY(cudaMemcpyAsync(rc.h_ctr, ctr->list_count, sizeof(uint32_t) * 5,
+                                cudaMemcpyDeviceToHost, rc.stream), rc.err);
+  MFBC_CUDA_TRY(cudaStreamSynchronize(rc.stream), rc.err);
+  rc.prof->drain();
+  return MFBC_OK;
+}
+
+#define PROF(id, ...)             \
+  do {                            \
+    rc.prof->begin(id);           \
+    __VA_ARGS__;                  \
+    rc.prof->end(id);             \
+  } while (0)
+
+mfbc_status general_batch(RunCtx& rc, GeneralState& s, const int32_t* d_src_batch, int nactive,
+                          double* lambda, int64_t* fwd_iters, int64_t* bwd_iters) {
+  const DevGraph& g = *rc.g;
+  const int32_t n = g.n;
+  const int nb = s.nb, W = s.W;
+  cudaStream_t st = rc.stream;
+  const size_t cells = (size_t)n * nb;
+  unsigned long long* B = rc.prof->count_bytes ? s.ctr->bytes : nullptr;
+  if (n == 0) return MFBC_OK;
+
+  // batch sources: active columns then padding
+  fill_i32(s.src, -1, (size_t)nb, st);
+  if (nactive)
+    MFBC_CUDA_TRY(cudaMemcpyAsync(s.src, d_src_batch, sizeof(int32_t) * nactive,
+                                  cudaMemcpyDeviceToDevice, st), rc.err);
+  PROF(K_FILL, {
+    fill_i32(s.dist, INF, cells, st);
+    fill_i32(s.cw, INF, cells, st);
+    cudaMemsetAsync(s.sig, 0, sizeof(double) * cells, st);
+    cudaMemsetAsync(s.cm, 0, sizeof(double) * cells, st);
+    cudaMemsetAsync(s.fmask, 0, sizeof(uint32_t) * (size_t)n * W, st);
+    cudaMemsetAsync(s.tmask, 0, sizeof(uint32_t) * (size_t)n * W, st);
+    cudaMemsetAsync(s.vflag, 0, sizeof(uint32_t) * (size_t)n, st);
+    cudaMemsetAsync(s.ctr->list_count, 0, sizeof(uint32_t) * 4, st);
+  });
+  rc.prof->k[K_FILL].bytes += 24.0 * cells + 8.0 * n * W + 4.0 * n;
+
+  int32_t* cur = s.listA;
+  int32_t* nxt = s.listB;
+  PROF(K_SEED, (k_gp_seed<<<(nb + 127) / 128, 128, 0, st>>>(s.src, nb, W, s.dist, s.sig, s.fm, s.fmask,
+                                                          s.vflag, cur, &s.ctr->list_count[0])));
+  mfbc_status e = read_counts(rc, s.ctr);
+  if (e) return e;
+  uint32_t fcount = rc.h_ctr[0];
+  if (fcount) k_clear_flags<<<(fcount + 255) / 256, 256, 0, st>>>(cur, fcount, s.vflag);
+
+  // ---- MFBF (Algorithm 1)
+  int64_t iters = 0;
+  while (fcount) {
+    if (++iters > (int64_t)n + 1) {
+      if (rc.err) *rc.err = "MFBF did not converge within n+1 products";
+      return MFBC_ERR_NO_CONVERGENCE;
+    }
+    MFBC_CUDA_TRY(cudaMemsetAsync(s.ctr->list_count, 0, sizeof(uint32_t) * 4, st), rc.err);
+    const uint64_t wp = (uint64_t)fcount * W;
+    PROF(K_RELAX_MIN, (k_gp_relax_min<<<warp_blocks(wp), 256, 0, st>>>(
+                          g.rowptr, g.col, g.w, cur, fcount, W, nb, s.fmask, s.dist, s.cw, s.tmask,
+                          s.vflag, nxt, &s.ctr->list_count[1], B ? B + K_RELAX_MIN : nullptr)));
+    PROF(K_RELAX_TIE, (k_gp_relax_tie<<<warp_blocks(wp), 256, 0, st>>>(
+                          g.rowptr, g.col, g.w, cur, fcount, W, nb, s.fmask, s.dist, s.fm, s.cw, s.cm,
+                          B ? B + K_RELAX_TIE : nullptr)));
+    PROF(K_CLEAR, (k_clear_mask_rows<<<(unsigned)((wp + 255) / 256), 256, 0, st>>>(cur, fcount, W,
+                                                                                   s.fmask)));
+    // the touched list lives in nxt; compact the next frontier into cur
+    PROF(K_ACCUM, (k_gp_accumulate<<<stride_blocks((uint64_t)n), 256, 0, st>>>(
+                      nxt, &s.ctr->list_count[1], W, nb, s.dist, s.sig, s.cw, s.cm, s.fm, s.fmask,
+                      s.tmask, s.vflag, cur, &s.ctr->list_count[0], B ? B + K_ACCUM : nullptr)));
+    e = read_counts(rc, s.ctr);
+    if (e) return e;
+    fcount = rc.h_ctr[0];
+  }
+  if (fwd_iters) *fwd_iters += iters;
+  check_sigma_exact(s.sig, cells, s.ctr, st);
+  if (!lambda) return MFBC_OK;
+
+  // ---- MFBr (Algorithm 2): cw holds the counters, cm the factors Z.p, fm the values
+  MFBC_CUDA_TRY(cudaMemsetAsync(s.ctr->list_count, 0, sizeof(uint32_t) * 4, st), rc.err);
+  PROF(K_COUNTERS, (k_gp_counters<<<warp_blocks((uint64_t)n), 256, 0, st>>>(
+                       n, g.rowptr, g.col, g.w, W, nb, s.src, s.dist, s.sig, s.cw, s.cm, s.fm, s.fmask,
+                       cur, &s.ctr->list_count[0], B ? B + K_COUNTERS : nullptr)));
+  e = read_counts(rc, s.ctr);
+  if (e) return e;
+  fcount = rc.h_ctr[0];
+  iters = 0;
+  while (fcount) {
+    if (++iters > (int64_t)n + 1) {
+      if (rc.err) *rc.err = "MFBr did not converge within n+1 products";
+      return MFBC_ERR_NO_CONVERGENCE;
+    }
+    MFBC_CUDA_TRY(cudaMemsetAsync(s.ctr->list_count, 0, sizeof(uint32_t) * 4, st), rc.err);
+    const uint64_t wp = (uint64_t)fcount * W;
+    PROF(K_PROPAGATE, (k_gp_propagate<<<warp_blocks(wp), 256, 0, st>>>(
+                          g.rowptr_t, g.col_t, g.w_t, cur, fcount, W, nb, s.fmask, s.dist, s.fm, s.cm,
+                          s.cw, s.tmask, s.vflag, nxt, &s.ctr->list_count[1],
+                          B ? B + K_PROPAGATE : nullptr)));
+    PROF(K_CLEAR, (k_clear_mask_rows<<<(unsigned)((wp + 255) / 256), 256, 0, st>>>(cur, fcount, W,
+                                                                                   s.fmask)));
+    PROF(K_FINAL, (k_gp_next_frontier<<<stride_blocks((uint64_t)n), 256, 0, st>>>(
+                      nxt, &s.ctr->list_count[1], W, nb, s.sig, s.cm, s.fm, s.fmask, s.tmask, s.vflag,
+                      cur, &s.ctr->list_count[0], B ? B + K_FINAL : nullptr)));
+    e = read_counts(rc, s.ctr);
+    if (e) return e;
+    fcount = rc.h_ctr[0];
+  }
+  if (bwd_iters) *bwd_iters += iters;
+  PROF(K_LAMBDA, (k_gp_lambda<<<warp_blocks((uint64_t)n), 256, 0, st>>>(n, W, nb, s.src, s.cm, s.sig,
+                                                                         lambda)));
+  rc.prof->k[K_LAMBDA].bytes += 16.0 * cells + 16.0 * n;
+  return MFBC_OK;
+}
+
+mfbc_status general_output(RunCtx& rc, GeneralState& s, int nactive, int32_t* dist_out,
+                           double* sigma_out) {
+  const int32_t n = rc.g->n;
+  PROF(K_OUTPUT, {
+    transpose_i32(s.dist, dist_out, n, s.nb, nactive, n, rc.stream);
+    if (sigma_out) transpose_f64(s.sig, sigma_out, n, s.nb, nactive, n, rc.stream);
+  });
+  return MFBC_OK;
+}
+
+}  // namespace mfbc

@@ -1,0 +1,200 @@
+// Internal declarations of the MFBC CUDA library (sm_103a).
+//
+// State layout (both kernel families): every per-(source, vertex) array of a
+// batch is VERTEX-MAJOR, x[v * nb + j] for vertex v and batch column j, so that
+// one warp touching 32 consecutive columns of one vertex reads or writes one
+// contiguous 128-byte (int32) or 256-byte (FP64) segment.  Frontier and
+// visited sets are bit masks, 32 columns per uint32 word, mask[v * W + j/32]
+// with W = nb / 32.  Column j of a batch belongs to source src[j]; src[j] < 0
+// marks a padding column (Theorem 1's padding of the last batch).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/mfbc.h"
+
+namespace mfbc {
+
+constexpr int32_t INF = 0x7fffffff;
+constexpr int WARP = 32;
+constexpr int CHUNK = 32;          // neighbours per work item of the level kernels
+
+// ------------------------------------------------------------------ graph
+struct ItemList {                  // work items (v, beg): arcs [beg, min(beg+CHUNK, rowptr[v+1]))
+  int64_t count = 0;
+  int32_t* v = nullptr;
+  int64_t* beg = nullptr;
+  int32_t nhub = 0;                // vertices whose row spans more than one item
+  int32_t* hub_of = nullptr;       // [n] hub index or -1
+  int32_t* hubs = nullptr;         // [nhub] vertex ids
+};
+
+struct DevGraph {
+  int32_t n = 0;
+  int64_t nnz = 0;
+  bool directed = true;
+  bool unit = true;                // every arc weighs 1 (w == NULL or all ones)
+  int32_t wmax = 1;
+  int64_t* rowptr = nullptr;       // CSR of A (out-arcs)
+  int32_t* col = nullptr;
+  int32_t* w = nullptr;            // nullptr when unit
+  int64_t* rowptr_t = nullptr;     // CSR of A^T (in-arcs); aliases CSR when undirected
+  int32_t* col_t = nullptr;
+  int32_t* w_t = nullptr;
+  ItemList items_in;               // over A^T rows (MFBF pull gathers in-arcs)
+  ItemList items_out;              // over A rows   (MFBr pull gathers out-arcs)
+  std::vector<void*> owned;        // device allocations to free
+};
+
+// ------------------------------------------------------------- profiling
+struct KStat {
+  const char* name;
+  uint64_t launches = 0;
+  double ms = 0.0;
+  double bytes = 0.0;
+};
+
+enum KId {
+  K_FILL = 0, K_SEED, K_RELAX_MIN, K_RELAX_TIE, K_ACCUM, K_COUNTERS, K_PROPAGATE, K_FINAL,
+  K_LAMBDA, K_CLEAR, K_LVL_FWD, K_LVL_VISIT, K_LVL_BWD, K_LVL_HUB, K_LVL_RESET, K_OUTPUT,
+  K_NUM
+};
+
+// Device-side counters of algorithmic bytes, one slot per kernel id.
+struct Counters {
+  unsigned long long bytes[K_NUM];
+  uint32_t list_count[4];          // frontier / touched list sizes
+  uint32_t flags;                  // bit0: level capacity exceeded, bit1: sigma >= 2^53
+};
+
+class Profiler {
+ public:
+  bool on = false;                 // record CUDA events around launches
+  bool count_bytes = false;        // kernels add their algorithmic bytes on the device
+  cudaStream_t stream = nullptr;
+  KStat k[K_NUM];
+  Profiler();
+  void begin(KId id);              // record start event of a launch of kernel id
+  void end(KId id);                // record stop event
+  void drain();                    // accumulate finished event pairs (stream synchronised)
+  void release();
+ private:
+  struct Pending { KId id; cudaEvent_t a, b; };
+  std::vector<Pending> pend;
+  std::vector<cudaEvent_t> pool;
+  cudaEvent_t get();
+};
+
+// ------------------------------------------------------------- workspaces
+struct Carver {
+  char* base; size_t off = 0, cap;
+  Carver(void* b, size_t c) : base((char*)b), cap(c) {}
+  template <class T> T* take(size_t count) {
+    size_t bytes = (count * sizeof(T) + 255) & ~size_t(255);
+    T* p = (T*)(base ? base + off : nullptr);
+    off += bytes;
+    return p;
+  }
+};
+
+// General (any integer weight) path: Algorithms 1 and 2 with the two-phase
+// monoid product.  See general.cu.
+struct GeneralState {
+  int nb = 0, W = 0;
+  int32_t* dist;      // T.w            [n][nb]
+  double* sig;        // T.m            [n][nb]
+  int32_t* cw;        // product weight / MFBr counter Z.c   [n][nb]
+  double* cm;         // product mult.  / MFBr factor Z.p    [n][nb]
+  double* fm;         // frontier mult. / MFBr frontier value [n][nb]
+  uint32_t* fmask;    // frontier bits  [n][W]
+  uint32_t* tmask;    // touched bits   [n][W]
+  uint32_t* vflag;    // per-vertex enqueue flags [n]
+  int32_t* listA;     // frontier vertex lists [n]
+  int32_t* listB;
+  int32_t* src;       // [nb]
+  Counters* ctr;
+};
+size_t general_bytes(int32_t n, int nb);
+void general_carve(Carver& c, int32_t n, int nb, GeneralState& s);
+
+// Level-synchronous path for unit weights: Algorithms 1 and 2 with the
+// frontiers kept as per-level bit masks.  See level.cu.
+struct LevelState {
+  int nb = 0, W = 0, Lcap = 0;
+  double* sv;         // sigma_bar, then zeta + 1/sigma_bar (in place)  [n][nb]
+  uint32_t* V;        // visited bits [n][W]
+  uint32_t* F;        // per-level frontier bits, level l at F + l*n*W
+  uint32_t* member;   // per-level vertex bitmaps, level l at member + l*mw
+  uint32_t* full;     // vertices visited by every active column  [mw]
+  int32_t* lists;     // per-level vertex lists, concatenated
+  int64_t list_cap;
+  double* zacc;       // [nhub_out][nb] backward partial sums of multi-item vertices
+  int32_t* src;       // [nb]
+  Counters* ctr;
+  int64_t mw;         // words per vertex bitmap
+};
+size_t level_bytes(const DevGraph& g, int nb, int Lcap, int64_t list_cap);
+void level_carve(Carver& c, const DevGraph& g, int nb, int Lcap, int64_t list_cap, LevelState& s);
+
+// --------------------------------------------------------------- drivers
+struct RunCtx {
+  const DevGraph* g;
+  cudaStream_t stream;
+  Profiler* prof;
+  uint32_t* h_ctr;                 // pinned host mirror of Counters::list_count / flags
+  std::string* err;
+};
+
+// One batch of the general path.  lambda != nullptr: full MFBC batch adding
+// into lambda; otherwise MFBF only.  Returns MFBC_OK or an error status.
+mfbc_status general_batch(RunCtx& rc, GeneralState& s, const int32_t* d_src_batch, int nactive,
+                          double* lambda, int64_t* fwd_iters, int64_t* bwd_iters);
+// Transposed copy of the general state's dist/sig into per-source rows.
+mfbc_status general_output(RunCtx& rc, GeneralState& s, int nactive, int32_t* dist_out,
+                           double* sigma_out);
+
+// One batch of the level path.  Returns MFBC_OK, an error, or
+// MFBC_ERR_NO_CONVERGENCE with *levels_exceeded set when Lcap was too small.
+mfbc_status level_batch(RunCtx& rc, LevelState& s, const int32_t* d_src_batch, int nactive,
+                        double* lambda, bool backward, int* levels_out, bool* levels_exceeded,
+                        int64_t* fwd_iters, int64_t* bwd_iters);
+mfbc_status level_output(RunCtx& rc, LevelState& s, int levels, int nactive, int32_t* dist_out,
+                         double* sigma_out);
+void level_reset(RunCtx& rc, LevelState& s, int levels);
+
+// Graph construction helpers (graph.cu).
+mfbc_status graph_build(int32_t n, int64_t nnz, const int64_t* h_rowptr, const int32_t* h_col,
+                        const int32_t* h_w, uint32_t flags, cudaStream_t st, DevGraph* g,
+                        std::string* err);
+void graph_free(DevGraph* g);
+
+// Small device utilities (util.cu).
+void fill_i32(int32_t* p, int32_t v, size_t count, cudaStream_t st);
+void fill_f64(double* p, double v, size_t count, cudaStream_t st);
+void check_sigma_exact(const double* sig, size_t count, Counters* ctr, cudaStream_t st);
+void transpose_i32(const int32_t* in, int32_t* out, int32_t n, int nb, int nactive, int64_t out_ld,
+                   cudaStream_t st);
+void transpose_f64(const double* in, double* out, int32_t n, int nb, int nactive, int64_t out_ld,
+                   cudaStream_t st);
+
+// ------------------------------------------------------------ device helpers
+__device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
+
+}  // namespace mfbc
+
+namespace mfbc {
+inline mfbc_status cuda_fail(std::string* errp, const char* what, cudaError_t e) {
+  if (errp) *errp = std::string(what) + ": " + cudaGetErrorString(e);
+  return MFBC_ERR_CUDA;
+}
+}  // namespace mfbc
+
+#define MFBC_CUDA_TRY(expr, errp)                                 \
+  do {                                                            \
+    cudaError_t _e = (expr);                                      \
+    if (_e != cudaSuccess) return mfbc::cuda_fail((errp), #expr, _e); \
+  } while (0)

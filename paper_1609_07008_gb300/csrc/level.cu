@@ -1,0 +1,501 @@
+// Level path: MFBF (Algorithm 1) and MFBr (Algorithm 2) for unit weights.
+//
+// With every arc of weight 1 the multpath frontier of MFBF iteration l holds
+// exactly the pairs (s,v) with tau(s,v) = l (Lemma 1: the frontier after
+// j-1 products carries the shortest paths of exactly j edges), each once.
+// The frontier is therefore stored as one bit per (column, vertex) and level,
+// F_l[v] (W words of 32 columns), plus a one-bit-per-vertex membership bitmap
+// and a vertex list per level.  Multiplicities live in one FP64 array
+// sv[v][j] (vertex-major).
+//
+// MFBF product of level l (gather form of the product F_l (+).f A): for every
+// vertex v not yet reached by all columns, and every in-neighbour u of v that
+// is in F_l,
+//     new(s,v)        = [s in F_l(u)] and not visited(s,v)
+//     sigma_bar(s,v) += sigma_bar(s,u)          for those s.
+// Over unit weights every candidate of the product has weight l+1, so the
+// monoid's minimum is decided by "not yet visited" alone and every candidate
+// is a tie that is summed (Sec. 4.1.1); the filter of Algorithm 1 keeps
+// exactly the new pairs, which form F_{l+1}.
+//
+// MFBr (Algorithm 2) over unit weights: a pair (s,v) at level l has its DAG
+// successors among the pairs (s,u), u an out-neighbour of v, at level l+1.
+// Processing levels in decreasing order makes every counter of Algorithm 2
+// reach zero at the level's turn, so the counters need not be stored: level
+// l gathers, for each (s,v) in F_l,
+//     zeta(s,v) = sum over out-neighbours u with (s,u) in F_{l+1} of
+//                 (zeta(s,u) + 1/sigma_bar(s,u))
+// (Sec. 4.2.1), adds zeta(s,v) * sigma_bar(s,v) to lambda(v) (Algorithm 3),
+// and overwrites sv(s,v) with the frontier value zeta + 1/sigma_bar that its
+// predecessors gather one level later.
+//
+// Work decomposition: the adjacency rows are cut into items of at most
+// CHUNK = 32 arcs; one warp takes one item.  Lane k reads arc k, so a row's
+// neighbour ids arrive in one 128-byte load, membership is one bit test per
+// lane, and the frontier masks of the member neighbours are read as whole
+// 4*W-byte rows (lane = 32-column word).  The gather then walks the columns
+// word by word with lane = column, so each member's multiplicities are read
+// as one contiguous 256-byte segment per word.  Rows longer than one item
+// ("hubs") combine their items with atomics (sv for MFBF, a per-hub
+// accumulator for MFBr followed by a finalisation pass).
+#include "internal.cuh"
+
+namespace mfbc {
+
+constexpr int LVL_WARPS = 8;                 // warps per block
+
+size_t level_bytes(const DevGraph& g, int nb, int Lcap, int64_t list_cap) {
+  Carver c(nullptr, 0);
+  LevelState s;
+  level_carve(c, g, nb, Lcap, list_cap, s);
+  return c.off;
+}
+
+void level_carve(Carver& c, const DevGraph& g, int nb, int Lcap, int64_t list_cap, LevelState& s) {
+  const int32_t n = g.n;
+  s.nb = nb;
+  s.W = nb / 32;
+  s.Lcap = Lcap;
+  s.mw = ((int64_t)n + 31) / 32;
+  s.sv = c.take<double>((size_t)n * nb);
+  s.V = c.take<uint32_t>((size_t)n * s.W);
+  s.F = c.take<uint32_t>((size_t)Lcap * n * s.W);
+  s.member = c.take<uint32_t>((size_t)Lcap * s.mw);
+  s.full = c.take<uint32_t>((size_t)s.mw);
+  s.list_cap = list_cap;
+  s.lists = c.take<int32_t>((size_t)list_cap);
+  s.zacc = c.take<double>((size_t)(g.items_out.nhub > 0 ? g.items_out.nhub : 1) * nb);
+  s.src = c.take<int32_t>((size_t)nb);
+  s.ctr = c.take<Counters>(1);
+}
+
+__device__ __forceinline__ bool test_bit(const uint32_t* bm, int32_t v) {
+  return (__ldg(&bm[v >> 5]) >> (v & 31)) & 1u;
+}
+
+// active-column mask of word w for nactive active columns
+__device__ __forceinline__ uint32_t active_mask(int w, int nactive) {
+  const int lo = w * 32;
+  if (lo + 32 <= nactive) return 0xffffffffu;
+  if (lo >= nactive) return 0u;
+  return (1u << (nactive - lo)) - 1u;
+}
+
+// sv rows of multi-item vertices start at zero (MFBF adds into them).
+__global__ void k_lvl_zero_hubs(const int32_t* __restrict__ hubs, int32_t nhub, int nb, double* sv) {
+  const uint64_t total = (uint64_t)nhub * nb;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (uint64_t)gridDim.x * blockDim.x)
+    sv[(size_t)hubs[i / nb] * nb + (i % nb)] = 0.0;
+}
+
+// Level 0: F_0(s_j) holds column j, sigma_bar(s_j, s_j) = 1.
+__global__ void k_lvl_seed(const int32_t* __restrict__ src, int nb, int W, double* sv, uint32_t* F0,
+                           uint32_t* member0, int32_t* list0, uint32_t* count) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= nb) return;
+  const int32_t s = src[j];
+  if (s < 0) return;
+  sv[(size_t)s * nb + j] = 1.0;
+  atomicOr(&F0[(size_t)s * W + (j >> 5)], 1u << (j & 31));
+  const uint32_t bit = 1u << (s & 31);
+  if (!(atomicOr(&member0[s >> 5], bit) & bit)) list0[atomicAdd(count, 1u)] = s;
+}
+
+// visited |= F_l for the vertices of level l; mark vertices reached by every column.
+__global__ void k_lvl_visit(const int32_t* __restrict__ list, uint32_t count, int W, int nactive,
+                            const uint32_t* __restrict__ Fl, uint32_t* V, uint32_t* full) {
+  const unsigned lane = lane_id();
+  const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  for (uint64_t i = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < count; i += nw) {
+    const int32_t v = list[i];
+    bool ok = true;
+    if ((int)lane < W) {
+      const size_t r = (size_t)v * W + lane;
+      const uint32_t x = V[r] | Fl[r];
+      V[r] = x;
+      const uint32_t am = active_mask(lane, nactive);
+      ok = (x & am) == am;
+    }
+    if (__all_sync(0xffffffffu, ok) && lane == 0) atomicOr(&full[v >> 5], 1u << (v & 31));
+  }
+}
+
+struct LvlSmem {
+  int32_t su[LVL_WARPS][32];                 // member neighbour ids of the item
+  uint32_t sF[LVL_WARPS][32][32];            // their (masked) frontier words
+};
+
+// MFBF product of level l (see file comment).
+__global__ void __launch_bounds__(LVL_WARPS * 32) k_lvl_fwd(
+    int64_t nitems, const int32_t* __restrict__ item_v, const int64_t* __restrict__ item_beg,
+    const int64_t* __restrict__ rowptr_t, const int32_t* __restrict__ col_t, int W, int nb,
+    const uint32_t* __restrict__ full, const uint32_t* __restrict__ V, const uint32_t* __restrict__ Fl,
+    const uint32_t* __restrict__ mem_l, uint32_t* Fn, uint32_t* mem_n, double* sv, int32_t* list_n,
+    uint32_t* count_n, int64_t cap_n, uint32_t* flags, unsigned long long* bytes) {
+  __shared__ LvlSmem sm;
+  const unsigned lane = lane_id();
+  const int wi = threadIdx.x >> 5;
+  const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  unsigned long long nbytes = 0, ngather = 0;
+  for (uint64_t it = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; it < (uint64_t)nitems;
+       it += nw) {
+    const int32_t v = item_v[it];
+    if (test_bit(full, v)) continue;
+    const int64_t beg = item_beg[it];
+    const int64_t rend = rowptr_t[v + 1];
+    const int64_t end = min(beg + CHUNK, rend);
+    const bool multi = (rend - rowptr_t[v]) > CHUNK;
+    const int64_t k = beg + lane;
+    const int32_t u = k < end ? __ldg(&col_t[k]) : -1;
+    const bool isMem = u >= 0 && test_bit(mem_l, u);
+    const uint32_t mm = __ballot_sync(0xffffffffu, isMem);
+    if (bytes) nbytes += 4ull * (end - beg) + 16ull;
+    if (!mm) continue;
+    const int nm = __popc(mm);
+    if (isMem) sm.su[wi][__popc(mm & ((1u << lane) - 1u))] = u;
+    __syncwarp();
+    const uint32_t Vv = (int)lane < W ? V[(size_t)v * W + lane] : 0xffffffffu;
+    uint32_t cand = 0;
+    for (int q = 0; q < nm; q++) {
+      const int32_t uq = sm.su[wi][q];
+      const uint32_t f = (int)lane < W ? __ldg(&Fl[(size_t)uq * W + lane]) : 0u;
+      const uint32_t mk = f & ~Vv;
+      sm.sF[wi][q][lane] = mk;
+      cand |= mk;
+    }
+    __syncwarp();
+    uint32_t nz = __ballot_sync(0xffffffffu, cand != 0u);
+    if (bytes) nbytes += 4ull * W * (nm + 1);
+    const size_t vrow = (size_t)v * nb;
+    while (nz) {
+      const int j = __ffs(nz) - 1;
+      nz &= nz - 1;
+      const uint32_t cj = __shfl_sync(0xffffffffu, cand, j);
+      const int col = j * 32 + lane;
+      double acc = 0.0;
+      int q = 0;
+      for (; q + 4 <= nm; q += 4) {
+        double x0 = 0.0, x1 = 0.0, x2 = 0.0, x3 = 0.0;
+        if ((sm.sF[wi][q + 0][j] >> lane) & 1u) x0 = __ldg(&sv[(size_t)sm.su[wi][q + 0] * nb + col]);
+        if ((sm.sF[wi][q + 1][j] >> lane) & 1u) x1 = __ldg(&sv[(size_t)sm.su[wi][q + 1] * nb + col]);
+        if ((sm.sF[wi][q + 2][j] >> lane) & 1u) x2 = __ldg(&sv[(size_t)sm.su[wi][q + 2] * nb + col]);
+        if ((sm.sF[wi][q + 3][j] >> lane) & 1u) x3 = __ldg(&sv[(size_t)sm.su[wi][q + 3] * nb + col]);
+        acc += x0; acc += x1; acc += x2; acc += x3;
+        if (bytes) ngather += ((sm.sF[wi][q][j] >> lane) & 1u) + ((sm.sF[wi][q + 1][j] >> lane) & 1u) +
+                              ((sm.sF[wi][q + 2][j] >> lane) & 1u) + ((sm.sF[wi][q + 3][j] >> lane) & 1u);
+      }
+      for (; q < nm; q++) {
+        if ((sm.sF[wi][q][j] >> lane) & 1u) {
+          acc += __ldg(&sv[(size_t)sm.su[wi][q] * nb + col]);
+          if (bytes) ngather++;
+        }
+      }
+      if ((cj >> lane) & 1u) {
+        // a multiplicity at or above 2^53 may have been rounded (flags bit 1)
+        double tot = acc;
+        if (multi) tot += atomicAdd(&sv[vrow + col], acc);
+        else sv[vrow + col] = acc;
+        if (tot >= 9007199254740992.0) atomicOr(flags, 2u);
+        if (bytes) ngather++;                       // the written multiplicity
+      }
+      if (bytes) nbytes += 4ull;
+    }
+    if ((int)lane < W && cand) {
+      if (multi) atomicOr(&Fn[(size_t)v * W + lane], cand);
+      else Fn[(size_t)v * W + lane] = cand;
+    }
+    if (__any_sync(0xffffffffu, cand != 0u) && lane == 0) {
+      const uint32_t bit = 1u << (v & 31);
+      if (!(atomicOr(&mem_n[v >> 5], bit) & bit)) {
+        const uint32_t pos = atomicAdd(count_n, 1u);
+        if ((int64_t)pos < cap_n) list_n[pos] = v;
+        else atomicOr(flags, 1u);
+      }
+    }
+    __syncwarp();
+  }
+  if (bytes) {
+    for (int o = 16; o; o >>= 1) ngather += __shfl_xor_sync(0xffffffffu, ngather, o);
+    if (lane == 0) atomicAdd(bytes, nbytes + 8ull * ngather);
+  }
+}
+
+// MFBr gather of level l >= 1 (see file comment).
+__global__ void __launch_bounds__(LVL_WARPS * 32) k_lvl_bwd(
+    int64_t nitems, const int32_t* __restrict__ item_v, const int64_t* __restrict__ item_beg,
+    const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col, const int32_t* __restrict__ hub_of,
+    int W, int nb, const uint32_t* __restrict__ Fl, const uint32_t* __restrict__ mem_l,
+    const uint32_t* __restrict__ Fn, const uint32_t* __restrict__ mem_n, double* sv, double* zacc,
+    double* lambda, unsigned long long* bytes) {
+  __shared__ LvlSmem sm;
+  const unsigned lane = lane_id();
+  const int wi = threadIdx.x >> 5;
+  const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  unsigned long long nbytes = 0, ngather = 0;
+  for (uint64_t it = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; it < (uint64_t)nitems;
+       it += nw) {
+    const int32_t v = item_v[it];
+    if (!test_bit(mem_l, v)) continue;
+    const int64_t beg = item_beg[it];
+    const int64_t rend = rowptr[v + 1];
+    const int64_t end = min(beg + CHUNK, rend);
+    const bool multi = (rend - rowptr[v]) > CHUNK;
+    const int64_t k = beg + lane;
+    const int32_t u = k < end ? __ldg(&col[k]) : -1;
+    const bool isMem = u >= 0 && test_bit(mem_n, u);
+    const uint32_t mm = __ballot_sync(0xffffffffu, isMem);
+    if (bytes) nbytes += 4ull * (end - beg) + 16ull;
+    if (multi && !mm) continue;                      // nothing to add to the hub accumulator
+    const int nm = __popc(mm);
+    if (isMem) sm.su[wi][__popc(mm & ((1u << lane) - 1u))] = u;
+    __syncwarp();
+    const uint32_t Fv = (int)lane < W ? __ldg(&Fl[(size_t)v * W + lane]) : 0u;
+    for (int q = 0; q < nm; q++) {
+      const int32_t uq = sm.su[wi][q];
+      const uint32_t f = (int)lane < W ? __ldg(&Fn[(size_t)uq * W + lane]) : 0u;
+      sm.sF[wi][q][lane] = f & Fv;
+    }
+    __syncwarp();
+    uint32_t nz = __ballot_sync(0xffffffffu, Fv != 0u);
+    if (bytes) nbytes += 4ull * W * (nm + 1);
+    const size_t vrow = (size_t)v * nb;
+    const int32_t hub = multi ? hub_of[v] : -1;
+    double lam = 0.0;
+    while (nz) {
+      const int j = __ffs(nz) - 1;
+      nz &= nz - 1;
+      const uint32_t fj = __shfl_sync(0xffffffffu, Fv, j);
+      const int col_j = j * 32 + lane;
+      double acc = 0.0;
+      int q = 0;
+      for (; q + 4 <= nm; q += 4) {
+        double x0 = 0.0, x1 = 0.0, x2 = 0.0, x3 = 0.0;
+        if ((sm.sF[wi][q + 0][j] >> lane) & 1u) x0 = __ldg(&sv[(size_t)sm.su[wi][q + 0] * nb + col_j]);
+        if ((sm.sF[wi][q + 1][j] >> lane) & 1u) x1 = __ldg(&sv[(size_t)sm.su[wi][q + 1] * nb + col_j]);
+        if ((sm.sF[wi][q + 2][j] >> lane) & 1u) x2 = __ldg(&sv[(size_t)sm.su[wi][q + 2] * nb + col_j]);
+        if ((sm.sF[wi][q + 3][j] >> lane) & 1u) x3 = __ldg(&sv[(size_t)sm.su[wi][q + 3] * nb + col_j]);
+        acc += x0; acc += x1; acc += x2; acc += x3;
+        if (bytes) ngather += ((sm.sF[wi][q][j] >> lane) & 1u) + ((sm.sF[wi][q + 1][j] >> lane) & 1u) +
+                              ((sm.sF[wi][q + 2][j] >> lane) & 1u) + ((sm.sF[wi][q + 3][j] >> lane) & 1u);
+      }
+      for (; q < nm; q++) {
+        if ((sm.sF[wi][q][j] >> lane) & 1u) {
+          acc += __ldg(&sv[(size_t)sm.su[wi][q] * nb + col_j]);
+          if (bytes) ngather++;
+        }
+      }
+      if ((fj >> lane) & 1u) {
+        if (multi) {
+          atomicAdd(&zacc[(size_t)hub * nb + col_j], acc);
+          if (bytes) ngather++;
+        } else {
+          const double sg = sv[vrow + col_j];
+          lam += acc * sg;
+          sv[vrow + col_j] = acc + 1.0 / sg;
+          if (bytes) ngather += 2;
+        }
+      }
+    }
+    if (!multi) {
+      for (int o = 16; o; o >>= 1) lam += __shfl_xor_sync(0xffffffffu, lam, o);
+      if (lane == 0) lambda[v] += lam;
+      if (bytes) nbytes += 16ull;
+    }
+    __syncwarp();
+  }
+  if (bytes) {
+    for (int o = 16; o; o >>= 1) ngather += __shfl_xor_sync(0xffffffffu, ngather, o);
+    if (lane == 0) atomicAdd(bytes, nbytes + 8ull * ngather);
+  }
+}
+
+// Finalise the multi-item vertices of level l: zeta from the hub accumulator.
+__global__ void k_lvl_hub_final(const int32_t* __restrict__ hubs, int32_t nhub, int W, int nb,
+                                const uint32_t* __restrict__ Fl, const uint32_t* __restrict__ mem_l,
+                                double* sv, double* zacc, double* lambda, unsigned long long* bytes) {
+  const unsigned lane = lane_id();
+  const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  unsigned long long nbytes = 0;
+  for (uint64_t h = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; h < (uint64_t)nhub; h += nw) {
+    const int32_t v = hubs[h];
+    if (!test_bit(mem_l, v)) continue;
+    double lam = 0.0;
+    for (int j = 0; j < W; j++) {
+      const uint32_t fj = Fl[(size_t)v * W + j];
+      if (!fj) continue;
+      if ((fj >> lane) & 1u) {
+        const size_t zi = (size_t)h * nb + j * 32 + lane;
+        const size_t vi = (size_t)v * nb + j * 32 + lane;
+        const double z = zacc[zi];
+        zacc[zi] = 0.0;
+        const double sg = sv[vi];
+        lam += z * sg;
+        sv[vi] = z + 1.0 / sg;
+      }
+      if (bytes) nbytes += 4ull + 32ull * __popc(fj);
+    }
+    for (int o = 16; o; o >>= 1) lam += __shfl_xor_sync(0xffffffffu, lam, o);
+    if (lane == 0) { lambda[v] += lam; if (bytes) atomicAdd(bytes, nbytes + 16ull); }
+    nbytes = 0;
+  }
+}
+
+// Return the bit masks touched by a batch to zero (F rows, visited rows).
+__global__ void k_lvl_clear_rows(const int32_t* __restrict__ list, uint32_t count, int W, uint32_t* Fl,
+                                 uint32_t* V) {
+  const uint64_t total = (uint64_t)count * W;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (uint64_t)gridDim.x * blockDim.x) {
+    const size_t r = (size_t)list[i / W] * W + (i % W);
+    Fl[r] = 0u;
+    V[r] = 0u;
+  }
+}
+
+// Per-source rows of tau and sigma_bar from the level masks (sssp output).
+__global__ void k_lvl_output(const int32_t* __restrict__ list, uint32_t count, int level, int W, int nb,
+                             int nactive, int32_t n, const uint32_t* __restrict__ Fl,
+                             const double* __restrict__ sv, int32_t* dist_out, double* sigma_out) {
+  const unsigned lane = lane_id();
+  const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  for (uint64_t i = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < count; i += nw) {
+    const int32_t v = list[i];
+    for (int j = 0; j < W; j++) {
+      const uint32_t fj = Fl[(size_t)v * W + j];
+      const int c = j * 32 + lane;
+      if (((fj >> lane) & 1u) && c < nactive) {
+        dist_out[(size_t)c * n + v] = level;
+        if (sigma_out) sigma_out[(size_t)c * n + v] = sv[(size_t)v * nb + c];
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------------ driver
+#define PROF(id, ...)             \
+  do {                            \
+    rc.prof->begin(id);           \
+    __VA_ARGS__;                  \
+    rc.prof->end(id);             \
+  } while (0)
+
+static inline unsigned grid_for_warps(uint64_t warps, unsigned cap) {
+  uint64_t b = (warps + LVL_WARPS - 1) / LVL_WARPS;
+  if (b < 1) b = 1;
+  return (unsigned)(b > cap ? cap : b);
+}
+
+struct LevelPlan {                 // host-side level bookkeeping of one batch
+  std::vector<int64_t> off;        // list offset of each level
+  std::vector<uint32_t> cnt;       // list length of each level
+};
+static thread_local LevelPlan tl_plan;
+
+mfbc_status level_batch(RunCtx& rc, LevelState& s, const int32_t* d_src_batch, int nactive,
+                        double* lambda, bool backward, int* levels_out, bool* levels_exceeded,
+                        int64_t* fwd_iters, int64_t* bwd_iters) {
+  const DevGraph& g = *rc.g;
+  const int32_t n = g.n;
+  const int nb = s.nb, W = s.W;
+  cudaStream_t st = rc.stream;
+  unsigned long long* B = rc.prof->count_bytes ? s.ctr->bytes : nullptr;
+  *levels_exceeded = false;
+  *levels_out = -1;
+  if (n == 0) return MFBC_OK;
+  const unsigned big_grid = 152u * 6u;       // resident blocks of the level kernels
+
+  fill_i32(s.src, -1, (size_t)nb, st);
+  if (nactive)
+    MFBC_CUDA_TRY(cudaMemcpyAsync(s.src, d_src_batch, sizeof(int32_t) * nactive, cudaMemcpyDeviceToDevice, st), rc.err);
+  MFBC_CUDA_TRY(cudaMemsetAsync(s.ctr->list_count, 0, sizeof(uint32_t) * 4, st), rc.err);
+  MFBC_CUDA_TRY(cudaMemsetAsync(s.full, 0, sizeof(uint32_t) * s.mw, st), rc.err);
+  if (g.items_in.nhub)
+    PROF(K_FILL, (k_lvl_zero_hubs<<<152 * 4, 256, 0, st>>>(g.items_in.hubs, g.items_in.nhub, nb, s.sv)));
+  rc.prof->k[K_FILL].bytes += 8.0 * g.items_in.nhub * nb;
+  PROF(K_SEED, (k_lvl_seed<<<(nb + 127) / 128, 128, 0, st>>>(s.src, nb, W, s.sv, s.F, s.member, s.lists,
+                                                           &s.ctr->list_count[0])));
+  MFBC_CUDA_TRY(cudaMemcpyAsync(rc.h_ctr, s.ctr->list_count, sizeof(uint32_t) * 5, cudaMemcpyDeviceToHost, st), rc.err);
+  MFBC_CUDA_TRY(cudaStreamSynchronize(st), rc.err);
+  LevelPlan& P = tl_plan;
+  P.off.assign(1, 0);
+  P.cnt.assign(1, rc.h_ctr[0]);
+  auto Fl = [&](int l) { return s.F + (size_t)l * n * W; };
+  auto Ml = [&](int l) { return s.member + (size_t)l * s.mw; };
+
+  int L = 0;
+  for (int l = 0;; l++) {
+    const uint32_t cl = P.cnt[l];
+    PROF(K_LVL_VISIT, (k_lvl_visit<<<grid_for_warps(cl, 152 * 16), LVL_WARPS * 32, 0, st>>>(
+                          s.lists + P.off[l], cl, W, nactive, Fl(l), s.V, s.full)));
+    rc.prof->k[K_LVL_VISIT].bytes += 12.0 * W * cl;
+    if (l + 1 >= s.Lcap) { *levels_exceeded = true; level_reset(rc, s, l); return MFBC_ERR_NO_CONVERGENCE; }
+    const int64_t off_n = P.off[l] + cl;
+    MFBC_CUDA_TRY(cudaMemsetAsync(&s.ctr->list_count[0], 0, sizeof(uint32_t), st), rc.err);
+    PROF(K_LVL_FWD, (k_lvl_fwd<<<grid_for_warps(g.items_in.count, big_grid), LVL_WARPS * 32, 0, st>>>(
+                        g.items_in.count, g.items_in.v, g.items_in.beg, g.rowptr_t, g.col_t, W, nb, s.full,
+                        s.V, Fl(l), Ml(l), Fl(l + 1), Ml(l + 1), s.sv, s.lists + off_n, &s.ctr->list_count[0],
+                        s.list_cap - off_n, &s.ctr->flags, B ? B + K_LVL_FWD : nullptr)));
+    MFBC_CUDA_TRY(cudaMemcpyAsync(rc.h_ctr, s.ctr->list_count, sizeof(uint32_t) * 5, cudaMemcpyDeviceToHost, st), rc.err);
+    MFBC_CUDA_TRY(cudaStreamSynchronize(st), rc.err);
+    rc.prof->drain();
+    if (rc.h_ctr[4] & 1u) { *levels_exceeded = true; level_reset(rc, s, l + 1); return MFBC_ERR_NO_CONVERGENCE; }
+    const uint32_t cn = rc.h_ctr[0];
+    P.off.push_back(off_n);
+    P.cnt.push_back(cn);
+    if (fwd_iters) (*fwd_iters)++;
+    if (cn == 0) { L = l; break; }
+  }
+  *levels_out = L;
+  if (!backward) return MFBC_OK;
+
+  // MFBr over levels L .. 1 (level L+1 is empty and all-zero)
+  for (int l = L; l >= 1; l--) {
+    PROF(K_LVL_BWD, (k_lvl_bwd<<<grid_for_warps(g.items_out.count, big_grid), LVL_WARPS * 32, 0, st>>>(
+                        g.items_out.count, g.items_out.v, g.items_out.beg, g.rowptr, g.col, g.items_out.hub_of,
+                        W, nb, Fl(l), Ml(l), Fl(l + 1), Ml(l + 1), s.sv, s.zacc, lambda,
+                        B ? B + K_LVL_BWD : nullptr)));
+    if (g.items_out.nhub)
+      PROF(K_LVL_HUB, (k_lvl_hub_final<<<grid_for_warps(g.items_out.nhub, 152 * 16), LVL_WARPS * 32, 0, st>>>(
+                          g.items_out.hubs, g.items_out.nhub, W, nb, Fl(l), Ml(l), s.sv, s.zacc, lambda,
+                          B ? B + K_LVL_HUB : nullptr)));
+    if (bwd_iters) (*bwd_iters)++;
+  }
+  return MFBC_OK;
+}
+
+void level_reset(RunCtx& rc, LevelState& s, int levels) {
+  const LevelPlan& P = tl_plan;
+  const int32_t n = rc.g->n;
+  for (int l = 0; l <= levels && l < (int)P.cnt.size(); l++) {
+    const uint32_t c = P.cnt[l];
+    if (c)
+      PROF(K_LVL_RESET, (k_lvl_clear_rows<<<grid_for_warps((uint64_t)c * s.W / 32 + 1, 152 * 8), 256, 0,
+                                            rc.stream>>>(s.lists + P.off[l], c, s.W,
+                                                         s.F + (size_t)l * n * s.W, s.V)));
+    cudaMemsetAsync(s.member + (size_t)l * s.mw, 0, sizeof(uint32_t) * s.mw, rc.stream);
+  }
+  // the level after the last one may hold stray bits only if the list overflowed
+  if (levels + 1 < s.Lcap)
+    cudaMemsetAsync(s.member + (size_t)(levels + 1) * s.mw, 0, sizeof(uint32_t) * s.mw, rc.stream);
+}
+
+mfbc_status level_output(RunCtx& rc, LevelState& s, int levels, int nactive, int32_t* dist_out,
+                         double* sigma_out) {
+  const LevelPlan& P = tl_plan;
+  const int32_t n = rc.g->n;
+  PROF(K_OUTPUT, {
+    fill_i32(dist_out, INF, (size_t)nactive * n, rc.stream);
+    if (sigma_out) cudaMemsetAsync(sigma_out, 0, sizeof(double) * (size_t)nactive * n, rc.stream);
+    for (int l = 0; l <= levels; l++) {
+      const uint32_t c = P.cnt[l];
+      if (!c) continue;
+      k_lvl_output<<<grid_for_warps(c, 152 * 16), LVL_WARPS * 32, 0, rc.stream>>>(
+          s.lists + P.off[l], c, l, s.W, s.nb, nactive, n, s.F + (size_t)l * n * s.W, s.sv, dist_out,
+          sigma_out);
+    }
+  });
+  return MFBC_OK;
+}
+
+}  // namespace mfbc
