@@ -99,7 +99,11 @@ static mfbc_status dev_alloc(DevGraph* g, T** p, size_t count, std::string* err)
     if (_s != MFBC_OK) return _s; \
   } while (0)
 
-static mfbc_status build_items(DevGraph* g, const std::vector<int64_t>& rp, ItemList* L,
+// empty_rows: give every row without arcs one empty item.  The MFBr gather
+// must visit DAG sinks too (their frontier value 1/sigma_bar is written by
+// that visit); in an undirected graph a vertex without arcs can only be a
+// source, so only directed graphs need it.
+static mfbc_status build_items(DevGraph* g, const std::vector<int64_t>& rp, ItemList* L, bool empty_rows,
                                cudaStream_t st, std::string* err) {
   const int32_t n = g->n;
   std::vector<int32_t> iv;
@@ -109,6 +113,7 @@ static mfbc_status build_items(DevGraph* g, const std::vector<int64_t>& rp, Item
     const int64_t deg = rp[v + 1] - rp[v];
     if (deg > CHUNK) { hub_of[v] = (int32_t)hubs.size(); hubs.push_back(v); }
     for (int64_t b = rp[v]; b < rp[v + 1]; b += CHUNK) { iv.push_back(v); ib.push_back(b); }
+    if (deg == 0 && empty_rows) { iv.push_back(v); ib.push_back(rp[v]); }
   }
   L->count = (int64_t)iv.size();
   L->nhub = (int32_t)hubs.size();
@@ -189,13 +194,13 @@ mfbc_status graph_build(int32_t n, int64_t nnz, const int64_t* h_rowptr, const i
     if (nnz) MFBC_CUDA_TRY(cudaMemcpyAsync(g->col_t, ct.data(), sizeof(int32_t) * ct.size(), cudaMemcpyHostToDevice, st), err);
     if (g->w && nnz) MFBC_CUDA_TRY(cudaMemcpyAsync(g->w_t, wtv.data(), sizeof(int32_t) * wtv.size(), cudaMemcpyHostToDevice, st), err);
     MFBC_CUDA_TRY(cudaStreamSynchronize(st), err);
-    TRY(build_items(g, rpt, &g->items_in, st, err));
-    TRY(build_items(g, rp, &g->items_out, st, err));
+    TRY(build_items(g, rpt, &g->items_in, false, st, err));
+    TRY(build_items(g, rp, &g->items_out, true, st, err));
   } else {
     g->rowptr_t = g->rowptr;
     g->col_t = g->col;
     g->w_t = g->w;
-    TRY(build_items(g, rp, &g->items_in, st, err));
+    TRY(build_items(g, rp, &g->items_in, false, st, err));
     g->items_out = g->items_in;
   }
   return MFBC_OK;
