@@ -158,7 +158,9 @@ static size_t plan_bytes(const DevGraph& g, int path, int nb, int32_t nsrc, int 
   p->nb = nb;
   if (path == MFBC_PATH_LEVEL) {
     level_caps(g, nb, &p->Lcap, &p->list_cap);
-    p->state_bytes = level_bytes(g, nb, p->Lcap, p->list_cap);
+    // room for the general kernels at n_b = 32 too: the fallback used when
+    // a batch is deeper than the level capacity runs in the same scratch
+    p->state_bytes = std::max(level_bytes(g, nb, p->Lcap, p->list_cap), general_bytes(g.n, 32));
   } else {
     p->state_bytes = general_bytes(g.n, nb);
   }
