@@ -106,13 +106,19 @@ static mfbc_status dev_alloc(DevGraph* g, T** p, size_t count, std::string* err)
 static mfbc_status build_items(DevGraph* g, const std::vector<int64_t>& rp, ItemList* L, bool empty_rows,
                                cudaStream_t st, std::string* err) {
   const int32_t n = g->n;
+  if (rp[n] >= (1ll << 40)) { *err = "graphs with 2^40 or more arcs are not supported"; return MFBC_ERR_INVALID; }
   std::vector<int32_t> iv;
   std::vector<int64_t> ib;
   std::vector<int32_t> hub_of((size_t)n, -1), hubs;
   for (int32_t v = 0; v < n; v++) {
     const int64_t deg = rp[v + 1] - rp[v];
     if (deg > CHUNK) { hub_of[v] = (int32_t)hubs.size(); hubs.push_back(v); }
-    for (int64_t b = rp[v]; b < rp[v + 1]; b += CHUNK) { iv.push_back(v); ib.push_back(b); }
+    // item metadata: first arc (bits 0..39), arc count (40..45), multi-item row (46)
+    const int64_t multi = deg > CHUNK ? (1ll << 46) : 0;
+    for (int64_t b = rp[v]; b < rp[v + 1]; b += CHUNK) {
+      iv.push_back(v);
+      ib.push_back(b | (std::min<int64_t>(CHUNK, rp[v + 1] - b) << 40) | multi);
+    }
     if (deg == 0 && empty_rows) { iv.push_back(v); ib.push_back(rp[v]); }
   }
   L->count = (int64_t)iv.size();

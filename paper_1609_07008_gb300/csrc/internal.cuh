@@ -24,10 +24,10 @@ constexpr int WARP = 32;
 constexpr int CHUNK = 32;          // neighbours per work item of the level kernels
 
 // ------------------------------------------------------------------ graph
-struct ItemList {                  // work items (v, beg): arcs [beg, min(beg+CHUNK, rowptr[v+1]))
+struct ItemList {                  // work items of <= CHUNK arcs of one row
   int64_t count = 0;
-  int32_t* v = nullptr;
-  int64_t* beg = nullptr;
+  int32_t* v = nullptr;            // row (vertex) of the item
+  int64_t* beg = nullptr;          // first arc | arc count << 40 | multi-item row << 46
   int32_t nhub = 0;                // vertices whose row spans more than one item
   int32_t* hub_of = nullptr;       // [n] hub index or -1
   int32_t* hubs = nullptr;         // [nhub] vertex ids

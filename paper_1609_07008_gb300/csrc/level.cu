@@ -121,99 +121,162 @@ __global__ void k_lvl_visit(const int32_t* __restrict__ list, uint32_t count, in
   }
 }
 
-struct LvlSmem {
-  int32_t su[LVL_WARPS][32];                 // member neighbour ids of the item
-  uint32_t sF[LVL_WARPS][32][32];            // their (masked) frontier words
+// Per-warp shared memory of the gather kernels.
+struct WarpSmem {
+  int32_t su[32];                            // member neighbour ids of the item
+  uint32_t sF[32][33];                       // member q's masked frontier word j (padded: no bank conflicts)
+  uint16_t pr[1024];                         // (member, word) pairs with a non-zero mask, word-major
 };
+constexpr size_t LVL_SMEM = sizeof(WarpSmem) * LVL_WARPS;
+constexpr int GATHER_U = 8;                  // independent 256-byte loads in flight per warp
 
-// MFBF product of level l (see file comment).
-__global__ void __launch_bounds__(LVL_WARPS * 32) k_lvl_fwd(
-    int64_t nitems, const int32_t* __restrict__ item_v, const int64_t* __restrict__ item_beg,
-    const int64_t* __restrict__ rowptr_t, const int32_t* __restrict__ col_t, int W, int nb,
-    const uint32_t* __restrict__ full, const uint32_t* __restrict__ V, const uint32_t* __restrict__ Fl,
-    const uint32_t* __restrict__ mem_l, uint32_t* Fn, uint32_t* mem_n, double* sv, int32_t* list_n,
-    uint32_t* count_n, int64_t cap_n, uint32_t* flags, unsigned long long* bytes) {
-  __shared__ LvlSmem sm;
+// Item metadata: first arc (bits 0..39), arc count (bits 40..45), multi-item row (bit 46).
+__device__ __forceinline__ int64_t meta_beg(int64_t m) { return m & ((1ll << 40) - 1); }
+__device__ __forceinline__ int meta_len(int64_t m) { return (int)((m >> 40) & 63); }
+__device__ __forceinline__ bool meta_multi(int64_t m) { return (m >> 46) & 1; }
+
+// Word-major list of the (member q, word j) pairs whose mask sF[q][j] is non-zero.
+__device__ __forceinline__ int build_pairs(WarpSmem& w, int nm, int W, uint32_t* haspair) {
   const unsigned lane = lane_id();
-  const int wi = threadIdx.x >> 5;
-  const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-  unsigned long long nbytes = 0, ngather = 0;
-  for (uint64_t it = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; it < (uint64_t)nitems;
-       it += nw) {
-    const int32_t v = item_v[it];
-    if (test_bit(full, v)) continue;
-    const int64_t beg = item_beg[it];
-    const int64_t rend = rowptr_t[v + 1];
-    const int64_t end = min(beg + CHUNK, rend);
-    const bool multi = (rend - rowptr_t[v]) > CHUNK;
-    const int64_t k = beg + lane;
-    const int32_t u = k < end ? __ldg(&col_t[k]) : -1;
-    const bool isMem = u >= 0 && test_bit(mem_l, u);
-    const uint32_t mm = __ballot_sync(0xffffffffu, isMem);
-    if (bytes) nbytes += 4ull * (end - beg) + 16ull;
-    if (!mm) continue;
-    const int nm = __popc(mm);
-    if (isMem) sm.su[wi][__popc(mm & ((1u << lane) - 1u))] = u;
-    __syncwarp();
-    const uint32_t Vv = (int)lane < W ? V[(size_t)v * W + lane] : 0xffffffffu;
-    uint32_t cand = 0;
-    for (int q = 0; q < nm; q++) {
-      const int32_t uq = sm.su[wi][q];
-      const uint32_t f = (int)lane < W ? __ldg(&Fl[(size_t)uq * W + lane]) : 0u;
-      const uint32_t mk = f & ~Vv;
-      sm.sF[wi][q][lane] = mk;
-      cand |= mk;
-    }
-    __syncwarp();
-    uint32_t nz = __ballot_sync(0xffffffffu, cand != 0u);
-    if (bytes) nbytes += 4ull * W * (nm + 1);
-    const size_t vrow = (size_t)v * nb;
-    while (nz) {
-      const int j = __ffs(nz) - 1;
-      nz &= nz - 1;
-      const uint32_t cj = __shfl_sync(0xffffffffu, cand, j);
-      const int col = j * 32 + lane;
-      double acc = 0.0;
-      int q = 0;
-      for (; q + 4 <= nm; q += 4) {
-        double x0 = 0.0, x1 = 0.0, x2 = 0.0, x3 = 0.0;
-        if ((sm.sF[wi][q + 0][j] >> lane) & 1u) x0 = __ldg(&sv[(size_t)sm.su[wi][q + 0] * nb + col]);
-        if ((sm.sF[wi][q + 1][j] >> lane) & 1u) x1 = __ldg(&sv[(size_t)sm.su[wi][q + 1] * nb + col]);
-        if ((sm.sF[wi][q + 2][j] >> lane) & 1u) x2 = __ldg(&sv[(size_t)sm.su[wi][q + 2] * nb + col]);
-        if ((sm.sF[wi][q + 3][j] >> lane) & 1u) x3 = __ldg(&sv[(size_t)sm.su[wi][q + 3] * nb + col]);
-        acc += x0; acc += x1; acc += x2; acc += x3;
-        if (bytes) ngather += ((sm.sF[wi][q][j] >> lane) & 1u) + ((sm.sF[wi][q + 1][j] >> lane) & 1u) +
-                              ((sm.sF[wi][q + 2][j] >> lane) & 1u) + ((sm.sF[wi][q + 3][j] >> lane) & 1u);
-      }
-      for (; q < nm; q++) {
-        if ((sm.sF[wi][q][j] >> lane) & 1u) {
-          acc += __ldg(&sv[(size_t)sm.su[wi][q] * nb + col]);
-          if (bytes) ngather++;
+  const uint32_t lt = (1u << lane) - 1u;
+  int P = 0;
+  uint32_t hp = 0;
+  for (int j = 0; j < W; j++) {
+    const bool nz = ((int)lane < nm) && w.sF[lane][j] != 0u;
+    const uint32_t mk = __ballot_sync(0xffffffffu, nz);
+    if (nz) w.pr[P + __popc(mk & lt)] = (uint16_t)(lane | (j << 5));
+    P += __popc(mk);
+    if (mk) hp |= 1u << j;
+  }
+  __syncwarp();
+  *haspair = hp;
+  return P;
+}
+
+// Sum, per word, the gathered values of the pairs; FLUSH(j, acc) is called once
+// per word with pairs, in word order, by the whole warp (lane = column).
+template <class Flush>
+__device__ __forceinline__ void gather_pairs(const WarpSmem& w, int P, const double* sv, int nb,
+                                             unsigned long long* ngather, Flush flush) {
+  const unsigned lane = lane_id();
+  double acc = 0.0;
+  int curj = -1;
+  for (int p0 = 0; p0 < P; p0 += GATHER_U) {
+    double x[GATHER_U];
+    int jj[GATHER_U];
+#pragma unroll
+    for (int t = 0; t < GATHER_U; t++) {
+      x[t] = 0.0;
+      jj[t] = -1;
+      const int p = p0 + t;
+      if (p < P) {
+        const uint32_t pr = w.pr[p];
+        const int q = pr & 31, j = pr >> 5;
+        jj[t] = j;
+        if ((w.sF[q][j] >> lane) & 1u) {
+          x[t] = __ldg(&sv[(size_t)w.su[q] * nb + j * 32 + lane]);
+          if (ngather) (*ngather)++;
         }
       }
-      if ((cj >> lane) & 1u) {
-        // a multiplicity at or above 2^53 may have been rounded (flags bit 1)
-        double tot = acc;
-        if (multi) tot += atomicAdd(&sv[vrow + col], acc);
-        else sv[vrow + col] = acc;
-        if (tot >= 9007199254740992.0) atomicOr(flags, 2u);
-        if (bytes) ngather++;                       // the written multiplicity
-      }
-      if (bytes) nbytes += 4ull;
     }
-    if ((int)lane < W && cand) {
-      if (multi) atomicOr(&Fn[(size_t)v * W + lane], cand);
-      else Fn[(size_t)v * W + lane] = cand;
-    }
-    if (__any_sync(0xffffffffu, cand != 0u) && lane == 0) {
-      const uint32_t bit = 1u << (v & 31);
-      if (!(atomicOr(&mem_n[v >> 5], bit) & bit)) {
-        const uint32_t pos = atomicAdd(count_n, 1u);
-        if ((int64_t)pos < cap_n) list_n[pos] = v;
-        else atomicOr(flags, 1u);
+#pragma unroll
+    for (int t = 0; t < GATHER_U; t++) {
+      if (jj[t] >= 0) {
+        if (jj[t] != curj) {
+          if (curj >= 0) flush(curj, acc);
+          acc = 0.0;
+          curj = jj[t];
+        }
+        acc += x[t];
       }
     }
-    __syncwarp();
+  }
+  if (curj >= 0) flush(curj, acc);
+}
+
+// MFBF product of level l (see file comment).
+__global__ void __launch_bounds__(LVL_WARPS * 32, 4) k_lvl_fwd(
+    int64_t nitems, const int32_t* __restrict__ item_v, const int64_t* __restrict__ item_meta,
+    const int32_t* __restrict__ col_t, int W, int nb, const uint32_t* __restrict__ full,
+    const uint32_t* __restrict__ V, const uint32_t* __restrict__ Fl, const uint32_t* __restrict__ mem_l,
+    uint32_t* Fn, uint32_t* mem_n, double* sv, int32_t* list_n, uint32_t* count_n, int64_t cap_n,
+    uint32_t* flags, unsigned long long* bytes) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  WarpSmem& sm = reinterpret_cast<WarpSmem*>(smem_raw)[threadIdx.x >> 5];
+  const unsigned lane = lane_id();
+  const uint32_t lt = (1u << lane) - 1u;
+  const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  unsigned long long nbytes = 0, ngather = 0;
+  unsigned long long* pg = bytes ? &ngather : nullptr;
+  for (uint64_t base = (((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; base < (uint64_t)nitems;
+       base += nw * 32) {
+    // lane-parallel precheck of 32 items: skip rows already reached by every column
+    const uint64_t myit = base + lane;
+    int32_t myv = 0;
+    int64_t mymeta = 0;
+    bool act = false;
+    if (myit < (uint64_t)nitems) {
+      myv = item_v[myit];
+      mymeta = item_meta[myit];
+      act = !test_bit(full, myv);
+    }
+    uint32_t am = __ballot_sync(0xffffffffu, act);
+    while (am) {
+      const int t = __ffs(am) - 1;
+      am &= am - 1;
+      const int32_t v = __shfl_sync(0xffffffffu, myv, t);
+      const int64_t meta = __shfl_sync(0xffffffffu, mymeta, t);
+      const int64_t beg = meta_beg(meta);
+      const int len = meta_len(meta);
+      const bool multi = meta_multi(meta);
+      const uint32_t Vv = (int)lane < W ? V[(size_t)v * W + lane] : 0xffffffffu;
+      const int32_t u = (int)lane < len ? __ldg(&col_t[beg + lane]) : -1;
+      const bool isMem = u >= 0 && test_bit(mem_l, u);
+      const uint32_t mm = __ballot_sync(0xffffffffu, isMem);
+      if (bytes) nbytes += 4ull * len + 12ull;
+      if (!mm) continue;
+      const int nm = __popc(mm);
+      if (isMem) sm.su[__popc(mm & lt)] = u;
+      __syncwarp();
+      uint32_t cand = 0;
+#pragma unroll 4
+      for (int q = 0; q < nm; q++) {
+        const uint32_t f = (int)lane < W ? __ldg(&Fl[(size_t)sm.su[q] * W + lane]) : 0u;
+        const uint32_t mk = f & ~Vv;
+        sm.sF[q][lane] = mk;
+        cand |= mk;
+      }
+      __syncwarp();
+      if (bytes) nbytes += 4ull * W * (nm + 1);
+      if (!__any_sync(0xffffffffu, cand != 0u)) continue;
+      uint32_t haspair;
+      const int P = build_pairs(sm, nm, W, &haspair);
+      const size_t vrow = (size_t)v * nb;
+      gather_pairs(sm, P, sv, nb, pg, [&](int j, double acc) {
+        const uint32_t cj = __shfl_sync(0xffffffffu, cand, j);
+        if ((cj >> lane) & 1u) {
+          // a multiplicity at or above 2^53 may have been rounded (flags bit 1)
+          double tot = acc;
+          if (multi) tot += atomicAdd(&sv[vrow + j * 32 + lane], acc);
+          else sv[vrow + j * 32 + lane] = acc;
+          if (tot >= 9007199254740992.0) atomicOr(flags, 2u);
+          if (bytes) ngather++;
+        }
+      });
+      if ((int)lane < W && cand) {
+        if (multi) atomicOr(&Fn[(size_t)v * W + lane], cand);
+        else Fn[(size_t)v * W + lane] = cand;
+      }
+      if (lane == 0) {
+        const uint32_t bit = 1u << (v & 31);
+        if (!(atomicOr(&mem_n[v >> 5], bit) & bit)) {
+          const uint32_t pos = atomicAdd(count_n, 1u);
+          if ((int64_t)pos < cap_n) list_n[pos] = v;
+          else atomicOr(flags, 1u);
+        }
+      }
+      __syncwarp();
+    }
   }
   if (bytes) {
     for (int o = 16; o; o >>= 1) ngather += __shfl_xor_sync(0xffffffffu, ngather, o);
@@ -222,87 +285,90 @@ __global__ void __launch_bounds__(LVL_WARPS * 32) k_lvl_fwd(
 }
 
 // MFBr gather of level l >= 1 (see file comment).
-__global__ void __launch_bounds__(LVL_WARPS * 32) k_lvl_bwd(
-    int64_t nitems, const int32_t* __restrict__ item_v, const int64_t* __restrict__ item_beg,
-    const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col, const int32_t* __restrict__ hub_of,
-    int W, int nb, const uint32_t* __restrict__ Fl, const uint32_t* __restrict__ mem_l,
-    const uint32_t* __restrict__ Fn, const uint32_t* __restrict__ mem_n, double* sv, double* zacc,
-    double* lambda, unsigned long long* bytes) {
-  __shared__ LvlSmem sm;
+__global__ void __launch_bounds__(LVL_WARPS * 32, 4) k_lvl_bwd(
+    int64_t nitems, const int32_t* __restrict__ item_v, const int64_t* __restrict__ item_meta,
+    const int32_t* __restrict__ col, const int32_t* __restrict__ hub_of, int W, int nb,
+    const uint32_t* __restrict__ Fl, const uint32_t* __restrict__ mem_l, const uint32_t* __restrict__ Fn,
+    const uint32_t* __restrict__ mem_n, double* sv, double* zacc, double* lambda,
+    unsigned long long* bytes) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  WarpSmem& sm = reinterpret_cast<WarpSmem*>(smem_raw)[threadIdx.x >> 5];
   const unsigned lane = lane_id();
-  const int wi = threadIdx.x >> 5;
+  const uint32_t lt = (1u << lane) - 1u;
   const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
   unsigned long long nbytes = 0, ngather = 0;
-  for (uint64_t it = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; it < (uint64_t)nitems;
-       it += nw) {
-    const int32_t v = item_v[it];
-    if (!test_bit(mem_l, v)) continue;
-    const int64_t beg = item_beg[it];
-    const int64_t rend = rowptr[v + 1];
-    const int64_t end = min(beg + CHUNK, rend);
-    const bool multi = (rend - rowptr[v]) > CHUNK;
-    const int64_t k = beg + lane;
-    const int32_t u = k < end ? __ldg(&col[k]) : -1;
-    const bool isMem = u >= 0 && test_bit(mem_n, u);
-    const uint32_t mm = __ballot_sync(0xffffffffu, isMem);
-    if (bytes) nbytes += 4ull * (end - beg) + 16ull;
-    if (multi && !mm) continue;                      // nothing to add to the hub accumulator
-    const int nm = __popc(mm);
-    if (isMem) sm.su[wi][__popc(mm & ((1u << lane) - 1u))] = u;
-    __syncwarp();
-    const uint32_t Fv = (int)lane < W ? __ldg(&Fl[(size_t)v * W + lane]) : 0u;
-    for (int q = 0; q < nm; q++) {
-      const int32_t uq = sm.su[wi][q];
-      const uint32_t f = (int)lane < W ? __ldg(&Fn[(size_t)uq * W + lane]) : 0u;
-      sm.sF[wi][q][lane] = f & Fv;
+  unsigned long long* pg = bytes ? &ngather : nullptr;
+  for (uint64_t base = (((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; base < (uint64_t)nitems;
+       base += nw * 32) {
+    // lane-parallel precheck of 32 items: only rows with a source at level l
+    const uint64_t myit = base + lane;
+    int32_t myv = 0;
+    int64_t mymeta = 0;
+    bool act = false;
+    if (myit < (uint64_t)nitems) {
+      myv = item_v[myit];
+      mymeta = item_meta[myit];
+      act = test_bit(mem_l, myv);
     }
-    __syncwarp();
-    uint32_t nz = __ballot_sync(0xffffffffu, Fv != 0u);
-    if (bytes) nbytes += 4ull * W * (nm + 1);
-    const size_t vrow = (size_t)v * nb;
-    const int32_t hub = multi ? hub_of[v] : -1;
-    double lam = 0.0;
-    while (nz) {
-      const int j = __ffs(nz) - 1;
-      nz &= nz - 1;
-      const uint32_t fj = __shfl_sync(0xffffffffu, Fv, j);
-      const int col_j = j * 32 + lane;
-      double acc = 0.0;
-      int q = 0;
-      for (; q + 4 <= nm; q += 4) {
-        double x0 = 0.0, x1 = 0.0, x2 = 0.0, x3 = 0.0;
-        if ((sm.sF[wi][q + 0][j] >> lane) & 1u) x0 = __ldg(&sv[(size_t)sm.su[wi][q + 0] * nb + col_j]);
-        if ((sm.sF[wi][q + 1][j] >> lane) & 1u) x1 = __ldg(&sv[(size_t)sm.su[wi][q + 1] * nb + col_j]);
-        if ((sm.sF[wi][q + 2][j] >> lane) & 1u) x2 = __ldg(&sv[(size_t)sm.su[wi][q + 2] * nb + col_j]);
-        if ((sm.sF[wi][q + 3][j] >> lane) & 1u) x3 = __ldg(&sv[(size_t)sm.su[wi][q + 3] * nb + col_j]);
-        acc += x0; acc += x1; acc += x2; acc += x3;
-        if (bytes) ngather += ((sm.sF[wi][q][j] >> lane) & 1u) + ((sm.sF[wi][q + 1][j] >> lane) & 1u) +
-                              ((sm.sF[wi][q + 2][j] >> lane) & 1u) + ((sm.sF[wi][q + 3][j] >> lane) & 1u);
+    uint32_t am = __ballot_sync(0xffffffffu, act);
+    while (am) {
+      const int t = __ffs(am) - 1;
+      am &= am - 1;
+      const int32_t v = __shfl_sync(0xffffffffu, myv, t);
+      const int64_t meta = __shfl_sync(0xffffffffu, mymeta, t);
+      const int64_t beg = meta_beg(meta);
+      const int len = meta_len(meta);
+      const bool multi = meta_multi(meta);
+      const uint32_t Fv = (int)lane < W ? __ldg(&Fl[(size_t)v * W + lane]) : 0u;
+      const int32_t u = (int)lane < len ? __ldg(&col[beg + lane]) : -1;
+      const bool isMem = u >= 0 && test_bit(mem_n, u);
+      const uint32_t mm = __ballot_sync(0xffffffffu, isMem);
+      if (bytes) nbytes += 4ull * len + 12ull;
+      if (multi && !mm) continue;                    // nothing to add to the hub accumulator
+      const int nm = __popc(mm);
+      if (isMem) sm.su[__popc(mm & lt)] = u;
+      __syncwarp();
+#pragma unroll 4
+      for (int q = 0; q < nm; q++) {
+        const uint32_t f = (int)lane < W ? __ldg(&Fn[(size_t)sm.su[q] * W + lane]) : 0u;
+        sm.sF[q][lane] = f & Fv;
       }
-      for (; q < nm; q++) {
-        if ((sm.sF[wi][q][j] >> lane) & 1u) {
-          acc += __ldg(&sv[(size_t)sm.su[wi][q] * nb + col_j]);
-          if (bytes) ngather++;
+      __syncwarp();
+      if (bytes) nbytes += 4ull * W * (nm + 1);
+      uint32_t haspair;
+      const int P = build_pairs(sm, nm, W, &haspair);
+      const size_t vrow = (size_t)v * nb;
+      const int32_t hub = multi ? hub_of[v] : -1;
+      double lam = 0.0;
+      auto finish = [&](int j, double acc) {
+        const uint32_t fj = __shfl_sync(0xffffffffu, Fv, j);
+        if ((fj >> lane) & 1u) {
+          if (multi) {
+            atomicAdd(&zacc[(size_t)hub * nb + j * 32 + lane], acc);
+            if (bytes) ngather++;
+          } else {
+            const double sg = sv[vrow + j * 32 + lane];
+            lam += acc * sg;
+            sv[vrow + j * 32 + lane] = acc + 1.0 / sg;
+            if (bytes) ngather += 2;
+          }
         }
-      }
-      if ((fj >> lane) & 1u) {
-        if (multi) {
-          atomicAdd(&zacc[(size_t)hub * nb + col_j], acc);
-          if (bytes) ngather++;
-        } else {
-          const double sg = sv[vrow + col_j];
-          lam += acc * sg;
-          sv[vrow + col_j] = acc + 1.0 / sg;
-          if (bytes) ngather += 2;
+      };
+      gather_pairs(sm, P, sv, nb, pg, finish);
+      if (!multi) {
+        // columns of level l whose word had no successor pair: zeta = 0
+        uint32_t rest = __ballot_sync(0xffffffffu, Fv != 0u) & ~haspair;
+        while (rest) {
+          const int j = __ffs(rest) - 1;
+          rest &= rest - 1;
+          finish(j, 0.0);
         }
+        for (int o = 16; o; o >>= 1) lam += __shfl_xor_sync(0xffffffffu, lam, o);
+        if (lane == 0) lambda[v] += lam;
+        if (bytes) nbytes += 16ull;
       }
+      __syncwarp();
     }
-    if (!multi) {
-      for (int o = 16; o; o >>= 1) lam += __shfl_xor_sync(0xffffffffu, lam, o);
-      if (lane == 0) lambda[v] += lam;
-      if (bytes) nbytes += 16ull;
-    }
-    __syncwarp();
   }
   if (bytes) {
     for (int o = 16; o; o >>= 1) ngather += __shfl_xor_sync(0xffffffffu, ngather, o);
@@ -380,6 +446,22 @@ __global__ void k_lvl_output(const int32_t* __restrict__ list, uint32_t count, i
     rc.prof->end(id);             \
   } while (0)
 
+// one warp per 32 items (the precheck group)
+static inline unsigned grid_for_items(int64_t items, unsigned cap) {
+  uint64_t warps = ((uint64_t)items + 31) / 32;
+  uint64_t b = (warps + LVL_WARPS - 1) / LVL_WARPS;
+  if (b < 1) b = 1;
+  return (unsigned)(b > cap ? cap : b);
+}
+
+static void set_smem_attrs() {
+  static bool done = false;
+  if (done) return;
+  cudaFuncSetAttribute(k_lvl_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LVL_SMEM);
+  cudaFuncSetAttribute(k_lvl_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LVL_SMEM);
+  done = true;
+}
+
 static inline unsigned grid_for_warps(uint64_t warps, unsigned cap) {
   uint64_t b = (warps + LVL_WARPS - 1) / LVL_WARPS;
   if (b < 1) b = 1;
@@ -403,7 +485,8 @@ mfbc_status level_batch(RunCtx& rc, LevelState& s, const int32_t* d_src_batch, i
   *levels_exceeded = false;
   *levels_out = -1;
   if (n == 0) return MFBC_OK;
-  const unsigned big_grid = 152u * 6u;       // resident blocks of the level kernels
+  const unsigned big_grid = 152u * 4u;       // resident blocks of the level gather kernels
+  set_smem_attrs();
 
   fill_i32(s.src, -1, (size_t)nb, st);
   if (nactive)
@@ -432,8 +515,8 @@ mfbc_status level_batch(RunCtx& rc, LevelState& s, const int32_t* d_src_batch, i
     if (l + 1 >= s.Lcap) { *levels_exceeded = true; level_reset(rc, s, l); return MFBC_ERR_NO_CONVERGENCE; }
     const int64_t off_n = P.off[l] + cl;
     MFBC_CUDA_TRY(cudaMemsetAsync(&s.ctr->list_count[0], 0, sizeof(uint32_t), st), rc.err);
-    PROF(K_LVL_FWD, (k_lvl_fwd<<<grid_for_warps(g.items_in.count, big_grid), LVL_WARPS * 32, 0, st>>>(
-                        g.items_in.count, g.items_in.v, g.items_in.beg, g.rowptr_t, g.col_t, W, nb, s.full,
+    PROF(K_LVL_FWD, (k_lvl_fwd<<<grid_for_items(g.items_in.count, big_grid), LVL_WARPS * 32, LVL_SMEM, st>>>(
+                        g.items_in.count, g.items_in.v, g.items_in.beg, g.col_t, W, nb, s.full,
                         s.V, Fl(l), Ml(l), Fl(l + 1), Ml(l + 1), s.sv, s.lists + off_n, &s.ctr->list_count[0],
                         s.list_cap - off_n, &s.ctr->flags, B ? B + K_LVL_FWD : nullptr)));
     MFBC_CUDA_TRY(cudaMemcpyAsync(rc.h_ctr, s.ctr->list_count, sizeof(uint32_t) * 5, cudaMemcpyDeviceToHost, st), rc.err);
@@ -451,8 +534,8 @@ mfbc_status level_batch(RunCtx& rc, LevelState& s, const int32_t* d_src_batch, i
 
   // MFBr over levels L .. 1 (level L+1 is empty and all-zero)
   for (int l = L; l >= 1; l--) {
-    PROF(K_LVL_BWD, (k_lvl_bwd<<<grid_for_warps(g.items_out.count, big_grid), LVL_WARPS * 32, 0, st>>>(
-                        g.items_out.count, g.items_out.v, g.items_out.beg, g.rowptr, g.col, g.items_out.hub_of,
+    PROF(K_LVL_BWD, (k_lvl_bwd<<<grid_for_items(g.items_out.count, big_grid), LVL_WARPS * 32, LVL_SMEM, st>>>(
+                        g.items_out.count, g.items_out.v, g.items_out.beg, g.col, g.items_out.hub_of,
                         W, nb, Fl(l), Ml(l), Fl(l + 1), Ml(l + 1), s.sv, s.zacc, lambda,
                         B ? B + K_LVL_BWD : nullptr)));
     if (g.items_out.nhub)
