@@ -44,6 +44,8 @@ sys.path.insert(0, ROOT)
 WORKLOADS = {
     "rmat22": dict(kind="rmat", scale=22, ef=16, nsrc=16384,
                    desc="R-MAT scale 22, edge factor 16, undirected, unweighted, 16384 sampled sources"),
+    "rmat20": dict(kind="rmat", scale=20, ef=16, nsrc=4096,
+                   desc="R-MAT scale 20, edge factor 16, undirected, unweighted, 4096 sampled sources (profiling size)"),
     "er20k32": dict(kind="er", n=1 << 20, k=32, nsrc=16384,
                     desc="Erdos-Renyi n=2^20, k=32, undirected, unweighted, 16384 sampled sources"),
     "rmat16w": dict(kind="rmat16w", nsrc=4096,
@@ -281,7 +283,7 @@ def main():
         tt = torch.tensor([te], dtype=torch.float64, device=dev)
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         te = float(tt.item())
-    e2e = args.e2e_steps * len(srcs) * g.m * world / te / 1e9
+    e2e = args.e2e_steps * len(srcs) * g.m * world / te / 1e9 if args.e2e_steps else None
 
     if rank == 0:
         peak, peak_kind = load_peaks()
