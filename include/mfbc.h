@@ -163,6 +163,31 @@ mfbc_status mfbc_sssp_batch_device(const mfbc_graph* g, const int32_t* sources, 
 mfbc_status mfbc_workspace_size(const mfbc_graph* g, int32_t nsrc, int32_t mode,
                                 const mfbc_options* opt, uint64_t* bytes);
 
+/* Allocation-free betweenness centrality.  The paper has no counterpart:
+ * this entry point exists for callers that must not allocate GPU memory at
+ * call time -- a serving process whose device memory is fully partitioned by
+ * its own pool, code inside an allocator callback or memory-pressure handler,
+ * a plug-in whose host framework owns all device memory, or a latency-bound
+ * loop that cannot absorb cudaMalloc's implicit synchronisation.
+ * It computes the same lambda as mfbc_bc_device (DEVICE sources int32[nsrc],
+ * DEVICE lambda_out double[n], overwritten; stream = cudaStream_t or NULL)
+ * with the general kernels at n_b = 32, keeping all scratch in one file-scope
+ * __device__ array of MFBC_STATIC_SCRATCH_BYTES that every GPU loading the
+ * library holds until exit.  It calls no cudaMalloc, cudaFree or allocating
+ * library routine.  The array's device address is looked up once per device
+ * (cudaGetSymbolAddress, device current) by the first call on that device, so
+ * make that first call before any stream capture.  Graphs with more than
+ * mfbc_static_max_vertices() vertices are rejected with MFBC_ERR_INVALID.
+ * All calls share the array and it keeps the last call's contents (each call
+ * clears what must start at zero); calls that overlap on the GPU race.  The
+ * call returns once lambda_out is complete on the stream. */
+#define MFBC_STATIC_SCRATCH_BYTES (32u << 20)
+mfbc_status mfbc_bc_static(const mfbc_graph* g, const int32_t* sources, int32_t nsrc,
+                           double* lambda_out, void* stream);
+
+/* Largest vertex count mfbc_bc_static accepts. */
+uint64_t mfbc_static_max_vertices(void);
+
 const char* mfbc_status_string(mfbc_status s);
 
 /* Detail of the last error on the calling thread ("" if none). */

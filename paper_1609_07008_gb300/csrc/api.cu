@@ -483,3 +483,12 @@ extern "C" mfbc_status mfbc_sssp_batch_device(const mfbc_graph* g, const int32_t
                                               int32_t* dist_out, double* sigma_out, const mfbc_options* opt) {
   return entry(g, sources, nsrc, 1, nullptr, dist_out, sigma_out, opt, false);
 }
+
+// Accessors for entry points defined in other translation units.
+namespace mfbc {
+const DevGraph* graph_device_view(const mfbc_graph* G) { return G ? &G->g : nullptr; }
+uint32_t* graph_counter_mirror(const mfbc_graph* G) { return G ? G->h_ctr : nullptr; }
+void graph_lock(const mfbc_graph* G) { const_cast<mfbc_graph*>(G)->mu.lock(); }
+void graph_unlock(const mfbc_graph* G) { const_cast<mfbc_graph*>(G)->mu.unlock(); }
+void set_last_error(const std::string& msg) { t_err = msg; }
+}  // namespace mfbc

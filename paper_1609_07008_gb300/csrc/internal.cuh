@@ -172,6 +172,13 @@ mfbc_status graph_build(int32_t n, int64_t nnz, const int64_t* h_rowptr, const i
                         std::string* err);
 void graph_free(DevGraph* g);
 
+// Graph-handle accessors (api.cu).
+const DevGraph* graph_device_view(const mfbc_graph* G);
+uint32_t* graph_counter_mirror(const mfbc_graph* G);
+void graph_lock(const mfbc_graph* G);
+void graph_unlock(const mfbc_graph* G);
+void set_last_error(const std::string& msg);
+
 // Small device utilities (util.cu).
 void fill_i32(int32_t* p, int32_t v, size_t count, cudaStream_t st);
 void fill_f64(double* p, double v, size_t count, cudaStream_t st);
