@@ -100,6 +100,7 @@ typedef struct {
 
 /* mfbc_options.flags */
 #define MFBC_OPT_COUNT_BYTES 1u  /* with profile: count algorithmic bytes on the device (slower) */
+#define MFBC_OPT_KEEP_ORDER  2u  /* mfbc_bc*: batch the sources in the given order (see below) */
 
 /* Build a device-resident graph from HOST CSR arrays (Sec. 2.1: A(i,j) = w(i,j)
  * for (i,j) in E; the paper's Tensor::write of the input, Sec. 6.1).
@@ -134,7 +135,12 @@ mfbc_status mfbc_graph_info(const mfbc_graph* g, int32_t* n, int64_t* nnz, uint3
  * every vertex listed once this is exact BC, otherwise the unscaled sum over
  * the sample.  HOST pointers: sources int32[nsrc], lambda_out double[n].
  * Sources are processed in batches of options->n_b (Algorithm 3's loop); a
- * short last batch is padded with inactive columns (Theorem 1's padding). */
+ * short last batch is padded with inactive columns (Theorem 1's padding).
+ * Unless MFBC_OPT_KEEP_ORDER is set, the unit-weight kernels on an
+ * undirected graph first group sources of similar depth into the same batch
+ * (sorted by their BFS distance to the two highest-degree vertices), which
+ * makes each batch's frontier masks denser; lambda is a sum over sources, so
+ * only the floating-point summation order changes. */
 mfbc_status mfbc_bc(const mfbc_graph* g, const int32_t* sources, int32_t nsrc,
                     double* lambda_out, const mfbc_options* opt);
 

@@ -32,6 +32,7 @@ MFBC_UNDIRECTED = 1
 MFBC_WARN_SIGMA_INEXACT = 1
 PATH_AUTO, PATH_GENERAL, PATH_LEVEL = 0, 1, 2
 MFBC_OPT_COUNT_BYTES = 1
+MFBC_OPT_KEEP_ORDER = 2
 INF = np.iinfo(np.int32).max
 MAX_KSTATS = 24
 
@@ -151,9 +152,9 @@ def _stream_handle(stream) -> ctypes.c_void_p | None:
     return ctypes.c_void_p(stream.cuda_stream)
 
 
-def _options(n_b, path, stream, workspace, warn, profile, count_bytes=False) -> Options:
+def _options(n_b, path, stream, workspace, warn, profile, count_bytes=False, keep_order=False) -> Options:
     o = Options()
-    o.flags = MFBC_OPT_COUNT_BYTES if count_bytes else 0
+    o.flags = (MFBC_OPT_COUNT_BYTES if count_bytes else 0) | (MFBC_OPT_KEEP_ORDER if keep_order else 0)
     o.n_b = int(n_b)
     o.path = int(path)
     o.stream = _stream_handle(stream)
@@ -221,7 +222,8 @@ class Graph:
 
     # ----------------------------------------------------------- entry points
     def bc(self, sources, *, n_b: int = 0, path: int = PATH_AUTO, out=None, stream=None, workspace=None,
-           profile: bool = False, count_bytes: bool = False, return_warn: bool = False):
+           profile: bool = False, count_bytes: bool = False, keep_order: bool = False,
+           return_warn: bool = False):
         """Betweenness centrality summed over `sources` (Algorithm 3).
 
         Host (numpy) sources -> numpy lambda via mfbc_bc; torch CUDA sources
@@ -229,7 +231,7 @@ class Graph:
         lib = load()
         warn = ctypes.c_uint32(0)
         prof = Profile() if (profile or count_bytes) else None
-        opt = _options(n_b, path, stream, workspace, warn, prof, count_bytes)
+        opt = _options(n_b, path, stream, workspace, warn, prof, count_bytes, keep_order)
         if _is_torch(sources):
             import torch
             src = sources.to(dtype=torch.int32).contiguous()

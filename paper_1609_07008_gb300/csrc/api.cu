@@ -141,6 +141,7 @@ static size_t extras(const DevGraph& g, int32_t nsrc, int mode, int nb, bool hos
   size_t b = 0;
   if (mode == 0) b += al256(sizeof(double) * (size_t)std::max(g.n, 1));        // device lambda
   if (host_io) b += al256(sizeof(int32_t) * (size_t)std::max(nsrc, 1));        // device sources
+  if (mode == 0) b += al256(sizeof(int32_t) * (size_t)std::max(nsrc, 1));      // reordered sources
   if (mode == 1 && host_io) b += al256((sizeof(int32_t) + sizeof(double)) * (size_t)nb * std::max(g.n, 1));
   return b;
 }
@@ -282,9 +283,61 @@ void finish_profile(Run& R, mfbc_profile* out, int64_t batches, int64_t fi, int6
   out->path = R.plan.path;
 }
 
+__global__ void k_order_keys(const int32_t* __restrict__ src, int32_t nsrc, const int32_t* __restrict__ d0,
+                             const int32_t* __restrict__ d1, int64_t* keys) {
+  const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nsrc) return;
+  const int32_t s = src[i];
+  const int64_t a = min(d0[s], 0xffff), b = min(d1[s], 0xffff);
+  keys[i] = (a << 48) | (b << 32) | (int64_t)i;
+}
+
+// Group sources of similar depth: sort by BFS distance to the two
+// highest-degree vertices (level kernels, undirected graphs).  Writes the
+// permuted list to d_out; returns false (and leaves the order alone) when it
+// does not apply.  The level state's sv array serves as scratch.
+mfbc_status order_sources(RunCtx& rc, LevelState& ls, const int32_t* d_src, int32_t nsrc, int32_t* d_out,
+                          bool* applied) {
+  const DevGraph& g = *rc.g;
+  const int32_t n = g.n;
+  *applied = false;
+  const size_t need = al256(sizeof(int32_t) * 2 * (size_t)n) + sizeof(int64_t) * (size_t)nsrc;
+  if (g.directed || g.top_hub[0] < 0 || need > sizeof(double) * (size_t)n * ls.nb) return MFBC_OK;
+  int32_t* rows = (int32_t*)ls.sv;
+  int64_t* keys = (int64_t*)((char*)ls.sv + al256(sizeof(int32_t) * 2 * (size_t)n));
+  for (int k = 0; k < 2; k++) {
+    int32_t* row = rows + (size_t)k * n;
+    const int32_t h = g.top_hub[k];
+    if (h < 0) { fill_i32(row, 0, (size_t)n, rc.stream); continue; }
+    MFBC_CUDA_TRY(cudaMemcpyAsync(d_out, &h, sizeof(int32_t), cudaMemcpyHostToDevice, rc.stream), rc.err);
+    MFBC_CUDA_TRY(cudaStreamSynchronize(rc.stream), rc.err);
+    int levels = -1;
+    bool exceeded = false;
+    mfbc_status s = level_batch(rc, ls, d_out, 1, nullptr, false, &levels, &exceeded, nullptr, nullptr);
+    if (s != MFBC_OK) {
+      if (!exceeded) return s;
+      return MFBC_OK;                  // too deep for the level masks: keep the given order
+    }
+    level_output(rc, ls, levels, 1, row, nullptr);
+    level_reset(rc, ls, levels);
+  }
+  k_order_keys<<<(nsrc + 255) / 256, 256, 0, rc.stream>>>(d_src, nsrc, rows, rows + n, keys);
+  std::vector<int64_t> hk((size_t)nsrc);
+  std::vector<int32_t> hs((size_t)nsrc), out((size_t)nsrc);
+  MFBC_CUDA_TRY(cudaMemcpyAsync(hk.data(), keys, sizeof(int64_t) * nsrc, cudaMemcpyDeviceToHost, rc.stream), rc.err);
+  MFBC_CUDA_TRY(cudaMemcpyAsync(hs.data(), d_src, sizeof(int32_t) * nsrc, cudaMemcpyDeviceToHost, rc.stream), rc.err);
+  MFBC_CUDA_TRY(cudaStreamSynchronize(rc.stream), rc.err);
+  std::sort(hk.begin(), hk.end());
+  for (int32_t i = 0; i < nsrc; i++) out[i] = hs[(size_t)(hk[i] & 0xffffffffll)];
+  MFBC_CUDA_TRY(cudaMemcpyAsync(d_out, out.data(), sizeof(int32_t) * nsrc, cudaMemcpyHostToDevice, rc.stream), rc.err);
+  MFBC_CUDA_TRY(cudaStreamSynchronize(rc.stream), rc.err);
+  *applied = true;
+  return MFBC_OK;
+}
+
 // mode 0: lambda (d_lambda device, n doubles, overwritten); mode 1: sssp rows.
 mfbc_status run(mfbc_graph* G, const int32_t* d_src, int32_t nsrc, int mode, double* d_lambda,
-                int32_t* dist_out, double* sigma_out, bool out_on_host, Run& R, char* extra) {
+                int32_t* dist_out, double* sigma_out, bool out_on_host, Run& R, char* extra, int32_t* d_sorted) {
   const DevGraph& g = G->g;
   const Plan& P = R.plan;
   const int nb = P.nb;
@@ -313,6 +366,12 @@ mfbc_status run(mfbc_graph* G, const int32_t* d_src, int32_t nsrc, int mode, dou
       MFBC_CUDA_TRY(cudaMemsetAsync(ls.zacc, 0, sizeof(double) * (size_t)g.items_out.nhub * nb, R.st), &R.err);
   }
   uint32_t warn = 0;
+  if (mode == 0 && P.path == MFBC_PATH_LEVEL && nsrc > nb && !(R.opt && (R.opt->flags & MFBC_OPT_KEEP_ORDER))) {
+    bool applied = false;
+    mfbc_status so = order_sources(rc, ls, d_src, nsrc, d_sorted, &applied);
+    if (so) return fail(so, R.err.empty() ? std::string(mfbc_status_string(so)) : R.err);
+    if (applied) d_src = d_sorted;
+  }
   for (int32_t b0 = 0; b0 < nsrc; b0 += nb) {
     const int na = std::min(nb, nsrc - b0);
     batches++;
@@ -447,7 +506,9 @@ mfbc_status entry(const mfbc_graph* Gc, const int32_t* sources, int32_t nsrc, in
     }
     for (int32_t v : hs) if (v < 0 || v >= n) return fail(MFBC_ERR_INVALID, "source id out of range");
   }
-  s = run(G, d_src, nsrc, mode, d_lambda, dist_out, sigma_out, host_io, R, extra);
+  int32_t* d_sorted = nullptr;
+  if (mode == 0) { d_sorted = (int32_t*)extra; extra += al256(sizeof(int32_t) * (size_t)std::max(nsrc, 1)); }
+  s = run(G, d_src, nsrc, mode, d_lambda, dist_out, sigma_out, host_io, R, extra, d_sorted);
   if (s == MFBC_OK && mode == 0 && host_io && n > 0) {
     cudaError_t e = cudaMemcpyAsync(lambda_out, d_lambda, sizeof(double) * (size_t)n, cudaMemcpyDeviceToHost, R.st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(R.st);

@@ -179,6 +179,14 @@ mfbc_status graph_build(int32_t n, int64_t nnz, const int64_t* h_rowptr, const i
 
   // host copy of the row pointers for the work-item lists
   std::vector<int64_t> rp(h_rowptr, h_rowptr + (size_t)n + 1);
+  {
+    int64_t d0 = 0, d1 = 0;
+    for (int32_t v = 0; v < n; v++) {
+      const int64_t d = rp[v + 1] - rp[v];
+      if (d > d0) { d1 = d0; g->top_hub[1] = g->top_hub[0]; d0 = d; g->top_hub[0] = v; }
+      else if (d > d1) { d1 = d; g->top_hub[1] = v; }
+    }
+  }
   if (g->directed) {
     // A^T by a stable counting sort on the host: rows of A^T are sorted by
     // source vertex, so the transposed graph is deterministic.

@@ -39,6 +39,7 @@ struct DevGraph {
   bool directed = true;
   bool unit = true;                // every arc weighs 1 (w == NULL or all ones)
   int32_t wmax = 1;
+  int32_t top_hub[2] = {-1, -1};   // the two highest out-degree vertices (source ordering)
   int64_t* rowptr = nullptr;       // CSR of A (out-arcs)
   int32_t* col = nullptr;
   int32_t* w = nullptr;            // nullptr when unit

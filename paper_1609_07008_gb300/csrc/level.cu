@@ -135,13 +135,16 @@ __device__ __forceinline__ int64_t meta_beg(int64_t m) { return m & ((1ll << 40)
 __device__ __forceinline__ int meta_len(int64_t m) { return (int)((m >> 40) & 63); }
 __device__ __forceinline__ bool meta_multi(int64_t m) { return (m >> 46) & 1; }
 
-// Word-major list of the (member q, word j) pairs whose mask sF[q][j] is non-zero.
-__device__ __forceinline__ int build_pairs(WarpSmem& w, int nm, int W, uint32_t* haspair) {
+// Word-major list of the (member q, word j) pairs whose mask sF[q][j] is
+// non-zero; only the words in `words` can hold pairs.
+__device__ __forceinline__ int build_pairs(WarpSmem& w, int nm, uint32_t words, uint32_t* haspair) {
   const unsigned lane = lane_id();
   const uint32_t lt = (1u << lane) - 1u;
   int P = 0;
   uint32_t hp = 0;
-  for (int j = 0; j < W; j++) {
+  while (words) {
+    const int j = __ffs(words) - 1;
+    words &= words - 1;
     const bool nz = ((int)lane < nm) && w.sF[lane][j] != 0u;
     const uint32_t mk = __ballot_sync(0xffffffffu, nz);
     if (nz) w.pr[P + __popc(mk & lt)] = (uint16_t)(lane | (j << 5));
@@ -200,16 +203,19 @@ __global__ void __launch_bounds__(LVL_WARPS * 32, 4) k_lvl_fwd(
     const int32_t* __restrict__ col_t, int W, int nb, const uint32_t* __restrict__ full,
     const uint32_t* __restrict__ V, const uint32_t* __restrict__ Fl, const uint32_t* __restrict__ mem_l,
     uint32_t* Fn, uint32_t* mem_n, double* sv, int32_t* list_n, uint32_t* count_n, int64_t cap_n,
-    uint32_t* flags, unsigned long long* bytes) {
+    uint32_t* flags, uint32_t* next_group, unsigned long long* bytes) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   WarpSmem& sm = reinterpret_cast<WarpSmem*>(smem_raw)[threadIdx.x >> 5];
   const unsigned lane = lane_id();
   const uint32_t lt = (1u << lane) - 1u;
-  const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
   unsigned long long nbytes = 0, ngather = 0;
   unsigned long long* pg = bytes ? &ngather : nullptr;
-  for (uint64_t base = (((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; base < (uint64_t)nitems;
-       base += nw * 32) {
+  // groups of 32 items are handed out dynamically (hub items cost far more than leaf items)
+  for (;;) {
+    uint32_t grp = 0;
+    if (lane == 0) grp = atomicAdd(next_group, 1u);
+    const uint64_t base = (uint64_t)__shfl_sync(0xffffffffu, grp, 0) * 32;
+    if (base >= (uint64_t)nitems) break;
     // lane-parallel precheck of 32 items: skip rows already reached by every column
     const uint64_t myit = base + lane;
     int32_t myv = 0;
@@ -248,9 +254,10 @@ __global__ void __launch_bounds__(LVL_WARPS * 32, 4) k_lvl_fwd(
       }
       __syncwarp();
       if (bytes) nbytes += 4ull * W * (nm + 1);
-      if (!__any_sync(0xffffffffu, cand != 0u)) continue;
+      const uint32_t cw = __ballot_sync(0xffffffffu, cand != 0u);
+      if (!cw) continue;
       uint32_t haspair;
-      const int P = build_pairs(sm, nm, W, &haspair);
+      const int P = build_pairs(sm, nm, cw, &haspair);
       const size_t vrow = (size_t)v * nb;
       gather_pairs(sm, P, sv, nb, pg, [&](int j, double acc) {
         const uint32_t cj = __shfl_sync(0xffffffffu, cand, j);
@@ -289,17 +296,20 @@ __global__ void __launch_bounds__(LVL_WARPS * 32, 4) k_lvl_bwd(
     int64_t nitems, const int32_t* __restrict__ item_v, const int64_t* __restrict__ item_meta,
     const int32_t* __restrict__ col, const int32_t* __restrict__ hub_of, int W, int nb,
     const uint32_t* __restrict__ Fl, const uint32_t* __restrict__ mem_l, const uint32_t* __restrict__ Fn,
-    const uint32_t* __restrict__ mem_n, double* sv, double* zacc, double* lambda,
+    const uint32_t* __restrict__ mem_n, double* sv, double* zacc, double* lambda, uint32_t* next_group,
     unsigned long long* bytes) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   WarpSmem& sm = reinterpret_cast<WarpSmem*>(smem_raw)[threadIdx.x >> 5];
   const unsigned lane = lane_id();
   const uint32_t lt = (1u << lane) - 1u;
-  const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
   unsigned long long nbytes = 0, ngather = 0;
   unsigned long long* pg = bytes ? &ngather : nullptr;
-  for (uint64_t base = (((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; base < (uint64_t)nitems;
-       base += nw * 32) {
+  // groups of 32 items are handed out dynamically (hub items cost far more than leaf items)
+  for (;;) {
+    uint32_t grp = 0;
+    if (lane == 0) grp = atomicAdd(next_group, 1u);
+    const uint64_t base = (uint64_t)__shfl_sync(0xffffffffu, grp, 0) * 32;
+    if (base >= (uint64_t)nitems) break;
     // lane-parallel precheck of 32 items: only rows with a source at level l
     const uint64_t myit = base + lane;
     int32_t myv = 0;
@@ -336,7 +346,8 @@ __global__ void __launch_bounds__(LVL_WARPS * 32, 4) k_lvl_bwd(
       __syncwarp();
       if (bytes) nbytes += 4ull * W * (nm + 1);
       uint32_t haspair;
-      const int P = build_pairs(sm, nm, W, &haspair);
+      const uint32_t fw = __ballot_sync(0xffffffffu, Fv != 0u);
+      const int P = build_pairs(sm, nm, fw, &haspair);
       const size_t vrow = (size_t)v * nb;
       const int32_t hub = multi ? hub_of[v] : -1;
       double lam = 0.0;
@@ -357,7 +368,7 @@ __global__ void __launch_bounds__(LVL_WARPS * 32, 4) k_lvl_bwd(
       gather_pairs(sm, P, sv, nb, pg, finish);
       if (!multi) {
         // columns of level l whose word had no successor pair: zeta = 0
-        uint32_t rest = __ballot_sync(0xffffffffu, Fv != 0u) & ~haspair;
+        uint32_t rest = fw & ~haspair;
         while (rest) {
           const int j = __ffs(rest) - 1;
           rest &= rest - 1;
@@ -377,34 +388,47 @@ __global__ void __launch_bounds__(LVL_WARPS * 32, 4) k_lvl_bwd(
 }
 
 // Finalise the multi-item vertices of level l: zeta from the hub accumulator.
+// 32 hubs are tested per warp at once; a hub's frontier row is read once.
 __global__ void k_lvl_hub_final(const int32_t* __restrict__ hubs, int32_t nhub, int W, int nb,
                                 const uint32_t* __restrict__ Fl, const uint32_t* __restrict__ mem_l,
                                 double* sv, double* zacc, double* lambda, unsigned long long* bytes) {
   const unsigned lane = lane_id();
   const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
   unsigned long long nbytes = 0;
-  for (uint64_t h = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; h < (uint64_t)nhub; h += nw) {
-    const int32_t v = hubs[h];
-    if (!test_bit(mem_l, v)) continue;
-    double lam = 0.0;
-    for (int j = 0; j < W; j++) {
-      const uint32_t fj = Fl[(size_t)v * W + j];
-      if (!fj) continue;
-      if ((fj >> lane) & 1u) {
-        const size_t zi = (size_t)h * nb + j * 32 + lane;
-        const size_t vi = (size_t)v * nb + j * 32 + lane;
-        const double z = zacc[zi];
-        zacc[zi] = 0.0;
-        const double sg = sv[vi];
-        lam += z * sg;
-        sv[vi] = z + 1.0 / sg;
+  for (uint64_t base = (((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; base < (uint64_t)nhub;
+       base += nw * 32) {
+    const uint64_t myh = base + lane;
+    const int32_t myv = myh < (uint64_t)nhub ? hubs[myh] : 0;
+    uint32_t am = __ballot_sync(0xffffffffu, myh < (uint64_t)nhub && test_bit(mem_l, myv));
+    while (am) {
+      const int t = __ffs(am) - 1;
+      am &= am - 1;
+      const uint64_t h = base + t;
+      const int32_t v = __shfl_sync(0xffffffffu, myv, t);
+      const uint32_t Fv = (int)lane < W ? Fl[(size_t)v * W + lane] : 0u;
+      uint32_t words = __ballot_sync(0xffffffffu, Fv != 0u);
+      double lam = 0.0;
+      while (words) {
+        const int j = __ffs(words) - 1;
+        words &= words - 1;
+        const uint32_t fj = __shfl_sync(0xffffffffu, Fv, j);
+        if ((fj >> lane) & 1u) {
+          const size_t zi = (size_t)h * nb + j * 32 + lane;
+          const size_t vi = (size_t)v * nb + j * 32 + lane;
+          const double z = zacc[zi];
+          zacc[zi] = 0.0;
+          const double sg = sv[vi];
+          lam += z * sg;
+          sv[vi] = z + 1.0 / sg;
+        }
+        if (bytes) nbytes += 32ull * __popc(fj);
       }
-      if (bytes) nbytes += 4ull + 32ull * __popc(fj);
+      for (int o = 16; o; o >>= 1) lam += __shfl_xor_sync(0xffffffffu, lam, o);
+      if (lane == 0) lambda[v] += lam;
+      if (bytes) nbytes += 4ull * W + 16ull;
     }
-    for (int o = 16; o; o >>= 1) lam += __shfl_xor_sync(0xffffffffu, lam, o);
-    if (lane == 0) { lambda[v] += lam; if (bytes) atomicAdd(bytes, nbytes + 16ull); }
-    nbytes = 0;
   }
+  if (bytes && lane == 0) atomicAdd(bytes, nbytes);
 }
 
 // Return the bit masks touched by a batch to zero (F rows, visited rows).
@@ -515,10 +539,11 @@ mfbc_status level_batch(RunCtx& rc, LevelState& s, const int32_t* d_src_batch, i
     if (l + 1 >= s.Lcap) { *levels_exceeded = true; level_reset(rc, s, l); return MFBC_ERR_NO_CONVERGENCE; }
     const int64_t off_n = P.off[l] + cl;
     MFBC_CUDA_TRY(cudaMemsetAsync(&s.ctr->list_count[0], 0, sizeof(uint32_t), st), rc.err);
+    MFBC_CUDA_TRY(cudaMemsetAsync(&s.ctr->list_count[2], 0, sizeof(uint32_t), st), rc.err);
     PROF(K_LVL_FWD, (k_lvl_fwd<<<grid_for_items(g.items_in.count, big_grid), LVL_WARPS * 32, LVL_SMEM, st>>>(
                         g.items_in.count, g.items_in.v, g.items_in.beg, g.col_t, W, nb, s.full,
                         s.V, Fl(l), Ml(l), Fl(l + 1), Ml(l + 1), s.sv, s.lists + off_n, &s.ctr->list_count[0],
-                        s.list_cap - off_n, &s.ctr->flags, B ? B + K_LVL_FWD : nullptr)));
+                        s.list_cap - off_n, &s.ctr->flags, &s.ctr->list_count[2], B ? B + K_LVL_FWD : nullptr)));
     MFBC_CUDA_TRY(cudaMemcpyAsync(rc.h_ctr, s.ctr->list_count, sizeof(uint32_t) * 5, cudaMemcpyDeviceToHost, st), rc.err);
     MFBC_CUDA_TRY(cudaStreamSynchronize(st), rc.err);
     rc.prof->drain();
@@ -534,12 +559,13 @@ mfbc_status level_batch(RunCtx& rc, LevelState& s, const int32_t* d_src_batch, i
 
   // MFBr over levels L .. 1 (level L+1 is empty and all-zero)
   for (int l = L; l >= 1; l--) {
+    MFBC_CUDA_TRY(cudaMemsetAsync(&s.ctr->list_count[2], 0, sizeof(uint32_t), st), rc.err);
     PROF(K_LVL_BWD, (k_lvl_bwd<<<grid_for_items(g.items_out.count, big_grid), LVL_WARPS * 32, LVL_SMEM, st>>>(
                         g.items_out.count, g.items_out.v, g.items_out.beg, g.col, g.items_out.hub_of,
-                        W, nb, Fl(l), Ml(l), Fl(l + 1), Ml(l + 1), s.sv, s.zacc, lambda,
+                        W, nb, Fl(l), Ml(l), Fl(l + 1), Ml(l + 1), s.sv, s.zacc, lambda, &s.ctr->list_count[2],
                         B ? B + K_LVL_BWD : nullptr)));
     if (g.items_out.nhub)
-      PROF(K_LVL_HUB, (k_lvl_hub_final<<<grid_for_warps(g.items_out.nhub, 152 * 16), LVL_WARPS * 32, 0, st>>>(
+      PROF(K_LVL_HUB, (k_lvl_hub_final<<<grid_for_items(g.items_out.nhub, 152 * 8), LVL_WARPS * 32, 0, st>>>(
                           g.items_out.hubs, g.items_out.nhub, W, nb, Fl(l), Ml(l), s.sv, s.zacc, lambda,
                           B ? B + K_LVL_HUB : nullptr)));
     if (bwd_iters) (*bwd_iters)++;

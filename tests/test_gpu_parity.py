@@ -294,3 +294,17 @@ def test_profile_reports_kernels():
         main = "level_mfbf_pull" if p == mfbc.PATH_LEVEL else "mfbf_relax_min"
         assert ks[main]["launches"] > 0 and ks[main]["ms"] > 0 and ks[main]["bytes"] > 0
     G.close()
+
+
+def test_source_ordering_does_not_change_lambda():
+    g = gg.rmat(13, 8, seed=9)
+    srcs = gg.sample_sources(g, 300, seed=5)
+    want = oracle.bc(g, srcs)
+    G = mfbc.Graph.from_csr(g)
+    for n_b in (32, 96):
+        a = G.bc(srcs, n_b=n_b)
+        b = G.bc(srcs, n_b=n_b, keep_order=True)
+        assert_lambda_close(a, want)
+        assert_lambda_close(b, want)
+        assert_lambda_close(a, b, rtol=1e-12)
+    G.close()
