@@ -18,7 +18,8 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "_build", "libmfbc.so")
+# MFBC_LIBRARY may point at another build of the same ABI (e.g. a tuning variant)
+LIB_PATH = os.environ.get("MFBC_LIBRARY") or os.path.join(_HERE, "_build", "libmfbc.so")
 
 MFBC_OK = 0
 MFBC_ERR_INVALID = 1

@@ -128,7 +128,13 @@ struct WarpSmem {
   uint16_t pr[1024];                         // (member, word) pairs with a non-zero mask, word-major
 };
 constexpr size_t LVL_SMEM = sizeof(WarpSmem) * LVL_WARPS;
-constexpr int GATHER_U = 8;                  // independent 256-byte loads in flight per warp
+#ifndef MFBC_GATHER_U
+#define MFBC_GATHER_U 4
+#endif
+#ifndef MFBC_LVL_MIN_BLOCKS
+#define MFBC_LVL_MIN_BLOCKS 4
+#endif
+constexpr int GATHER_U = MFBC_GATHER_U;      // loads per gather round (two rounds in flight)
 
 // Item metadata: first arc (bits 0..39), arc count (bits 40..45), multi-item row (bit 46).
 __device__ __forceinline__ int64_t meta_beg(int64_t m) { return m & ((1ll << 40) - 1); }
@@ -159,46 +165,67 @@ __device__ __forceinline__ int build_pairs(WarpSmem& w, int nm, uint32_t words, 
 // Sum, per word, the gathered values of the pairs; FLUSH(j, acc) is called once
 // per word with pairs, in word order, by the whole warp (lane = column).
 template <class Flush>
-__device__ __forceinline__ void gather_pairs(const WarpSmem& w, int P, const double* sv, int nb,
-                                             unsigned long long* ngather, Flush flush) {
+__device__ __forceinline__ void gather_issue(const WarpSmem& w, int P, int p0, const double* sv, int nb,
+                                             unsigned long long* ngather, double (&x)[GATHER_U]) {
   const unsigned lane = lane_id();
-  double acc = 0.0;
-  int curj = -1;
-  for (int p0 = 0; p0 < P; p0 += GATHER_U) {
-    double x[GATHER_U];
-    int jj[GATHER_U];
 #pragma unroll
-    for (int t = 0; t < GATHER_U; t++) {
-      x[t] = 0.0;
-      jj[t] = -1;
-      const int p = p0 + t;
-      if (p < P) {
-        const uint32_t pr = w.pr[p];
-        const int q = pr & 31, j = pr >> 5;
-        jj[t] = j;
-        if ((w.sF[q][j] >> lane) & 1u) {
-          x[t] = __ldg(&sv[(size_t)w.su[q] * nb + j * 32 + lane]);
-          if (ngather) (*ngather)++;
-        }
+  for (int t = 0; t < GATHER_U; t++) {
+    x[t] = 0.0;
+    const int p = p0 + t;
+    if (p < P) {
+      const uint32_t pr = w.pr[p];
+      const int q = pr & 31, j = pr >> 5;
+      if ((w.sF[q][j] >> lane) & 1u) {
+        x[t] = __ldg(&sv[(size_t)w.su[q] * nb + j * 32 + lane]);
+        if (ngather) (*ngather)++;
       }
     }
+  }
+}
+
+template <class Flush>
+__device__ __forceinline__ void gather_consume(const WarpSmem& w, int P, int p0, const double (&x)[GATHER_U],
+                                               double& acc, int& curj, Flush& flush) {
 #pragma unroll
-    for (int t = 0; t < GATHER_U; t++) {
-      if (jj[t] >= 0) {
-        if (jj[t] != curj) {
-          if (curj >= 0) flush(curj, acc);
-          acc = 0.0;
-          curj = jj[t];
-        }
-        acc += x[t];
+  for (int t = 0; t < GATHER_U; t++) {
+    const int p = p0 + t;
+    if (p < P) {
+      const int j = w.pr[p] >> 5;
+      if (j != curj) {
+        if (curj >= 0) flush(curj, acc);
+        acc = 0.0;
+        curj = j;
       }
+      acc += x[t];
+    }
+  }
+}
+
+// Sum, per word, the gathered values of the pairs; FLUSH(j, acc) is called once
+// per word with pairs, in word order, by the whole warp (lane = column).
+// Rounds of GATHER_U loads are double-buffered: the next round is in flight
+// while the previous one is summed.
+template <class Flush>
+__device__ __forceinline__ void gather_pairs(const WarpSmem& w, int P, const double* sv, int nb,
+                                             unsigned long long* ngather, Flush flush) {
+  double acc = 0.0;
+  int curj = -1;
+  double xa[GATHER_U], xb[GATHER_U];
+  if (P > 0) gather_issue<Flush>(w, P, 0, sv, nb, ngather, xa);
+  for (int p0 = 0; p0 < P; p0 += 2 * GATHER_U) {
+    const bool more = p0 + GATHER_U < P;
+    if (more) gather_issue<Flush>(w, P, p0 + GATHER_U, sv, nb, ngather, xb);
+    gather_consume(w, P, p0, xa, acc, curj, flush);
+    if (more) {
+      if (p0 + 2 * GATHER_U < P) gather_issue<Flush>(w, P, p0 + 2 * GATHER_U, sv, nb, ngather, xa);
+      gather_consume(w, P, p0 + GATHER_U, xb, acc, curj, flush);
     }
   }
   if (curj >= 0) flush(curj, acc);
 }
 
 // MFBF product of level l (see file comment).
-__global__ void __launch_bounds__(LVL_WARPS * 32, 4) k_lvl_fwd(
+__global__ void __launch_bounds__(LVL_WARPS * 32, MFBC_LVL_MIN_BLOCKS) k_lvl_fwd(
     int64_t nitems, const int32_t* __restrict__ item_v, const int64_t* __restrict__ item_meta,
     const int32_t* __restrict__ col_t, int W, int nb, const uint32_t* __restrict__ full,
     const uint32_t* __restrict__ V, const uint32_t* __restrict__ Fl, const uint32_t* __restrict__ mem_l,
@@ -227,16 +254,34 @@ __global__ void __launch_bounds__(LVL_WARPS * 32, 4) k_lvl_fwd(
       act = !test_bit(full, myv);
     }
     uint32_t am = __ballot_sync(0xffffffffu, act);
-    while (am) {
+    // the next active item's neighbour ids and visited row are loaded one item ahead
+    int32_t nv = 0, nu = -1;
+    int64_t nmeta = 0;
+    uint32_t nVv = 0xffffffffu;
+    if (am) {
       const int t = __ffs(am) - 1;
+      nv = __shfl_sync(0xffffffffu, myv, t);
+      nmeta = __shfl_sync(0xffffffffu, mymeta, t);
+      nu = (int)lane < meta_len(nmeta) ? __ldg(&col_t[meta_beg(nmeta) + lane]) : -1;
+      nVv = (int)lane < W ? V[(size_t)nv * W + lane] : 0xffffffffu;
       am &= am - 1;
-      const int32_t v = __shfl_sync(0xffffffffu, myv, t);
-      const int64_t meta = __shfl_sync(0xffffffffu, mymeta, t);
-      const int64_t beg = meta_beg(meta);
+    }
+    for (bool have = __ballot_sync(0xffffffffu, act) != 0u; have;) {
+      const int32_t v = nv;
+      const int64_t meta = nmeta;
+      const int32_t u = nu;
+      const uint32_t Vv = nVv;
+      have = am != 0u;
+      if (have) {
+        const int t = __ffs(am) - 1;
+        nv = __shfl_sync(0xffffffffu, myv, t);
+        nmeta = __shfl_sync(0xffffffffu, mymeta, t);
+        nu = (int)lane < meta_len(nmeta) ? __ldg(&col_t[meta_beg(nmeta) + lane]) : -1;
+        nVv = (int)lane < W ? V[(size_t)nv * W + lane] : 0xffffffffu;
+        am &= am - 1;
+      }
       const int len = meta_len(meta);
       const bool multi = meta_multi(meta);
-      const uint32_t Vv = (int)lane < W ? V[(size_t)v * W + lane] : 0xffffffffu;
-      const int32_t u = (int)lane < len ? __ldg(&col_t[beg + lane]) : -1;
       const bool isMem = u >= 0 && test_bit(mem_l, u);
       const uint32_t mm = __ballot_sync(0xffffffffu, isMem);
       if (bytes) nbytes += 4ull * len + 12ull;
@@ -292,7 +337,7 @@ __global__ void __launch_bounds__(LVL_WARPS * 32, 4) k_lvl_fwd(
 }
 
 // MFBr gather of level l >= 1 (see file comment).
-__global__ void __launch_bounds__(LVL_WARPS * 32, 4) k_lvl_bwd(
+__global__ void __launch_bounds__(LVL_WARPS * 32, MFBC_LVL_MIN_BLOCKS) k_lvl_bwd(
     int64_t nitems, const int32_t* __restrict__ item_v, const int64_t* __restrict__ item_meta,
     const int32_t* __restrict__ col, const int32_t* __restrict__ hub_of, int W, int nb,
     const uint32_t* __restrict__ Fl, const uint32_t* __restrict__ mem_l, const uint32_t* __restrict__ Fn,
@@ -321,16 +366,34 @@ __global__ void __launch_bounds__(LVL_WARPS * 32, 4) k_lvl_bwd(
       act = test_bit(mem_l, myv);
     }
     uint32_t am = __ballot_sync(0xffffffffu, act);
-    while (am) {
+    // the next active item's neighbour ids and frontier row are loaded one item ahead
+    int32_t nv = 0, nu = -1;
+    int64_t nmeta = 0;
+    uint32_t nFv = 0u;
+    if (am) {
       const int t = __ffs(am) - 1;
+      nv = __shfl_sync(0xffffffffu, myv, t);
+      nmeta = __shfl_sync(0xffffffffu, mymeta, t);
+      nu = (int)lane < meta_len(nmeta) ? __ldg(&col[meta_beg(nmeta) + lane]) : -1;
+      nFv = (int)lane < W ? __ldg(&Fl[(size_t)nv * W + lane]) : 0u;
       am &= am - 1;
-      const int32_t v = __shfl_sync(0xffffffffu, myv, t);
-      const int64_t meta = __shfl_sync(0xffffffffu, mymeta, t);
-      const int64_t beg = meta_beg(meta);
+    }
+    for (bool have = __ballot_sync(0xffffffffu, act) != 0u; have;) {
+      const int32_t v = nv;
+      const int64_t meta = nmeta;
+      const int32_t u = nu;
+      const uint32_t Fv = nFv;
+      have = am != 0u;
+      if (have) {
+        const int t = __ffs(am) - 1;
+        nv = __shfl_sync(0xffffffffu, myv, t);
+        nmeta = __shfl_sync(0xffffffffu, mymeta, t);
+        nu = (int)lane < meta_len(nmeta) ? __ldg(&col[meta_beg(nmeta) + lane]) : -1;
+        nFv = (int)lane < W ? __ldg(&Fl[(size_t)nv * W + lane]) : 0u;
+        am &= am - 1;
+      }
       const int len = meta_len(meta);
       const bool multi = meta_multi(meta);
-      const uint32_t Fv = (int)lane < W ? __ldg(&Fl[(size_t)v * W + lane]) : 0u;
-      const int32_t u = (int)lane < len ? __ldg(&col[beg + lane]) : -1;
       const bool isMem = u >= 0 && test_bit(mem_n, u);
       const uint32_t mm = __ballot_sync(0xffffffffu, isMem);
       if (bytes) nbytes += 4ull * len + 12ull;
@@ -509,7 +572,7 @@ mfbc_status level_batch(RunCtx& rc, LevelState& s, const int32_t* d_src_batch, i
   *levels_exceeded = false;
   *levels_out = -1;
   if (n == 0) return MFBC_OK;
-  const unsigned big_grid = 152u * 4u;       // resident blocks of the level gather kernels
+  const unsigned big_grid = 152u * MFBC_LVL_MIN_BLOCKS;  // resident blocks of the level gather kernels
   set_smem_attrs();
 
   fill_i32(s.src, -1, (size_t)nb, st);
