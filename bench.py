@@ -306,6 +306,8 @@ def main():
                          "peak_kind": f"{peak_kind} copy bandwidth", "unit": "GB/s",
                          "frac": achieved / peak, "traffic": None,
                          "bytes_per_launch": per_launch_bytes, "avg_launch_ms": avg_ms},
+            "gather_stats": {k: prof_bytes.get(k) for k in ("pairs_fwd", "pairs_bwd", "values_fwd", "values_bwd",
+                                                            "fwd_iters", "bwd_iters", "batches")},
             "kernels_ms_share": {k: round(v["ms"] / sum(x["ms"] for x in kstats.values()), 4)
                                  for k, v in sorted(kstats.items(), key=lambda kv: -kv[1]["ms"])},
         }

@@ -85,6 +85,8 @@ typedef struct {
   uint64_t bwd_iters;          /* MFBr products over all batches */
   int32_t n_b;                 /* batch width used */
   int32_t path;                /* MFBC_PATH_GENERAL or MFBC_PATH_LEVEL */
+  uint64_t stat[4];            /* with MFBC_OPT_COUNT_BYTES, level kernels: (neighbour, word)
+                                  pairs gathered by MFBF / MFBr, values gathered by MFBF / MFBr */
 } mfbc_profile;
 
 typedef struct {

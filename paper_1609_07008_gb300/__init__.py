@@ -52,7 +52,8 @@ class KernelStat(ctypes.Structure):
 class Profile(ctypes.Structure):
     _fields_ = [("nkernels", ctypes.c_int32), ("k", KernelStat * MAX_KSTATS),
                 ("batches", ctypes.c_uint64), ("fwd_iters", ctypes.c_uint64),
-                ("bwd_iters", ctypes.c_uint64), ("n_b", ctypes.c_int32), ("path", ctypes.c_int32)]
+                ("bwd_iters", ctypes.c_uint64), ("n_b", ctypes.c_int32), ("path", ctypes.c_int32),
+                ("stat", ctypes.c_uint64 * 4)]
 
     def as_dict(self) -> dict:
         return {
@@ -61,6 +62,8 @@ class Profile(ctypes.Structure):
                         for i in range(self.nkernels)},
             "batches": int(self.batches), "fwd_iters": int(self.fwd_iters),
             "bwd_iters": int(self.bwd_iters), "n_b": int(self.n_b), "path": int(self.path),
+            "pairs_fwd": int(self.stat[0]), "pairs_bwd": int(self.stat[1]),
+            "values_fwd": int(self.stat[2]), "values_bwd": int(self.stat[3]),
         }
 
 

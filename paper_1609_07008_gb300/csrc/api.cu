@@ -260,11 +260,14 @@ mfbc_status get_workspace(Run& R) {
 void finish_profile(Run& R, mfbc_profile* out, int64_t batches, int64_t fi, int64_t bi, Counters* ctr) {
   if (!out) return;
   R.prof.drain();
-  unsigned long long bytes[K_NUM];
-  if (cudaMemcpy(bytes, ctr->bytes, sizeof(bytes), cudaMemcpyDeviceToHost) != cudaSuccess) {
+  unsigned long long bytes[K_NUM], stat[4];
+  if (cudaMemcpy(bytes, ctr->bytes, sizeof(bytes), cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemcpy(stat, ctr->stat, sizeof(stat), cudaMemcpyDeviceToHost) != cudaSuccess) {
     cudaGetLastError();
     memset(bytes, 0, sizeof(bytes));
+    memset(stat, 0, sizeof(stat));
   }
+  for (int i = 0; i < 4; i++) out->stat[i] = stat[i];
   out->nkernels = 0;
   for (int i = 0; i < K_NUM && out->nkernels < MFBC_MAX_KSTATS; i++) {
     KStat& k = R.prof.k[i];

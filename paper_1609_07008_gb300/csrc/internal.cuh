@@ -68,6 +68,7 @@ enum KId {
 // Device-side counters of algorithmic bytes, one slot per kernel id.
 struct Counters {
   unsigned long long bytes[K_NUM];
+  unsigned long long stat[4];      // (counting pass) pairs fwd/bwd, gathered values fwd/bwd
   uint32_t list_count[4];          // frontier / touched list sizes
   uint32_t flags;                  // bit0: level capacity exceeded, bit1: sigma >= 2^53
 };

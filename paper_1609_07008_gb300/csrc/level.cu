@@ -230,13 +230,13 @@ __global__ void __launch_bounds__(LVL_WARPS * 32, MFBC_LVL_MIN_BLOCKS) k_lvl_fwd
     const int32_t* __restrict__ col_t, int W, int nb, const uint32_t* __restrict__ full,
     const uint32_t* __restrict__ V, const uint32_t* __restrict__ Fl, const uint32_t* __restrict__ mem_l,
     uint32_t* Fn, uint32_t* mem_n, double* sv, int32_t* list_n, uint32_t* count_n, int64_t cap_n,
-    uint32_t* flags, uint32_t* next_group, unsigned long long* bytes) {
+    uint32_t* flags, uint32_t* next_group, unsigned long long* bytes, unsigned long long* stat) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   WarpSmem& sm = reinterpret_cast<WarpSmem*>(smem_raw)[threadIdx.x >> 5];
   const unsigned lane = lane_id();
   const uint32_t lt = (1u << lane) - 1u;
-  unsigned long long nbytes = 0, ngather = 0;
-  unsigned long long* pg = bytes ? &ngather : nullptr;
+  unsigned long long nbytes = 0, ngather = 0, npairs = 0, nvals = 0;
+  unsigned long long* pg = bytes ? &nvals : nullptr;
   // groups of 32 items are handed out dynamically (hub items cost far more than leaf items)
   for (;;) {
     uint32_t grp = 0;
@@ -303,6 +303,7 @@ __global__ void __launch_bounds__(LVL_WARPS * 32, MFBC_LVL_MIN_BLOCKS) k_lvl_fwd
       if (!cw) continue;
       uint32_t haspair;
       const int P = build_pairs(sm, nm, cw, &haspair);
+      if (bytes) npairs += P;
       const size_t vrow = (size_t)v * nb;
       gather_pairs(sm, P, sv, nb, pg, [&](int j, double acc) {
         const uint32_t cj = __shfl_sync(0xffffffffu, cand, j);
@@ -331,8 +332,14 @@ __global__ void __launch_bounds__(LVL_WARPS * 32, MFBC_LVL_MIN_BLOCKS) k_lvl_fwd
     }
   }
   if (bytes) {
+    ngather += nvals;
     for (int o = 16; o; o >>= 1) ngather += __shfl_xor_sync(0xffffffffu, ngather, o);
-    if (lane == 0) atomicAdd(bytes, nbytes + 8ull * ngather);
+    for (int o = 16; o; o >>= 1) nvals += __shfl_xor_sync(0xffffffffu, nvals, o);
+    if (lane == 0) {
+      atomicAdd(bytes, nbytes + 8ull * ngather);
+      atomicAdd(&stat[0], npairs);
+      atomicAdd(&stat[2], nvals);
+    }
   }
 }
 
@@ -342,13 +349,13 @@ __global__ void __launch_bounds__(LVL_WARPS * 32, MFBC_LVL_MIN_BLOCKS) k_lvl_bwd
     const int32_t* __restrict__ col, const int32_t* __restrict__ hub_of, int W, int nb,
     const uint32_t* __restrict__ Fl, const uint32_t* __restrict__ mem_l, const uint32_t* __restrict__ Fn,
     const uint32_t* __restrict__ mem_n, double* sv, double* zacc, double* lambda, uint32_t* next_group,
-    unsigned long long* bytes) {
+    unsigned long long* bytes, unsigned long long* stat) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   WarpSmem& sm = reinterpret_cast<WarpSmem*>(smem_raw)[threadIdx.x >> 5];
   const unsigned lane = lane_id();
   const uint32_t lt = (1u << lane) - 1u;
-  unsigned long long nbytes = 0, ngather = 0;
-  unsigned long long* pg = bytes ? &ngather : nullptr;
+  unsigned long long nbytes = 0, ngather = 0, npairs = 0, nvals = 0;
+  unsigned long long* pg = bytes ? &nvals : nullptr;
   // groups of 32 items are handed out dynamically (hub items cost far more than leaf items)
   for (;;) {
     uint32_t grp = 0;
@@ -411,6 +418,7 @@ __global__ void __launch_bounds__(LVL_WARPS * 32, MFBC_LVL_MIN_BLOCKS) k_lvl_bwd
       uint32_t haspair;
       const uint32_t fw = __ballot_sync(0xffffffffu, Fv != 0u);
       const int P = build_pairs(sm, nm, fw, &haspair);
+      if (bytes) npairs += P;
       const size_t vrow = (size_t)v * nb;
       const int32_t hub = multi ? hub_of[v] : -1;
       double lam = 0.0;
@@ -445,8 +453,14 @@ __global__ void __launch_bounds__(LVL_WARPS * 32, MFBC_LVL_MIN_BLOCKS) k_lvl_bwd
     }
   }
   if (bytes) {
+    ngather += nvals;
     for (int o = 16; o; o >>= 1) ngather += __shfl_xor_sync(0xffffffffu, ngather, o);
-    if (lane == 0) atomicAdd(bytes, nbytes + 8ull * ngather);
+    for (int o = 16; o; o >>= 1) nvals += __shfl_xor_sync(0xffffffffu, nvals, o);
+    if (lane == 0) {
+      atomicAdd(bytes, nbytes + 8ull * ngather);
+      atomicAdd(&stat[1], npairs);
+      atomicAdd(&stat[3], nvals);
+    }
   }
 }
 
@@ -606,7 +620,8 @@ mfbc_status level_batch(RunCtx& rc, LevelState& s, const int32_t* d_src_batch, i
     PROF(K_LVL_FWD, (k_lvl_fwd<<<grid_for_items(g.items_in.count, big_grid), LVL_WARPS * 32, LVL_SMEM, st>>>(
                         g.items_in.count, g.items_in.v, g.items_in.beg, g.col_t, W, nb, s.full,
                         s.V, Fl(l), Ml(l), Fl(l + 1), Ml(l + 1), s.sv, s.lists + off_n, &s.ctr->list_count[0],
-                        s.list_cap - off_n, &s.ctr->flags, &s.ctr->list_count[2], B ? B + K_LVL_FWD : nullptr)));
+                        s.list_cap - off_n, &s.ctr->flags, &s.ctr->list_count[2], B ? B + K_LVL_FWD : nullptr,
+                        s.ctr->stat)));
     MFBC_CUDA_TRY(cudaMemcpyAsync(rc.h_ctr, s.ctr->list_count, sizeof(uint32_t) * 5, cudaMemcpyDeviceToHost, st), rc.err);
     MFBC_CUDA_TRY(cudaStreamSynchronize(st), rc.err);
     rc.prof->drain();
@@ -626,7 +641,7 @@ mfbc_status level_batch(RunCtx& rc, LevelState& s, const int32_t* d_src_batch, i
     PROF(K_LVL_BWD, (k_lvl_bwd<<<grid_for_items(g.items_out.count, big_grid), LVL_WARPS * 32, LVL_SMEM, st>>>(
                         g.items_out.count, g.items_out.v, g.items_out.beg, g.col, g.items_out.hub_of,
                         W, nb, Fl(l), Ml(l), Fl(l + 1), Ml(l + 1), s.sv, s.zacc, lambda, &s.ctr->list_count[2],
-                        B ? B + K_LVL_BWD : nullptr)));
+                        B ? B + K_LVL_BWD : nullptr, s.ctr->stat)));
     if (g.items_out.nhub)
       PROF(K_LVL_HUB, (k_lvl_hub_final<<<grid_for_items(g.items_out.nhub, 152 * 8), LVL_WARPS * 32, 0, st>>>(
                           g.items_out.hubs, g.items_out.nhub, W, nb, Fl(l), Ml(l), s.sv, s.zacc, lambda,
