@@ -149,7 +149,7 @@ static size_t extras(const DevGraph& g, int32_t nsrc, int mode, int nb, bool hos
 static void level_caps(const DevGraph& g, int nb, int* Lcap, int64_t* list_cap) {
   (void)nb;
   const int64_t n = g.n;
-  *Lcap = (int)std::min<int64_t>(n + 2, 64);
+  *Lcap = (int)std::min<int64_t>(n + 2, 48);
   *list_cap = n * std::min<int64_t>(*Lcap, 24) + 64;
 }
 

@@ -62,7 +62,7 @@ struct KStat {
 enum KId {
   K_FILL = 0, K_SEED, K_RELAX_MIN, K_RELAX_TIE, K_ACCUM, K_COUNTERS, K_PROPAGATE, K_FINAL,
   K_LAMBDA, K_CLEAR, K_LVL_FWD, K_LVL_VISIT, K_LVL_BWD, K_LVL_HUB, K_LVL_RESET, K_OUTPUT,
-  K_NUM
+  K_LVL_FWD_G, K_LVL_BWD_G, K_NUM
 };
 
 // Device-side counters of algorithmic bytes, one slot per kernel id.
@@ -71,6 +71,7 @@ struct Counters {
   unsigned long long stat[4];      // (counting pass) pairs fwd/bwd, gathered values fwd/bwd
   uint32_t list_count[4];          // frontier / touched list sizes
   uint32_t flags;                  // bit0: level capacity exceeded, bit1: sigma >= 2^53
+  uint32_t work[4];                // level kernels: pairs, segments, gather group counter, overflow
 };
 
 class Profiler {
@@ -135,6 +136,9 @@ struct LevelState {
   int32_t* lists;     // per-level vertex lists, concatenated
   int64_t list_cap;
   double* zacc;       // [nhub_out][nb] backward partial sums of multi-item vertices
+  uint2* pairs;       // (neighbour, column mask) pairs of one product round
+  uint4* segs;        // segment headers of one product round
+  uint32_t pair_cap, seg_cap;
   int32_t* src;       // [nb]
   Counters* ctr;
   int64_t mw;         // words per vertex bitmap

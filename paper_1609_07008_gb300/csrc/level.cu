@@ -38,6 +38,8 @@
 // as one contiguous 256-byte segment per word.  Rows longer than one item
 // ("hubs") combine their items with atomics (sv for MFBF, a per-hub
 // accumulator for MFBr followed by a finalisation pass).
+#include <algorithm>
+
 #include "internal.cuh"
 
 namespace mfbc {
@@ -65,6 +67,13 @@ void level_carve(Carver& c, const DevGraph& g, int nb, int Lcap, int64_t list_ca
   s.list_cap = list_cap;
   s.lists = c.take<int32_t>((size_t)list_cap);
   s.zacc = c.take<double>((size_t)(g.items_out.nhub > 0 ? g.items_out.nhub : 1) * nb);
+  // pair / segment buffers of one product round; a round that overflows them
+  // is split over halves of the item range
+  const int64_t items = std::max(g.items_in.count, g.items_out.count);
+  s.pair_cap = (uint32_t)std::min<int64_t>(0x7fffffff, std::max<int64_t>(1 << 16, g.nnz * s.W / 2));
+  s.seg_cap = (uint32_t)std::min<int64_t>(0x7fffffff, std::max<int64_t>(1 << 16, items * s.W));
+  s.pairs = c.take<uint2>((size_t)s.pair_cap);
+  s.segs = c.take<uint4>((size_t)s.seg_cap);
   s.src = c.take<int32_t>((size_t)nb);
   s.ctr = c.take<Counters>(1);
 }
@@ -121,134 +130,107 @@ __global__ void k_lvl_visit(const int32_t* __restrict__ list, uint32_t count, in
   }
 }
 
-// Per-warp shared memory of the gather kernels.
+// Per-warp shared memory of the pair kernels.
 struct WarpSmem {
   int32_t su[32];                            // member neighbour ids of the item
   uint32_t sF[32][33];                       // member q's masked frontier word j (padded: no bank conflicts)
-  uint16_t pr[1024];                         // (member, word) pairs with a non-zero mask, word-major
 };
 constexpr size_t LVL_SMEM = sizeof(WarpSmem) * LVL_WARPS;
+
 #ifndef MFBC_GATHER_U
-#define MFBC_GATHER_U 4
+#define MFBC_GATHER_U 8
 #endif
-#ifndef MFBC_LVL_MIN_BLOCKS
-#define MFBC_LVL_MIN_BLOCKS 4
-#endif
-constexpr int GATHER_U = MFBC_GATHER_U;      // loads per gather round (two rounds in flight)
+constexpr int GATHER_U = MFBC_GATHER_U;      // gather loads in flight per warp
 
 // Item metadata: first arc (bits 0..39), arc count (bits 40..45), multi-item row (bit 46).
 __device__ __forceinline__ int64_t meta_beg(int64_t m) { return m & ((1ll << 40) - 1); }
 __device__ __forceinline__ int meta_len(int64_t m) { return (int)((m >> 40) & 63); }
 __device__ __forceinline__ bool meta_multi(int64_t m) { return (m >> 46) & 1; }
 
-// Word-major list of the (member q, word j) pairs whose mask sF[q][j] is
-// non-zero; only the words in `words` can hold pairs.
-__device__ __forceinline__ int build_pairs(WarpSmem& w, int nm, uint32_t words, uint32_t* haspair) {
+// Segment header: (v, first pair, count | word << 8 | multi << 16, column bits).
+__device__ __forceinline__ uint4 make_seg(int32_t v, uint32_t pb, int cnt, int j, bool multi, uint32_t bits) {
+  return make_uint4((uint32_t)v, pb, (uint32_t)cnt | ((uint32_t)j << 8) | ((uint32_t)multi << 16), bits);
+}
+
+// Emit the (member, mask) pairs of one item, word by word over `words`
+// (ascending), as segments into the level's pair and segment buffers.  The
+// counts are reserved with one atomic per buffer.  Returns false (and writes
+// nothing) when the buffers are full.
+__device__ __forceinline__ bool emit_pairs(const WarpSmem& w, int nm, int32_t v, bool multi, uint32_t words,
+                                           uint32_t colbits, uint2* pairs, uint4* segs, uint32_t* work,
+                                           uint32_t pair_cap, uint32_t seg_cap, unsigned long long* npairs) {
   const unsigned lane = lane_id();
   const uint32_t lt = (1u << lane) - 1u;
-  int P = 0;
-  uint32_t hp = 0;
-  while (words) {
-    const int j = __ffs(words) - 1;
-    words &= words - 1;
+  int mycnt = 0;
+  for (uint32_t wl = words; wl; wl &= wl - 1) {
+    const int j = __ffs(wl) - 1;
+    const uint32_t mk = __ballot_sync(0xffffffffu, ((int)lane < nm) && w.sF[lane][j] != 0u);
+    if ((int)lane == j) mycnt = __popc(mk);
+  }
+  int incl = mycnt;
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, incl, o);
+    if ((int)lane >= o) incl += y;
+  }
+  const int excl = incl - mycnt;
+  const uint32_t P = (uint32_t)__shfl_sync(0xffffffffu, incl, 31);
+  const uint32_t S = (uint32_t)__popc(words);
+  uint32_t pb = 0, sb = 0;
+  if (lane == 0) {
+    pb = P ? atomicAdd(&work[0], P) : 0u;
+    sb = atomicAdd(&work[1], S);
+  }
+  pb = __shfl_sync(0xffffffffu, pb, 0);
+  sb = __shfl_sync(0xffffffffu, sb, 0);
+  if ((uint64_t)pb + P > pair_cap || (uint64_t)sb + S > seg_cap) {
+    if (lane == 0) atomicOr(&work[3], 1u);
+    return false;
+  }
+  if (npairs) *npairs += P;
+  int r = 0;
+  for (uint32_t wl = words; wl; wl &= wl - 1, r++) {
+    const int j = __ffs(wl) - 1;
     const bool nz = ((int)lane < nm) && w.sF[lane][j] != 0u;
     const uint32_t mk = __ballot_sync(0xffffffffu, nz);
-    if (nz) w.pr[P + __popc(mk & lt)] = (uint16_t)(lane | (j << 5));
-    P += __popc(mk);
-    if (mk) hp |= 1u << j;
+    const uint32_t off = (uint32_t)__shfl_sync(0xffffffffu, excl, j);
+    const uint32_t bits = __shfl_sync(0xffffffffu, colbits, j);
+    if (nz) pairs[pb + off + __popc(mk & lt)] = make_uint2((uint32_t)w.su[lane], w.sF[lane][j]);
+    if (lane == 0) segs[sb + r] = make_seg(v, pb + off, __popc(mk), j, multi, bits);
   }
-  __syncwarp();
-  *haspair = hp;
-  return P;
+  return true;
 }
 
-// Sum, per word, the gathered values of the pairs; FLUSH(j, acc) is called once
-// per word with pairs, in word order, by the whole warp (lane = column).
-template <class Flush>
-__device__ __forceinline__ void gather_issue(const WarpSmem& w, int P, int p0, const double* sv, int nb,
-                                             unsigned long long* ngather, double (&x)[GATHER_U]) {
-  const unsigned lane = lane_id();
-#pragma unroll
-  for (int t = 0; t < GATHER_U; t++) {
-    x[t] = 0.0;
-    const int p = p0 + t;
-    if (p < P) {
-      const uint32_t pr = w.pr[p];
-      const int q = pr & 31, j = pr >> 5;
-      if ((w.sF[q][j] >> lane) & 1u) {
-        x[t] = __ldg(&sv[(size_t)w.su[q] * nb + j * 32 + lane]);
-        if (ngather) (*ngather)++;
-      }
-    }
-  }
-}
+// Work items are handed out in groups of 32 (hub items cost far more than
+// leaf items); the group counter is zeroed before each launch.
+#define FOR_ITEM_GROUPS(ib, ie, counter)                                                    \
+  for (;;) {                                                                              \
+    uint32_t grp_ = 0;                                                                    \
+    if (lane == 0) grp_ = atomicAdd(counter, 1u);                                         \
+    const uint64_t base = (uint64_t)(ib) + (uint64_t)__shfl_sync(0xffffffffu, grp_, 0) * 32; \
+    if (base >= (uint64_t)(ie)) break;
 
-template <class Flush>
-__device__ __forceinline__ void gather_consume(const WarpSmem& w, int P, int p0, const double (&x)[GATHER_U],
-                                               double& acc, int& curj, Flush& flush) {
-#pragma unroll
-  for (int t = 0; t < GATHER_U; t++) {
-    const int p = p0 + t;
-    if (p < P) {
-      const int j = w.pr[p] >> 5;
-      if (j != curj) {
-        if (curj >= 0) flush(curj, acc);
-        acc = 0.0;
-        curj = j;
-      }
-      acc += x[t];
-    }
-  }
-}
-
-// Sum, per word, the gathered values of the pairs; FLUSH(j, acc) is called once
-// per word with pairs, in word order, by the whole warp (lane = column).
-// Rounds of GATHER_U loads are double-buffered: the next round is in flight
-// while the previous one is summed.
-template <class Flush>
-__device__ __forceinline__ void gather_pairs(const WarpSmem& w, int P, const double* sv, int nb,
-                                             unsigned long long* ngather, Flush flush) {
-  double acc = 0.0;
-  int curj = -1;
-  double xa[GATHER_U], xb[GATHER_U];
-  if (P > 0) gather_issue<Flush>(w, P, 0, sv, nb, ngather, xa);
-  for (int p0 = 0; p0 < P; p0 += 2 * GATHER_U) {
-    const bool more = p0 + GATHER_U < P;
-    if (more) gather_issue<Flush>(w, P, p0 + GATHER_U, sv, nb, ngather, xb);
-    gather_consume(w, P, p0, xa, acc, curj, flush);
-    if (more) {
-      if (p0 + 2 * GATHER_U < P) gather_issue<Flush>(w, P, p0 + 2 * GATHER_U, sv, nb, ngather, xa);
-      gather_consume(w, P, p0 + GATHER_U, xb, acc, curj, flush);
-    }
-  }
-  if (curj >= 0) flush(curj, acc);
-}
-
-// MFBF product of level l (see file comment).
-__global__ void __launch_bounds__(LVL_WARPS * 32, MFBC_LVL_MIN_BLOCKS) k_lvl_fwd(
-    int64_t nitems, const int32_t* __restrict__ item_v, const int64_t* __restrict__ item_meta,
-    const int32_t* __restrict__ col_t, int W, int nb, const uint32_t* __restrict__ full,
-    const uint32_t* __restrict__ V, const uint32_t* __restrict__ Fl, const uint32_t* __restrict__ mem_l,
-    uint32_t* Fn, uint32_t* mem_n, double* sv, int32_t* list_n, uint32_t* count_n, int64_t cap_n,
-    uint32_t* flags, uint32_t* next_group, unsigned long long* bytes, unsigned long long* stat) {
+// MFBF pairs of level l (see file comment): for items [ib, ie) of rows not yet
+// reached by every column, the masks F_l(u) & ~visited(v) of the in-neighbours
+// u in F_l, the next frontier bits F_{l+1}(v), and the level-(l+1) list.
+__global__ void __launch_bounds__(LVL_WARPS * 32) k_lvl_fwd_pairs(
+    int64_t ib, int64_t ie, const int32_t* __restrict__ item_v, const int64_t* __restrict__ item_meta,
+    const int32_t* __restrict__ col_t, int W, const uint32_t* __restrict__ full, const uint32_t* __restrict__ V,
+    const uint32_t* __restrict__ Fl, const uint32_t* __restrict__ mem_l, uint32_t* Fn, uint32_t* mem_n,
+    int32_t* list_n, uint32_t* count_n, int64_t cap_n, uint32_t* flags, uint32_t* next_group, uint2* pairs,
+    uint4* segs, uint32_t* work, uint32_t pair_cap, uint32_t seg_cap, unsigned long long* bytes,
+    unsigned long long* stat) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   WarpSmem& sm = reinterpret_cast<WarpSmem*>(smem_raw)[threadIdx.x >> 5];
   const unsigned lane = lane_id();
   const uint32_t lt = (1u << lane) - 1u;
-  unsigned long long nbytes = 0, ngather = 0, npairs = 0, nvals = 0;
-  unsigned long long* pg = bytes ? &nvals : nullptr;
-  // groups of 32 items are handed out dynamically (hub items cost far more than leaf items)
-  for (;;) {
-    uint32_t grp = 0;
-    if (lane == 0) grp = atomicAdd(next_group, 1u);
-    const uint64_t base = (uint64_t)__shfl_sync(0xffffffffu, grp, 0) * 32;
-    if (base >= (uint64_t)nitems) break;
+  unsigned long long nbytes = 0, npairs = 0;
+  FOR_ITEM_GROUPS(ib, ie, next_group)
     // lane-parallel precheck of 32 items: skip rows already reached by every column
     const uint64_t myit = base + lane;
     int32_t myv = 0;
     int64_t mymeta = 0;
     bool act = false;
-    if (myit < (uint64_t)nitems) {
+    if (myit < (uint64_t)ie) {
       myv = item_v[myit];
       mymeta = item_meta[myit];
       act = !test_bit(full, myv);
@@ -301,21 +283,7 @@ __global__ void __launch_bounds__(LVL_WARPS * 32, MFBC_LVL_MIN_BLOCKS) k_lvl_fwd
       if (bytes) nbytes += 4ull * W * (nm + 1);
       const uint32_t cw = __ballot_sync(0xffffffffu, cand != 0u);
       if (!cw) continue;
-      uint32_t haspair;
-      const int P = build_pairs(sm, nm, cw, &haspair);
-      if (bytes) npairs += P;
-      const size_t vrow = (size_t)v * nb;
-      gather_pairs(sm, P, sv, nb, pg, [&](int j, double acc) {
-        const uint32_t cj = __shfl_sync(0xffffffffu, cand, j);
-        if ((cj >> lane) & 1u) {
-          // a multiplicity at or above 2^53 may have been rounded (flags bit 1)
-          double tot = acc;
-          if (multi) tot += atomicAdd(&sv[vrow + j * 32 + lane], acc);
-          else sv[vrow + j * 32 + lane] = acc;
-          if (tot >= 9007199254740992.0) atomicOr(flags, 2u);
-          if (bytes) ngather++;
-        }
-      });
+      emit_pairs(sm, nm, v, multi, cw, cand, pairs, segs, work, pair_cap, seg_cap, bytes ? &npairs : nullptr);
       if ((int)lane < W && cand) {
         if (multi) atomicOr(&Fn[(size_t)v * W + lane], cand);
         else Fn[(size_t)v * W + lane] = cand;
@@ -331,43 +299,35 @@ __global__ void __launch_bounds__(LVL_WARPS * 32, MFBC_LVL_MIN_BLOCKS) k_lvl_fwd
       __syncwarp();
     }
   }
-  if (bytes) {
-    ngather += nvals;
-    for (int o = 16; o; o >>= 1) ngather += __shfl_xor_sync(0xffffffffu, ngather, o);
-    for (int o = 16; o; o >>= 1) nvals += __shfl_xor_sync(0xffffffffu, nvals, o);
-    if (lane == 0) {
-      atomicAdd(bytes, nbytes + 8ull * ngather);
-      atomicAdd(&stat[0], npairs);
-      atomicAdd(&stat[2], nvals);
-    }
+  if (bytes && lane == 0) {
+    atomicAdd(bytes, nbytes + 16ull * npairs);
+    atomicAdd(&stat[0], npairs);
   }
 }
 
-// MFBr gather of level l >= 1 (see file comment).
-__global__ void __launch_bounds__(LVL_WARPS * 32, MFBC_LVL_MIN_BLOCKS) k_lvl_bwd(
-    int64_t nitems, const int32_t* __restrict__ item_v, const int64_t* __restrict__ item_meta,
-    const int32_t* __restrict__ col, const int32_t* __restrict__ hub_of, int W, int nb,
-    const uint32_t* __restrict__ Fl, const uint32_t* __restrict__ mem_l, const uint32_t* __restrict__ Fn,
-    const uint32_t* __restrict__ mem_n, double* sv, double* zacc, double* lambda, uint32_t* next_group,
-    unsigned long long* bytes, unsigned long long* stat) {
+// MFBr pairs of level l >= 1: for items [ib, ie) of rows with a column at
+// level l, the masks F_{l+1}(u) & F_l(v) of the out-neighbours u in F_{l+1}.
+// Every level-l word of a single-item row gets a segment (its columns are
+// finalised by the gather even without successors); multi-item rows only emit
+// words with pairs (their finalisation is k_lvl_hub_final).
+__global__ void __launch_bounds__(LVL_WARPS * 32) k_lvl_bwd_pairs(
+    int64_t ib, int64_t ie, const int32_t* __restrict__ item_v, const int64_t* __restrict__ item_meta,
+    const int32_t* __restrict__ col, int W, const uint32_t* __restrict__ Fl, const uint32_t* __restrict__ mem_l,
+    const uint32_t* __restrict__ Fn, const uint32_t* __restrict__ mem_n, uint32_t* next_group, uint2* pairs,
+    uint4* segs, uint32_t* work, uint32_t pair_cap, uint32_t seg_cap, unsigned long long* bytes,
+    unsigned long long* stat) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   WarpSmem& sm = reinterpret_cast<WarpSmem*>(smem_raw)[threadIdx.x >> 5];
   const unsigned lane = lane_id();
   const uint32_t lt = (1u << lane) - 1u;
-  unsigned long long nbytes = 0, ngather = 0, npairs = 0, nvals = 0;
-  unsigned long long* pg = bytes ? &nvals : nullptr;
-  // groups of 32 items are handed out dynamically (hub items cost far more than leaf items)
-  for (;;) {
-    uint32_t grp = 0;
-    if (lane == 0) grp = atomicAdd(next_group, 1u);
-    const uint64_t base = (uint64_t)__shfl_sync(0xffffffffu, grp, 0) * 32;
-    if (base >= (uint64_t)nitems) break;
-    // lane-parallel precheck of 32 items: only rows with a source at level l
+  unsigned long long nbytes = 0, npairs = 0;
+  FOR_ITEM_GROUPS(ib, ie, next_group)
+    // lane-parallel precheck of 32 items: only rows with a column at level l
     const uint64_t myit = base + lane;
     int32_t myv = 0;
     int64_t mymeta = 0;
     bool act = false;
-    if (myit < (uint64_t)nitems) {
+    if (myit < (uint64_t)ie) {
       myv = item_v[myit];
       mymeta = item_meta[myit];
       act = test_bit(mem_l, myv);
@@ -408,57 +368,143 @@ __global__ void __launch_bounds__(LVL_WARPS * 32, MFBC_LVL_MIN_BLOCKS) k_lvl_bwd
       const int nm = __popc(mm);
       if (isMem) sm.su[__popc(mm & lt)] = u;
       __syncwarp();
+      uint32_t any = 0;
 #pragma unroll 4
       for (int q = 0; q < nm; q++) {
         const uint32_t f = (int)lane < W ? __ldg(&Fn[(size_t)sm.su[q] * W + lane]) : 0u;
         sm.sF[q][lane] = f & Fv;
+        any |= f & Fv;
       }
       __syncwarp();
       if (bytes) nbytes += 4ull * W * (nm + 1);
-      uint32_t haspair;
-      const uint32_t fw = __ballot_sync(0xffffffffu, Fv != 0u);
-      const int P = build_pairs(sm, nm, fw, &haspair);
-      if (bytes) npairs += P;
-      const size_t vrow = (size_t)v * nb;
-      const int32_t hub = multi ? hub_of[v] : -1;
-      double lam = 0.0;
-      auto finish = [&](int j, double acc) {
-        const uint32_t fj = __shfl_sync(0xffffffffu, Fv, j);
-        if ((fj >> lane) & 1u) {
-          if (multi) {
-            atomicAdd(&zacc[(size_t)hub * nb + j * 32 + lane], acc);
-            if (bytes) ngather++;
-          } else {
-            const double sg = sv[vrow + j * 32 + lane];
-            lam += acc * sg;
-            sv[vrow + j * 32 + lane] = acc + 1.0 / sg;
-            if (bytes) ngather += 2;
-          }
-        }
-      };
-      gather_pairs(sm, P, sv, nb, pg, finish);
-      if (!multi) {
-        // columns of level l whose word had no successor pair: zeta = 0
-        uint32_t rest = fw & ~haspair;
-        while (rest) {
-          const int j = __ffs(rest) - 1;
-          rest &= rest - 1;
-          finish(j, 0.0);
-        }
-        for (int o = 16; o; o >>= 1) lam += __shfl_xor_sync(0xffffffffu, lam, o);
-        if (lane == 0) lambda[v] += lam;
-        if (bytes) nbytes += 16ull;
-      }
+      const uint32_t words = __ballot_sync(0xffffffffu, multi ? any != 0u : Fv != 0u);
+      if (words) emit_pairs(sm, nm, v, multi, words, Fv, pairs, segs, work, pair_cap, seg_cap,
+                            bytes ? &npairs : nullptr);
       __syncwarp();
     }
   }
+  if (bytes && lane == 0) {
+    atomicAdd(bytes, nbytes + 16ull * npairs);
+    atomicAdd(&stat[1], npairs);
+  }
+}
+
+// Segments are handed out in groups of 32; FOR_SEGMENTS binds, per segment,
+// v, pb (first pair), cnt, j (word), multi and bits (column bits).
+#define FOR_SEGMENTS(nseg, counter)                                                          \
+  for (;;) {                                                                               \
+    uint32_t grp_ = 0;                                                                     \
+    if (lane == 0) grp_ = atomicAdd(counter, 1u);                                          \
+    const uint64_t base = (uint64_t)__shfl_sync(0xffffffffu, grp_, 0) * 32;                \
+    if (base >= (uint64_t)(nseg)) break;                                                   \
+    uint4 myseg = make_uint4(0u, 0u, 0u, 0u);                                              \
+    if (base + lane < (uint64_t)(nseg)) myseg = segs[base + lane];                         \
+    const int nin = (uint64_t)(nseg) - base < 32 ? (int)((uint64_t)(nseg) - base) : 32;     \
+    for (int t = 0; t < nin; t++) {                                                        \
+      const int32_t v = (int32_t)__shfl_sync(0xffffffffu, myseg.x, t);                     \
+      const uint32_t pb = __shfl_sync(0xffffffffu, myseg.y, t);                            \
+      const uint32_t z = __shfl_sync(0xffffffffu, myseg.z, t);                             \
+      const uint32_t bits = __shfl_sync(0xffffffffu, myseg.w, t);                          \
+      const int cnt = (int)(z & 0xffu), j = (int)((z >> 8) & 0xffu);                       \
+      const bool multi = (z >> 16) & 1u;
+
+// Sum over the segment's pairs of the predicated 256-byte gathers (lane = column).
+__device__ __forceinline__ double gather_segment(const uint2* __restrict__ pairs, uint32_t pb, int cnt, int j,
+                                                 const double* sv, int nb, unsigned long long* nvals) {
+  const unsigned lane = lane_id();
+  uint2 pr = make_uint2(0u, 0u);
+  if ((int)lane < cnt) pr = pairs[pb + lane];
+  double acc = 0.0;
+  for (int q0 = 0; q0 < cnt; q0 += GATHER_U) {
+    double x[GATHER_U];
+#pragma unroll
+    for (int t = 0; t < GATHER_U; t++) {
+      const uint32_t u = __shfl_sync(0xffffffffu, pr.x, (q0 + t) & 31);
+      const uint32_t m = __shfl_sync(0xffffffffu, pr.y, (q0 + t) & 31);
+      x[t] = 0.0;
+      if (q0 + t < cnt && ((m >> lane) & 1u)) {
+        x[t] = __ldg(&sv[(size_t)u * nb + j * 32 + lane]);
+        if (nvals) (*nvals)++;
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < GATHER_U; t++) acc += x[t];
+  }
+  return acc;
+}
+
+// MFBF gather of level l: sigma_bar(s,v) = sum over the segment's pairs.
+__global__ void __launch_bounds__(256) k_lvl_fwd_gather(
+    const uint4* __restrict__ segs, const uint32_t* nseg_p, const uint2* __restrict__ pairs, int nb, double* sv,
+    uint32_t* flags, uint32_t* next_group, unsigned long long* bytes, unsigned long long* stat) {
+  const unsigned lane = lane_id();
+  const uint32_t nseg = *nseg_p;
+  unsigned long long nvals = 0, nw = 0;
+  unsigned long long* pv = bytes ? &nvals : nullptr;
+  FOR_SEGMENTS(nseg, next_group)
+      const double acc = gather_segment(pairs, pb, cnt, j, sv, nb, pv);
+      if ((bits >> lane) & 1u) {
+        // a multiplicity at or above 2^53 may have been rounded (flags bit 1)
+        double tot = acc;
+        const size_t idx = (size_t)v * nb + j * 32 + lane;
+        if (multi) tot += atomicAdd(&sv[idx], acc);
+        else sv[idx] = acc;
+        if (tot >= 9007199254740992.0) atomicOr(flags, 2u);
+        if (bytes) nw++;
+      }
+    }
+  }
   if (bytes) {
-    ngather += nvals;
-    for (int o = 16; o; o >>= 1) ngather += __shfl_xor_sync(0xffffffffu, ngather, o);
-    for (int o = 16; o; o >>= 1) nvals += __shfl_xor_sync(0xffffffffu, nvals, o);
+    for (int o = 16; o; o >>= 1) {
+      nvals += __shfl_xor_sync(0xffffffffu, nvals, o);
+      nw += __shfl_xor_sync(0xffffffffu, nw, o);
+    }
     if (lane == 0) {
-      atomicAdd(bytes, nbytes + 8ull * ngather);
-      atomicAdd(&stat[1], npairs);
+      atomicAdd(bytes, 8ull * (nvals + nw));
+      atomicAdd(&stat[2], nvals);
+    }
+  }
+}
+
+// MFBr gather of level l: zeta(s,v) = sum over the segment's pairs of the
+// successors' values; single-item rows are finalised here (lambda, value
+// zeta + 1/sigma_bar), multi-item rows add into their hub accumulator.
+__global__ void __launch_bounds__(256) k_lvl_bwd_gather(
+    const uint4* __restrict__ segs, const uint32_t* nseg_p, const uint2* __restrict__ pairs, int nb,
+    const int32_t* __restrict__ hub_of, double* sv, double* zacc, double* lambda, uint32_t* next_group,
+    unsigned long long* bytes, unsigned long long* stat) {
+  const unsigned lane = lane_id();
+  const uint32_t nseg = *nseg_p;
+  unsigned long long nvals = 0, nw = 0;
+  unsigned long long* pv = bytes ? &nvals : nullptr;
+  FOR_SEGMENTS(nseg, next_group)
+      const double acc = gather_segment(pairs, pb, cnt, j, sv, nb, pv);
+      const bool mine = (bits >> lane) & 1u;
+      if (multi) {
+        const int32_t hub = hub_of[v];
+        if (mine) atomicAdd(&zacc[(size_t)hub * nb + j * 32 + lane], acc);
+        if (bytes && mine) nw++;
+      } else {
+        double lam = 0.0;
+        if (mine) {
+          const size_t idx = (size_t)v * nb + j * 32 + lane;
+          const double sg = sv[idx];
+          lam = acc * sg;
+          sv[idx] = acc + 1.0 / sg;
+          if (bytes) nw += 2;
+        }
+        for (int o = 16; o; o >>= 1) lam += __shfl_xor_sync(0xffffffffu, lam, o);
+        if (lane == 0 && lam != 0.0) atomicAdd(&lambda[v], lam);
+      }
+    }
+  }
+  if (bytes) {
+    for (int o = 16; o; o >>= 1) {
+      nvals += __shfl_xor_sync(0xffffffffu, nvals, o);
+      nw += __shfl_xor_sync(0xffffffffu, nw, o);
+    }
+    if (lane == 0) {
+      atomicAdd(bytes, 8ull * (nvals + nw));
       atomicAdd(&stat[3], nvals);
     }
   }
@@ -558,8 +604,8 @@ static inline unsigned grid_for_items(int64_t items, unsigned cap) {
 static void set_smem_attrs() {
   static bool done = false;
   if (done) return;
-  cudaFuncSetAttribute(k_lvl_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LVL_SMEM);
-  cudaFuncSetAttribute(k_lvl_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LVL_SMEM);
+  cudaFuncSetAttribute(k_lvl_fwd_pairs, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LVL_SMEM);
+  cudaFuncSetAttribute(k_lvl_bwd_pairs, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LVL_SMEM);
   done = true;
 }
 
@@ -575,6 +621,69 @@ struct LevelPlan {                 // host-side level bookkeeping of one batch
 };
 static thread_local LevelPlan tl_plan;
 
+static const unsigned kPairGrid = 152u * 6u;     // resident blocks of the pair kernels
+static const unsigned kGatherGrid = 152u * 8u;   // resident blocks of the gather kernels
+
+// One MFBF (fwd) or MFBr product of level l over the items [ib, ie): the pair
+// kernel, a check of the pair buffers, then the gather kernel.  When the
+// buffers overflow the range is split in halves; the pair kernels' side
+// effects (frontier bits, membership, list appends) are idempotent, so a
+// re-run of a range is harmless.
+static mfbc_status level_round(RunCtx& rc, LevelState& s, bool fwd, int l, int64_t ib, int64_t ie, int nactive,
+                               int64_t off_n, double* lambda) {
+  const DevGraph& g = *rc.g;
+  const int32_t n = g.n;
+  const int nb = s.nb, W = s.W;
+  cudaStream_t st = rc.stream;
+  unsigned long long* B = rc.prof->count_bytes ? s.ctr->bytes : nullptr;
+  const uint32_t* Fl = s.F + (size_t)l * n * W;
+  const uint32_t* Ml = s.member + (size_t)l * s.mw;
+  uint32_t* Fn = s.F + (size_t)(l + 1) * n * W;
+  uint32_t* Mn = s.member + (size_t)(l + 1) * s.mw;
+  (void)nactive;
+  MFBC_CUDA_TRY(cudaMemsetAsync(s.ctr->work, 0, sizeof(uint32_t) * 4, st), rc.err);
+  MFBC_CUDA_TRY(cudaMemsetAsync(&s.ctr->list_count[2], 0, sizeof(uint32_t), st), rc.err);
+  const unsigned pgrid = grid_for_items(ie - ib, kPairGrid);
+  if (fwd)
+    PROF(K_LVL_FWD, (k_lvl_fwd_pairs<<<pgrid, LVL_WARPS * 32, LVL_SMEM, st>>>(
+                        ib, ie, g.items_in.v, g.items_in.beg, g.col_t, W, s.full, s.V, Fl, Ml, Fn, Mn,
+                        s.lists + off_n, &s.ctr->list_count[0], s.list_cap - off_n, &s.ctr->flags,
+                        &s.ctr->list_count[2], s.pairs, s.segs, s.ctr->work, s.pair_cap, s.seg_cap,
+                        B ? B + K_LVL_FWD : nullptr, s.ctr->stat)));
+  else
+    PROF(K_LVL_BWD, (k_lvl_bwd_pairs<<<pgrid, LVL_WARPS * 32, LVL_SMEM, st>>>(
+                        ib, ie, g.items_out.v, g.items_out.beg, g.col, W, Fl, Ml, Fn, Mn,
+                        &s.ctr->list_count[2], s.pairs, s.segs, s.ctr->work, s.pair_cap, s.seg_cap,
+                        B ? B + K_LVL_BWD : nullptr, s.ctr->stat)));
+  MFBC_CUDA_TRY(cudaMemcpyAsync(rc.h_ctr, s.ctr->list_count, sizeof(uint32_t) * 9, cudaMemcpyDeviceToHost, st), rc.err);
+  MFBC_CUDA_TRY(cudaStreamSynchronize(st), rc.err);
+  rc.prof->drain();
+  if (rc.h_ctr[8]) {
+    if (ie - ib <= 32) {
+      if (rc.err) *rc.err = "level pair buffers cannot hold one group of 32 work items";
+      return MFBC_ERR_OOM;
+    }
+    const int64_t mid = ib + ((ie - ib) / 2 + 31) / 32 * 32;
+    mfbc_status e = level_round(rc, s, fwd, l, ib, mid, nactive, off_n, lambda);
+    if (e) return e;
+    return level_round(rc, s, fwd, l, mid, ie, nactive, off_n, lambda);
+  }
+  const uint32_t nseg = rc.h_ctr[6];
+  if (!nseg) return MFBC_OK;
+  MFBC_CUDA_TRY(cudaMemsetAsync(&s.ctr->work[2], 0, sizeof(uint32_t), st), rc.err);
+  const unsigned ggrid = grid_for_items(nseg, kGatherGrid);
+  if (fwd)
+    PROF(K_LVL_FWD_G, (k_lvl_fwd_gather<<<ggrid, 256, 0, st>>>(s.segs, &s.ctr->work[1], s.pairs, nb, s.sv,
+                                                              &s.ctr->flags, &s.ctr->work[2],
+                                                              B ? B + K_LVL_FWD_G : nullptr, s.ctr->stat)));
+  else
+    PROF(K_LVL_BWD_G, (k_lvl_bwd_gather<<<ggrid, 256, 0, st>>>(s.segs, &s.ctr->work[1], s.pairs, nb,
+                                                              g.items_out.hub_of, s.sv, s.zacc, lambda,
+                                                              &s.ctr->work[2], B ? B + K_LVL_BWD_G : nullptr,
+                                                              s.ctr->stat)));
+  return MFBC_OK;
+}
+
 mfbc_status level_batch(RunCtx& rc, LevelState& s, const int32_t* d_src_batch, int nactive,
                         double* lambda, bool backward, int* levels_out, bool* levels_exceeded,
                         int64_t* fwd_iters, int64_t* bwd_iters) {
@@ -586,7 +695,6 @@ mfbc_status level_batch(RunCtx& rc, LevelState& s, const int32_t* d_src_batch, i
   *levels_exceeded = false;
   *levels_out = -1;
   if (n == 0) return MFBC_OK;
-  const unsigned big_grid = 152u * MFBC_LVL_MIN_BLOCKS;  // resident blocks of the level gather kernels
   set_smem_attrs();
 
   fill_i32(s.src, -1, (size_t)nb, st);
@@ -616,12 +724,8 @@ mfbc_status level_batch(RunCtx& rc, LevelState& s, const int32_t* d_src_batch, i
     if (l + 1 >= s.Lcap) { *levels_exceeded = true; level_reset(rc, s, l); return MFBC_ERR_NO_CONVERGENCE; }
     const int64_t off_n = P.off[l] + cl;
     MFBC_CUDA_TRY(cudaMemsetAsync(&s.ctr->list_count[0], 0, sizeof(uint32_t), st), rc.err);
-    MFBC_CUDA_TRY(cudaMemsetAsync(&s.ctr->list_count[2], 0, sizeof(uint32_t), st), rc.err);
-    PROF(K_LVL_FWD, (k_lvl_fwd<<<grid_for_items(g.items_in.count, big_grid), LVL_WARPS * 32, LVL_SMEM, st>>>(
-                        g.items_in.count, g.items_in.v, g.items_in.beg, g.col_t, W, nb, s.full,
-                        s.V, Fl(l), Ml(l), Fl(l + 1), Ml(l + 1), s.sv, s.lists + off_n, &s.ctr->list_count[0],
-                        s.list_cap - off_n, &s.ctr->flags, &s.ctr->list_count[2], B ? B + K_LVL_FWD : nullptr,
-                        s.ctr->stat)));
+    mfbc_status e = level_round(rc, s, true, l, 0, g.items_in.count, nactive, off_n, nullptr);
+    if (e) return e;
     MFBC_CUDA_TRY(cudaMemcpyAsync(rc.h_ctr, s.ctr->list_count, sizeof(uint32_t) * 5, cudaMemcpyDeviceToHost, st), rc.err);
     MFBC_CUDA_TRY(cudaStreamSynchronize(st), rc.err);
     rc.prof->drain();
@@ -637,11 +741,8 @@ mfbc_status level_batch(RunCtx& rc, LevelState& s, const int32_t* d_src_batch, i
 
   // MFBr over levels L .. 1 (level L+1 is empty and all-zero)
   for (int l = L; l >= 1; l--) {
-    MFBC_CUDA_TRY(cudaMemsetAsync(&s.ctr->list_count[2], 0, sizeof(uint32_t), st), rc.err);
-    PROF(K_LVL_BWD, (k_lvl_bwd<<<grid_for_items(g.items_out.count, big_grid), LVL_WARPS * 32, LVL_SMEM, st>>>(
-                        g.items_out.count, g.items_out.v, g.items_out.beg, g.col, g.items_out.hub_of,
-                        W, nb, Fl(l), Ml(l), Fl(l + 1), Ml(l + 1), s.sv, s.zacc, lambda, &s.ctr->list_count[2],
-                        B ? B + K_LVL_BWD : nullptr, s.ctr->stat)));
+    mfbc_status e = level_round(rc, s, false, l, 0, g.items_out.count, nactive, 0, lambda);
+    if (e) return e;
     if (g.items_out.nhub)
       PROF(K_LVL_HUB, (k_lvl_hub_final<<<grid_for_items(g.items_out.nhub, 152 * 8), LVL_WARPS * 32, 0, st>>>(
                           g.items_out.hubs, g.items_out.nhub, W, nb, Fl(l), Ml(l), s.sv, s.zacc, lambda,

@@ -291,7 +291,7 @@ def test_profile_reports_kernels():
         lam, prof = G.bc(srcs, n_b=64, path=p, profile=True, count_bytes=True)
         assert prof["batches"] == 1 and prof["fwd_iters"] > 0 and prof["bwd_iters"] > 0
         ks = prof["kernels"]
-        main = "level_mfbf_pull" if p == mfbc.PATH_LEVEL else "mfbf_relax_min"
+        main = "level_mfbf_gather" if p == mfbc.PATH_LEVEL else "mfbf_relax_min"
         assert ks[main]["launches"] > 0 and ks[main]["ms"] > 0 and ks[main]["bytes"] > 0
     G.close()
 
