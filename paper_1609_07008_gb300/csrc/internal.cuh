@@ -62,7 +62,7 @@ struct KStat {
 enum KId {
   K_FILL = 0, K_SEED, K_RELAX_MIN, K_RELAX_TIE, K_ACCUM, K_COUNTERS, K_PROPAGATE, K_FINAL,
   K_LAMBDA, K_CLEAR, K_LVL_FWD, K_LVL_VISIT, K_LVL_BWD, K_LVL_HUB, K_LVL_RESET, K_OUTPUT,
-  K_LVL_FWD_G, K_LVL_BWD_G, K_NUM
+  K_LVL_FWD_G, K_LVL_BWD_G, K_LVL_SPLIT, K_NUM
 };
 
 // Device-side counters of algorithmic bytes, one slot per kernel id.

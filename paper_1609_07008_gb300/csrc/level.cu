@@ -389,9 +389,77 @@ __global__ void __launch_bounds__(LVL_WARPS * 32) k_lvl_bwd_pairs(
   }
 }
 
-// Segments are handed out in groups of 32; FOR_SEGMENTS binds, per segment,
-// v, pb (first pair), cnt, j (word), multi and bits (column bits).
-#define FOR_SEGMENTS(nseg, counter)                                                          \
+// Gather over a group of up to 32 segments (lane k holds segment k's header).
+// The group's pairs are flattened with a warp scan and streamed in chunks of
+// 32 (lane = pair for the pair loads, lane = column for the gathers); rounds
+// of GATHER_U predicated 256-byte gathers are double-buffered across segment
+// boundaries.  FLUSH(k, acc) is called once per segment with pairs, in order,
+// by the whole warp; segments without pairs are not flushed.
+template <class Flush>
+__device__ __forceinline__ void gather_group(const uint4& myseg, int nin, const uint2* __restrict__ pairs,
+                                             const double* sv, int nb, unsigned long long* nvals, Flush flush) {
+  const unsigned lane = lane_id();
+  const int mycnt = (int)lane < nin ? (int)(myseg.z & 0xffu) : 0;
+  int incl = mycnt;
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, incl, o);
+    if ((int)lane >= o) incl += y;
+  }
+  const int excl = incl - mycnt;
+  const int T = __shfl_sync(0xffffffffu, incl, 31);
+  const int myj = (int)((myseg.z >> 8) & 0xffu);
+  double acc = 0.0;
+  int cur = -1;
+  for (int p0 = 0; p0 < T; p0 += 32) {
+    // lane-parallel load of flattened pairs p0 .. p0+31
+    const int p = p0 + (int)lane;
+    int t = 0;
+#pragma unroll
+    for (int step = 16; step; step >>= 1) {            // largest t with excl_t <= p
+      const int e = __shfl_sync(0xffffffffu, excl, t + step > 31 ? 31 : t + step);
+      if (t + step <= 31 && e <= p) t += step;
+    }
+    // excl is non-decreasing and empty segments share their successor's excl,
+    // so the largest such t is the segment that holds pair p
+    const uint32_t tpb = __shfl_sync(0xffffffffu, myseg.y, t);
+    const int texcl = __shfl_sync(0xffffffffu, excl, t);
+    uint2 pr = make_uint2(0u, 0u);
+    if (p < T) pr = pairs[tpb + (uint32_t)(p - texcl)];
+    const int tj = __shfl_sync(0xffffffffu, myj, t);
+    const int nq = T - p0 < 32 ? T - p0 : 32;
+    for (int q0 = 0; q0 < nq; q0 += GATHER_U) {
+      double x[GATHER_U];
+      int ts[GATHER_U];
+#pragma unroll
+      for (int r = 0; r < GATHER_U; r++) {
+        const int q = (q0 + r) & 31;
+        const uint32_t u = __shfl_sync(0xffffffffu, pr.x, q);
+        const uint32_t m = __shfl_sync(0xffffffffu, pr.y, q);
+        const int jj = __shfl_sync(0xffffffffu, tj, q);
+        ts[r] = __shfl_sync(0xffffffffu, t, q);
+        x[r] = 0.0;
+        if (q0 + r < nq && ((m >> lane) & 1u)) {
+          x[r] = __ldg(&sv[(size_t)u * nb + jj * 32 + lane]);
+          if (nvals) (*nvals)++;
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < GATHER_U; r++) {
+        if (q0 + r < nq) {
+          if (ts[r] != cur) {
+            if (cur >= 0) flush(cur, acc);
+            acc = 0.0;
+            cur = ts[r];
+          }
+          acc += x[r];
+        }
+      }
+    }
+  }
+  if (cur >= 0) flush(cur, acc);
+}
+
+#define FOR_SEGMENT_GROUPS(nseg, counter)                                                    \
   for (;;) {                                                                               \
     uint32_t grp_ = 0;                                                                     \
     if (lane == 0) grp_ = atomicAdd(counter, 1u);                                          \
@@ -399,60 +467,32 @@ __global__ void __launch_bounds__(LVL_WARPS * 32) k_lvl_bwd_pairs(
     if (base >= (uint64_t)(nseg)) break;                                                   \
     uint4 myseg = make_uint4(0u, 0u, 0u, 0u);                                              \
     if (base + lane < (uint64_t)(nseg)) myseg = segs[base + lane];                         \
-    const int nin = (uint64_t)(nseg) - base < 32 ? (int)((uint64_t)(nseg) - base) : 32;     \
-    for (int t = 0; t < nin; t++) {                                                        \
-      const int32_t v = (int32_t)__shfl_sync(0xffffffffu, myseg.x, t);                     \
-      const uint32_t pb = __shfl_sync(0xffffffffu, myseg.y, t);                            \
-      const uint32_t z = __shfl_sync(0xffffffffu, myseg.z, t);                             \
-      const uint32_t bits = __shfl_sync(0xffffffffu, myseg.w, t);                          \
-      const int cnt = (int)(z & 0xffu), j = (int)((z >> 8) & 0xffu);                       \
-      const bool multi = (z >> 16) & 1u;
-
-// Sum over the segment's pairs of the predicated 256-byte gathers (lane = column).
-__device__ __forceinline__ double gather_segment(const uint2* __restrict__ pairs, uint32_t pb, int cnt, int j,
-                                                 const double* sv, int nb, unsigned long long* nvals) {
-  const unsigned lane = lane_id();
-  uint2 pr = make_uint2(0u, 0u);
-  if ((int)lane < cnt) pr = pairs[pb + lane];
-  double acc = 0.0;
-  for (int q0 = 0; q0 < cnt; q0 += GATHER_U) {
-    double x[GATHER_U];
-#pragma unroll
-    for (int t = 0; t < GATHER_U; t++) {
-      const uint32_t u = __shfl_sync(0xffffffffu, pr.x, (q0 + t) & 31);
-      const uint32_t m = __shfl_sync(0xffffffffu, pr.y, (q0 + t) & 31);
-      x[t] = 0.0;
-      if (q0 + t < cnt && ((m >> lane) & 1u)) {
-        x[t] = __ldg(&sv[(size_t)u * nb + j * 32 + lane]);
-        if (nvals) (*nvals)++;
-      }
-    }
-#pragma unroll
-    for (int t = 0; t < GATHER_U; t++) acc += x[t];
-  }
-  return acc;
-}
+    const int nin = (uint64_t)(nseg) - base < 32 ? (int)((uint64_t)(nseg) - base) : 32;
 
 // MFBF gather of level l: sigma_bar(s,v) = sum over the segment's pairs.
-__global__ void __launch_bounds__(256) k_lvl_fwd_gather(
+__global__ void __launch_bounds__(256, 4) k_lvl_fwd_gather(
     const uint4* __restrict__ segs, const uint32_t* nseg_p, const uint2* __restrict__ pairs, int nb, double* sv,
     uint32_t* flags, uint32_t* next_group, unsigned long long* bytes, unsigned long long* stat) {
   const unsigned lane = lane_id();
   const uint32_t nseg = *nseg_p;
   unsigned long long nvals = 0, nw = 0;
   unsigned long long* pv = bytes ? &nvals : nullptr;
-  FOR_SEGMENTS(nseg, next_group)
-      const double acc = gather_segment(pairs, pb, cnt, j, sv, nb, pv);
+  FOR_SEGMENT_GROUPS(nseg, next_group)
+    gather_group(myseg, nin, pairs, sv, nb, pv, [&](int k, double acc) {
+      const int32_t v = (int32_t)__shfl_sync(0xffffffffu, myseg.x, k);
+      const uint32_t z = __shfl_sync(0xffffffffu, myseg.z, k);
+      const uint32_t bits = __shfl_sync(0xffffffffu, myseg.w, k);
+      const int j = (int)((z >> 8) & 0xffu);
       if ((bits >> lane) & 1u) {
         // a multiplicity at or above 2^53 may have been rounded (flags bit 1)
         double tot = acc;
         const size_t idx = (size_t)v * nb + j * 32 + lane;
-        if (multi) tot += atomicAdd(&sv[idx], acc);
+        if ((z >> 16) & 1u) tot += atomicAdd(&sv[idx], acc);
         else sv[idx] = acc;
         if (tot >= 9007199254740992.0) atomicOr(flags, 2u);
         if (bytes) nw++;
       }
-    }
+    });
   }
   if (bytes) {
     for (int o = 16; o; o >>= 1) {
@@ -469,7 +509,7 @@ __global__ void __launch_bounds__(256) k_lvl_fwd_gather(
 // MFBr gather of level l: zeta(s,v) = sum over the segment's pairs of the
 // successors' values; single-item rows are finalised here (lambda, value
 // zeta + 1/sigma_bar), multi-item rows add into their hub accumulator.
-__global__ void __launch_bounds__(256) k_lvl_bwd_gather(
+__global__ void __launch_bounds__(256, 4) k_lvl_bwd_gather(
     const uint4* __restrict__ segs, const uint32_t* nseg_p, const uint2* __restrict__ pairs, int nb,
     const int32_t* __restrict__ hub_of, double* sv, double* zacc, double* lambda, uint32_t* next_group,
     unsigned long long* bytes, unsigned long long* stat) {
@@ -477,13 +517,19 @@ __global__ void __launch_bounds__(256) k_lvl_bwd_gather(
   const uint32_t nseg = *nseg_p;
   unsigned long long nvals = 0, nw = 0;
   unsigned long long* pv = bytes ? &nvals : nullptr;
-  FOR_SEGMENTS(nseg, next_group)
-      const double acc = gather_segment(pairs, pb, cnt, j, sv, nb, pv);
+  FOR_SEGMENT_GROUPS(nseg, next_group)
+    auto finish = [&](int k, double acc) {
+      const int32_t v = (int32_t)__shfl_sync(0xffffffffu, myseg.x, k);
+      const uint32_t z = __shfl_sync(0xffffffffu, myseg.z, k);
+      const uint32_t bits = __shfl_sync(0xffffffffu, myseg.w, k);
+      const int j = (int)((z >> 8) & 0xffu);
       const bool mine = (bits >> lane) & 1u;
-      if (multi) {
+      if ((z >> 16) & 1u) {
         const int32_t hub = hub_of[v];
-        if (mine) atomicAdd(&zacc[(size_t)hub * nb + j * 32 + lane], acc);
-        if (bytes && mine) nw++;
+        if (mine) {
+          atomicAdd(&zacc[(size_t)hub * nb + j * 32 + lane], acc);
+          if (bytes) nw++;
+        }
       } else {
         double lam = 0.0;
         if (mine) {
@@ -496,6 +542,14 @@ __global__ void __launch_bounds__(256) k_lvl_bwd_gather(
         for (int o = 16; o; o >>= 1) lam += __shfl_xor_sync(0xffffffffu, lam, o);
         if (lane == 0 && lam != 0.0) atomicAdd(&lambda[v], lam);
       }
+    };
+    gather_group(myseg, nin, pairs, sv, nb, pv, finish);
+    // segments without successor pairs: zeta = 0
+    uint32_t empty = __ballot_sync(0xffffffffu, (int)lane < nin && (myseg.z & 0xffu) == 0u);
+    while (empty) {
+      const int k = __ffs(empty) - 1;
+      empty &= empty - 1;
+      finish(k, 0.0);
     }
   }
   if (bytes) {
@@ -622,7 +676,7 @@ struct LevelPlan {                 // host-side level bookkeeping of one batch
 static thread_local LevelPlan tl_plan;
 
 static const unsigned kPairGrid = 152u * 6u;     // resident blocks of the pair kernels
-static const unsigned kGatherGrid = 152u * 8u;   // resident blocks of the gather kernels
+static const unsigned kGatherGrid = 152u * 4u;   // resident blocks of the gather kernels
 
 // One MFBF (fwd) or MFBr product of level l over the items [ib, ie): the pair
 // kernel, a check of the pair buffers, then the gather kernel.  When the
@@ -659,6 +713,7 @@ static mfbc_status level_round(RunCtx& rc, LevelState& s, bool fwd, int l, int64
   MFBC_CUDA_TRY(cudaStreamSynchronize(st), rc.err);
   rc.prof->drain();
   if (rc.h_ctr[8]) {
+    rc.prof->k[K_LVL_SPLIT].launches++;          // reported as "level_round_split"
     if (ie - ib <= 32) {
       if (rc.err) *rc.err = "level pair buffers cannot hold one group of 32 work items";
       return MFBC_ERR_OOM;
