@@ -188,6 +188,7 @@ def main():
     ap.add_argument("--ref-sources", type=int, default=64)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--sources", type=int, default=0, help="use only the first N sources (probing)")
+    ap.add_argument("--keep-order", action="store_true", help="batch sources in the given order")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -221,7 +222,7 @@ def main():
     lam = torch.empty(g.n, dtype=torch.float64, device=dev)
 
     def step(profile=False):
-        out = G.bc(d_src, n_b=nb_req, out=lam, profile=profile)
+        out = G.bc(d_src, n_b=nb_req, out=lam, profile=profile, keep_order=args.keep_order)
         if dist:
             dist.all_reduce(lam)
         return out
@@ -233,7 +234,7 @@ def main():
         torch.cuda.synchronize()
 
     # untimed pass that counts algorithmic bytes per kernel on the device
-    _, prof_bytes = G.bc(d_src, n_b=nb_req, out=lam, count_bytes=True)
+    _, prof_bytes = G.bc(d_src, n_b=nb_req, out=lam, count_bytes=True, keep_order=args.keep_order)
     for _ in range(args.warmup):
         step()
     clocks = ClockSampler(local)
@@ -272,7 +273,7 @@ def main():
     t0 = time.perf_counter()
     for _ in range(args.e2e_steps):
         with mfbc.Graph(rp, cl, None, directed=g.directed) as Ge:
-            Ge.bc(hs, n_b=nb_req, out=hl)
+            Ge.bc(hs, n_b=nb_req, out=hl, keep_order=args.keep_order)
         if dist:
             x = torch.from_numpy(hl).to(dev)
             dist.all_reduce(x)
