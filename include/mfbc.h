@@ -90,7 +90,8 @@ typedef struct {
 } mfbc_profile;
 
 typedef struct {
-  int32_t n_b;                 /* sources per batch; 0 = largest that fits; rounded up to 32 */
+  int32_t n_b;                 /* sources per batch; 0 = largest that fits; rounded up to 32
+                                  (general kernels) or 128 (level kernels) */
   int32_t path;                /* MFBC_PATH_* */
   void* stream;                /* cudaStream_t to run on; NULL = legacy default stream */
   void* workspace;             /* optional caller-owned device scratch, 256-byte aligned */

@@ -180,10 +180,12 @@ static mfbc_status make_plan(const mfbc_graph* G, int32_t nsrc, int mode, const 
   else if (path != MFBC_PATH_GENERAL && path != MFBC_PATH_LEVEL)
     return fail(MFBC_ERR_INVALID, "unknown path");
   const int maxnb = path == MFBC_PATH_LEVEL ? 1024 : 4096;
+  // the level kernels move 128 columns (four 32-column words) at a time
+  const int gran = path == MFBC_PATH_LEVEL ? 128 : 32;
   int req = opt ? opt->n_b : 0;
   if (req < 0) return fail(MFBC_ERR_INVALID, "n_b must be >= 0");
   if (req > 0) {
-    int nb = (req + 31) / 32 * 32;
+    int nb = (req + gran - 1) / gran * gran;
     if (nb > maxnb) return fail(MFBC_ERR_INVALID, "n_b too large for this path (max " + std::to_string(maxnb) + ")");
     plan_bytes(g, path, nb, nsrc, mode, host_io, p);
     return MFBC_OK;
@@ -196,11 +198,11 @@ static mfbc_status make_plan(const mfbc_graph* G, int32_t nsrc, int mode, const 
     if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) { cudaGetLastError(); return fail(MFBC_ERR_CUDA, "cudaMemGetInfo failed"); }
     budget = (size_t)(0.80 * (double)(fr + G->ws_bytes));
   }
-  int nb = std::min(maxnb, std::max(32, (nsrc + 31) / 32 * 32));
+  int nb = std::min(maxnb, std::max(gran, (nsrc + gran - 1) / gran * gran));
   while (true) {
     plan_bytes(g, path, nb, nsrc, mode, host_io, p);
-    if (p->total <= budget || nb == 32) break;
-    nb -= 32;
+    if (p->total <= budget || nb == gran) break;
+    nb -= gran;
   }
   return MFBC_OK;
 }

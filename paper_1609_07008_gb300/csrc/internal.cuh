@@ -136,7 +136,8 @@ struct LevelState {
   int32_t* lists;     // per-level vertex lists, concatenated
   int64_t list_cap;
   double* zacc;       // [nhub_out][nb] backward partial sums of multi-item vertices
-  uint2* pairs;       // (neighbour, column mask) pairs of one product round
+  uint32_t* prow;     // pairs of one product round: row index u*Q + quad
+  uint4* pmask;       //   and the pair's 128-column mask
   uint4* segs;        // segment headers of one product round
   uint32_t pair_cap, seg_cap;
   int32_t* src;       // [nb]

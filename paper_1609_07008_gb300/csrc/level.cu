@@ -69,10 +69,14 @@ void level_carve(Carver& c, const DevGraph& g, int nb, int Lcap, int64_t list_ca
   s.zacc = c.take<double>((size_t)(g.items_out.nhub > 0 ? g.items_out.nhub : 1) * nb);
   // pair / segment buffers of one product round; a round that overflows them
   // is split over halves of the item range
+  // (each arc gives at most Q pairs and each item at most Q segments per
+  // round, so these caps only bind for graphs beyond 2^31 of either)
   const int64_t items = std::max(g.items_in.count, g.items_out.count);
-  s.pair_cap = (uint32_t)std::min<int64_t>(0x7fffffff, std::max<int64_t>(1 << 16, g.nnz * s.W / 2));
-  s.seg_cap = (uint32_t)std::min<int64_t>(0x7fffffff, std::max<int64_t>(1 << 16, items * s.W));
-  s.pairs = c.take<uint2>((size_t)s.pair_cap);
+  const int64_t Q = std::max(1, s.W / 4);
+  s.pair_cap = (uint32_t)std::min<int64_t>(0x7fffffff, std::max<int64_t>(1 << 16, g.nnz * Q));
+  s.seg_cap = (uint32_t)std::min<int64_t>(0x7fffffff, std::max<int64_t>(1 << 16, items * Q));
+  s.prow = c.take<uint32_t>((size_t)s.pair_cap);
+  s.pmask = c.take<uint4>((size_t)s.pair_cap);
   s.segs = c.take<uint4>((size_t)s.seg_cap);
   s.src = c.take<int32_t>((size_t)nb);
   s.ctr = c.take<Counters>(1);
@@ -138,7 +142,7 @@ struct WarpSmem {
 constexpr size_t LVL_SMEM = sizeof(WarpSmem) * LVL_WARPS;
 
 #ifndef MFBC_GATHER_U
-#define MFBC_GATHER_U 8
+#define MFBC_GATHER_U 2
 #endif
 constexpr int GATHER_U = MFBC_GATHER_U;      // gather loads in flight per warp
 
@@ -147,25 +151,36 @@ __device__ __forceinline__ int64_t meta_beg(int64_t m) { return m & ((1ll << 40)
 __device__ __forceinline__ int meta_len(int64_t m) { return (int)((m >> 40) & 63); }
 __device__ __forceinline__ bool meta_multi(int64_t m) { return (m >> 46) & 1; }
 
-// Segment header: (v, first pair, count | word << 8 | multi << 16, column bits).
-__device__ __forceinline__ uint4 make_seg(int32_t v, uint32_t pb, int cnt, int j, bool multi, uint32_t bits) {
-  return make_uint4((uint32_t)v, pb, (uint32_t)cnt | ((uint32_t)j << 8) | ((uint32_t)multi << 16), bits);
+// Gathers move 128 columns at a time ("quads"): lane l of a warp covers the
+// four columns 4l..4l+3 of the quad, i.e. exactly one 32-byte sector of a
+// vertex row, so a lane loads a sector only when one of its four columns is
+// needed.  n_b is a multiple of 128 on the level path; Q = n_b / 128 quads
+// per row, and row index u*Q + d names quad d of vertex u.
+//
+// Pair record: row index (uint32) and the 128-column mask (uint4, word w of
+// the quad in component w).  Segment header: (v, first pair, count | quad << 8
+// | multi-item row << 16, 0); a segment is one (vertex, quad) of one work item.
+__device__ __forceinline__ uint4 make_seg(int32_t v, uint32_t pb, int cnt, int d, bool multi) {
+  return make_uint4((uint32_t)v, pb, (uint32_t)cnt | ((uint32_t)d << 8) | ((uint32_t)multi << 16), 0u);
 }
 
-// Emit the (member, mask) pairs of one item, word by word over `words`
-// (ascending), as segments into the level's pair and segment buffers.  The
-// counts are reserved with one atomic per buffer.  Returns false (and writes
-// nothing) when the buffers are full.
-__device__ __forceinline__ bool emit_pairs(const WarpSmem& w, int nm, int32_t v, bool multi, uint32_t words,
-                                           uint32_t colbits, uint2* pairs, uint4* segs, uint32_t* work,
+__device__ __forceinline__ uint32_t quad_or(const WarpSmem& w, int q, int d) {
+  return w.sF[q][4 * d] | w.sF[q][4 * d + 1] | w.sF[q][4 * d + 2] | w.sF[q][4 * d + 3];
+}
+
+// Emit the (member, mask) pairs of one item, quad by quad over `quads`
+// (ascending), as segments.  Space is reserved with one atomic per buffer;
+// returns false (writing nothing) when the buffers are full.
+__device__ __forceinline__ bool emit_quads(const WarpSmem& w, int nm, int32_t v, bool multi, uint32_t quads, int Q,
+                                           uint32_t* prow, uint4* pmask, uint4* segs, uint32_t* work,
                                            uint32_t pair_cap, uint32_t seg_cap, unsigned long long* npairs) {
   const unsigned lane = lane_id();
   const uint32_t lt = (1u << lane) - 1u;
   int mycnt = 0;
-  for (uint32_t wl = words; wl; wl &= wl - 1) {
-    const int j = __ffs(wl) - 1;
-    const uint32_t mk = __ballot_sync(0xffffffffu, ((int)lane < nm) && w.sF[lane][j] != 0u);
-    if ((int)lane == j) mycnt = __popc(mk);
+  for (uint32_t ql = quads; ql; ql &= ql - 1) {
+    const int d = __ffs(ql) - 1;
+    const uint32_t mk = __ballot_sync(0xffffffffu, ((int)lane < nm) && quad_or(w, lane, d) != 0u);
+    if ((int)lane == d) mycnt = __popc(mk);
   }
   int incl = mycnt;
   for (int o = 1; o < 32; o <<= 1) {
@@ -174,7 +189,7 @@ __device__ __forceinline__ bool emit_pairs(const WarpSmem& w, int nm, int32_t v,
   }
   const int excl = incl - mycnt;
   const uint32_t P = (uint32_t)__shfl_sync(0xffffffffu, incl, 31);
-  const uint32_t S = (uint32_t)__popc(words);
+  const uint32_t S = (uint32_t)__popc(quads);
   uint32_t pb = 0, sb = 0;
   if (lane == 0) {
     pb = P ? atomicAdd(&work[0], P) : 0u;
@@ -188,16 +203,27 @@ __device__ __forceinline__ bool emit_pairs(const WarpSmem& w, int nm, int32_t v,
   }
   if (npairs) *npairs += P;
   int r = 0;
-  for (uint32_t wl = words; wl; wl &= wl - 1, r++) {
-    const int j = __ffs(wl) - 1;
-    const bool nz = ((int)lane < nm) && w.sF[lane][j] != 0u;
+  for (uint32_t ql = quads; ql; ql &= ql - 1, r++) {
+    const int d = __ffs(ql) - 1;
+    const bool nz = ((int)lane < nm) && quad_or(w, lane, d) != 0u;
     const uint32_t mk = __ballot_sync(0xffffffffu, nz);
-    const uint32_t off = (uint32_t)__shfl_sync(0xffffffffu, excl, j);
-    const uint32_t bits = __shfl_sync(0xffffffffu, colbits, j);
-    if (nz) pairs[pb + off + __popc(mk & lt)] = make_uint2((uint32_t)w.su[lane], w.sF[lane][j]);
-    if (lane == 0) segs[sb + r] = make_seg(v, pb + off, __popc(mk), j, multi, bits);
+    const uint32_t off = (uint32_t)__shfl_sync(0xffffffffu, excl, d);
+    if (nz) {
+      const uint32_t at = pb + off + __popc(mk & lt);
+      prow[at] = (uint32_t)w.su[lane] * (uint32_t)Q + (uint32_t)d;
+      pmask[at] = make_uint4(w.sF[lane][4 * d], w.sF[lane][4 * d + 1], w.sF[lane][4 * d + 2], w.sF[lane][4 * d + 3]);
+    }
+    if (lane == 0) segs[sb + r] = make_seg(v, pb + off, __popc(mk), d, multi);
   }
   return true;
+}
+
+// quads (bit d) touched by the non-zero words of a word ballot
+__device__ __forceinline__ uint32_t quads_of_words(uint32_t words, int Q) {
+  uint32_t q = 0;
+  for (int d = 0; d < Q; d++)
+    if ((words >> (4 * d)) & 0xfu) q |= 1u << d;
+  return q;
 }
 
 // Work items are handed out in groups of 32 (hub items cost far more than
@@ -216,13 +242,14 @@ __global__ void __launch_bounds__(LVL_WARPS * 32) k_lvl_fwd_pairs(
     int64_t ib, int64_t ie, const int32_t* __restrict__ item_v, const int64_t* __restrict__ item_meta,
     const int32_t* __restrict__ col_t, int W, const uint32_t* __restrict__ full, const uint32_t* __restrict__ V,
     const uint32_t* __restrict__ Fl, const uint32_t* __restrict__ mem_l, uint32_t* Fn, uint32_t* mem_n,
-    int32_t* list_n, uint32_t* count_n, int64_t cap_n, uint32_t* flags, uint32_t* next_group, uint2* pairs,
-    uint4* segs, uint32_t* work, uint32_t pair_cap, uint32_t seg_cap, unsigned long long* bytes,
+    int32_t* list_n, uint32_t* count_n, int64_t cap_n, uint32_t* flags, uint32_t* next_group, uint32_t* prow,
+    uint4* pmask, uint4* segs, uint32_t* work, uint32_t pair_cap, uint32_t seg_cap, unsigned long long* bytes,
     unsigned long long* stat) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   WarpSmem& sm = reinterpret_cast<WarpSmem*>(smem_raw)[threadIdx.x >> 5];
   const unsigned lane = lane_id();
   const uint32_t lt = (1u << lane) - 1u;
+  const int Q = W / 4;
   unsigned long long nbytes = 0, npairs = 0;
   FOR_ITEM_GROUPS(ib, ie, next_group)
     // lane-parallel precheck of 32 items: skip rows already reached by every column
@@ -283,7 +310,8 @@ __global__ void __launch_bounds__(LVL_WARPS * 32) k_lvl_fwd_pairs(
       if (bytes) nbytes += 4ull * W * (nm + 1);
       const uint32_t cw = __ballot_sync(0xffffffffu, cand != 0u);
       if (!cw) continue;
-      emit_pairs(sm, nm, v, multi, cw, cand, pairs, segs, work, pair_cap, seg_cap, bytes ? &npairs : nullptr);
+      emit_quads(sm, nm, v, multi, quads_of_words(cw, Q), Q, prow, pmask, segs, work, pair_cap, seg_cap,
+                 bytes ? &npairs : nullptr);
       if ((int)lane < W && cand) {
         if (multi) atomicOr(&Fn[(size_t)v * W + lane], cand);
         else Fn[(size_t)v * W + lane] = cand;
@@ -300,26 +328,27 @@ __global__ void __launch_bounds__(LVL_WARPS * 32) k_lvl_fwd_pairs(
     }
   }
   if (bytes && lane == 0) {
-    atomicAdd(bytes, nbytes + 16ull * npairs);
+    atomicAdd(bytes, nbytes + 20ull * npairs);
     atomicAdd(&stat[0], npairs);
   }
 }
 
 // MFBr pairs of level l >= 1: for items [ib, ie) of rows with a column at
 // level l, the masks F_{l+1}(u) & F_l(v) of the out-neighbours u in F_{l+1}.
-// Every level-l word of a single-item row gets a segment (its columns are
+// Every level-l quad of a single-item row gets a segment (its columns are
 // finalised by the gather even without successors); multi-item rows only emit
-// words with pairs (their finalisation is k_lvl_hub_final).
+// quads with pairs (their finalisation is k_lvl_hub_final).
 __global__ void __launch_bounds__(LVL_WARPS * 32) k_lvl_bwd_pairs(
     int64_t ib, int64_t ie, const int32_t* __restrict__ item_v, const int64_t* __restrict__ item_meta,
     const int32_t* __restrict__ col, int W, const uint32_t* __restrict__ Fl, const uint32_t* __restrict__ mem_l,
-    const uint32_t* __restrict__ Fn, const uint32_t* __restrict__ mem_n, uint32_t* next_group, uint2* pairs,
-    uint4* segs, uint32_t* work, uint32_t pair_cap, uint32_t seg_cap, unsigned long long* bytes,
+    const uint32_t* __restrict__ Fn, const uint32_t* __restrict__ mem_n, uint32_t* next_group, uint32_t* prow,
+    uint4* pmask, uint4* segs, uint32_t* work, uint32_t pair_cap, uint32_t seg_cap, unsigned long long* bytes,
     unsigned long long* stat) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   WarpSmem& sm = reinterpret_cast<WarpSmem*>(smem_raw)[threadIdx.x >> 5];
   const unsigned lane = lane_id();
   const uint32_t lt = (1u << lane) - 1u;
+  const int Q = W / 4;
   unsigned long long nbytes = 0, npairs = 0;
   FOR_ITEM_GROUPS(ib, ie, next_group)
     // lane-parallel precheck of 32 items: only rows with a column at level l
@@ -378,26 +407,44 @@ __global__ void __launch_bounds__(LVL_WARPS * 32) k_lvl_bwd_pairs(
       __syncwarp();
       if (bytes) nbytes += 4ull * W * (nm + 1);
       const uint32_t words = __ballot_sync(0xffffffffu, multi ? any != 0u : Fv != 0u);
-      if (words) emit_pairs(sm, nm, v, multi, words, Fv, pairs, segs, work, pair_cap, seg_cap,
-                            bytes ? &npairs : nullptr);
+      if (words) emit_quads(sm, nm, v, multi, quads_of_words(words, Q), Q, prow, pmask, segs, work, pair_cap,
+                            seg_cap, bytes ? &npairs : nullptr);
       __syncwarp();
     }
   }
   if (bytes && lane == 0) {
-    atomicAdd(bytes, nbytes + 16ull * npairs);
+    atomicAdd(bytes, nbytes + 20ull * npairs);
     atomicAdd(&stat[1], npairs);
   }
 }
 
+// Per-warp shared staging of one chunk of 32 pairs in the gather kernels.
+struct GatherSmem {
+  uint4 mask[32];
+  uint32_t row[32];
+  int32_t seg[32];
+};
+
+__device__ __forceinline__ void ld4(const double* p, double& a, double& b, double& c, double& d) {
+  asm volatile("ld.global.nc.v4.f64 {%0,%1,%2,%3}, [%4];" : "=d"(a), "=d"(b), "=d"(c), "=d"(d) : "l"(p));
+}
+__device__ __forceinline__ void ld4_coherent(const double* p, double& a, double& b, double& c, double& d) {
+  asm volatile("ld.global.v4.f64 {%0,%1,%2,%3}, [%4];" : "=d"(a), "=d"(b), "=d"(c), "=d"(d) : "l"(p) : "memory");
+}
+__device__ __forceinline__ void st4(double* p, double a, double b, double c, double d) {
+  asm volatile("st.global.v4.f64 [%0], {%1,%2,%3,%4};" ::"l"(p), "d"(a), "d"(b), "d"(c), "d"(d) : "memory");
+}
+
 // Gather over a group of up to 32 segments (lane k holds segment k's header).
-// The group's pairs are flattened with a warp scan and streamed in chunks of
-// 32 (lane = pair for the pair loads, lane = column for the gathers); rounds
-// of GATHER_U predicated 256-byte gathers are double-buffered across segment
-// boundaries.  FLUSH(k, acc) is called once per segment with pairs, in order,
-// by the whole warp; segments without pairs are not flushed.
-template <class Flush>
-__device__ __forceinline__ void gather_group(const uint4& myseg, int nin, const uint2* __restrict__ pairs,
-                                             const double* sv, int nb, unsigned long long* nvals, Flush flush) {
+// The group's pairs are flattened with a warp scan and staged 32 at a time in
+// shared memory; each pair costs every lane one broadcast row read, one mask
+// word read and, when one of its four columns is set, one 32-byte load.
+// FLUSH(k, acc) is called once per segment with pairs, in order, by the whole
+// warp, with the lane's four column sums and the OR of its 4-bit slices.
+template <bool COUNT, class Flush>
+__device__ __forceinline__ void gather_group(const uint4& myseg, int nin, const uint32_t* __restrict__ prow,
+                                             const uint4* __restrict__ pmask, GatherSmem& gs, const double* sv,
+                                             unsigned long long& nvals, Flush flush) {
   const unsigned lane = lane_id();
   const int mycnt = (int)lane < nin ? (int)(myseg.z & 0xffu) : 0;
   int incl = mycnt;
@@ -407,11 +454,11 @@ __device__ __forceinline__ void gather_group(const uint4& myseg, int nin, const 
   }
   const int excl = incl - mycnt;
   const int T = __shfl_sync(0xffffffffu, incl, 31);
-  const int myj = (int)((myseg.z >> 8) & 0xffu);
-  double acc = 0.0;
-  int cur = -1;
+  const int shift = 4 * (int)(lane & 7u);
+  const int mword = (int)(lane >> 3);
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+  uint32_t cs = 0;
   for (int p0 = 0; p0 < T; p0 += 32) {
-    // lane-parallel load of flattened pairs p0 .. p0+31
     const int p = p0 + (int)lane;
     int t = 0;
 #pragma unroll
@@ -423,40 +470,52 @@ __device__ __forceinline__ void gather_group(const uint4& myseg, int nin, const 
     // so the largest such t is the segment that holds pair p
     const uint32_t tpb = __shfl_sync(0xffffffffu, myseg.y, t);
     const int texcl = __shfl_sync(0xffffffffu, excl, t);
-    uint2 pr = make_uint2(0u, 0u);
-    if (p < T) pr = pairs[tpb + (uint32_t)(p - texcl)];
-    const int tj = __shfl_sync(0xffffffffu, myj, t);
+    const int tincl = __shfl_sync(0xffffffffu, incl, t);
+    __syncwarp();
+    if (p < T) {
+      const uint32_t at = tpb + (uint32_t)(p - texcl);
+      gs.mask[lane] = pmask[at];
+      gs.row[lane] = prow[at];
+      gs.seg[lane] = t;
+    }
+    const uint32_t lastmask = __ballot_sync(0xffffffffu, p < T && p + 1 == tincl);
+    __syncwarp();
     const int nq = T - p0 < 32 ? T - p0 : 32;
     for (int q0 = 0; q0 < nq; q0 += GATHER_U) {
-      double x[GATHER_U];
-      int ts[GATHER_U];
+      double x[GATHER_U][4];
+      uint32_t sl[GATHER_U];
 #pragma unroll
       for (int r = 0; r < GATHER_U; r++) {
-        const int q = (q0 + r) & 31;
-        const uint32_t u = __shfl_sync(0xffffffffu, pr.x, q);
-        const uint32_t m = __shfl_sync(0xffffffffu, pr.y, q);
-        const int jj = __shfl_sync(0xffffffffu, tj, q);
-        ts[r] = __shfl_sync(0xffffffffu, t, q);
-        x[r] = 0.0;
-        if (q0 + r < nq && ((m >> lane) & 1u)) {
-          x[r] = __ldg(&sv[(size_t)u * nb + jj * 32 + lane]);
-          if (nvals) (*nvals)++;
+        const int q = q0 + r;
+        sl[r] = 0u;
+        x[r][0] = x[r][1] = x[r][2] = x[r][3] = 0.0;
+        if (q < nq) {
+          const uint32_t mw = reinterpret_cast<const uint32_t*>(&gs.mask[q])[mword];
+          sl[r] = (mw >> shift) & 0xfu;
+          if (sl[r]) {
+            ld4(sv + (size_t)gs.row[q] * 128 + 4 * lane, x[r][0], x[r][1], x[r][2], x[r][3]);
+            if (COUNT) nvals += __popc(sl[r]);
+          }
         }
       }
 #pragma unroll
       for (int r = 0; r < GATHER_U; r++) {
-        if (q0 + r < nq) {
-          if (ts[r] != cur) {
-            if (cur >= 0) flush(cur, acc);
-            acc = 0.0;
-            cur = ts[r];
+        const int q = q0 + r;
+        if (q < nq) {
+          if (sl[r] & 1u) a0 += x[r][0];
+          if (sl[r] & 2u) a1 += x[r][1];
+          if (sl[r] & 4u) a2 += x[r][2];
+          if (sl[r] & 8u) a3 += x[r][3];
+          cs |= sl[r];
+          if ((lastmask >> q) & 1u) {
+            flush(gs.seg[q], a0, a1, a2, a3, cs);
+            a0 = a1 = a2 = a3 = 0.0;
+            cs = 0u;
           }
-          acc += x[r];
         }
       }
     }
   }
-  if (cur >= 0) flush(cur, acc);
 }
 
 #define FOR_SEGMENT_GROUPS(nseg, counter)                                                    \
@@ -470,37 +529,54 @@ __device__ __forceinline__ void gather_group(const uint4& myseg, int nin, const 
     const int nin = (uint64_t)(nseg) - base < 32 ? (int)((uint64_t)(nseg) - base) : 32;
 
 // MFBF gather of level l: sigma_bar(s,v) = sum over the segment's pairs.
+template <bool COUNT>
 __global__ void __launch_bounds__(256, 4) k_lvl_fwd_gather(
-    const uint4* __restrict__ segs, const uint32_t* nseg_p, const uint2* __restrict__ pairs, int nb, double* sv,
-    uint32_t* flags, uint32_t* next_group, unsigned long long* bytes, unsigned long long* stat) {
+    const uint4* __restrict__ segs, const uint32_t* nseg_p, const uint32_t* __restrict__ prow,
+    const uint4* __restrict__ pmask, int nb, double* sv, uint32_t* flags, uint32_t* next_group,
+    unsigned long long* bytes, unsigned long long* stat) {
+  __shared__ GatherSmem gsm[8];
+  GatherSmem& gs = gsm[threadIdx.x >> 5];
   const unsigned lane = lane_id();
   const uint32_t nseg = *nseg_p;
   unsigned long long nvals = 0, nw = 0;
-  unsigned long long* pv = bytes ? &nvals : nullptr;
   FOR_SEGMENT_GROUPS(nseg, next_group)
-    gather_group(myseg, nin, pairs, sv, nb, pv, [&](int k, double acc) {
+    gather_group<COUNT>(myseg, nin, prow, pmask, gs, sv, nvals,
+                        [&](int k, double a0, double a1, double a2, double a3, uint32_t cs) {
       const int32_t v = (int32_t)__shfl_sync(0xffffffffu, myseg.x, k);
       const uint32_t z = __shfl_sync(0xffffffffu, myseg.z, k);
-      const uint32_t bits = __shfl_sync(0xffffffffu, myseg.w, k);
-      const int j = (int)((z >> 8) & 0xffu);
-      if ((bits >> lane) & 1u) {
+      const int d = (int)((z >> 8) & 0xffu);
+      if (cs) {
+        double* dst = sv + (size_t)v * nb + 128 * d + 4 * lane;
+        double t0 = a0, t1 = a1, t2 = a2, t3 = a3;
+        if ((z >> 16) & 1u) {
+          if (cs & 1u) t0 += atomicAdd(dst + 0, a0);
+          if (cs & 2u) t1 += atomicAdd(dst + 1, a1);
+          if (cs & 4u) t2 += atomicAdd(dst + 2, a2);
+          if (cs & 8u) t3 += atomicAdd(dst + 3, a3);
+        } else if (cs == 0xfu) {
+          st4(dst, a0, a1, a2, a3);
+        } else {
+          if (cs & 1u) dst[0] = a0;
+          if (cs & 2u) dst[1] = a1;
+          if (cs & 4u) dst[2] = a2;
+          if (cs & 8u) dst[3] = a3;
+        }
         // a multiplicity at or above 2^53 may have been rounded (flags bit 1)
-        double tot = acc;
-        const size_t idx = (size_t)v * nb + j * 32 + lane;
-        if ((z >> 16) & 1u) tot += atomicAdd(&sv[idx], acc);
-        else sv[idx] = acc;
-        if (tot >= 9007199254740992.0) atomicOr(flags, 2u);
-        if (bytes) nw++;
+        const double big = 9007199254740992.0;
+        if (((cs & 1u) && t0 >= big) || ((cs & 2u) && t1 >= big) || ((cs & 4u) && t2 >= big) ||
+            ((cs & 8u) && t3 >= big))
+          atomicOr(flags, 2u);
+        if (COUNT) nw += __popc(cs);
       }
     });
   }
-  if (bytes) {
+  if (COUNT) {
     for (int o = 16; o; o >>= 1) {
       nvals += __shfl_xor_sync(0xffffffffu, nvals, o);
       nw += __shfl_xor_sync(0xffffffffu, nw, o);
     }
     if (lane == 0) {
-      atomicAdd(bytes, 8ull * (nvals + nw));
+      atomicAdd(bytes, 8ull * (nvals + nw) + 16ull * nseg / 32);
       atomicAdd(&stat[2], nvals);
     }
   }
@@ -509,56 +585,72 @@ __global__ void __launch_bounds__(256, 4) k_lvl_fwd_gather(
 // MFBr gather of level l: zeta(s,v) = sum over the segment's pairs of the
 // successors' values; single-item rows are finalised here (lambda, value
 // zeta + 1/sigma_bar), multi-item rows add into their hub accumulator.
+template <bool COUNT>
 __global__ void __launch_bounds__(256, 4) k_lvl_bwd_gather(
-    const uint4* __restrict__ segs, const uint32_t* nseg_p, const uint2* __restrict__ pairs, int nb,
+    const uint4* __restrict__ segs, const uint32_t* nseg_p, const uint32_t* __restrict__ prow,
+    const uint4* __restrict__ pmask, int nb, int W, const uint32_t* __restrict__ Fl,
     const int32_t* __restrict__ hub_of, double* sv, double* zacc, double* lambda, uint32_t* next_group,
     unsigned long long* bytes, unsigned long long* stat) {
+  __shared__ GatherSmem gsm[8];
+  GatherSmem& gs = gsm[threadIdx.x >> 5];
   const unsigned lane = lane_id();
   const uint32_t nseg = *nseg_p;
+  const int shift = 4 * (int)(lane & 7u);
   unsigned long long nvals = 0, nw = 0;
-  unsigned long long* pv = bytes ? &nvals : nullptr;
   FOR_SEGMENT_GROUPS(nseg, next_group)
-    auto finish = [&](int k, double acc) {
+    auto finish = [&](int k, double a0, double a1, double a2, double a3, uint32_t) {
       const int32_t v = (int32_t)__shfl_sync(0xffffffffu, myseg.x, k);
       const uint32_t z = __shfl_sync(0xffffffffu, myseg.z, k);
-      const uint32_t bits = __shfl_sync(0xffffffffu, myseg.w, k);
-      const int j = (int)((z >> 8) & 0xffu);
-      const bool mine = (bits >> lane) & 1u;
+      const int d = (int)((z >> 8) & 0xffu);
+      // this lane's four columns of v's level-l frontier
+      const uint32_t fs = (__ldg(&Fl[(size_t)v * W + 4 * d + (lane >> 3)]) >> shift) & 0xfu;
+      const size_t col = (size_t)128 * d + 4 * lane;
       if ((z >> 16) & 1u) {
-        const int32_t hub = hub_of[v];
-        if (mine) {
-          atomicAdd(&zacc[(size_t)hub * nb + j * 32 + lane], acc);
-          if (bytes) nw++;
+        if (fs) {
+          double* za = zacc + (size_t)hub_of[v] * nb + col;
+          if (fs & 1u) atomicAdd(za + 0, a0);
+          if (fs & 2u) atomicAdd(za + 1, a1);
+          if (fs & 4u) atomicAdd(za + 2, a2);
+          if (fs & 8u) atomicAdd(za + 3, a3);
+          if (COUNT) nw += __popc(fs);
         }
       } else {
         double lam = 0.0;
-        if (mine) {
-          const size_t idx = (size_t)v * nb + j * 32 + lane;
-          const double sg = sv[idx];
-          lam = acc * sg;
-          sv[idx] = acc + 1.0 / sg;
-          if (bytes) nw += 2;
+        if (fs) {
+          // read-modify-write of the lane's sector: only the set columns
+          // change (this segment is the only writer of them in this launch)
+          double* p = sv + (size_t)v * nb + col;
+          double s0, s1, s2, s3;
+          ld4_coherent(p, s0, s1, s2, s3);
+          if (fs & 1u) { lam += a0 * s0; s0 = a0 + 1.0 / s0; }
+          if (fs & 2u) { lam += a1 * s1; s1 = a1 + 1.0 / s1; }
+          if (fs & 4u) { lam += a2 * s2; s2 = a2 + 1.0 / s2; }
+          if (fs & 8u) { lam += a3 * s3; s3 = a3 + 1.0 / s3; }
+          st4(p, s0, s1, s2, s3);
+          if (COUNT) nw += 2 * __popc(fs);
         }
-        for (int o = 16; o; o >>= 1) lam += __shfl_xor_sync(0xffffffffu, lam, o);
-        if (lane == 0 && lam != 0.0) atomicAdd(&lambda[v], lam);
+        if (__any_sync(0xffffffffu, lam != 0.0)) {
+          for (int o = 16; o; o >>= 1) lam += __shfl_xor_sync(0xffffffffu, lam, o);
+          if (lane == 0) atomicAdd(&lambda[v], lam);
+        }
       }
     };
-    gather_group(myseg, nin, pairs, sv, nb, pv, finish);
+    gather_group<COUNT>(myseg, nin, prow, pmask, gs, sv, nvals, finish);
     // segments without successor pairs: zeta = 0
     uint32_t empty = __ballot_sync(0xffffffffu, (int)lane < nin && (myseg.z & 0xffu) == 0u);
     while (empty) {
       const int k = __ffs(empty) - 1;
       empty &= empty - 1;
-      finish(k, 0.0);
+      finish(k, 0.0, 0.0, 0.0, 0.0, 0u);
     }
   }
-  if (bytes) {
+  if (COUNT) {
     for (int o = 16; o; o >>= 1) {
       nvals += __shfl_xor_sync(0xffffffffu, nvals, o);
       nw += __shfl_xor_sync(0xffffffffu, nw, o);
     }
     if (lane == 0) {
-      atomicAdd(bytes, 8ull * (nvals + nw));
+      atomicAdd(bytes, 8ull * (nvals + nw) + 16ull * nseg / 32);
       atomicAdd(&stat[3], nvals);
     }
   }
@@ -702,12 +794,12 @@ static mfbc_status level_round(RunCtx& rc, LevelState& s, bool fwd, int l, int64
     PROF(K_LVL_FWD, (k_lvl_fwd_pairs<<<pgrid, LVL_WARPS * 32, LVL_SMEM, st>>>(
                         ib, ie, g.items_in.v, g.items_in.beg, g.col_t, W, s.full, s.V, Fl, Ml, Fn, Mn,
                         s.lists + off_n, &s.ctr->list_count[0], s.list_cap - off_n, &s.ctr->flags,
-                        &s.ctr->list_count[2], s.pairs, s.segs, s.ctr->work, s.pair_cap, s.seg_cap,
+                        &s.ctr->list_count[2], s.prow, s.pmask, s.segs, s.ctr->work, s.pair_cap, s.seg_cap,
                         B ? B + K_LVL_FWD : nullptr, s.ctr->stat)));
   else
     PROF(K_LVL_BWD, (k_lvl_bwd_pairs<<<pgrid, LVL_WARPS * 32, LVL_SMEM, st>>>(
                         ib, ie, g.items_out.v, g.items_out.beg, g.col, W, Fl, Ml, Fn, Mn,
-                        &s.ctr->list_count[2], s.pairs, s.segs, s.ctr->work, s.pair_cap, s.seg_cap,
+                        &s.ctr->list_count[2], s.prow, s.pmask, s.segs, s.ctr->work, s.pair_cap, s.seg_cap,
                         B ? B + K_LVL_BWD : nullptr, s.ctr->stat)));
   MFBC_CUDA_TRY(cudaMemcpyAsync(rc.h_ctr, s.ctr->list_count, sizeof(uint32_t) * 9, cudaMemcpyDeviceToHost, st), rc.err);
   MFBC_CUDA_TRY(cudaStreamSynchronize(st), rc.err);
@@ -727,15 +819,25 @@ static mfbc_status level_round(RunCtx& rc, LevelState& s, bool fwd, int l, int64
   if (!nseg) return MFBC_OK;
   MFBC_CUDA_TRY(cudaMemsetAsync(&s.ctr->work[2], 0, sizeof(uint32_t), st), rc.err);
   const unsigned ggrid = grid_for_items(nseg, kGatherGrid);
-  if (fwd)
-    PROF(K_LVL_FWD_G, (k_lvl_fwd_gather<<<ggrid, 256, 0, st>>>(s.segs, &s.ctr->work[1], s.pairs, nb, s.sv,
-                                                              &s.ctr->flags, &s.ctr->work[2],
-                                                              B ? B + K_LVL_FWD_G : nullptr, s.ctr->stat)));
-  else
-    PROF(K_LVL_BWD_G, (k_lvl_bwd_gather<<<ggrid, 256, 0, st>>>(s.segs, &s.ctr->work[1], s.pairs, nb,
-                                                              g.items_out.hub_of, s.sv, s.zacc, lambda,
-                                                              &s.ctr->work[2], B ? B + K_LVL_BWD_G : nullptr,
-                                                              s.ctr->stat)));
+  if (fwd) {
+    if (B)
+      PROF(K_LVL_FWD_G, (k_lvl_fwd_gather<true><<<ggrid, 256, 0, st>>>(
+                            s.segs, &s.ctr->work[1], s.prow, s.pmask, nb, s.sv, &s.ctr->flags, &s.ctr->work[2],
+                            B + K_LVL_FWD_G, s.ctr->stat)));
+    else
+      PROF(K_LVL_FWD_G, (k_lvl_fwd_gather<false><<<ggrid, 256, 0, st>>>(
+                            s.segs, &s.ctr->work[1], s.prow, s.pmask, nb, s.sv, &s.ctr->flags, &s.ctr->work[2],
+                            nullptr, s.ctr->stat)));
+  } else {
+    if (B)
+      PROF(K_LVL_BWD_G, (k_lvl_bwd_gather<true><<<ggrid, 256, 0, st>>>(
+                            s.segs, &s.ctr->work[1], s.prow, s.pmask, nb, W, Fl, g.items_out.hub_of, s.sv, s.zacc,
+                            lambda, &s.ctr->work[2], B + K_LVL_BWD_G, s.ctr->stat)));
+    else
+      PROF(K_LVL_BWD_G, (k_lvl_bwd_gather<false><<<ggrid, 256, 0, st>>>(
+                            s.segs, &s.ctr->work[1], s.prow, s.pmask, nb, W, Fl, g.items_out.hub_of, s.sv, s.zacc,
+                            lambda, &s.ctr->work[2], nullptr, s.ctr->stat)));
+  }
   return MFBC_OK;
 }
 
