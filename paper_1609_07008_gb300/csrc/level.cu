@@ -94,6 +94,83 @@ __device__ __forceinline__ uint32_t active_mask(int w, int nactive) {
   return (1u << (nactive - lo)) - 1u;
 }
 
+// ---------------------------------------------------------------- arithmetic
+// GB300 executes FP64 at a small fraction of its FP32 rate, so the hot loops
+// avoid it: MFBF path counts are exact 64-bit integers, and MFBr values
+// zeta + 1/sigma_bar are double-float pairs (hi + lo, about 48 significant
+// bits) kept in the same 8-byte slots and combined on the FP32 pipes with
+// error-free transformations (Dekker / Knuth two-sum, FMA-based products).
+struct dfl { float hi, lo; };
+
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+__device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& e) {   // |a| >= |b|
+  s = a + b;
+  e = b - (s - a);
+}
+__device__ __forceinline__ dfl df_add(dfl a, dfl b) {
+  float s, e, t, f;
+  two_sum(a.hi, b.hi, s, e);
+  two_sum(a.lo, b.lo, t, f);
+  e += t;
+  fast_two_sum(s, e, s, e);
+  e += f;
+  fast_two_sum(s, e, s, e);
+  return {s, e};
+}
+__device__ __forceinline__ dfl df_of_u64(uint64_t x) {      // exact below 2^48
+  const float h = __ull2float_rn(x);
+  const long long r = (long long)(x - (uint64_t)h);
+  return {h, __ll2float_rn(r)};
+}
+__device__ __forceinline__ dfl df_mul(dfl a, dfl b) {
+  const float p = a.hi * b.hi;
+  float e = fmaf(a.hi, b.hi, -p);
+  e = fmaf(a.hi, b.lo, e);
+  e = fmaf(a.lo, b.hi, e);
+  float s, t;
+  fast_two_sum(p, e, s, t);
+  return {s, t};
+}
+// 1/x for x >= 1: FP32 reciprocal refined by one Newton step.
+__device__ __forceinline__ dfl df_rcp(dfl a) {
+  const float r = 1.0f / a.hi;
+  float e = fmaf(-a.hi, r, 1.0f);
+  e = fmaf(-a.lo, r, e);
+  float s, t;
+  fast_two_sum(r, r * e, s, t);
+  return {s, t};
+}
+__device__ __forceinline__ uint64_t df_pack(dfl a) {
+  return (uint64_t)__float_as_uint(a.hi) | ((uint64_t)__float_as_uint(a.lo) << 32);
+}
+__device__ __forceinline__ dfl df_unpack(uint64_t u) {
+  return {__uint_as_float((uint32_t)u), __uint_as_float((uint32_t)(u >> 32))};
+}
+__device__ __forceinline__ double df_to_double(dfl a) { return (double)a.hi + (double)a.lo; }
+__device__ __forceinline__ dfl df_of_double(double x) {
+  const float h = __double2float_rn(x);
+  return {h, __double2float_rn(x - (double)h)};
+}
+// compensated accumulation of double-float terms into (s, c) (Neumaier)
+__device__ __forceinline__ void acc_add(float& s, float& c, uint64_t x) {
+  const dfl v = df_unpack(x);
+  const float t = s + v.hi;
+  c += (fabsf(s) >= fabsf(v.hi)) ? ((s - t) + v.hi) : ((v.hi - t) + s);
+  c += v.lo;
+  s = t;
+}
+__device__ __forceinline__ dfl acc_value(float s, float c) {
+  float h, l;
+  fast_two_sum(s, c, h, l);
+  return {h, l};
+}
+
+__global__ void k_clear_flag_bits(uint32_t* flags, uint32_t bits) { atomicAnd(flags, ~bits); }
+
 // sv rows of multi-item vertices start at zero (MFBF adds into them).
 __global__ void k_lvl_zero_hubs(const int32_t* __restrict__ hubs, int32_t nhub, int nb, double* sv) {
   const uint64_t total = (uint64_t)nhub * nb;
@@ -109,7 +186,7 @@ __global__ void k_lvl_seed(const int32_t* __restrict__ src, int nb, int W, doubl
   if (j >= nb) return;
   const int32_t s = src[j];
   if (s < 0) return;
-  sv[(size_t)s * nb + j] = 1.0;
+  reinterpret_cast<uint64_t*>(sv)[(size_t)s * nb + j] = 1ull;   // sigma_bar as an exact integer
   atomicOr(&F0[(size_t)s * W + (j >> 5)], 1u << (j & 31));
   const uint32_t bit = 1u << (s & 31);
   if (!(atomicOr(&member0[s >> 5], bit) & bit)) list0[atomicAdd(count, 1u)] = s;
@@ -441,10 +518,50 @@ __device__ __forceinline__ void st4(double* p, double a, double b, double c, dou
 // word read and, when one of its four columns is set, one 32-byte load.
 // FLUSH(k, acc) is called once per segment with pairs, in order, by the whole
 // warp, with the lane's four column sums and the OR of its 4-bit slices.
-template <bool COUNT, class Flush>
+template <bool COUNT>
+__device__ __forceinline__ void stage_chunk(const uint4& myseg, int excl, int incl, int T, int p0,
+                                            const uint32_t* __restrict__ prow, const uint4* __restrict__ pmask,
+                                            GatherSmem& gs, uint32_t* lastmask) {
+  const unsigned lane = lane_id();
+  const int p = p0 + (int)lane;
+  int t = 0;
+#pragma unroll
+  for (int step = 16; step; step >>= 1) {            // largest t with excl_t <= p
+    const int e = __shfl_sync(0xffffffffu, excl, t + step > 31 ? 31 : t + step);
+    if (t + step <= 31 && e <= p) t += step;
+  }
+  // excl is non-decreasing and empty segments share their successor's excl,
+  // so the largest such t is the segment that holds pair p
+  const uint32_t tpb = __shfl_sync(0xffffffffu, myseg.y, t);
+  const int texcl = __shfl_sync(0xffffffffu, excl, t);
+  const int tincl = __shfl_sync(0xffffffffu, incl, t);
+  __syncwarp();
+  if (p < T) {
+    const uint32_t at = tpb + (uint32_t)(p - texcl);
+    gs.mask[lane] = pmask[at];
+    gs.row[lane] = prow[at];
+    gs.seg[lane] = t;
+  }
+  *lastmask = __ballot_sync(0xffffffffu, p < T && p + 1 == tincl);
+  __syncwarp();
+}
+
+__device__ __forceinline__ void ld4u(const uint64_t* p, uint64_t& a, uint64_t& b, uint64_t& c, uint64_t& d) {
+  asm volatile("ld.global.nc.v4.u64 {%0,%1,%2,%3}, [%4];" : "=l"(a), "=l"(b), "=l"(c), "=l"(d) : "l"(p));
+}
+
+// Gather over a group of up to 32 segments (lane k holds segment k's header).
+// The group's pairs are flattened with a warp scan and staged 32 at a time in
+// shared memory; each pair costs every lane one broadcast row read, one mask
+// word read and, when one of its four columns is set, one 32-byte load.
+// MFBF (INT = true) sums exact 64-bit path counts; MFBr sums double-float
+// values with compensation.  FLUSH(k, ...) is called once per segment with
+// pairs, in order, by the whole warp, with the lane's four column sums and
+// the OR of its 4-bit slices.
+template <bool COUNT, bool INT, class Flush>
 __device__ __forceinline__ void gather_group(const uint4& myseg, int nin, const uint32_t* __restrict__ prow,
-                                             const uint4* __restrict__ pmask, GatherSmem& gs, const double* sv,
-                                             unsigned long long& nvals, Flush flush) {
+                                             const uint4* __restrict__ pmask, GatherSmem& gs, const uint64_t* sv,
+                                             unsigned long long& nvals, uint32_t& ovf, Flush flush) {
   const unsigned lane = lane_id();
   const int mycnt = (int)lane < nin ? (int)(myseg.z & 0xffu) : 0;
   int incl = mycnt;
@@ -456,44 +573,27 @@ __device__ __forceinline__ void gather_group(const uint4& myseg, int nin, const 
   const int T = __shfl_sync(0xffffffffu, incl, 31);
   const int shift = 4 * (int)(lane & 7u);
   const int mword = (int)(lane >> 3);
-  double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+  uint64_t i0 = 0, i1 = 0, i2 = 0, i3 = 0;                 // MFBF sums
+  float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;            // MFBr sums
+  float c0 = 0.f, c1 = 0.f, c2 = 0.f, c3 = 0.f;            //   and their compensations
   uint32_t cs = 0;
   for (int p0 = 0; p0 < T; p0 += 32) {
-    const int p = p0 + (int)lane;
-    int t = 0;
-#pragma unroll
-    for (int step = 16; step; step >>= 1) {            // largest t with excl_t <= p
-      const int e = __shfl_sync(0xffffffffu, excl, t + step > 31 ? 31 : t + step);
-      if (t + step <= 31 && e <= p) t += step;
-    }
-    // excl is non-decreasing and empty segments share their successor's excl,
-    // so the largest such t is the segment that holds pair p
-    const uint32_t tpb = __shfl_sync(0xffffffffu, myseg.y, t);
-    const int texcl = __shfl_sync(0xffffffffu, excl, t);
-    const int tincl = __shfl_sync(0xffffffffu, incl, t);
-    __syncwarp();
-    if (p < T) {
-      const uint32_t at = tpb + (uint32_t)(p - texcl);
-      gs.mask[lane] = pmask[at];
-      gs.row[lane] = prow[at];
-      gs.seg[lane] = t;
-    }
-    const uint32_t lastmask = __ballot_sync(0xffffffffu, p < T && p + 1 == tincl);
-    __syncwarp();
+    uint32_t lastmask;
+    stage_chunk<COUNT>(myseg, excl, incl, T, p0, prow, pmask, gs, &lastmask);
     const int nq = T - p0 < 32 ? T - p0 : 32;
     for (int q0 = 0; q0 < nq; q0 += GATHER_U) {
-      double x[GATHER_U][4];
+      uint64_t x[GATHER_U][4];
       uint32_t sl[GATHER_U];
 #pragma unroll
       for (int r = 0; r < GATHER_U; r++) {
         const int q = q0 + r;
         sl[r] = 0u;
-        x[r][0] = x[r][1] = x[r][2] = x[r][3] = 0.0;
+        x[r][0] = x[r][1] = x[r][2] = x[r][3] = 0ull;
         if (q < nq) {
           const uint32_t mw = reinterpret_cast<const uint32_t*>(&gs.mask[q])[mword];
           sl[r] = (mw >> shift) & 0xfu;
           if (sl[r]) {
-            ld4(sv + (size_t)gs.row[q] * 128 + 4 * lane, x[r][0], x[r][1], x[r][2], x[r][3]);
+            ld4u(sv + (size_t)gs.row[q] * 128 + 4 * lane, x[r][0], x[r][1], x[r][2], x[r][3]);
             if (COUNT) nvals += __popc(sl[r]);
           }
         }
@@ -502,14 +602,24 @@ __device__ __forceinline__ void gather_group(const uint4& myseg, int nin, const 
       for (int r = 0; r < GATHER_U; r++) {
         const int q = q0 + r;
         if (q < nq) {
-          if (sl[r] & 1u) a0 += x[r][0];
-          if (sl[r] & 2u) a1 += x[r][1];
-          if (sl[r] & 4u) a2 += x[r][2];
-          if (sl[r] & 8u) a3 += x[r][3];
+          if (INT) {
+            const uint64_t o0 = i0, o1 = i1, o2 = i2, o3 = i3;
+            if (sl[r] & 1u) i0 += x[r][0];
+            if (sl[r] & 2u) i1 += x[r][1];
+            if (sl[r] & 4u) i2 += x[r][2];
+            if (sl[r] & 8u) i3 += x[r][3];
+            ovf |= (uint32_t)((i0 < o0) | (i1 < o1) | (i2 < o2) | (i3 < o3));
+          } else {
+            if (sl[r] & 1u) acc_add(s0, c0, x[r][0]);
+            if (sl[r] & 2u) acc_add(s1, c1, x[r][1]);
+            if (sl[r] & 4u) acc_add(s2, c2, x[r][2]);
+            if (sl[r] & 8u) acc_add(s3, c3, x[r][3]);
+          }
           cs |= sl[r];
           if ((lastmask >> q) & 1u) {
-            flush(gs.seg[q], a0, a1, a2, a3, cs);
-            a0 = a1 = a2 = a3 = 0.0;
+            flush(gs.seg[q], i0, i1, i2, i3, s0, s1, s2, s3, c0, c1, c2, c3, cs);
+            i0 = i1 = i2 = i3 = 0ull;
+            s0 = s1 = s2 = s3 = c0 = c1 = c2 = c3 = 0.f;
             cs = 0u;
           }
         }
@@ -528,48 +638,55 @@ __device__ __forceinline__ void gather_group(const uint4& myseg, int nin, const 
     if (base + lane < (uint64_t)(nseg)) myseg = segs[base + lane];                         \
     const int nin = (uint64_t)(nseg) - base < 32 ? (int)((uint64_t)(nseg) - base) : 32;
 
-// MFBF gather of level l: sigma_bar(s,v) = sum over the segment's pairs.
+// MFBF gather of level l: sigma_bar(s,v) = sum over the segment's pairs
+// (exact 64-bit integers).  flags: bit 1 some sigma_bar >= 2^53, bit 3 a sum
+// passed 2^64 (the batch is then recomputed by the general kernels).
 template <bool COUNT>
 __global__ void __launch_bounds__(256, 4) k_lvl_fwd_gather(
     const uint4* __restrict__ segs, const uint32_t* nseg_p, const uint32_t* __restrict__ prow,
-    const uint4* __restrict__ pmask, int nb, double* sv, uint32_t* flags, uint32_t* next_group,
+    const uint4* __restrict__ pmask, int nb, double* svd, uint32_t* flags, uint32_t* next_group,
     unsigned long long* bytes, unsigned long long* stat) {
   __shared__ GatherSmem gsm[8];
   GatherSmem& gs = gsm[threadIdx.x >> 5];
+  uint64_t* sv = reinterpret_cast<uint64_t*>(svd);
   const unsigned lane = lane_id();
   const uint32_t nseg = *nseg_p;
   unsigned long long nvals = 0, nw = 0;
+  uint32_t ovf = 0, big = 0;
   FOR_SEGMENT_GROUPS(nseg, next_group)
-    gather_group<COUNT>(myseg, nin, prow, pmask, gs, sv, nvals,
-                        [&](int k, double a0, double a1, double a2, double a3, uint32_t cs) {
+    gather_group<COUNT, true>(myseg, nin, prow, pmask, gs, sv, nvals, ovf,
+        [&](int k, uint64_t a0, uint64_t a1, uint64_t a2, uint64_t a3, float, float, float, float, float, float,
+            float, float, uint32_t cs) {
       const int32_t v = (int32_t)__shfl_sync(0xffffffffu, myseg.x, k);
       const uint32_t z = __shfl_sync(0xffffffffu, myseg.z, k);
       const int d = (int)((z >> 8) & 0xffu);
       if (cs) {
-        double* dst = sv + (size_t)v * nb + 128 * d + 4 * lane;
-        double t0 = a0, t1 = a1, t2 = a2, t3 = a3;
+        uint64_t* dst = sv + (size_t)v * nb + 128 * d + 4 * lane;
+        uint64_t t0 = a0, t1 = a1, t2 = a2, t3 = a3;
         if ((z >> 16) & 1u) {
-          if (cs & 1u) t0 += atomicAdd(dst + 0, a0);
-          if (cs & 2u) t1 += atomicAdd(dst + 1, a1);
-          if (cs & 4u) t2 += atomicAdd(dst + 2, a2);
-          if (cs & 8u) t3 += atomicAdd(dst + 3, a3);
+          unsigned long long* da = reinterpret_cast<unsigned long long*>(dst);
+          if (cs & 1u) { const uint64_t o = atomicAdd(da + 0, (unsigned long long)a0); t0 = o + a0; ovf |= t0 < o; }
+          if (cs & 2u) { const uint64_t o = atomicAdd(da + 1, (unsigned long long)a1); t1 = o + a1; ovf |= t1 < o; }
+          if (cs & 4u) { const uint64_t o = atomicAdd(da + 2, (unsigned long long)a2); t2 = o + a2; ovf |= t2 < o; }
+          if (cs & 8u) { const uint64_t o = atomicAdd(da + 3, (unsigned long long)a3); t3 = o + a3; ovf |= t3 < o; }
         } else if (cs == 0xfu) {
-          st4(dst, a0, a1, a2, a3);
+          asm volatile("st.global.v4.u64 [%0], {%1,%2,%3,%4};" ::"l"(dst), "l"(a0), "l"(a1), "l"(a2), "l"(a3)
+                       : "memory");
         } else {
           if (cs & 1u) dst[0] = a0;
           if (cs & 2u) dst[1] = a1;
           if (cs & 4u) dst[2] = a2;
           if (cs & 8u) dst[3] = a3;
         }
-        // a multiplicity at or above 2^53 may have been rounded (flags bit 1)
-        const double big = 9007199254740992.0;
-        if (((cs & 1u) && t0 >= big) || ((cs & 2u) && t1 >= big) || ((cs & 4u) && t2 >= big) ||
-            ((cs & 8u) && t3 >= big))
-          atomicOr(flags, 2u);
+        const uint64_t b53 = 1ull << 53;
+        big |= (uint32_t)(((cs & 1u) && t0 >= b53) || ((cs & 2u) && t1 >= b53) || ((cs & 4u) && t2 >= b53) ||
+                          ((cs & 8u) && t3 >= b53));
         if (COUNT) nw += __popc(cs);
       }
     });
   }
+  if (__any_sync(0xffffffffu, big != 0u) && lane == 0) atomicOr(flags, 2u);
+  if (__any_sync(0xffffffffu, ovf != 0u) && lane == 0) atomicOr(flags, 8u);
   if (COUNT) {
     for (int o = 16; o; o >>= 1) {
       nvals += __shfl_xor_sync(0xffffffffu, nvals, o);
@@ -583,22 +700,27 @@ __global__ void __launch_bounds__(256, 4) k_lvl_fwd_gather(
 }
 
 // MFBr gather of level l: zeta(s,v) = sum over the segment's pairs of the
-// successors' values; single-item rows are finalised here (lambda, value
-// zeta + 1/sigma_bar), multi-item rows add into their hub accumulator.
+// successors' values (double-float, compensated).  Single-item rows are
+// finalised here: lambda(v) += zeta * sigma_bar and the slot of (s,v) takes
+// the value zeta + 1/sigma_bar; multi-item rows add their partial zeta into
+// the row's FP64 accumulator.
 template <bool COUNT>
 __global__ void __launch_bounds__(256, 4) k_lvl_bwd_gather(
     const uint4* __restrict__ segs, const uint32_t* nseg_p, const uint32_t* __restrict__ prow,
     const uint4* __restrict__ pmask, int nb, int W, const uint32_t* __restrict__ Fl,
-    const int32_t* __restrict__ hub_of, double* sv, double* zacc, double* lambda, uint32_t* next_group,
+    const int32_t* __restrict__ hub_of, double* svd, double* zacc, double* lambda, uint32_t* next_group,
     unsigned long long* bytes, unsigned long long* stat) {
   __shared__ GatherSmem gsm[8];
   GatherSmem& gs = gsm[threadIdx.x >> 5];
+  uint64_t* sv = reinterpret_cast<uint64_t*>(svd);
   const unsigned lane = lane_id();
   const uint32_t nseg = *nseg_p;
   const int shift = 4 * (int)(lane & 7u);
   unsigned long long nvals = 0, nw = 0;
+  uint32_t ovf = 0;
   FOR_SEGMENT_GROUPS(nseg, next_group)
-    auto finish = [&](int k, double a0, double a1, double a2, double a3, uint32_t) {
+    auto finish = [&](int k, uint64_t, uint64_t, uint64_t, uint64_t, float s0, float s1, float s2, float s3, float c0,
+                      float c1, float c2, float c3, uint32_t) {
       const int32_t v = (int32_t)__shfl_sync(0xffffffffu, myseg.x, k);
       const uint32_t z = __shfl_sync(0xffffffffu, myseg.z, k);
       const int d = (int)((z >> 8) & 0xffu);
@@ -608,40 +730,49 @@ __global__ void __launch_bounds__(256, 4) k_lvl_bwd_gather(
       if ((z >> 16) & 1u) {
         if (fs) {
           double* za = zacc + (size_t)hub_of[v] * nb + col;
-          if (fs & 1u) atomicAdd(za + 0, a0);
-          if (fs & 2u) atomicAdd(za + 1, a1);
-          if (fs & 4u) atomicAdd(za + 2, a2);
-          if (fs & 8u) atomicAdd(za + 3, a3);
+          if (fs & 1u) atomicAdd(za + 0, df_to_double(acc_value(s0, c0)));
+          if (fs & 2u) atomicAdd(za + 1, df_to_double(acc_value(s1, c1)));
+          if (fs & 4u) atomicAdd(za + 2, df_to_double(acc_value(s2, c2)));
+          if (fs & 8u) atomicAdd(za + 3, df_to_double(acc_value(s3, c3)));
           if (COUNT) nw += __popc(fs);
         }
       } else {
-        double lam = 0.0;
+        dfl lam = {0.f, 0.f};
         if (fs) {
-          // read-modify-write of the lane's sector: only the set columns
-          // change (this segment is the only writer of them in this launch)
-          double* p = sv + (size_t)v * nb + col;
-          double s0, s1, s2, s3;
-          ld4_coherent(p, s0, s1, s2, s3);
-          if (fs & 1u) { lam += a0 * s0; s0 = a0 + 1.0 / s0; }
-          if (fs & 2u) { lam += a1 * s1; s1 = a1 + 1.0 / s1; }
-          if (fs & 4u) { lam += a2 * s2; s2 = a2 + 1.0 / s2; }
-          if (fs & 8u) { lam += a3 * s3; s3 = a3 + 1.0 / s3; }
-          st4(p, s0, s1, s2, s3);
+          // read-modify-write of the lane's sector: only the set columns change
+          // (this segment is the only writer of them in this launch)
+          uint64_t* p = sv + (size_t)v * nb + col;
+          uint64_t w0, w1, w2, w3;
+          asm volatile("ld.global.v4.u64 {%0,%1,%2,%3}, [%4];"
+                       : "=l"(w0), "=l"(w1), "=l"(w2), "=l"(w3) : "l"(p) : "memory");
+          if (fs & 1u) { const dfl zt = acc_value(s0, c0); const dfl sg = df_of_u64(w0);
+                         lam = df_add(lam, df_mul(zt, sg)); w0 = df_pack(df_add(zt, df_rcp(sg))); }
+          if (fs & 2u) { const dfl zt = acc_value(s1, c1); const dfl sg = df_of_u64(w1);
+                         lam = df_add(lam, df_mul(zt, sg)); w1 = df_pack(df_add(zt, df_rcp(sg))); }
+          if (fs & 4u) { const dfl zt = acc_value(s2, c2); const dfl sg = df_of_u64(w2);
+                         lam = df_add(lam, df_mul(zt, sg)); w2 = df_pack(df_add(zt, df_rcp(sg))); }
+          if (fs & 8u) { const dfl zt = acc_value(s3, c3); const dfl sg = df_of_u64(w3);
+                         lam = df_add(lam, df_mul(zt, sg)); w3 = df_pack(df_add(zt, df_rcp(sg))); }
+          asm volatile("st.global.v4.u64 [%0], {%1,%2,%3,%4};" ::"l"(p), "l"(w0), "l"(w1), "l"(w2), "l"(w3)
+                       : "memory");
           if (COUNT) nw += 2 * __popc(fs);
         }
-        if (__any_sync(0xffffffffu, lam != 0.0)) {
-          for (int o = 16; o; o >>= 1) lam += __shfl_xor_sync(0xffffffffu, lam, o);
-          if (lane == 0) atomicAdd(&lambda[v], lam);
+        if (__any_sync(0xffffffffu, lam.hi != 0.f)) {
+          for (int o = 16; o; o >>= 1) {
+            const dfl other = {__shfl_xor_sync(0xffffffffu, lam.hi, o), __shfl_xor_sync(0xffffffffu, lam.lo, o)};
+            lam = df_add(lam, other);
+          }
+          if (lane == 0) atomicAdd(&lambda[v], df_to_double(lam));
         }
       }
     };
-    gather_group<COUNT>(myseg, nin, prow, pmask, gs, sv, nvals, finish);
+    gather_group<COUNT, false>(myseg, nin, prow, pmask, gs, sv, nvals, ovf, finish);
     // segments without successor pairs: zeta = 0
     uint32_t empty = __ballot_sync(0xffffffffu, (int)lane < nin && (myseg.z & 0xffu) == 0u);
     while (empty) {
       const int k = __ffs(empty) - 1;
       empty &= empty - 1;
-      finish(k, 0.0, 0.0, 0.0, 0.0, 0u);
+      finish(k, 0, 0, 0, 0, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0u);
     }
   }
   if (COUNT) {
@@ -686,9 +817,10 @@ __global__ void k_lvl_hub_final(const int32_t* __restrict__ hubs, int32_t nhub, 
           const size_t vi = (size_t)v * nb + j * 32 + lane;
           const double z = zacc[zi];
           zacc[zi] = 0.0;
-          const double sg = sv[vi];
-          lam += z * sg;
-          sv[vi] = z + 1.0 / sg;
+          uint64_t* slot = reinterpret_cast<uint64_t*>(sv) + vi;
+          const uint64_t sg = *slot;
+          lam += z * (double)sg;
+          *slot = df_pack(df_add(df_of_double(z), df_rcp(df_of_u64(sg))));
         }
         if (bytes) nbytes += 32ull * __popc(fj);
       }
@@ -725,7 +857,7 @@ __global__ void k_lvl_output(const int32_t* __restrict__ list, uint32_t count, i
       const int c = j * 32 + lane;
       if (((fj >> lane) & 1u) && c < nactive) {
         dist_out[(size_t)c * n + v] = level;
-        if (sigma_out) sigma_out[(size_t)c * n + v] = sv[(size_t)v * nb + c];
+        if (sigma_out) sigma_out[(size_t)c * n + v] = (double)reinterpret_cast<const uint64_t*>(sv)[(size_t)v * nb + c];
       }
     }
   }
@@ -886,7 +1018,14 @@ mfbc_status level_batch(RunCtx& rc, LevelState& s, const int32_t* d_src_batch, i
     MFBC_CUDA_TRY(cudaMemcpyAsync(rc.h_ctr, s.ctr->list_count, sizeof(uint32_t) * 5, cudaMemcpyDeviceToHost, st), rc.err);
     MFBC_CUDA_TRY(cudaStreamSynchronize(st), rc.err);
     rc.prof->drain();
-    if (rc.h_ctr[4] & 1u) { *levels_exceeded = true; level_reset(rc, s, l + 1); return MFBC_ERR_NO_CONVERGENCE; }
+    if (rc.h_ctr[4] & 9u) {
+      // list capacity exceeded (bit 0) or a path count passed 2^64 (bit 3):
+      // the general kernels redo this batch
+      k_clear_flag_bits<<<1, 1, 0, st>>>(&s.ctr->flags, 9u);
+      *levels_exceeded = true;
+      level_reset(rc, s, l + 1);
+      return MFBC_ERR_NO_CONVERGENCE;
+    }
     const uint32_t cn = rc.h_ctr[0];
     P.off.push_back(off_n);
     P.cnt.push_back(cn);
