@@ -278,7 +278,7 @@ __device__ __forceinline__ bool emit_quads(const WarpSmem& w, int nm, int32_t v,
     if (lane == 0) atomicOr(&work[3], 1u);
     return false;
   }
-  if (npairs) *npairs += P;
+  if (npairs) *npairs += P + (uint64_t)S * (1ull << 32);   // pairs in the low word, segments in the high
   int r = 0;
   for (uint32_t ql = quads; ql; ql &= ql - 1, r++) {
     const int d = __ffs(ql) - 1;
@@ -405,8 +405,9 @@ __global__ void __launch_bounds__(LVL_WARPS * 32) k_lvl_fwd_pairs(
     }
   }
   if (bytes && lane == 0) {
-    atomicAdd(bytes, nbytes + 20ull * npairs);
-    atomicAdd(&stat[0], npairs);
+    const unsigned long long np = npairs & 0xffffffffull, ns = npairs >> 32;
+    atomicAdd(bytes, nbytes + 20ull * np + 16ull * ns);
+    atomicAdd(&stat[0], np);
   }
 }
 
@@ -490,8 +491,9 @@ __global__ void __launch_bounds__(LVL_WARPS * 32) k_lvl_bwd_pairs(
     }
   }
   if (bytes && lane == 0) {
-    atomicAdd(bytes, nbytes + 20ull * npairs);
-    atomicAdd(&stat[1], npairs);
+    const unsigned long long np = npairs & 0xffffffffull, ns = npairs >> 32;
+    atomicAdd(bytes, nbytes + 20ull * np + 16ull * ns);
+    atomicAdd(&stat[1], np);
   }
 }
 
@@ -561,7 +563,8 @@ __device__ __forceinline__ void ld4u(const uint64_t* p, uint64_t& a, uint64_t& b
 template <bool COUNT, bool INT, class Flush>
 __device__ __forceinline__ void gather_group(const uint4& myseg, int nin, const uint32_t* __restrict__ prow,
                                              const uint4* __restrict__ pmask, GatherSmem& gs, const uint64_t* sv,
-                                             unsigned long long& nvals, uint32_t& ovf, Flush flush) {
+                                             unsigned long long& nvals, unsigned long long& nvals_rec, uint32_t& ovf,
+                                             Flush flush) {
   const unsigned lane = lane_id();
   const int mycnt = (int)lane < nin ? (int)(myseg.z & 0xffu) : 0;
   int incl = mycnt;
@@ -571,6 +574,9 @@ __device__ __forceinline__ void gather_group(const uint4& myseg, int nin, const 
   }
   const int excl = incl - mycnt;
   const int T = __shfl_sync(0xffffffffu, incl, 31);
+  // algorithmic bytes of the group's records: 16 B per segment header and
+  // 20 B per pair (row index + mask), counted once (by lane 0)
+  if (COUNT && lane == 0) nvals_rec += 16ull * nin + 20ull * T;
   const int shift = 4 * (int)(lane & 7u);
   const int mword = (int)(lane >> 3);
   uint64_t i0 = 0, i1 = 0, i2 = 0, i3 = 0;                 // MFBF sums
@@ -651,10 +657,10 @@ __global__ void __launch_bounds__(256, 4) k_lvl_fwd_gather(
   uint64_t* sv = reinterpret_cast<uint64_t*>(svd);
   const unsigned lane = lane_id();
   const uint32_t nseg = *nseg_p;
-  unsigned long long nvals = 0, nw = 0;
+  unsigned long long nvals = 0, nw = 0, nrec = 0;
   uint32_t ovf = 0, big = 0;
   FOR_SEGMENT_GROUPS(nseg, next_group)
-    gather_group<COUNT, true>(myseg, nin, prow, pmask, gs, sv, nvals, ovf,
+    gather_group<COUNT, true>(myseg, nin, prow, pmask, gs, sv, nvals, nrec, ovf,
         [&](int k, uint64_t a0, uint64_t a1, uint64_t a2, uint64_t a3, float, float, float, float, float, float,
             float, float, uint32_t cs) {
       const int32_t v = (int32_t)__shfl_sync(0xffffffffu, myseg.x, k);
@@ -692,8 +698,9 @@ __global__ void __launch_bounds__(256, 4) k_lvl_fwd_gather(
       nvals += __shfl_xor_sync(0xffffffffu, nvals, o);
       nw += __shfl_xor_sync(0xffffffffu, nw, o);
     }
+    for (int o = 16; o; o >>= 1) nrec += __shfl_xor_sync(0xffffffffu, nrec, o);
     if (lane == 0) {
-      atomicAdd(bytes, 8ull * (nvals + nw) + 16ull * nseg / 32);
+      atomicAdd(bytes, 8ull * (nvals + nw) + nrec);
       atomicAdd(&stat[2], nvals);
     }
   }
@@ -716,7 +723,7 @@ __global__ void __launch_bounds__(256, 4) k_lvl_bwd_gather(
   const unsigned lane = lane_id();
   const uint32_t nseg = *nseg_p;
   const int shift = 4 * (int)(lane & 7u);
-  unsigned long long nvals = 0, nw = 0;
+  unsigned long long nvals = 0, nw = 0, nrec = 0;
   uint32_t ovf = 0;
   FOR_SEGMENT_GROUPS(nseg, next_group)
     auto finish = [&](int k, uint64_t, uint64_t, uint64_t, uint64_t, float s0, float s1, float s2, float s3, float c0,
@@ -763,10 +770,11 @@ __global__ void __launch_bounds__(256, 4) k_lvl_bwd_gather(
             lam = df_add(lam, other);
           }
           if (lane == 0) atomicAdd(&lambda[v], df_to_double(lam));
+          if (COUNT && lane == 0) nrec += 8ull;
         }
       }
     };
-    gather_group<COUNT, false>(myseg, nin, prow, pmask, gs, sv, nvals, ovf, finish);
+    gather_group<COUNT, false>(myseg, nin, prow, pmask, gs, sv, nvals, nrec, ovf, finish);
     // segments without successor pairs: zeta = 0
     uint32_t empty = __ballot_sync(0xffffffffu, (int)lane < nin && (myseg.z & 0xffu) == 0u);
     while (empty) {
@@ -780,20 +788,26 @@ __global__ void __launch_bounds__(256, 4) k_lvl_bwd_gather(
       nvals += __shfl_xor_sync(0xffffffffu, nvals, o);
       nw += __shfl_xor_sync(0xffffffffu, nw, o);
     }
+    for (int o = 16; o; o >>= 1) nrec += __shfl_xor_sync(0xffffffffu, nrec, o);
     if (lane == 0) {
-      atomicAdd(bytes, 8ull * (nvals + nw) + 16ull * nseg / 32);
+      atomicAdd(bytes, 8ull * (nvals + nw) + nrec);
       atomicAdd(&stat[3], nvals);
     }
   }
 }
 
-// Finalise the multi-item vertices of level l: zeta from the hub accumulator.
-// 32 hubs are tested per warp at once; a hub's frontier row is read once.
+// Finalise the multi-item vertices of level l: zeta from the row's FP64
+// accumulator, lambda(v) += zeta * sigma_bar, slot value zeta + 1/sigma_bar
+// (double-float), accumulator reset.  32 hubs are tested per warp at once;
+// lane l handles columns 4l..4l+3 of each 128-column quad.
 __global__ void k_lvl_hub_final(const int32_t* __restrict__ hubs, int32_t nhub, int W, int nb,
                                 const uint32_t* __restrict__ Fl, const uint32_t* __restrict__ mem_l,
-                                double* sv, double* zacc, double* lambda, unsigned long long* bytes) {
+                                double* svd, double* zacc, double* lambda, unsigned long long* bytes) {
   const unsigned lane = lane_id();
   const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  const int Q = W / 4;
+  const int shift = 4 * (int)(lane & 7u);
+  uint64_t* sv = reinterpret_cast<uint64_t*>(svd);
   unsigned long long nbytes = 0;
   for (uint64_t base = (((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; base < (uint64_t)nhub;
        base += nw * 32) {
@@ -805,31 +819,42 @@ __global__ void k_lvl_hub_final(const int32_t* __restrict__ hubs, int32_t nhub, 
       am &= am - 1;
       const uint64_t h = base + t;
       const int32_t v = __shfl_sync(0xffffffffu, myv, t);
-      const uint32_t Fv = (int)lane < W ? Fl[(size_t)v * W + lane] : 0u;
-      uint32_t words = __ballot_sync(0xffffffffu, Fv != 0u);
-      double lam = 0.0;
-      while (words) {
-        const int j = __ffs(words) - 1;
-        words &= words - 1;
-        const uint32_t fj = __shfl_sync(0xffffffffu, Fv, j);
-        if ((fj >> lane) & 1u) {
-          const size_t zi = (size_t)h * nb + j * 32 + lane;
-          const size_t vi = (size_t)v * nb + j * 32 + lane;
-          const double z = zacc[zi];
-          zacc[zi] = 0.0;
-          uint64_t* slot = reinterpret_cast<uint64_t*>(sv) + vi;
-          const uint64_t sg = *slot;
-          lam += z * (double)sg;
-          *slot = df_pack(df_add(df_of_double(z), df_rcp(df_of_u64(sg))));
+      dfl lam = {0.f, 0.f};
+      for (int d = 0; d < Q; d++) {
+        const uint32_t fs = (Fl[(size_t)v * W + 4 * d + (lane >> 3)] >> shift) & 0xfu;
+        if (!__any_sync(0xffffffffu, fs != 0u)) continue;
+        if (fs) {
+          double* za = zacc + (size_t)h * nb + 128 * d + 4 * lane;
+          uint64_t* p = sv + (size_t)v * nb + 128 * d + 4 * lane;
+          double z0, z1, z2, z3;
+          uint64_t w0, w1, w2, w3;
+          asm volatile("ld.global.v4.f64 {%0,%1,%2,%3}, [%4];" : "=d"(z0), "=d"(z1), "=d"(z2), "=d"(z3) : "l"(za) : "memory");
+          asm volatile("ld.global.v4.u64 {%0,%1,%2,%3}, [%4];" : "=l"(w0), "=l"(w1), "=l"(w2), "=l"(w3) : "l"(p) : "memory");
+          if (fs & 1u) { const dfl zt = df_of_double(z0); const dfl sg = df_of_u64(w0);
+                         lam = df_add(lam, df_mul(zt, sg)); w0 = df_pack(df_add(zt, df_rcp(sg))); z0 = 0.0; }
+          if (fs & 2u) { const dfl zt = df_of_double(z1); const dfl sg = df_of_u64(w1);
+                         lam = df_add(lam, df_mul(zt, sg)); w1 = df_pack(df_add(zt, df_rcp(sg))); z1 = 0.0; }
+          if (fs & 4u) { const dfl zt = df_of_double(z2); const dfl sg = df_of_u64(w2);
+                         lam = df_add(lam, df_mul(zt, sg)); w2 = df_pack(df_add(zt, df_rcp(sg))); z2 = 0.0; }
+          if (fs & 8u) { const dfl zt = df_of_double(z3); const dfl sg = df_of_u64(w3);
+                         lam = df_add(lam, df_mul(zt, sg)); w3 = df_pack(df_add(zt, df_rcp(sg))); z3 = 0.0; }
+          asm volatile("st.global.v4.f64 [%0], {%1,%2,%3,%4};" ::"l"(za), "d"(z0), "d"(z1), "d"(z2), "d"(z3) : "memory");
+          asm volatile("st.global.v4.u64 [%0], {%1,%2,%3,%4};" ::"l"(p), "l"(w0), "l"(w1), "l"(w2), "l"(w3) : "memory");
+          if (bytes) nbytes += 32ull * __popc(fs);
         }
-        if (bytes) nbytes += 32ull * __popc(fj);
       }
-      for (int o = 16; o; o >>= 1) lam += __shfl_xor_sync(0xffffffffu, lam, o);
-      if (lane == 0) lambda[v] += lam;
-      if (bytes) nbytes += 4ull * W + 16ull;
+      for (int o = 16; o; o >>= 1) {
+        const dfl other = {__shfl_xor_sync(0xffffffffu, lam.hi, o), __shfl_xor_sync(0xffffffffu, lam.lo, o)};
+        lam = df_add(lam, other);
+      }
+      if (lane == 0) lambda[v] += df_to_double(lam);
+      if (bytes && lane == 0) nbytes += 4ull * W + 16ull;
     }
   }
-  if (bytes && lane == 0) atomicAdd(bytes, nbytes);
+  if (bytes) {
+    for (int o = 16; o; o >>= 1) nbytes += __shfl_xor_sync(0xffffffffu, nbytes, o);
+    if (lane == 0) atomicAdd(bytes, nbytes);
+  }
 }
 
 // Return the bit masks touched by a batch to zero (F rows, visited rows).
