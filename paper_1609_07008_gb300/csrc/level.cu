@@ -219,7 +219,7 @@ struct WarpSmem {
 constexpr size_t LVL_SMEM = sizeof(WarpSmem) * LVL_WARPS;
 
 #ifndef MFBC_GATHER_U
-#define MFBC_GATHER_U 2
+#define MFBC_GATHER_U 4
 #endif
 constexpr int GATHER_U = MFBC_GATHER_U;      // gather loads in flight per warp
 
