@@ -288,28 +288,47 @@ void finish_profile(Run& R, mfbc_profile* out, int64_t batches, int64_t fi, int6
   out->path = R.plan.path;
 }
 
-__global__ void k_order_keys(const int32_t* __restrict__ src, int32_t nsrc, const int32_t* __restrict__ d0,
-                             const int32_t* __restrict__ d1, int64_t* keys) {
-  const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= nsrc) return;
-  const int32_t s = src[i];
-  const int64_t a = min(d0[s], 0xffff), b = min(d1[s], 0xffff);
-  keys[i] = (a << 48) | (b << 32) | (int64_t)i;
+// Per source: its depth d1 from the highest-degree vertex, its BFS parent
+// toward that vertex (the smallest-id neighbour one level closer; itself for
+// the root or when unreachable) and its depth d2 from the second hub.
+// One warp per source, lanes over the neighbours.
+__global__ void k_order_info(const int32_t* __restrict__ src, int32_t nsrc, const int64_t* __restrict__ rowptr,
+                             const int32_t* __restrict__ col, const int32_t* __restrict__ d1,
+                             const int32_t* __restrict__ d2, int4* info) {
+  const uint64_t gw = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const unsigned lane = threadIdx.x & 31u;
+  if (gw >= (uint64_t)nsrc) return;
+  const int32_t s = src[gw];
+  const int32_t ds = d1[s];
+  int32_t best = 0x7fffffff;
+  if (ds > 0 && ds != 0x7fffffff)
+    for (int64_t k = rowptr[s] + lane; k < rowptr[s + 1]; k += 32) {
+      const int32_t u = col[k];
+      if (d1[u] == ds - 1 && u < best) best = u;
+    }
+  for (int o = 16; o; o >>= 1) best = min(best, __shfl_xor_sync(0xffffffffu, best, o));
+  if (lane == 0) {
+    const int32_t par = best == 0x7fffffff ? s : best;
+    info[gw] = make_int4(min(ds, 0xffff), par, min(d2[par], 0xffff), min(d2[s], 0xffff));
+  }
 }
 
-// Group sources of similar depth: sort by BFS distance to the two
-// highest-degree vertices (level kernels, undirected graphs).  Writes the
-// permuted list to d_out; returns false (and leaves the order alone) when it
-// does not apply.  The level state's sv array serves as scratch.
+// Group sources of similar distance profile into the same batches (level
+// kernels, undirected graphs): sort by (depth from the highest-degree vertex,
+// depth of the BFS parent from the second hub, parent, own depth from the
+// second hub).  Sources hanging off one parent see every other vertex at
+// almost the same distance, so their frontier bits land in the same words.
+// Writes the permuted list to d_out; leaves the order alone when it does not
+// apply.  The level state's sv array serves as scratch.
 mfbc_status order_sources(RunCtx& rc, LevelState& ls, const int32_t* d_src, int32_t nsrc, int32_t* d_out,
                           bool* applied) {
   const DevGraph& g = *rc.g;
   const int32_t n = g.n;
   *applied = false;
-  const size_t need = al256(sizeof(int32_t) * 2 * (size_t)n) + sizeof(int64_t) * (size_t)nsrc;
+  const size_t need = al256(sizeof(int32_t) * 2 * (size_t)n) + sizeof(int4) * (size_t)nsrc;
   if (g.directed || g.top_hub[0] < 0 || need > sizeof(double) * (size_t)n * ls.nb) return MFBC_OK;
   int32_t* rows = (int32_t*)ls.sv;
-  int64_t* keys = (int64_t*)((char*)ls.sv + al256(sizeof(int32_t) * 2 * (size_t)n));
+  int4* info = (int4*)((char*)ls.sv + al256(sizeof(int32_t) * 2 * (size_t)n));
   for (int k = 0; k < 2; k++) {
     int32_t* row = rows + (size_t)k * n;
     const int32_t h = g.top_hub[k];
@@ -326,14 +345,23 @@ mfbc_status order_sources(RunCtx& rc, LevelState& ls, const int32_t* d_src, int3
     level_output(rc, ls, levels, 1, row, nullptr);
     level_reset(rc, ls, levels);
   }
-  k_order_keys<<<(nsrc + 255) / 256, 256, 0, rc.stream>>>(d_src, nsrc, rows, rows + n, keys);
-  std::vector<int64_t> hk((size_t)nsrc);
-  std::vector<int32_t> hs((size_t)nsrc), out((size_t)nsrc);
-  MFBC_CUDA_TRY(cudaMemcpyAsync(hk.data(), keys, sizeof(int64_t) * nsrc, cudaMemcpyDeviceToHost, rc.stream), rc.err);
+  k_order_info<<<(unsigned)(((uint64_t)nsrc * 32 + 255) / 256), 256, 0, rc.stream>>>(d_src, nsrc, g.rowptr, g.col,
+                                                                                   rows, rows + n, info);
+  std::vector<int4> hi((size_t)nsrc);
+  std::vector<int32_t> hs((size_t)nsrc), out((size_t)nsrc), idx((size_t)nsrc);
+  MFBC_CUDA_TRY(cudaMemcpyAsync(hi.data(), info, sizeof(int4) * nsrc, cudaMemcpyDeviceToHost, rc.stream), rc.err);
   MFBC_CUDA_TRY(cudaMemcpyAsync(hs.data(), d_src, sizeof(int32_t) * nsrc, cudaMemcpyDeviceToHost, rc.stream), rc.err);
   MFBC_CUDA_TRY(cudaStreamSynchronize(rc.stream), rc.err);
-  std::sort(hk.begin(), hk.end());
-  for (int32_t i = 0; i < nsrc; i++) out[i] = hs[(size_t)(hk[i] & 0xffffffffll)];
+  for (int32_t i = 0; i < nsrc; i++) idx[i] = i;
+  std::sort(idx.begin(), idx.end(), [&](int32_t a, int32_t b) {
+    const int4 x = hi[a], y = hi[b];
+    if (x.x != y.x) return x.x < y.x;
+    if (x.z != y.z) return x.z < y.z;
+    if (x.y != y.y) return x.y < y.y;
+    if (x.w != y.w) return x.w < y.w;
+    return a < b;
+  });
+  for (int32_t i = 0; i < nsrc; i++) out[i] = hs[(size_t)idx[i]];
   MFBC_CUDA_TRY(cudaMemcpyAsync(d_out, out.data(), sizeof(int32_t) * nsrc, cudaMemcpyHostToDevice, rc.stream), rc.err);
   MFBC_CUDA_TRY(cudaStreamSynchronize(rc.stream), rc.err);
   *applied = true;

@@ -222,6 +222,9 @@ constexpr size_t LVL_SMEM = sizeof(WarpSmem) * LVL_WARPS;
 #define MFBC_GATHER_U 4
 #endif
 constexpr int GATHER_U = MFBC_GATHER_U;      // gather loads in flight per warp
+#ifndef MFBC_GATHER_MIN_BLOCKS
+#define MFBC_GATHER_MIN_BLOCKS 4
+#endif
 
 // Item metadata: first arc (bits 0..39), arc count (bits 40..45), multi-item row (bit 46).
 __device__ __forceinline__ int64_t meta_beg(int64_t m) { return m & ((1ll << 40) - 1); }
@@ -609,12 +612,12 @@ __device__ __forceinline__ void gather_group(const uint4& myseg, int nin, const 
         const int q = q0 + r;
         if (q < nq) {
           if (INT) {
-            const uint64_t o0 = i0, o1 = i1, o2 = i2, o3 = i3;
+            // no wrap check per add: stored counts stay below 2^58 (larger
+            // sums are flagged at the flush), and a segment adds <= 32 of them
             if (sl[r] & 1u) i0 += x[r][0];
             if (sl[r] & 2u) i1 += x[r][1];
             if (sl[r] & 4u) i2 += x[r][2];
             if (sl[r] & 8u) i3 += x[r][3];
-            ovf |= (uint32_t)((i0 < o0) | (i1 < o1) | (i2 < o2) | (i3 < o3));
           } else {
             if (sl[r] & 1u) acc_add(s0, c0, x[r][0]);
             if (sl[r] & 2u) acc_add(s1, c1, x[r][1]);
@@ -648,7 +651,7 @@ __device__ __forceinline__ void gather_group(const uint4& myseg, int nin, const 
 // (exact 64-bit integers).  flags: bit 1 some sigma_bar >= 2^53, bit 3 a sum
 // passed 2^64 (the batch is then recomputed by the general kernels).
 template <bool COUNT>
-__global__ void __launch_bounds__(256, 4) k_lvl_fwd_gather(
+__global__ void __launch_bounds__(256, MFBC_GATHER_MIN_BLOCKS) k_lvl_fwd_gather(
     const uint4* __restrict__ segs, const uint32_t* nseg_p, const uint32_t* __restrict__ prow,
     const uint4* __restrict__ pmask, int nb, double* svd, uint32_t* flags, uint32_t* next_group,
     unsigned long long* bytes, unsigned long long* stat) {
@@ -684,9 +687,13 @@ __global__ void __launch_bounds__(256, 4) k_lvl_fwd_gather(
           if (cs & 4u) dst[2] = a2;
           if (cs & 8u) dst[3] = a3;
         }
-        const uint64_t b53 = 1ull << 53;
-        big |= (uint32_t)(((cs & 1u) && t0 >= b53) || ((cs & 2u) && t1 >= b53) || ((cs & 4u) && t2 >= b53) ||
-                          ((cs & 8u) && t3 >= b53));
+        // bit 1: a count reached 2^53 (FP64 output inexact); bit 3: a count
+        // reached 2^58 (later sums could wrap 2^64: the batch is redone by the
+        // general kernels)
+        const uint64_t m = ((cs & 1u) ? t0 : 0ull) | ((cs & 2u) ? t1 : 0ull) | ((cs & 4u) ? t2 : 0ull) |
+                           ((cs & 8u) ? t3 : 0ull);
+        big |= (uint32_t)(m >= (1ull << 53));
+        ovf |= (uint32_t)(m >= (1ull << 58));
         if (COUNT) nw += __popc(cs);
       }
     });
@@ -712,7 +719,7 @@ __global__ void __launch_bounds__(256, 4) k_lvl_fwd_gather(
 // the value zeta + 1/sigma_bar; multi-item rows add their partial zeta into
 // the row's FP64 accumulator.
 template <bool COUNT>
-__global__ void __launch_bounds__(256, 4) k_lvl_bwd_gather(
+__global__ void __launch_bounds__(256, MFBC_GATHER_MIN_BLOCKS) k_lvl_bwd_gather(
     const uint4* __restrict__ segs, const uint32_t* nseg_p, const uint32_t* __restrict__ prow,
     const uint4* __restrict__ pmask, int nb, int W, const uint32_t* __restrict__ Fl,
     const int32_t* __restrict__ hub_of, double* svd, double* zacc, double* lambda, uint32_t* next_group,
@@ -925,7 +932,7 @@ struct LevelPlan {                 // host-side level bookkeeping of one batch
 static thread_local LevelPlan tl_plan;
 
 static const unsigned kPairGrid = 152u * 6u;     // resident blocks of the pair kernels
-static const unsigned kGatherGrid = 152u * 4u;   // resident blocks of the gather kernels
+static const unsigned kGatherGrid = 152u * MFBC_GATHER_MIN_BLOCKS;   // resident blocks of the gather kernels
 
 // One MFBF (fwd) or MFBr product of level l over the items [ib, ie): the pair
 // kernel, a check of the pair buffers, then the gather kernel.  When the
