@@ -379,12 +379,19 @@ __global__ void __launch_bounds__(LVL_WARPS * 32) k_lvl_fwd_pairs(
       if (isMem) sm.su[__popc(mm & lt)] = u;
       __syncwarp();
       uint32_t cand = 0;
-#pragma unroll 4
-      for (int q = 0; q < nm; q++) {
-        const uint32_t f = (int)lane < W ? __ldg(&Fl[(size_t)sm.su[q] * W + lane]) : 0u;
-        const uint32_t mk = f & ~Vv;
-        sm.sF[q][lane] = mk;
-        cand |= mk;
+      for (int q0 = 0; q0 < nm; q0 += 8) {          // eight frontier rows in flight
+        uint32_t f[8];
+#pragma unroll
+        for (int t = 0; t < 8; t++)
+          f[t] = (q0 + t < nm && (int)lane < W) ? __ldg(&Fl[(size_t)sm.su[q0 + t] * W + lane]) : 0u;
+#pragma unroll
+        for (int t = 0; t < 8; t++) {
+          if (q0 + t < nm) {
+            const uint32_t mk = f[t] & ~Vv;
+            sm.sF[q0 + t][lane] = mk;
+            cand |= mk;
+          }
+        }
       }
       __syncwarp();
       if (bytes) nbytes += 4ull * W * (nm + 1);
@@ -479,11 +486,18 @@ __global__ void __launch_bounds__(LVL_WARPS * 32) k_lvl_bwd_pairs(
       if (isMem) sm.su[__popc(mm & lt)] = u;
       __syncwarp();
       uint32_t any = 0;
-#pragma unroll 4
-      for (int q = 0; q < nm; q++) {
-        const uint32_t f = (int)lane < W ? __ldg(&Fn[(size_t)sm.su[q] * W + lane]) : 0u;
-        sm.sF[q][lane] = f & Fv;
-        any |= f & Fv;
+      for (int q0 = 0; q0 < nm; q0 += 8) {          // eight frontier rows in flight
+        uint32_t f[8];
+#pragma unroll
+        for (int t = 0; t < 8; t++)
+          f[t] = (q0 + t < nm && (int)lane < W) ? __ldg(&Fn[(size_t)sm.su[q0 + t] * W + lane]) : 0u;
+#pragma unroll
+        for (int t = 0; t < 8; t++) {
+          if (q0 + t < nm) {
+            sm.sF[q0 + t][lane] = f[t] & Fv;
+            any |= f[t] & Fv;
+          }
+        }
       }
       __syncwarp();
       if (bytes) nbytes += 4ull * W * (nm + 1);
