@@ -45,6 +45,13 @@
 namespace mfbc {
 
 constexpr int LVL_WARPS = 8;                 // warps per block
+#ifndef MFBC_PAIR_MIN_BLOCKS
+#define MFBC_PAIR_MIN_BLOCKS 5
+#endif
+constexpr unsigned PAIR_GRID = 152u * MFBC_PAIR_MIN_BLOCKS;   // resident blocks of the pair kernels
+constexpr uint32_t PAIR_CHUNK = 1024;        // pair slots a warp reserves at a time
+constexpr uint32_t SEG_CHUNK = 64;           // segment slots a warp reserves at a time
+constexpr uint32_t SEG_DUMMY = 0xffffffffu;  // vertex field of a filler segment
 
 size_t level_bytes(const DevGraph& g, int nb, int Lcap, int64_t list_cap) {
   Carver c(nullptr, 0);
@@ -73,8 +80,12 @@ void level_carve(Carver& c, const DevGraph& g, int nb, int Lcap, int64_t list_ca
   // round, so these caps only bind for graphs beyond 2^31 of either)
   const int64_t items = std::max(g.items_in.count, g.items_out.count);
   const int64_t Q = std::max(1, s.W / 4);
-  s.pair_cap = (uint32_t)std::min<int64_t>(0x7fffffff, std::max<int64_t>(1 << 16, g.nnz * Q));
-  s.seg_cap = (uint32_t)std::min<int64_t>(0x7fffffff, std::max<int64_t>(1 << 16, items * Q));
+  // (warps reserve slots in chunks: the slack covers one partly used chunk
+  // per resident warp of the pair kernels; a round whose abandoned chunk
+  // tails still overflow is split like any other)
+  const int64_t warps = (int64_t)PAIR_GRID * LVL_WARPS;
+  s.pair_cap = (uint32_t)std::min<int64_t>(0x7fffffff, std::max<int64_t>(1 << 16, g.nnz * Q) + warps * PAIR_CHUNK);
+  s.seg_cap = (uint32_t)std::min<int64_t>(0x7fffffff, std::max<int64_t>(1 << 16, items * Q) + warps * SEG_CHUNK);
   s.prow = c.take<uint32_t>((size_t)s.pair_cap);
   s.pmask = c.take<uint4>((size_t)s.pair_cap);
   s.segs = c.take<uint4>((size_t)s.seg_cap);
@@ -99,27 +110,13 @@ __device__ __forceinline__ uint32_t active_mask(int w, int nactive) {
 // avoid it: MFBF path counts are exact 64-bit integers, and MFBr values
 // zeta + 1/sigma_bar are double-float pairs (hi + lo, about 48 significant
 // bits) kept in the same 8-byte slots and combined on the FP32 pipes with
-// error-free transformations (Dekker / Knuth two-sum, FMA-based products).
+// error-free transformations (Fast2Sum, FMA-based products).  Every MFBr
+// quantity is non-negative, so no sum cancels.
 struct dfl { float hi, lo; };
 
-__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
-  s = a + b;
-  const float bb = s - a;
-  e = (a - (s - bb)) + (b - bb);
-}
 __device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& e) {   // |a| >= |b|
   s = a + b;
   e = b - (s - a);
-}
-__device__ __forceinline__ dfl df_add(dfl a, dfl b) {
-  float s, e, t, f;
-  two_sum(a.hi, b.hi, s, e);
-  two_sum(a.lo, b.lo, t, f);
-  e += t;
-  fast_two_sum(s, e, s, e);
-  e += f;
-  fast_two_sum(s, e, s, e);
-  return {s, e};
 }
 __device__ __forceinline__ dfl df_of_u64(uint64_t x) {      // exact below 2^48
   const float h = __ull2float_rn(x);
@@ -135,14 +132,27 @@ __device__ __forceinline__ dfl df_mul(dfl a, dfl b) {
   fast_two_sum(p, e, s, t);
   return {s, t};
 }
-// 1/x for x >= 1: FP32 reciprocal refined by one Newton step.
+// 1/x for x >= 1: the FP32 reciprocal approximation (rcp.approx, relative
+// error about 2^-23) refined by one Newton step in double-float, e = 1 - x r,
+// 1/x = r (1 + e + e^2 + ...) ~ r + r e (error about e^2 ~ 2^-46).
 __device__ __forceinline__ dfl df_rcp(dfl a) {
-  const float r = 1.0f / a.hi;
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(a.hi));
   float e = fmaf(-a.hi, r, 1.0f);
   e = fmaf(-a.lo, r, e);
   float s, t;
   fast_two_sum(r, r * e, s, t);
   return {s, t};
+}
+// a + b for a, b >= 0: no cancellation, so Fast2Sum on the ordered high
+// parts plus the low parts gives a relative error of a few 2^-48.
+__device__ __forceinline__ dfl df_add_pos(dfl a, dfl b) {
+  const float x = fmaxf(a.hi, b.hi), y = fminf(a.hi, b.hi);
+  const float s = x + y;
+  const float e = (y - (s - x)) + (a.lo + b.lo);
+  float h, l;
+  fast_two_sum(s, e, h, l);
+  return {h, l};
 }
 __device__ __forceinline__ uint64_t df_pack(dfl a) {
   return (uint64_t)__float_as_uint(a.hi) | ((uint64_t)__float_as_uint(a.lo) << 32);
@@ -150,23 +160,46 @@ __device__ __forceinline__ uint64_t df_pack(dfl a) {
 __device__ __forceinline__ dfl df_unpack(uint64_t u) {
   return {__uint_as_float((uint32_t)u), __uint_as_float((uint32_t)(u >> 32))};
 }
-__device__ __forceinline__ double df_to_double(dfl a) { return (double)a.hi + (double)a.lo; }
 __device__ __forceinline__ dfl df_of_double(double x) {
   const float h = __double2float_rn(x);
   return {h, __double2float_rn(x - (double)h)};
 }
-// compensated accumulation of double-float terms into (s, c) (Neumaier)
+// compensated accumulation of non-negative double-float terms (hi, lo) into
+// (s, c): Fast2Sum on the ordered pair (max, min) gives the exact rounding
+// error of s + hi (Neumaier's summation without its branch)
+__device__ __forceinline__ void acc_add(float& s, float& c, float hi, float lo) {
+  const float a = fmaxf(s, hi), b = fminf(s, hi);
+  const float t = a + b;
+  c += (b - (t - a)) + lo;
+  s = t;
+}
 __device__ __forceinline__ void acc_add(float& s, float& c, uint64_t x) {
   const dfl v = df_unpack(x);
-  const float t = s + v.hi;
-  c += (fabsf(s) >= fabsf(v.hi)) ? ((s - t) + v.hi) : ((v.hi - t) + s);
-  c += v.lo;
-  s = t;
+  acc_add(s, c, v.hi, v.lo);
 }
 __device__ __forceinline__ dfl acc_value(float s, float c) {
   float h, l;
   fast_two_sum(s, c, h, l);
   return {h, l};
+}
+
+// One column of a finished level-l pair (s,v) with zeta(s,v) = zt: the
+// lambda term zeta * sigma_bar(s,v) goes into the compensated sum (ls, lc),
+// and the slot's new value zeta + 1/sigma_bar is returned (Sec. 4.2.1,
+// Algorithm 3).  w holds sigma_bar(s,v) as an integer below 2^58.
+__device__ __forceinline__ uint64_t finish_col(dfl zt, uint64_t w, float& ls, float& lc) {
+  const dfl sg = df_of_u64(w);
+  const dfl p = df_mul(zt, sg);
+  acc_add(ls, lc, p.hi, p.lo);
+  return df_pack(df_add_pos(zt, df_rcp(sg)));
+}
+// warp sum of non-negative compensated sums (s, c), as a double on every lane
+__device__ __forceinline__ double warp_acc_sum(float s, float c) {
+  for (int o = 16; o; o >>= 1) {
+    const float s2 = __shfl_xor_sync(0xffffffffu, s, o), c2 = __shfl_xor_sync(0xffffffffu, c, o);
+    acc_add(s, c, s2, c2);
+  }
+  return (double)s + (double)c;
 }
 
 __global__ void k_clear_flag_bits(uint32_t* flags, uint32_t bits) { atomicAnd(flags, ~bits); }
@@ -214,6 +247,7 @@ __global__ void k_lvl_visit(const int32_t* __restrict__ list, uint32_t count, in
 // Per-warp shared memory of the pair kernels.
 struct WarpSmem {
   int32_t su[32];                            // member neighbour ids of the item
+  int32_t newv[32];                          // vertices entering the next level, not yet appended
   uint32_t sF[32][33];                       // member q's masked frontier word j (padded: no bank conflicts)
 };
 constexpr size_t LVL_SMEM = sizeof(WarpSmem) * LVL_WARPS;
@@ -224,6 +258,9 @@ constexpr size_t LVL_SMEM = sizeof(WarpSmem) * LVL_WARPS;
 constexpr int GATHER_U = MFBC_GATHER_U;      // gather loads in flight per warp
 #ifndef MFBC_GATHER_MIN_BLOCKS
 #define MFBC_GATHER_MIN_BLOCKS 4
+#endif
+#ifndef MFBC_BWD_GATHER_MIN_BLOCKS
+#define MFBC_BWD_GATHER_MIN_BLOCKS MFBC_GATHER_MIN_BLOCKS
 #endif
 
 // Item metadata: first arc (bits 0..39), arc count (bits 40..45), multi-item row (bit 46).
@@ -248,12 +285,43 @@ __device__ __forceinline__ uint32_t quad_or(const WarpSmem& w, int q, int d) {
   return w.sF[q][4 * d] | w.sF[q][4 * d + 1] | w.sF[q][4 * d + 2] | w.sF[q][4 * d + 3];
 }
 
+// Pair and segment slots reserved by one warp.  Slots are taken from the
+// round's counters in chunks (one atomic per chunk rather than two per item:
+// the counters sit in one L2 slice).  Pair slots left at the end of a chunk
+// are never referenced; segment slots left over when a warp takes a new
+// chunk or finishes are filled with headers whose vertex is SEG_DUMMY, which
+// the gathers skip.
+struct SlotCursor { uint32_t p = 0, pe = 0, s = 0, se = 0; };
+
+// Reserve max(need, chunk) slots; false (cursor emptied, overflow flagged)
+// when the buffer cannot hold them.
+__device__ __forceinline__ bool reserve_slots(uint32_t* counter, uint32_t need, uint32_t chunk, uint32_t cap,
+                                              uint32_t* overflow, uint32_t& b, uint32_t& e) {
+  const uint32_t sz = need > chunk ? need : chunk;
+  uint32_t x = 0;
+  if (lane_id() == 0) x = atomicAdd(counter, sz);
+  x = __shfl_sync(0xffffffffu, x, 0);
+  if ((uint64_t)x + sz > cap) {
+    if (lane_id() == 0) atomicOr(overflow, 1u);
+    b = e = 0;
+    return false;
+  }
+  b = x;
+  e = x + sz;
+  return true;
+}
+
+__device__ __forceinline__ void fill_dummy_segs(uint4* segs, uint32_t b, uint32_t e) {
+  for (uint32_t i = b + lane_id(); i < e; i += 32) segs[i] = make_uint4(SEG_DUMMY, 0u, 0u, 0u);
+}
+
 // Emit the (member, mask) pairs of one item, quad by quad over `quads`
-// (ascending), as segments.  Space is reserved with one atomic per buffer;
-// returns false (writing nothing) when the buffers are full.
+// (ascending), as segments.  Returns false (writing nothing) when the
+// buffers are full.
 __device__ __forceinline__ bool emit_quads(const WarpSmem& w, int nm, int32_t v, bool multi, uint32_t quads, int Q,
                                            uint32_t* prow, uint4* pmask, uint4* segs, uint32_t* work,
-                                           uint32_t pair_cap, uint32_t seg_cap, unsigned long long* npairs) {
+                                           uint32_t pair_cap, uint32_t seg_cap, SlotCursor& cur,
+                                           unsigned long long* npairs) {
   const unsigned lane = lane_id();
   const uint32_t lt = (1u << lane) - 1u;
   int mycnt = 0;
@@ -270,17 +338,15 @@ __device__ __forceinline__ bool emit_quads(const WarpSmem& w, int nm, int32_t v,
   const int excl = incl - mycnt;
   const uint32_t P = (uint32_t)__shfl_sync(0xffffffffu, incl, 31);
   const uint32_t S = (uint32_t)__popc(quads);
-  uint32_t pb = 0, sb = 0;
-  if (lane == 0) {
-    pb = P ? atomicAdd(&work[0], P) : 0u;
-    sb = atomicAdd(&work[1], S);
-  }
-  pb = __shfl_sync(0xffffffffu, pb, 0);
-  sb = __shfl_sync(0xffffffffu, sb, 0);
-  if ((uint64_t)pb + P > pair_cap || (uint64_t)sb + S > seg_cap) {
-    if (lane == 0) atomicOr(&work[3], 1u);
+  if (cur.p + P > cur.pe && !reserve_slots(&work[0], P, PAIR_CHUNK, pair_cap, &work[3], cur.p, cur.pe))
     return false;
+  if (cur.s + S > cur.se) {
+    fill_dummy_segs(segs, cur.s, cur.se);
+    if (!reserve_slots(&work[1], S, SEG_CHUNK, seg_cap, &work[3], cur.s, cur.se)) return false;
   }
+  const uint32_t pb = cur.p, sb = cur.s;
+  cur.p += P;
+  cur.s += S;
   if (npairs) *npairs += P + (uint64_t)S * (1ull << 32);   // pairs in the low word, segments in the high
   int r = 0;
   for (uint32_t ql = quads; ql; ql &= ql - 1, r++) {
@@ -318,7 +384,7 @@ __device__ __forceinline__ uint32_t quads_of_words(uint32_t words, int Q) {
 // MFBF pairs of level l (see file comment): for items [ib, ie) of rows not yet
 // reached by every column, the masks F_l(u) & ~visited(v) of the in-neighbours
 // u in F_l, the next frontier bits F_{l+1}(v), and the level-(l+1) list.
-__global__ void __launch_bounds__(LVL_WARPS * 32) k_lvl_fwd_pairs(
+__global__ void __launch_bounds__(LVL_WARPS * 32, MFBC_PAIR_MIN_BLOCKS) k_lvl_fwd_pairs(
     int64_t ib, int64_t ie, const int32_t* __restrict__ item_v, const int64_t* __restrict__ item_meta,
     const int32_t* __restrict__ col_t, int W, const uint32_t* __restrict__ full, const uint32_t* __restrict__ V,
     const uint32_t* __restrict__ Fl, const uint32_t* __restrict__ mem_l, uint32_t* Fn, uint32_t* mem_n,
@@ -331,6 +397,22 @@ __global__ void __launch_bounds__(LVL_WARPS * 32) k_lvl_fwd_pairs(
   const uint32_t lt = (1u << lane) - 1u;
   const int Q = W / 4;
   unsigned long long nbytes = 0, npairs = 0;
+  SlotCursor cur;
+  int nnew = 0;                                    // entries of sm.newv
+  // append sm.newv to the level-(l+1) list with one atomic
+  auto flush_new = [&]() {
+    uint32_t b = 0;
+    if (lane == 0) b = atomicAdd(count_n, (uint32_t)nnew);
+    b = __shfl_sync(0xffffffffu, b, 0);
+    __syncwarp();
+    if ((int)lane < nnew) {
+      const uint32_t pos = b + lane;
+      if ((int64_t)pos < cap_n) list_n[pos] = sm.newv[lane];
+      else atomicOr(flags, 1u);
+    }
+    __syncwarp();
+    nnew = 0;
+  };
   FOR_ITEM_GROUPS(ib, ie, next_group)
     // lane-parallel precheck of 32 items: skip rows already reached by every column
     const uint64_t myit = base + lane;
@@ -397,23 +479,25 @@ __global__ void __launch_bounds__(LVL_WARPS * 32) k_lvl_fwd_pairs(
       if (bytes) nbytes += 4ull * W * (nm + 1);
       const uint32_t cw = __ballot_sync(0xffffffffu, cand != 0u);
       if (!cw) continue;
-      emit_quads(sm, nm, v, multi, quads_of_words(cw, Q), Q, prow, pmask, segs, work, pair_cap, seg_cap,
+      emit_quads(sm, nm, v, multi, quads_of_words(cw, Q), Q, prow, pmask, segs, work, pair_cap, seg_cap, cur,
                  bytes ? &npairs : nullptr);
       if ((int)lane < W && cand) {
         if (multi) atomicOr(&Fn[(size_t)v * W + lane], cand);
         else Fn[(size_t)v * W + lane] = cand;
       }
+      uint32_t isnew = 0;
       if (lane == 0) {
         const uint32_t bit = 1u << (v & 31);
-        if (!(atomicOr(&mem_n[v >> 5], bit) & bit)) {
-          const uint32_t pos = atomicAdd(count_n, 1u);
-          if ((int64_t)pos < cap_n) list_n[pos] = v;
-          else atomicOr(flags, 1u);
-        }
+        isnew = !(atomicOr(&mem_n[v >> 5], bit) & bit);
+        if (isnew) sm.newv[nnew] = v;
       }
+      nnew += (int)__shfl_sync(0xffffffffu, isnew, 0);
       __syncwarp();
+      if (nnew == 32) flush_new();
     }
   }
+  if (nnew) flush_new();
+  fill_dummy_segs(segs, cur.s, cur.se);
   if (bytes && lane == 0) {
     const unsigned long long np = npairs & 0xffffffffull, ns = npairs >> 32;
     atomicAdd(bytes, nbytes + 20ull * np + 16ull * ns);
@@ -426,7 +510,7 @@ __global__ void __launch_bounds__(LVL_WARPS * 32) k_lvl_fwd_pairs(
 // Every level-l quad of a single-item row gets a segment (its columns are
 // finalised by the gather even without successors); multi-item rows only emit
 // quads with pairs (their finalisation is k_lvl_hub_final).
-__global__ void __launch_bounds__(LVL_WARPS * 32) k_lvl_bwd_pairs(
+__global__ void __launch_bounds__(LVL_WARPS * 32, MFBC_PAIR_MIN_BLOCKS) k_lvl_bwd_pairs(
     int64_t ib, int64_t ie, const int32_t* __restrict__ item_v, const int64_t* __restrict__ item_meta,
     const int32_t* __restrict__ col, int W, const uint32_t* __restrict__ Fl, const uint32_t* __restrict__ mem_l,
     const uint32_t* __restrict__ Fn, const uint32_t* __restrict__ mem_n, uint32_t* next_group, uint32_t* prow,
@@ -438,6 +522,7 @@ __global__ void __launch_bounds__(LVL_WARPS * 32) k_lvl_bwd_pairs(
   const uint32_t lt = (1u << lane) - 1u;
   const int Q = W / 4;
   unsigned long long nbytes = 0, npairs = 0;
+  SlotCursor cur;
   FOR_ITEM_GROUPS(ib, ie, next_group)
     // lane-parallel precheck of 32 items: only rows with a column at level l
     const uint64_t myit = base + lane;
@@ -503,10 +588,11 @@ __global__ void __launch_bounds__(LVL_WARPS * 32) k_lvl_bwd_pairs(
       if (bytes) nbytes += 4ull * W * (nm + 1);
       const uint32_t words = __ballot_sync(0xffffffffu, multi ? any != 0u : Fv != 0u);
       if (words) emit_quads(sm, nm, v, multi, quads_of_words(words, Q), Q, prow, pmask, segs, work, pair_cap,
-                            seg_cap, bytes ? &npairs : nullptr);
+                            seg_cap, cur, bytes ? &npairs : nullptr);
       __syncwarp();
     }
   }
+  fill_dummy_segs(segs, cur.s, cur.se);
   if (bytes && lane == 0) {
     const unsigned long long np = npairs & 0xffffffffull, ns = npairs >> 32;
     atomicAdd(bytes, nbytes + 20ull * np + 16ull * ns);
@@ -593,7 +679,10 @@ __device__ __forceinline__ void gather_group(const uint4& myseg, int nin, const 
   const int T = __shfl_sync(0xffffffffu, incl, 31);
   // algorithmic bytes of the group's records: 16 B per segment header and
   // 20 B per pair (row index + mask), counted once (by lane 0)
-  if (COUNT && lane == 0) nvals_rec += 16ull * nin + 20ull * T;
+  if (COUNT) {
+    const uint32_t real = __ballot_sync(0xffffffffu, (int)lane < nin && myseg.x != SEG_DUMMY);
+    if (lane == 0) nvals_rec += 16ull * __popc(real) + 20ull * T;
+  }
   const int shift = 4 * (int)(lane & 7u);
   const int mword = (int)(lane >> 3);
   uint64_t i0 = 0, i1 = 0, i2 = 0, i3 = 0;                 // MFBF sums
@@ -727,21 +816,32 @@ __global__ void __launch_bounds__(256, MFBC_GATHER_MIN_BLOCKS) k_lvl_fwd_gather(
   }
 }
 
+// Per-warp staging of one segment's frontier columns in the MFBr gather.
+struct FinishSmem {
+  float s[128], c[128];                      // compensated zeta sum of the column
+  uint8_t col[128];                          // column within the quad
+};
+
 // MFBr gather of level l: zeta(s,v) = sum over the segment's pairs of the
 // successors' values (double-float, compensated).  Single-item rows are
 // finalised here: lambda(v) += zeta * sigma_bar and the slot of (s,v) takes
 // the value zeta + 1/sigma_bar; multi-item rows add their partial zeta into
-// the row's FP64 accumulator.
+// the row's FP64 accumulator.  Only the columns of v's level-l frontier are
+// finalised (about one in six of the quad on R-MAT inputs), so they are
+// first compacted through shared memory and then finalised one per lane.
 template <bool COUNT>
-__global__ void __launch_bounds__(256, MFBC_GATHER_MIN_BLOCKS) k_lvl_bwd_gather(
+__global__ void __launch_bounds__(256, MFBC_BWD_GATHER_MIN_BLOCKS) k_lvl_bwd_gather(
     const uint4* __restrict__ segs, const uint32_t* nseg_p, const uint32_t* __restrict__ prow,
     const uint4* __restrict__ pmask, int nb, int W, const uint32_t* __restrict__ Fl,
     const int32_t* __restrict__ hub_of, double* svd, double* zacc, double* lambda, uint32_t* next_group,
     unsigned long long* bytes, unsigned long long* stat) {
   __shared__ GatherSmem gsm[8];
+  __shared__ FinishSmem fsm[8];
   GatherSmem& gs = gsm[threadIdx.x >> 5];
+  FinishSmem& fm = fsm[threadIdx.x >> 5];
   uint64_t* sv = reinterpret_cast<uint64_t*>(svd);
   const unsigned lane = lane_id();
+  const uint32_t lt = (1u << lane) - 1u;
   const uint32_t nseg = *nseg_p;
   const int shift = 4 * (int)(lane & 7u);
   unsigned long long nvals = 0, nw = 0, nrec = 0;
@@ -754,50 +854,40 @@ __global__ void __launch_bounds__(256, MFBC_GATHER_MIN_BLOCKS) k_lvl_bwd_gather(
       const int d = (int)((z >> 8) & 0xffu);
       // this lane's four columns of v's level-l frontier
       const uint32_t fs = (__ldg(&Fl[(size_t)v * W + 4 * d + (lane >> 3)]) >> shift) & 0xfu;
-      const size_t col = (size_t)128 * d + 4 * lane;
+      const uint32_t b0 = __ballot_sync(0xffffffffu, fs & 1u), b1 = __ballot_sync(0xffffffffu, fs & 2u);
+      const uint32_t b2 = __ballot_sync(0xffffffffu, fs & 4u), b3 = __ballot_sync(0xffffffffu, fs & 8u);
+      const int total = __popc(b0) + __popc(b1) + __popc(b2) + __popc(b3);
+      if (total == 0) return;
+      int at = __popc(b0 & lt) + __popc(b1 & lt) + __popc(b2 & lt) + __popc(b3 & lt);
+      __syncwarp();                                   // the previous segment's entries are consumed
+      if (fs & 1u) { fm.s[at] = s0; fm.c[at] = c0; fm.col[at] = (uint8_t)(4 * lane + 0); at++; }
+      if (fs & 2u) { fm.s[at] = s1; fm.c[at] = c1; fm.col[at] = (uint8_t)(4 * lane + 1); at++; }
+      if (fs & 4u) { fm.s[at] = s2; fm.c[at] = c2; fm.col[at] = (uint8_t)(4 * lane + 2); at++; }
+      if (fs & 8u) { fm.s[at] = s3; fm.c[at] = c3; fm.col[at] = (uint8_t)(4 * lane + 3); }
+      __syncwarp();
       if ((z >> 16) & 1u) {
-        if (fs) {
-          double* za = zacc + (size_t)hub_of[v] * nb + col;
-          if (fs & 1u) atomicAdd(za + 0, df_to_double(acc_value(s0, c0)));
-          if (fs & 2u) atomicAdd(za + 1, df_to_double(acc_value(s1, c1)));
-          if (fs & 4u) atomicAdd(za + 2, df_to_double(acc_value(s2, c2)));
-          if (fs & 8u) atomicAdd(za + 3, df_to_double(acc_value(s3, c3)));
-          if (COUNT) nw += __popc(fs);
-        }
+        double* za = zacc + (size_t)hub_of[v] * nb + 128 * d;
+        for (int i = (int)lane; i < total; i += 32) atomicAdd(za + fm.col[i], (double)fm.s[i] + (double)fm.c[i]);
+        if (COUNT && lane == 0) nw += (unsigned long long)total;
       } else {
-        dfl lam = {0.f, 0.f};
-        if (fs) {
-          // read-modify-write of the lane's sector: only the set columns change
-          // (this segment is the only writer of them in this launch)
-          uint64_t* p = sv + (size_t)v * nb + col;
-          uint64_t w0, w1, w2, w3;
-          asm volatile("ld.global.v4.u64 {%0,%1,%2,%3}, [%4];"
-                       : "=l"(w0), "=l"(w1), "=l"(w2), "=l"(w3) : "l"(p) : "memory");
-          if (fs & 1u) { const dfl zt = acc_value(s0, c0); const dfl sg = df_of_u64(w0);
-                         lam = df_add(lam, df_mul(zt, sg)); w0 = df_pack(df_add(zt, df_rcp(sg))); }
-          if (fs & 2u) { const dfl zt = acc_value(s1, c1); const dfl sg = df_of_u64(w1);
-                         lam = df_add(lam, df_mul(zt, sg)); w1 = df_pack(df_add(zt, df_rcp(sg))); }
-          if (fs & 4u) { const dfl zt = acc_value(s2, c2); const dfl sg = df_of_u64(w2);
-                         lam = df_add(lam, df_mul(zt, sg)); w2 = df_pack(df_add(zt, df_rcp(sg))); }
-          if (fs & 8u) { const dfl zt = acc_value(s3, c3); const dfl sg = df_of_u64(w3);
-                         lam = df_add(lam, df_mul(zt, sg)); w3 = df_pack(df_add(zt, df_rcp(sg))); }
-          asm volatile("st.global.v4.u64 [%0], {%1,%2,%3,%4};" ::"l"(p), "l"(w0), "l"(w1), "l"(w2), "l"(w3)
-                       : "memory");
-          if (COUNT) nw += 2 * __popc(fs);
+        // this segment is the only writer of these slots in this launch
+        uint64_t* row = sv + (size_t)v * nb + 128 * d;
+        float ls = 0.f, lc = 0.f;                     // lambda(v) terms of this lane's columns
+        for (int i = (int)lane; i < total; i += 32) {
+          uint64_t* slot = row + fm.col[i];
+          *slot = finish_col(acc_value(fm.s[i], fm.c[i]), *slot, ls, lc);
         }
-        if (__any_sync(0xffffffffu, lam.hi != 0.f)) {
-          for (int o = 16; o; o >>= 1) {
-            const dfl other = {__shfl_xor_sync(0xffffffffu, lam.hi, o), __shfl_xor_sync(0xffffffffu, lam.lo, o)};
-            lam = df_add(lam, other);
-          }
-          if (lane == 0) atomicAdd(&lambda[v], df_to_double(lam));
+        if (COUNT && lane == 0) nw += 2ull * (unsigned long long)total;
+        if (__any_sync(0xffffffffu, ls != 0.f)) {
+          const double lam = warp_acc_sum(ls, lc);
+          if (lane == 0) atomicAdd(&lambda[v], lam);
           if (COUNT && lane == 0) nrec += 8ull;
         }
       }
     };
     gather_group<COUNT, false>(myseg, nin, prow, pmask, gs, sv, nvals, nrec, ovf, finish);
     // segments without successor pairs: zeta = 0
-    uint32_t empty = __ballot_sync(0xffffffffu, (int)lane < nin && (myseg.z & 0xffu) == 0u);
+    uint32_t empty = __ballot_sync(0xffffffffu, (int)lane < nin && (myseg.z & 0xffu) == 0u && myseg.x != SEG_DUMMY);
     while (empty) {
       const int k = __ffs(empty) - 1;
       empty &= empty - 1;
@@ -840,7 +930,7 @@ __global__ void k_lvl_hub_final(const int32_t* __restrict__ hubs, int32_t nhub, 
       am &= am - 1;
       const uint64_t h = base + t;
       const int32_t v = __shfl_sync(0xffffffffu, myv, t);
-      dfl lam = {0.f, 0.f};
+      float ls = 0.f, lc = 0.f;
       for (int d = 0; d < Q; d++) {
         const uint32_t fs = (Fl[(size_t)v * W + 4 * d + (lane >> 3)] >> shift) & 0xfu;
         if (!__any_sync(0xffffffffu, fs != 0u)) continue;
@@ -851,24 +941,17 @@ __global__ void k_lvl_hub_final(const int32_t* __restrict__ hubs, int32_t nhub, 
           uint64_t w0, w1, w2, w3;
           asm volatile("ld.global.v4.f64 {%0,%1,%2,%3}, [%4];" : "=d"(z0), "=d"(z1), "=d"(z2), "=d"(z3) : "l"(za) : "memory");
           asm volatile("ld.global.v4.u64 {%0,%1,%2,%3}, [%4];" : "=l"(w0), "=l"(w1), "=l"(w2), "=l"(w3) : "l"(p) : "memory");
-          if (fs & 1u) { const dfl zt = df_of_double(z0); const dfl sg = df_of_u64(w0);
-                         lam = df_add(lam, df_mul(zt, sg)); w0 = df_pack(df_add(zt, df_rcp(sg))); z0 = 0.0; }
-          if (fs & 2u) { const dfl zt = df_of_double(z1); const dfl sg = df_of_u64(w1);
-                         lam = df_add(lam, df_mul(zt, sg)); w1 = df_pack(df_add(zt, df_rcp(sg))); z1 = 0.0; }
-          if (fs & 4u) { const dfl zt = df_of_double(z2); const dfl sg = df_of_u64(w2);
-                         lam = df_add(lam, df_mul(zt, sg)); w2 = df_pack(df_add(zt, df_rcp(sg))); z2 = 0.0; }
-          if (fs & 8u) { const dfl zt = df_of_double(z3); const dfl sg = df_of_u64(w3);
-                         lam = df_add(lam, df_mul(zt, sg)); w3 = df_pack(df_add(zt, df_rcp(sg))); z3 = 0.0; }
+          if (fs & 1u) { w0 = finish_col(df_of_double(z0), w0, ls, lc); z0 = 0.0; }
+          if (fs & 2u) { w1 = finish_col(df_of_double(z1), w1, ls, lc); z1 = 0.0; }
+          if (fs & 4u) { w2 = finish_col(df_of_double(z2), w2, ls, lc); z2 = 0.0; }
+          if (fs & 8u) { w3 = finish_col(df_of_double(z3), w3, ls, lc); z3 = 0.0; }
           asm volatile("st.global.v4.f64 [%0], {%1,%2,%3,%4};" ::"l"(za), "d"(z0), "d"(z1), "d"(z2), "d"(z3) : "memory");
           asm volatile("st.global.v4.u64 [%0], {%1,%2,%3,%4};" ::"l"(p), "l"(w0), "l"(w1), "l"(w2), "l"(w3) : "memory");
           if (bytes) nbytes += 32ull * __popc(fs);
         }
       }
-      for (int o = 16; o; o >>= 1) {
-        const dfl other = {__shfl_xor_sync(0xffffffffu, lam.hi, o), __shfl_xor_sync(0xffffffffu, lam.lo, o)};
-        lam = df_add(lam, other);
-      }
-      if (lane == 0) lambda[v] += df_to_double(lam);
+      const double lam = warp_acc_sum(ls, lc);
+      if (lane == 0) lambda[v] += lam;
       if (bytes && lane == 0) nbytes += 4ull * W + 16ull;
     }
   }
@@ -945,8 +1028,8 @@ struct LevelPlan {                 // host-side level bookkeeping of one batch
 };
 static thread_local LevelPlan tl_plan;
 
-static const unsigned kPairGrid = 152u * 6u;     // resident blocks of the pair kernels
 static const unsigned kGatherGrid = 152u * MFBC_GATHER_MIN_BLOCKS;   // resident blocks of the gather kernels
+static const unsigned kBwdGatherGrid = 152u * MFBC_BWD_GATHER_MIN_BLOCKS;
 
 // One MFBF (fwd) or MFBr product of level l over the items [ib, ie): the pair
 // kernel, a check of the pair buffers, then the gather kernel.  When the
@@ -967,7 +1050,7 @@ static mfbc_status level_round(RunCtx& rc, LevelState& s, bool fwd, int l, int64
   (void)nactive;
   MFBC_CUDA_TRY(cudaMemsetAsync(s.ctr->work, 0, sizeof(uint32_t) * 4, st), rc.err);
   MFBC_CUDA_TRY(cudaMemsetAsync(&s.ctr->list_count[2], 0, sizeof(uint32_t), st), rc.err);
-  const unsigned pgrid = grid_for_items(ie - ib, kPairGrid);
+  const unsigned pgrid = grid_for_items(ie - ib, PAIR_GRID);
   if (fwd)
     PROF(K_LVL_FWD, (k_lvl_fwd_pairs<<<pgrid, LVL_WARPS * 32, LVL_SMEM, st>>>(
                         ib, ie, g.items_in.v, g.items_in.beg, g.col_t, W, s.full, s.V, Fl, Ml, Fn, Mn,
@@ -996,7 +1079,7 @@ static mfbc_status level_round(RunCtx& rc, LevelState& s, bool fwd, int l, int64
   const uint32_t nseg = rc.h_ctr[6];
   if (!nseg) return MFBC_OK;
   MFBC_CUDA_TRY(cudaMemsetAsync(&s.ctr->work[2], 0, sizeof(uint32_t), st), rc.err);
-  const unsigned ggrid = grid_for_items(nseg, kGatherGrid);
+  const unsigned ggrid = grid_for_items(nseg, fwd ? kGatherGrid : kBwdGatherGrid);
   if (fwd) {
     if (B)
       PROF(K_LVL_FWD_G, (k_lvl_fwd_gather<true><<<ggrid, 256, 0, st>>>(
