@@ -67,6 +67,28 @@ def make_workload(name, rank=0):
     return g, srcs
 
 
+# DRAM traffic of the dominant kernel: dram__bytes_read.sum + dram__bytes_write.sum
+# per launch from one ncu capture (profiles/level_kernels_rmat22.md), expressed per
+# algorithmic byte so that it scales with the launches this run makes.  Each entry
+# records the SHA-1 of the kernel source it was taken on; once that source changes
+# the figure is reported as null.
+TRAFFIC = {
+    ("rmat22", "level_mfbr_gather"): {"per_alg_byte": 104.95 / 37.919, "sha1": "78d7e264ed20b98ce5fd3541e8d6690baeabde2b",
+                                      "source": "paper_1609_07008_gb300/csrc/level.cu"},
+}
+
+
+def traffic_per_launch(workload, kernel, alg_bytes):
+    import hashlib
+    t = TRAFFIC.get((workload, kernel))
+    if not t:
+        return None
+    with open(os.path.join(ROOT, t["source"]), "rb") as f:
+        if hashlib.sha1(f.read()).hexdigest() != t["sha1"]:
+            return None
+    return t["per_alg_byte"] * alg_bytes
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -305,7 +327,7 @@ def main():
             "gpu_launches": int(launches),
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
                          "peak_kind": f"{peak_kind} copy bandwidth", "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None,
+                         "frac": achieved / peak, "traffic": traffic_per_launch(args.workload, dom, per_launch_bytes),
                          "bytes_per_launch": per_launch_bytes, "avg_launch_ms": avg_ms},
             "gather_stats": {k: prof_bytes.get(k) for k in ("pairs_fwd", "pairs_bwd", "values_fwd", "values_bwd",
                                                             "fwd_iters", "bwd_iters", "batches")},

@@ -46,7 +46,7 @@ namespace mfbc {
 
 constexpr int LVL_WARPS = 8;                 // warps per block
 #ifndef MFBC_PAIR_MIN_BLOCKS
-#define MFBC_PAIR_MIN_BLOCKS 5
+#define MFBC_PAIR_MIN_BLOCKS 4
 #endif
 constexpr unsigned PAIR_GRID = 152u * MFBC_PAIR_MIN_BLOCKS;   // resident blocks of the pair kernels
 constexpr uint32_t PAIR_CHUNK = 1024;        // pair slots a warp reserves at a time
