@@ -89,6 +89,37 @@ def traffic_per_launch(workload, kernel, alg_bytes):
     return t["per_alg_byte"] * alg_bytes
 
 
+def model_roofline(g, srcs, prof_bytes, step_s, peak_gbs):
+    """Whole-step roofline of the traffic model for MFBF + counters + MFBr + lambda
+    (unweighted graphs, 4-byte arcs): per step
+      B_fwd = 12 R + 4 F + 16 D + 24 G,  B_cnt = 4 R + 4 nnz + 4 F + 8 D,
+      B_bwd = 12 R + 4 F + 24 D,         B_acc = 16 R + 16 n,
+    with R reachable (source, vertex) pairs, F arc visits from reachable pairs
+    (sum over sources of the arcs in the source's component), D tight-arc hits
+    (the values the MFBr gathers read, counted on the device) and G the entries touched
+    by the products, taken as 2 R (it lies between R and 3 R).  The frontier-row
+    terms (a few bytes per vertex and level) are left out.  Returns None for
+    weighted or directed workloads."""
+    if g.w is not None or g.directed:
+        return None
+    import scipy.sparse as sp
+    from scipy.sparse.csgraph import connected_components
+    a = sp.csr_matrix((np.ones(g.nnz, dtype=np.int8), g.col, g.rowptr), shape=(g.n, g.n))
+    _, lab = connected_components(a, directed=False)
+    size = np.bincount(lab).astype(np.float64)
+    arcs = np.bincount(lab, weights=np.diff(g.rowptr).astype(np.float64))
+    R = float(size[lab[srcs]].sum())
+    F = float(arcs[lab[srcs]].sum())
+    D = float(prof_bytes["values_bwd"])
+    G = 2.0 * R
+    total = (12 * R + 4 * F + 16 * D + 24 * G) + (4 * R + 4 * g.nnz + 4 * F + 8 * D) + (12 * R + 4 * F + 24 * D) \
+        + (16 * R + 16 * g.n)
+    teps = len(srcs) * g.m
+    at_peak = peak_gbs * 1e9 / (total / teps) / 1e9
+    return {"bytes_per_step": total, "bytes_per_tep": total / teps, "gteps_at_peak": at_peak,
+            "frac": (total / (peak_gbs * 1e9)) / step_s, "reachable_pairs": R, "arc_visits": F, "tight_arcs": D}
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -329,6 +360,7 @@ def main():
                          "peak_kind": f"{peak_kind} copy bandwidth", "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic_per_launch(args.workload, dom, per_launch_bytes),
                          "bytes_per_launch": per_launch_bytes, "avg_launch_ms": avg_ms},
+            "model_roofline": model_roofline(g, srcs, prof_bytes, t / args.steps, peak),
             "gather_stats": {k: prof_bytes.get(k) for k in ("pairs_fwd", "pairs_bwd", "values_fwd", "values_bwd",
                                                             "fwd_iters", "bwd_iters", "batches")},
             "kernels_ms_share": {k: round(v["ms"] / sum(x["ms"] for x in kstats.values()), 4)

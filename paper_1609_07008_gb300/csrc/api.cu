@@ -179,7 +179,7 @@ static mfbc_status make_plan(const mfbc_graph* G, int32_t nsrc, int mode, const 
     return fail(MFBC_ERR_INVALID, "MFBC_PATH_LEVEL needs unit weights");
   else if (path != MFBC_PATH_GENERAL && path != MFBC_PATH_LEVEL)
     return fail(MFBC_ERR_INVALID, "unknown path");
-  const int maxnb = path == MFBC_PATH_LEVEL ? 1024 : 4096;
+  const int maxnb = path == MFBC_PATH_LEVEL ? LEVEL_MAX_NB : 4096;
   // the level kernels move 128 columns (four 32-column words) at a time
   const int gran = path == MFBC_PATH_LEVEL ? 128 : 32;
   int req = opt ? opt->n_b : 0;
@@ -288,77 +288,74 @@ void finish_profile(Run& R, mfbc_profile* out, int64_t batches, int64_t fi, int6
   out->path = R.plan.path;
 }
 
-// Per source: its depth d1 from the highest-degree vertex, its BFS parent
-// toward that vertex (the smallest-id neighbour one level closer; itself for
-// the root or when unreachable) and its depth d2 from the second hub.
-// One warp per source, lanes over the neighbours.
-__global__ void k_order_info(const int32_t* __restrict__ src, int32_t nsrc, const int64_t* __restrict__ rowptr,
-                             const int32_t* __restrict__ col, const int32_t* __restrict__ d1,
-                             const int32_t* __restrict__ d2, int4* info) {
+// Ordering key of each source: its distances to the K landmarks (rows[k][v],
+// capped at 0xffff) followed by its BFS parent toward landmark 0 (the
+// smallest-id neighbour one level closer; itself for the landmark or when
+// unreachable).  One warp per source.
+__global__ void k_order_keys(const int32_t* __restrict__ src, int32_t nsrc, const int64_t* __restrict__ rowptr,
+                             const int32_t* __restrict__ col, const int32_t* __restrict__ rows, int32_t n, int K,
+                             int32_t* keys) {
   const uint64_t gw = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const unsigned lane = threadIdx.x & 31u;
   if (gw >= (uint64_t)nsrc) return;
   const int32_t s = src[gw];
-  const int32_t ds = d1[s];
+  int32_t* key = keys + gw * (uint64_t)(K + 1);
+  for (int k = (int)lane; k < K; k += 32) key[k] = min(rows[(size_t)k * n + s], 0xffff);
+  const int32_t ds = rows[s];
   int32_t best = 0x7fffffff;
   if (ds > 0 && ds != 0x7fffffff)
     for (int64_t k = rowptr[s] + lane; k < rowptr[s + 1]; k += 32) {
       const int32_t u = col[k];
-      if (d1[u] == ds - 1 && u < best) best = u;
+      if (rows[u] == ds - 1 && u < best) best = u;
     }
   for (int o = 16; o; o >>= 1) best = min(best, __shfl_xor_sync(0xffffffffu, best, o));
-  if (lane == 0) {
-    const int32_t par = best == 0x7fffffff ? s : best;
-    info[gw] = make_int4(min(ds, 0xffff), par, min(d2[par], 0xffff), min(d2[s], 0xffff));
-  }
+  if (lane == 0) key[K] = best == 0x7fffffff ? s : best;
 }
 
 // Group sources of similar distance profile into the same batches (level
-// kernels, undirected graphs): sort by (depth from the highest-degree vertex,
-// depth of the BFS parent from the second hub, parent, own depth from the
-// second hub).  Sources hanging off one parent see every other vertex at
-// almost the same distance, so their frontier bits land in the same words.
-// Writes the permuted list to d_out; leaves the order alone when it does not
-// apply.  The level state's sv array serves as scratch.
+// kernels, undirected graphs): one MFBF pass from the K highest-degree
+// vertices gives every vertex's distances to them, and the sources are sorted
+// by that vector (lexicographically), then by BFS parent.  Sources at equal
+// distances from many well-connected vertices reach most other vertices at
+// the same levels, so their frontier bits share words and sectors.  Writes the
+// permuted list to d_out; leaves the order alone when it does not apply.  The
+// level state's sv array serves as scratch.
 mfbc_status order_sources(RunCtx& rc, LevelState& ls, const int32_t* d_src, int32_t nsrc, int32_t* d_out,
                           bool* applied) {
   const DevGraph& g = *rc.g;
   const int32_t n = g.n;
+  const int K = (int)g.landmarks.size();
   *applied = false;
-  const size_t need = al256(sizeof(int32_t) * 2 * (size_t)n) + sizeof(int4) * (size_t)nsrc;
-  if (g.directed || g.top_hub[0] < 0 || need > sizeof(double) * (size_t)n * ls.nb) return MFBC_OK;
+  const size_t rows_bytes = al256(sizeof(int32_t) * (size_t)K * n);
+  const size_t need = rows_bytes + sizeof(int32_t) * (size_t)(K + 1) * nsrc;
+  if (g.directed || K == 0 || K > ls.nb || K > nsrc || need > sizeof(double) * (size_t)n * ls.nb) return MFBC_OK;
   int32_t* rows = (int32_t*)ls.sv;
-  int4* info = (int4*)((char*)ls.sv + al256(sizeof(int32_t) * 2 * (size_t)n));
-  for (int k = 0; k < 2; k++) {
-    int32_t* row = rows + (size_t)k * n;
-    const int32_t h = g.top_hub[k];
-    if (h < 0) { fill_i32(row, 0, (size_t)n, rc.stream); continue; }
-    MFBC_CUDA_TRY(cudaMemcpyAsync(d_out, &h, sizeof(int32_t), cudaMemcpyHostToDevice, rc.stream), rc.err);
-    MFBC_CUDA_TRY(cudaStreamSynchronize(rc.stream), rc.err);
-    int levels = -1;
-    bool exceeded = false;
-    mfbc_status s = level_batch(rc, ls, d_out, 1, nullptr, false, &levels, &exceeded, nullptr, nullptr);
-    if (s != MFBC_OK) {
-      if (!exceeded) return s;
-      return MFBC_OK;                  // too deep for the level masks: keep the given order
-    }
-    level_output(rc, ls, levels, 1, row, nullptr);
-    level_reset(rc, ls, levels);
+  int32_t* keys = (int32_t*)((char*)ls.sv + rows_bytes);
+  MFBC_CUDA_TRY(cudaMemcpyAsync(d_out, g.landmarks.data(), sizeof(int32_t) * K, cudaMemcpyHostToDevice, rc.stream),
+                rc.err);
+  int levels = -1;
+  bool exceeded = false;
+  mfbc_status s = level_batch(rc, ls, d_out, K, nullptr, false, &levels, &exceeded, nullptr, nullptr);
+  if (s != MFBC_OK) {
+    if (!exceeded) return s;
+    return MFBC_OK;                    // too deep for the level masks: keep the given order
   }
-  k_order_info<<<(unsigned)(((uint64_t)nsrc * 32 + 255) / 256), 256, 0, rc.stream>>>(d_src, nsrc, g.rowptr, g.col,
-                                                                                   rows, rows + n, info);
-  std::vector<int4> hi((size_t)nsrc);
+  level_output(rc, ls, levels, K, rows, nullptr);
+  level_reset(rc, ls, levels);
+  k_order_keys<<<(unsigned)(((uint64_t)nsrc * 32 + 255) / 256), 256, 0, rc.stream>>>(d_src, nsrc, g.rowptr, g.col,
+                                                                                    rows, n, K, keys);
+  std::vector<int32_t> hk((size_t)(K + 1) * nsrc);
   std::vector<int32_t> hs((size_t)nsrc), out((size_t)nsrc), idx((size_t)nsrc);
-  MFBC_CUDA_TRY(cudaMemcpyAsync(hi.data(), info, sizeof(int4) * nsrc, cudaMemcpyDeviceToHost, rc.stream), rc.err);
+  MFBC_CUDA_TRY(cudaMemcpyAsync(hk.data(), keys, sizeof(int32_t) * hk.size(), cudaMemcpyDeviceToHost, rc.stream),
+                rc.err);
   MFBC_CUDA_TRY(cudaMemcpyAsync(hs.data(), d_src, sizeof(int32_t) * nsrc, cudaMemcpyDeviceToHost, rc.stream), rc.err);
   MFBC_CUDA_TRY(cudaStreamSynchronize(rc.stream), rc.err);
   for (int32_t i = 0; i < nsrc; i++) idx[i] = i;
   std::sort(idx.begin(), idx.end(), [&](int32_t a, int32_t b) {
-    const int4 x = hi[a], y = hi[b];
-    if (x.x != y.x) return x.x < y.x;
-    if (x.z != y.z) return x.z < y.z;
-    if (x.y != y.y) return x.y < y.y;
-    if (x.w != y.w) return x.w < y.w;
+    const int32_t* x = &hk[(size_t)a * (K + 1)];
+    const int32_t* y = &hk[(size_t)b * (K + 1)];
+    for (int k = 0; k <= K; k++)
+      if (x[k] != y[k]) return x[k] < y[k];
     return a < b;
   });
   for (int32_t i = 0; i < nsrc; i++) out[i] = hs[(size_t)idx[i]];

@@ -180,12 +180,18 @@ mfbc_status graph_build(int32_t n, int64_t nnz, const int64_t* h_rowptr, const i
   // host copy of the row pointers for the work-item lists
   std::vector<int64_t> rp(h_rowptr, h_rowptr + (size_t)n + 1);
   {
-    int64_t d0 = 0, d1 = 0;
-    for (int32_t v = 0; v < n; v++) {
-      const int64_t d = rp[v + 1] - rp[v];
-      if (d > d0) { d1 = d0; g->top_hub[1] = g->top_hub[0]; d0 = d; g->top_hub[0] = v; }
-      else if (d > d1) { d1 = d; g->top_hub[1] = v; }
-    }
+    // landmarks for source ordering: the highest out-degree vertices
+    // (degree descending, then id), isolated vertices excluded
+    std::vector<int32_t> ids;
+    ids.reserve((size_t)n);
+    for (int32_t v = 0; v < n; v++)
+      if (rp[v + 1] > rp[v]) ids.push_back(v);
+    const size_t k = std::min<size_t>(ids.size(), (size_t)ORDER_LANDMARKS);
+    std::partial_sort(ids.begin(), ids.begin() + k, ids.end(), [&](int32_t a, int32_t b) {
+      const int64_t da = rp[a + 1] - rp[a], db = rp[b + 1] - rp[b];
+      return da != db ? da > db : a < b;
+    });
+    g->landmarks.assign(ids.begin(), ids.begin() + k);
   }
   if (g->directed) {
     // A^T by a stable counting sort on the host: rows of A^T are sorted by

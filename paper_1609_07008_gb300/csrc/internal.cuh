@@ -39,7 +39,7 @@ struct DevGraph {
   bool directed = true;
   bool unit = true;                // every arc weighs 1 (w == NULL or all ones)
   int32_t wmax = 1;
-  int32_t top_hub[2] = {-1, -1};   // the two highest out-degree vertices (source ordering)
+  std::vector<int32_t> landmarks;   // highest out-degree vertices, descending (source ordering)
   int64_t* rowptr = nullptr;       // CSR of A (out-arcs)
   int32_t* col = nullptr;
   int32_t* w = nullptr;            // nullptr when unit
@@ -126,6 +126,8 @@ void general_carve(Carver& c, int32_t n, int nb, GeneralState& s);
 
 // Level-synchronous path for unit weights: Algorithms 1 and 2 with the
 // frontiers kept as per-level bit masks.  See level.cu.
+constexpr int LEVEL_MAX_NB = 1024;   // widest batch of the level kernels
+constexpr int ORDER_LANDMARKS = 128; // distance profile length used to order sources
 struct LevelState {
   int nb = 0, W = 0, Lcap = 0;
   double* sv;         // sigma_bar, then zeta + 1/sigma_bar (in place)  [n][nb]

@@ -910,14 +910,15 @@ __global__ void __launch_bounds__(256, MFBC_BWD_GATHER_MIN_BLOCKS) k_lvl_bwd_gat
 // Finalise the multi-item vertices of level l: zeta from the row's FP64
 // accumulator, lambda(v) += zeta * sigma_bar, slot value zeta + 1/sigma_bar
 // (double-float), accumulator reset.  32 hubs are tested per warp at once;
-// lane l handles columns 4l..4l+3 of each 128-column quad.
-__global__ void k_lvl_hub_final(const int32_t* __restrict__ hubs, int32_t nhub, int W, int nb,
-                                const uint32_t* __restrict__ Fl, const uint32_t* __restrict__ mem_l,
-                                double* svd, double* zacc, double* lambda, unsigned long long* bytes) {
+// the level-l columns of a hub (lane j holds frontier word j) are compacted
+// into shared memory and finalised one per lane.
+__global__ void __launch_bounds__(LVL_WARPS * 32) k_lvl_hub_final(
+    const int32_t* __restrict__ hubs, int32_t nhub, int W, int nb, const uint32_t* __restrict__ Fl,
+    const uint32_t* __restrict__ mem_l, double* svd, double* zacc, double* lambda, unsigned long long* bytes) {
+  __shared__ uint16_t cols_all[LVL_WARPS][LEVEL_MAX_NB];
+  uint16_t* cols = cols_all[threadIdx.x >> 5];
   const unsigned lane = lane_id();
   const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-  const int Q = W / 4;
-  const int shift = 4 * (int)(lane & 7u);
   uint64_t* sv = reinterpret_cast<uint64_t*>(svd);
   unsigned long long nbytes = 0;
   for (uint64_t base = (((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; base < (uint64_t)nhub;
@@ -930,29 +931,32 @@ __global__ void k_lvl_hub_final(const int32_t* __restrict__ hubs, int32_t nhub, 
       am &= am - 1;
       const uint64_t h = base + t;
       const int32_t v = __shfl_sync(0xffffffffu, myv, t);
+      uint32_t x = (int)lane < W ? Fl[(size_t)v * W + lane] : 0u;
+      const int cnt = __popc(x);
+      int incl = cnt;
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if ((int)lane >= o) incl += y;
+      }
+      const int total = __shfl_sync(0xffffffffu, incl, 31);
+      int at = incl - cnt;
+      __syncwarp();                                   // the previous hub's columns are consumed
+      while (x) {
+        cols[at++] = (uint16_t)(32 * lane + (__ffs(x) - 1));
+        x &= x - 1;
+      }
+      __syncwarp();
+      double* za = zacc + (size_t)h * nb;
+      uint64_t* row = sv + (size_t)v * nb;
       float ls = 0.f, lc = 0.f;
-      for (int d = 0; d < Q; d++) {
-        const uint32_t fs = (Fl[(size_t)v * W + 4 * d + (lane >> 3)] >> shift) & 0xfu;
-        if (!__any_sync(0xffffffffu, fs != 0u)) continue;
-        if (fs) {
-          double* za = zacc + (size_t)h * nb + 128 * d + 4 * lane;
-          uint64_t* p = sv + (size_t)v * nb + 128 * d + 4 * lane;
-          double z0, z1, z2, z3;
-          uint64_t w0, w1, w2, w3;
-          asm volatile("ld.global.v4.f64 {%0,%1,%2,%3}, [%4];" : "=d"(z0), "=d"(z1), "=d"(z2), "=d"(z3) : "l"(za) : "memory");
-          asm volatile("ld.global.v4.u64 {%0,%1,%2,%3}, [%4];" : "=l"(w0), "=l"(w1), "=l"(w2), "=l"(w3) : "l"(p) : "memory");
-          if (fs & 1u) { w0 = finish_col(df_of_double(z0), w0, ls, lc); z0 = 0.0; }
-          if (fs & 2u) { w1 = finish_col(df_of_double(z1), w1, ls, lc); z1 = 0.0; }
-          if (fs & 4u) { w2 = finish_col(df_of_double(z2), w2, ls, lc); z2 = 0.0; }
-          if (fs & 8u) { w3 = finish_col(df_of_double(z3), w3, ls, lc); z3 = 0.0; }
-          asm volatile("st.global.v4.f64 [%0], {%1,%2,%3,%4};" ::"l"(za), "d"(z0), "d"(z1), "d"(z2), "d"(z3) : "memory");
-          asm volatile("st.global.v4.u64 [%0], {%1,%2,%3,%4};" ::"l"(p), "l"(w0), "l"(w1), "l"(w2), "l"(w3) : "memory");
-          if (bytes) nbytes += 32ull * __popc(fs);
-        }
+      for (int i = (int)lane; i < total; i += 32) {
+        const int c = cols[i];
+        row[c] = finish_col(df_of_double(za[c]), row[c], ls, lc);
+        za[c] = 0.0;
       }
       const double lam = warp_acc_sum(ls, lc);
       if (lane == 0) lambda[v] += lam;
-      if (bytes && lane == 0) nbytes += 4ull * W + 16ull;
+      if (bytes && lane == 0) nbytes += 32ull * total + 4ull * W + 16ull;
     }
   }
   if (bytes) {
