@@ -120,6 +120,69 @@ def model_roofline(g, srcs, prof_bytes, step_s, peak_gbs):
             "frac": (total / (peak_gbs * 1e9)) / step_s, "reachable_pairs": R, "arc_visits": F, "tight_arcs": D}
 
 
+SERVE_POOL = "resident graphs R-MAT 16/18/20 (edge factor 16, undirected), Erdos-Renyi n=2^16 k=16, " \
+             "weighted 2D grid 256^2 w U[1,16]; requests with log-uniform [64, 4096] sampled sources"
+
+
+def serving_bench(n_requests=120, seed=5):
+    """Served (packed, continuous batching, memory-budget admission, one worker
+    per graph) against plain (one mfbc_bc_device call per request, in arrival
+    order) on the same requests: both saturated (every request at t = 0:
+    capacity) and at an offered Poisson rate of 0.8x the plain capacity
+    (latency).  Also the largest relative difference between the two forms'
+    lambdas (equal accuracy)."""
+    import torch
+    import graphgen as gg
+    import paper_1609_07008_gb300 as mfbc
+    from paper_1609_07008_gb300 import serve
+    host = {"rmat16": gg.rmat(16, 16, seed=1), "rmat18": gg.rmat(18, 16, seed=1), "rmat20": gg.rmat(20, 16, seed=1),
+            "er16": gg.erdos_renyi(1 << 16, 16, seed=1), "grid256w": gg.grid2d(256, weights=(1, 16), seed=1)}
+    graphs = {k: mfbc.Graph.from_csr(g) for k, g in host.items()}
+    edges = {k: g.m for k, g in host.items()}
+    elig = {k: np.flatnonzero(g.out_degree() > 0).astype(np.int32) for k, g in host.items()}
+    sizes = {k: g.n for k, g in host.items()}
+    free, _ = torch.cuda.mem_get_info()
+    budget = int(0.6 * free)
+
+    def reqs(rate):
+        return serve.make_requests(sizes, n_requests, rate, lo=64, hi=4096, seed=seed, eligible=elig)
+
+    def served(rs):
+        srv = serve.Server(graphs, budget_bytes=budget, max_cols=4096, n_b=1024).start()
+        try:
+            serve.run_served(srv, rs, timeout=900)
+        finally:
+            srv.close()
+        return serve.latency_stats(rs, edges), len(srv.log)
+
+    # warm both forms once (library scratch, torch allocator, module load)
+    w = serve.make_requests(sizes, 10, 0, lo=64, hi=256, seed=seed + 1, eligible=elig)
+    serve.run_plain(graphs, w)
+    served(serve.make_requests(sizes, 10, 0, lo=64, hi=256, seed=seed + 1, eligible=elig))
+    sat_plain = serve.latency_stats(serve.run_plain(graphs, reqs(0)), edges)
+    sat_served, _ = served(reqs(0))
+    cap = n_requests / sat_plain["span_s"]
+    rate = 0.8 * cap
+    rp = serve.run_plain(graphs, reqs(rate))
+    plain = serve.latency_stats(rp, edges)
+    rs = reqs(rate)
+    srv_stats, groups = served(rs)
+    diff = 0.0
+    for a, b in zip(sorted(rp, key=lambda r: r.rid), sorted(rs, key=lambda r: r.rid)):
+        nz = b.result != 0
+        if np.any(a.result[~nz] != 0):
+            diff = float("inf")
+        if nz.any():
+            diff = max(diff, float(np.max(np.abs(a.result[nz] - b.result[nz]) / np.abs(b.result[nz]))))
+    for G in graphs.values():
+        G.close()
+    return {"workload": SERVE_POOL, "requests": n_requests, "budget_bytes": budget,
+            "saturated": {"plain_gteps": sat_plain["gteps"], "served_gteps": sat_served["gteps"],
+                          "plain_span_s": sat_plain["span_s"], "served_span_s": sat_served["span_s"]},
+            "offered_rate_per_s": rate, "offered_load_vs_plain_capacity": 0.8,
+            "plain": plain, "served": dict(srv_stats, groups=groups), "max_rel_diff": diff}
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -240,6 +303,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--ref-sources", type=int, default=64)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
     ap.add_argument("--sources", type=int, default=0, help="use only the first N sources (probing)")
     ap.add_argument("--keep-order", action="store_true", help="batch sources in the given order")
     args = ap.parse_args()
@@ -316,16 +380,17 @@ def main():
     # end to end through the host-buffer C ABI
     rp = torch.from_numpy(g.rowptr).pin_memory().numpy()
     cl = torch.from_numpy(g.col).pin_memory().numpy()
+    wt = torch.from_numpy(g.w).pin_memory().numpy() if g.w is not None else None
     hs = torch.from_numpy(srcs).pin_memory().numpy()
     hl = torch.empty(g.n, dtype=torch.float64).pin_memory().numpy()
-    h2d = rp.nbytes + cl.nbytes + hs.nbytes
+    h2d = rp.nbytes + cl.nbytes + hs.nbytes + (wt.nbytes if wt is not None else 0)
     G.close()
     del G
     torch.cuda.empty_cache()
     barrier_sync()
     t0 = time.perf_counter()
     for _ in range(args.e2e_steps):
-        with mfbc.Graph(rp, cl, None, directed=g.directed) as Ge:
+        with mfbc.Graph(rp, cl, wt, directed=g.directed) as Ge:
             Ge.bc(hs, n_b=nb_req, out=hl, keep_order=args.keep_order)
         if dist:
             x = torch.from_numpy(hl).to(dev)
@@ -366,6 +431,8 @@ def main():
             "kernels_ms_share": {k: round(v["ms"] / sum(x["ms"] for x in kstats.values()), 4)
                                  for k, v in sorted(kstats.items(), key=lambda kv: -kv[1]["ms"])},
         }
+        if world == 1 and not args.no_serve:
+            line["serving"] = serving_bench()
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(g, srcs)
         print(json.dumps(line), flush=True)

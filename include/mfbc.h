@@ -30,6 +30,11 @@
  *    pointer to caller memory after a call returns.
  *  - Calls on one graph handle must not overlap (the handle caches scratch
  *    memory); distinct handles are independent.
+ *  - mfbc_bc[_device] and mfbc_sssp_batch[_device] set the current CUDA
+ *    context's L2 fetch-granularity hint (cudaLimitMaxL2FetchGranularity) to
+ *    32 bytes while they run and restore the previous value before returning;
+ *    other work in the same context sees the hint meanwhile (performance
+ *    only, never results).
  */
 #ifndef MFBC_H
 #define MFBC_H
@@ -140,10 +145,11 @@ mfbc_status mfbc_graph_info(const mfbc_graph* g, int32_t* n, int64_t* nnz, uint3
  * Sources are processed in batches of options->n_b (Algorithm 3's loop); a
  * short last batch is padded with inactive columns (Theorem 1's padding).
  * Unless MFBC_OPT_KEEP_ORDER is set, the unit-weight kernels on an
- * undirected graph first group sources of similar depth into the same batch
- * (sorted by their BFS distance to the two highest-degree vertices), which
- * makes each batch's frontier masks denser; lambda is a sum over sources, so
- * only the floating-point summation order changes. */
+ * undirected graph with more sources than one batch first sort the sources
+ * by their BFS distances to the 128 highest-degree vertices (one extra MFBF
+ * pass), so that each batch holds sources of similar distance profile and
+ * its frontier masks are denser; lambda is a sum over sources, so only the
+ * floating-point summation order changes. */
 mfbc_status mfbc_bc(const mfbc_graph* g, const int32_t* sources, int32_t nsrc,
                     double* lambda_out, const mfbc_options* opt);
 
@@ -152,6 +158,22 @@ mfbc_status mfbc_bc(const mfbc_graph* g, const int32_t* sources, int32_t nsrc,
  * result is complete on that stream. */
 mfbc_status mfbc_bc_device(const mfbc_graph* g, const int32_t* sources, int32_t nsrc,
                            double* lambda_out, const mfbc_options* opt);
+
+/* Several betweenness requests in one pass.  The paper has no such call:
+ * it serves callers that collect source lists of independent requests on one
+ * graph (continuous batching) and packs their columns into shared batches of
+ * Algorithm 3's loop.  DEVICE sources int32[nsrc] hold the requests' lists
+ * back to back; HOST req_offsets int32[nreq+1] (req_offsets[0] = 0,
+ * non-decreasing, req_offsets[nreq] = nsrc) delimit them: request r owns
+ * sources[req_offsets[r] .. req_offsets[r+1]).  DEVICE lambda_out
+ * double[nreq*n] is overwritten; row r (lambda_out + r*n) receives request
+ * r's lambda exactly as mfbc_bc_device would compute it for that list alone,
+ * up to the floating-point summation order.  Each request starts on a
+ * 32-column boundary of a batch and may continue into the next batch; sources
+ * are not reordered.  Returns once lambda_out is complete on opt->stream. */
+mfbc_status mfbc_bc_multi_device(const mfbc_graph* g, const int32_t* sources, int32_t nsrc,
+                                 const int32_t* req_offsets, int32_t nreq, double* lambda_out,
+                                 const mfbc_options* opt);
 
 /* MFBF alone (Algorithm 1, Lemma 1): for each i < nsrc,
  *   dist_out [i*n + v] = tau(sources[i], v)        (INT32_MAX if unreachable)
@@ -165,8 +187,9 @@ mfbc_status mfbc_sssp_batch_device(const mfbc_graph* g, const int32_t* sources, 
                                    int32_t* dist_out, double* sigma_out,
                                    const mfbc_options* opt);
 
-/* Device scratch (bytes) that mfbc_bc* (mode 0) or mfbc_sssp_batch* (mode 1)
- * needs for nsrc sources under *opt (n_b, path).  A caller that passes its
+/* Device scratch (bytes) that mfbc_bc* (mode 0), mfbc_sssp_batch* (mode 1)
+ * or mfbc_bc_multi_device (mode 2; nsrc = the packed columns, each request
+ * rounded up to 32) needs for nsrc sources under *opt (n_b, path).  A caller that passes its
  * own opt->workspace of at least this size makes the call allocate nothing
  * on the device. */
 mfbc_status mfbc_workspace_size(const mfbc_graph* g, int32_t nsrc, int32_t mode,

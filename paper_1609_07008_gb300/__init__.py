@@ -98,6 +98,7 @@ def load(path: str | None = None):
                                 ctypes.POINTER(i32)],
             "mfbc_bc": [vp, vp, i32, vp, ctypes.POINTER(Options)],
             "mfbc_bc_device": [vp, vp, i32, vp, ctypes.POINTER(Options)],
+            "mfbc_bc_multi_device": [vp, vp, i32, vp, i32, vp, ctypes.POINTER(Options)],
             "mfbc_sssp_batch": [vp, vp, i32, vp, vp, ctypes.POINTER(Options)],
             "mfbc_sssp_batch_device": [vp, vp, i32, vp, vp, ctypes.POINTER(Options)],
             "mfbc_workspace_size": [vp, i32, i32, ctypes.POINTER(Options), ctypes.POINTER(ctypes.c_uint64)],
@@ -252,6 +253,33 @@ class Graph:
         if profile or count_bytes:
             res.append(prof.as_dict())
         return res[0] if len(res) == 1 else tuple(res)
+
+    def bc_multi(self, source_lists, *, n_b: int = 0, path: int = PATH_AUTO, out=None, stream=None,
+                 workspace=None, profile: bool = False):
+        """One lambda row per request: `source_lists` is a sequence of torch
+        CUDA int tensors (or one concatenated tensor with a host `offsets`
+        pair: (sources, offsets)).  Returns a [nreq, n] float64 CUDA tensor
+        (mfbc_bc_multi_device)."""
+        import torch
+        lib = load()
+        if isinstance(source_lists, tuple) and len(source_lists) == 2 and not _is_torch(source_lists[1]):
+            src, offs = source_lists
+            src = src.to(dtype=torch.int32).contiguous()
+            off = np.ascontiguousarray(offs, dtype=np.int32)
+        else:
+            parts = [t.to(dtype=torch.int32).reshape(-1) for t in source_lists]
+            if not parts:
+                raise ValueError("no requests")
+            src = torch.cat(parts).contiguous()
+            off = np.zeros(len(parts) + 1, dtype=np.int32)
+            off[1:] = np.cumsum([p.numel() for p in parts])
+        nreq = len(off) - 1
+        lam = out if out is not None else torch.empty((nreq, self.n), dtype=torch.float64, device=src.device)
+        prof = Profile() if profile else None
+        opt = _options(n_b, path, stream, workspace, None, prof)
+        _check(lib.mfbc_bc_multi_device(self._h, _dptr(src), src.numel(), _hptr(off), nreq, _dptr(lam),
+                                        ctypes.byref(opt)))
+        return (lam, prof.as_dict()) if profile else lam
 
     def sssp(self, sources, *, n_b: int = 0, path: int = PATH_AUTO, with_sigma: bool = True, stream=None,
              workspace=None, profile: bool = False, return_warn: bool = False):

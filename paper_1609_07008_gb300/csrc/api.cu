@@ -143,6 +143,7 @@ static size_t extras(const DevGraph& g, int32_t nsrc, int mode, int nb, bool hos
   if (host_io) b += al256(sizeof(int32_t) * (size_t)std::max(nsrc, 1));        // device sources
   if (mode == 0) b += al256(sizeof(int32_t) * (size_t)std::max(nsrc, 1));      // reordered sources
   if (mode == 1 && host_io) b += al256((sizeof(int32_t) + sizeof(double)) * (size_t)nb * std::max(g.n, 1));
+  if (mode == 2) b += 2 * al256(sizeof(int32_t) * (size_t)nb);                 // packed batch columns
   return b;
 }
 
@@ -210,11 +211,11 @@ static mfbc_status make_plan(const mfbc_graph* G, int32_t nsrc, int mode, const 
 extern "C" mfbc_status mfbc_workspace_size(const mfbc_graph* G, int32_t nsrc, int32_t mode,
                                            const mfbc_options* opt, uint64_t* bytes) {
   if (!G || !bytes) return fail(MFBC_ERR_INVALID, "graph and bytes must not be NULL");
-  if (nsrc < 0 || (mode != 0 && mode != 1)) return fail(MFBC_ERR_INVALID, "bad nsrc or mode");
+  if (nsrc < 0 || mode < 0 || mode > 2) return fail(MFBC_ERR_INVALID, "bad nsrc or mode");
   Plan p;
   mfbc_options o = opt ? *opt : mfbc_options{};
   o.workspace = nullptr;
-  mfbc_status s = make_plan(G, nsrc, mode, &o, true, &p);
+  mfbc_status s = make_plan(G, nsrc, mode, &o, mode != 2, &p);
   if (s) return s;
   *bytes = p.total;
   return MFBC_OK;
@@ -232,6 +233,8 @@ struct Run {
   Plan plan;
   char* ws = nullptr;
   size_t ws_bytes = 0;
+  const int32_t* req_off = nullptr;  // mode 2: host offsets of the requests in the source list
+  int32_t nreq = 0;
 };
 
 mfbc_status get_workspace(Run& R) {
@@ -365,7 +368,54 @@ mfbc_status order_sources(RunCtx& rc, LevelState& ls, const int32_t* d_src, int3
   return MFBC_OK;
 }
 
-// mode 0: lambda (d_lambda device, n doubles, overwritten); mode 1: sssp rows.
+// out[j] = src[colidx[j]] for the packed columns of one batch, -1 where empty.
+__global__ void k_gather_sources(const int32_t* __restrict__ src, const int32_t* __restrict__ colidx, int nb,
+                                 int32_t* out) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < nb) out[j] = colidx[j] >= 0 ? src[colidx[j]] : -1;
+}
+
+// Column layout of several requests packed into batches of nb columns:
+// requests in the given order, each starting on a 32-column word boundary,
+// spilling into the next batch when one fills.  colidx[b*nb + j] is the
+// index into the source list of batch b's column j (-1 empty), wreq[b*W + w]
+// the request owning word w (-1 empty), used[b] the columns up to the last
+// filled one.
+struct Packing {
+  std::vector<int32_t> colidx, wreq, used;
+  int64_t batches = 0;
+};
+static Packing pack_requests(const int32_t* off, int32_t nreq, int nb) {
+  Packing p;
+  const int W = nb / 32;
+  auto open_batch = [&]() {
+    p.colidx.resize((size_t)(p.batches + 1) * nb, -1);
+    p.wreq.resize((size_t)(p.batches + 1) * W, -1);
+    p.used.push_back(0);
+    p.batches++;
+  };
+  int col = nb;                                  // no batch open yet
+  for (int32_t r = 0; r < nreq; r++) {
+    int64_t i = off[r];
+    const int64_t e = off[r + 1];
+    if (i == e) continue;
+    col = (col + 31) / 32 * 32;
+    while (i < e) {
+      if (col >= nb) { open_batch(); col = 0; }
+      const int64_t b = p.batches - 1;
+      const int take = (int)std::min<int64_t>(e - i, nb - col);
+      for (int t = 0; t < take; t++) p.colidx[(size_t)b * nb + col + t] = (int32_t)(i + t);
+      for (int w = col / 32; w <= (col + take - 1) / 32; w++) p.wreq[(size_t)b * W + w] = r;
+      col += take;
+      i += take;
+      p.used[(size_t)b] = col;
+    }
+  }
+  return p;
+}
+
+// mode 0: lambda (d_lambda device, n doubles, overwritten); mode 1: sssp rows;
+// mode 2: one lambda row per request (d_lambda device, nreq * n doubles).
 mfbc_status run(mfbc_graph* G, const int32_t* d_src, int32_t nsrc, int mode, double* d_lambda,
                 int32_t* dist_out, double* sigma_out, bool out_on_host, Run& R, char* extra, int32_t* d_sorted) {
   const DevGraph& g = G->g;
@@ -386,7 +436,21 @@ mfbc_status run(mfbc_graph* G, const int32_t* d_src, int32_t nsrc, int mode, dou
     stage_s = (double*)(extra + al256(sizeof(int32_t) * (size_t)nb * std::max(g.n, 1)));
   }
   MFBC_CUDA_TRY(cudaMemsetAsync(ctr, 0, sizeof(Counters), R.st), &R.err);
-  if (mode == 0 && g.n) MFBC_CUDA_TRY(cudaMemsetAsync(d_lambda, 0, sizeof(double) * (size_t)g.n, R.st), &R.err);
+  const bool multi = mode == 2;
+  const bool want_lambda = mode != 1;
+  if (want_lambda && g.n) {
+    const size_t rows = multi ? (size_t)R.nreq : 1;
+    MFBC_CUDA_TRY(cudaMemsetAsync(d_lambda, 0, sizeof(double) * rows * (size_t)g.n, R.st), &R.err);
+  }
+  Packing pk;
+  int32_t* d_colidx = nullptr;
+  int32_t* d_batch = nullptr;
+  if (multi) {
+    pk = pack_requests(R.req_off, R.nreq, nb);
+    d_colidx = (int32_t*)extra;
+    d_batch = (int32_t*)(extra + al256(sizeof(int32_t) * (size_t)nb));
+  }
+  const int64_t nbatches = multi ? pk.batches : ((int64_t)nsrc + nb - 1) / nb;
   if (P.path == MFBC_PATH_LEVEL && g.n) {
     // masks start clean; each batch returns them to zero
     MFBC_CUDA_TRY(cudaMemsetAsync(ls.V, 0, sizeof(uint32_t) * (size_t)g.n * ls.W, R.st), &R.err);
@@ -402,15 +466,30 @@ mfbc_status run(mfbc_graph* G, const int32_t* d_src, int32_t nsrc, int mode, dou
     if (so) return fail(so, R.err.empty() ? std::string(mfbc_status_string(so)) : R.err);
     if (applied) d_src = d_sorted;
   }
-  for (int32_t b0 = 0; b0 < nsrc; b0 += nb) {
-    const int na = std::min(nb, nsrc - b0);
+  for (int64_t bx = 0; bx < nbatches; bx++) {
+    const int32_t b0 = multi ? 0 : (int32_t)(bx * nb);
+    int na;
+    const int32_t* bsrc;
+    const int32_t* bwreq = nullptr;
+    if (multi) {
+      MFBC_CUDA_TRY(cudaMemcpyAsync(d_colidx, &pk.colidx[(size_t)bx * nb], sizeof(int32_t) * nb,
+                                    cudaMemcpyHostToDevice, R.st), &R.err);
+      k_gather_sources<<<(nb + 255) / 256, 256, 0, R.st>>>(d_src, d_colidx, nb, d_batch);
+      bsrc = d_batch;
+      na = pk.used[(size_t)bx];
+      bwreq = &pk.wreq[(size_t)bx * (nb / 32)];
+    } else {
+      bsrc = d_src + b0;
+      na = std::min(nb, nsrc - b0);
+    }
+    rc.word_req = bwreq;
     batches++;
     mfbc_status s;
     bool fallback = false;
     if (P.path == MFBC_PATH_LEVEL) {
       int levels = -1;
       bool exceeded = false;
-      s = level_batch(rc, ls, d_src + b0, na, mode == 0 ? d_lambda : nullptr, mode == 0, &levels, &exceeded,
+      s = level_batch(rc, ls, bsrc, na, want_lambda ? d_lambda : nullptr, want_lambda, &levels, &exceeded,
                       &fi, &bi);
       if (s == MFBC_OK) {
         if (mode == 1) {
@@ -444,7 +523,8 @@ mfbc_status run(mfbc_graph* G, const int32_t* d_src, int32_t nsrc, int mode, dou
       }
       for (int sb = 0; sb < na; sb += nbg) {
         const int nsa = std::min(nbg, na - sb);
-        s = general_batch(rc, *gp, d_src + b0 + sb, nsa, mode == 0 ? d_lambda : nullptr, &fi, &bi);
+        rc.word_req = bwreq ? bwreq + sb / 32 : nullptr;
+        s = general_batch(rc, *gp, bsrc + sb, nsa, want_lambda ? d_lambda : nullptr, &fi, &bi);
         if (s) break;
         if (mode == 1) {
           int32_t* dd = out_on_host ? stage_d + (size_t)sb * g.n : dist_out + (size_t)(b0 + sb) * g.n;
@@ -486,12 +566,40 @@ mfbc_status run(mfbc_graph* G, const int32_t* d_src, int32_t nsrc, int mode, dou
   return MFBC_OK;
 }
 
+// The level gathers read scattered 32-byte sectors; with the context's
+// default L2 fetch granularity (64 bytes) a miss also brings in the
+// neighbouring sector, which is mostly not needed (measured: 5 % slower on
+// R-MAT 22).  A call sets the hint to 32 bytes while it runs and restores the
+// previous value when it returns (its work is complete by then).
+struct L2FetchHint {
+  size_t prev = 0;
+  bool set = false;
+  L2FetchHint() {
+    if (cudaDeviceGetLimit(&prev, cudaLimitMaxL2FetchGranularity) == cudaSuccess && prev != 32 &&
+        cudaDeviceSetLimit(cudaLimitMaxL2FetchGranularity, 32) == cudaSuccess)
+      set = true;
+    else
+      cudaGetLastError();
+  }
+  ~L2FetchHint() {
+    if (set && cudaDeviceSetLimit(cudaLimitMaxL2FetchGranularity, prev) != cudaSuccess) cudaGetLastError();
+  }
+};
+
 mfbc_status entry(const mfbc_graph* Gc, const int32_t* sources, int32_t nsrc, int mode, double* lambda_out,
-                  int32_t* dist_out, double* sigma_out, const mfbc_options* opt, bool host_io) {
+                  int32_t* dist_out, double* sigma_out, const mfbc_options* opt, bool host_io,
+                  const int32_t* req_off = nullptr, int32_t nreq = 0) {
   if (!Gc) return fail(MFBC_ERR_INVALID, "graph must not be NULL");
   if (nsrc < 0) return fail(MFBC_ERR_INVALID, "nsrc must be >= 0");
   if (nsrc > 0 && !sources) return fail(MFBC_ERR_INVALID, "sources must not be NULL");
-  if (mode == 0 && Gc->g.n > 0 && !lambda_out) return fail(MFBC_ERR_INVALID, "lambda_out must not be NULL");
+  if (mode != 1 && Gc->g.n > 0 && !lambda_out) return fail(MFBC_ERR_INVALID, "lambda_out must not be NULL");
+  if (mode == 2) {
+    if (nreq < 1 || !req_off) return fail(MFBC_ERR_INVALID, "need nreq >= 1 and req_offsets");
+    if (req_off[0] != 0 || req_off[nreq] != nsrc)
+      return fail(MFBC_ERR_INVALID, "req_offsets must start at 0 and end at nsrc");
+    for (int32_t r = 0; r < nreq; r++)
+      if (req_off[r + 1] < req_off[r]) return fail(MFBC_ERR_INVALID, "req_offsets must be non-decreasing");
+  }
   if (mode == 1 && nsrc > 0 && Gc->g.n > 0 && !dist_out) return fail(MFBC_ERR_INVALID, "dist_out must not be NULL");
   mfbc_graph* G = const_cast<mfbc_graph*>(Gc);
   std::lock_guard<std::mutex> lock(G->mu);
@@ -502,9 +610,12 @@ mfbc_status entry(const mfbc_graph* Gc, const int32_t* sources, int32_t nsrc, in
   }
   if (opt && opt->warn_out) *opt->warn_out = 0;
   t_err.clear();
+  L2FetchHint l2hint;
   Run R;
   R.G = G;
   R.opt = opt;
+  R.req_off = req_off;
+  R.nreq = nreq;
   R.st = opt ? (cudaStream_t)opt->stream : nullptr;
   mfbc_status s = make_plan(G, nsrc, mode, opt, host_io, &R.plan);
   if (s) return s;
@@ -563,6 +674,12 @@ extern "C" mfbc_status mfbc_bc(const mfbc_graph* g, const int32_t* sources, int3
 extern "C" mfbc_status mfbc_bc_device(const mfbc_graph* g, const int32_t* sources, int32_t nsrc,
                                       double* lambda_out, const mfbc_options* opt) {
   return entry(g, sources, nsrc, 0, lambda_out, nullptr, nullptr, opt, false);
+}
+
+extern "C" mfbc_status mfbc_bc_multi_device(const mfbc_graph* g, const int32_t* sources, int32_t nsrc,
+                                            const int32_t* req_offsets, int32_t nreq, double* lambda_out,
+                                            const mfbc_options* opt) {
+  return entry(g, sources, nsrc, 2, lambda_out, nullptr, nullptr, opt, false, req_offsets, nreq);
 }
 
 extern "C" mfbc_status mfbc_sssp_batch(const mfbc_graph* g, const int32_t* sources, int32_t nsrc,

@@ -59,6 +59,7 @@ void general_carve(Carver& c, int32_t n, int nb, GeneralState& s) {
   s.listA = c.take<int32_t>((size_t)n);
   s.listB = c.take<int32_t>((size_t)n);
   s.src = c.take<int32_t>((size_t)nb);
+  s.word_req = c.take<int32_t>((size_t)s.W);
   s.ctr = c.take<Counters>(1);
 }
 
@@ -349,15 +350,29 @@ __global__ void __launch_bounds__(256) k_gp_next_frontier(
 }
 
 // Algorithm 3 accumulation, one warp per vertex, no atomics.
+// word_req: request (lambda row) of each 32-column word, or nullptr when the
+// whole batch adds into row 0.
 __global__ void __launch_bounds__(256) k_gp_lambda(int32_t n, int W, int nb, const int32_t* __restrict__ src,
                                                    const double* __restrict__ zp,
-                                                   const double* __restrict__ sig, double* lambda) {
+                                                   const double* __restrict__ sig, double* lambda,
+                                                   const int32_t* __restrict__ word_req) {
   uint64_t gw = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (gw >= (uint64_t)n) return;
   const unsigned lane = lane_id();
   const int32_t v = (int32_t)gw;
   double acc = 0.0;
+  int cur = word_req ? -1 : 0;
   for (int word = 0; word < W; word++) {
+    if (word_req) {
+      const int r = word_req[word];
+      if (r != cur) {                          // a new request's words begin: flush the previous one
+        for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0 && cur >= 0) lambda[(size_t)cur * n + v] += acc;
+        acc = 0.0;
+        cur = r;
+      }
+      if (r < 0) continue;
+    }
     const int j = word * 32 + lane;
     const size_t idx = (size_t)v * nb + j;
     const int32_t s = src[j];
@@ -365,7 +380,7 @@ __global__ void __launch_bounds__(256) k_gp_lambda(int32_t n, int W, int nb, con
     if (s >= 0 && s != v && sg > 0.0) acc += zp[idx] * sg;
   }
   for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-  if (lane == 0) lambda[v] += acc;
+  if (lane == 0 && cur >= 0) lambda[(size_t)cur * n + v] += acc;
 }
 
 // ------------------------------------------------------------------ driver
@@ -486,8 +501,15 @@ mfbc_status general_batch(RunCtx& rc, GeneralState& s, const int32_t* d_src_batc
     fcount = rc.h_ctr[0];
   }
   if (bwd_iters) *bwd_iters += iters;
+  const int32_t* wreq = nullptr;
+  if (rc.word_req && batch_uniform_request(rc.word_req, W) < 0) {
+    MFBC_CUDA_TRY(cudaMemcpyAsync(s.word_req, rc.word_req, sizeof(int32_t) * W, cudaMemcpyHostToDevice, st), rc.err);
+    wreq = s.word_req;
+  }
+  const int urq = rc.word_req ? batch_uniform_request(rc.word_req, W) : 0;
+  double* lam0 = wreq ? lambda : lambda + (size_t)(urq < 0 ? 0 : urq) * n;
   PROF(K_LAMBDA, (k_gp_lambda<<<warp_blocks((uint64_t)n), 256, 0, st>>>(n, W, nb, s.src, s.cm, s.sig,
-                                                                         lambda)));
+                                                                         lam0, wreq)));
   rc.prof->k[K_LAMBDA].bytes += 16.0 * cells + 16.0 * n;
   return MFBC_OK;
 }

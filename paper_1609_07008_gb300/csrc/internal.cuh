@@ -119,6 +119,7 @@ struct GeneralState {
   int32_t* listA;     // frontier vertex lists [n]
   int32_t* listB;
   int32_t* src;       // [nb]
+  int32_t* word_req;  // [W] request of each word (lambda row), see RunCtx
   Counters* ctr;
 };
 size_t general_bytes(int32_t n, int nb);
@@ -143,6 +144,9 @@ struct LevelState {
   uint4* segs;        // segment headers of one product round
   uint32_t pair_cap, seg_cap;
   int32_t* src;       // [nb]
+  uint32_t* colmask;  // [W] columns of the batch that hold a source
+  int32_t* word_req;  // [W] request of each word (lambda row), see RunCtx
+  int32_t* quad_req;  // [W/4] request of each quad, -1 none, -2 mixed
   Counters* ctr;
   int64_t mw;         // words per vertex bitmap
 };
@@ -156,7 +160,16 @@ struct RunCtx {
   Profiler* prof;
   uint32_t* h_ctr;                 // pinned host mirror of Counters::list_count / flags
   std::string* err;
+  // Requests packed into the current batch (host array, one entry per
+  // 32-column word: the request owning the word's columns, -1 for none).
+  // Request r adds into lambda + r * n.  nullptr: the whole batch is
+  // request 0.
+  const int32_t* word_req = nullptr;
 };
+
+// Request of the batch as a whole: r >= 0 when every used word belongs to
+// request r (or word_req is null: 0), -2 when the batch mixes requests.
+int batch_uniform_request(const int32_t* word_req, int W);
 
 // One batch of the general path.  lambda != nullptr: full MFBC batch adding
 // into lambda; otherwise MFBF only.  Returns MFBC_OK or an error status.

@@ -90,19 +90,14 @@ void level_carve(Carver& c, const DevGraph& g, int nb, int Lcap, int64_t list_ca
   s.pmask = c.take<uint4>((size_t)s.pair_cap);
   s.segs = c.take<uint4>((size_t)s.seg_cap);
   s.src = c.take<int32_t>((size_t)nb);
+  s.colmask = c.take<uint32_t>((size_t)s.W);
+  s.word_req = c.take<int32_t>((size_t)s.W);
+  s.quad_req = c.take<int32_t>((size_t)std::max(1, s.W / 4));
   s.ctr = c.take<Counters>(1);
 }
 
 __device__ __forceinline__ bool test_bit(const uint32_t* bm, int32_t v) {
   return (__ldg(&bm[v >> 5]) >> (v & 31)) & 1u;
-}
-
-// active-column mask of word w for nactive active columns
-__device__ __forceinline__ uint32_t active_mask(int w, int nactive) {
-  const int lo = w * 32;
-  if (lo + 32 <= nactive) return 0xffffffffu;
-  if (lo >= nactive) return 0u;
-  return (1u << (nactive - lo)) - 1u;
 }
 
 // ---------------------------------------------------------------- arithmetic
@@ -202,6 +197,21 @@ __device__ __forceinline__ double warp_acc_sum(float s, float c) {
   return (double)s + (double)c;
 }
 
+// Segmented warp sum of non-negative compensated sums (s, c) over runs of
+// equal, non-decreasing keys; true on the last lane of each run, which then
+// holds the run's sum.
+__device__ __forceinline__ bool warp_acc_seg_sum(float& s, float& c, int key) {
+  const unsigned lane = lane_id();
+  for (int o = 1; o < 32; o <<= 1) {
+    const float s2 = __shfl_up_sync(0xffffffffu, s, o), c2 = __shfl_up_sync(0xffffffffu, c, o);
+    const int k2 = __shfl_up_sync(0xffffffffu, key, o);
+    if ((int)lane >= o && k2 == key) acc_add(s, c, s2, c2);
+  }
+  const int kn = __shfl_down_sync(0xffffffffu, key, 1);
+  return lane == 31 || kn != key;
+}
+constexpr int NO_REQ = 0x7fffffff;           // key of a lane without a column
+
 __global__ void k_clear_flag_bits(uint32_t* flags, uint32_t bits) { atomicAnd(flags, ~bits); }
 
 // sv rows of multi-item vertices start at zero (MFBF adds into them).
@@ -225,9 +235,19 @@ __global__ void k_lvl_seed(const int32_t* __restrict__ src, int nb, int W, doubl
   if (!(atomicOr(&member0[s >> 5], bit) & bit)) list0[atomicAdd(count, 1u)] = s;
 }
 
-// visited |= F_l for the vertices of level l; mark vertices reached by every column.
-__global__ void k_lvl_visit(const int32_t* __restrict__ list, uint32_t count, int W, int nactive,
-                            const uint32_t* __restrict__ Fl, uint32_t* V, uint32_t* full) {
+// colmask[w] = the columns of word w whose source is set (one warp per word).
+__global__ void k_lvl_colmask(const int32_t* __restrict__ src, int W, uint32_t* colmask) {
+  const int w = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  if (w >= W) return;
+  const uint32_t m = __ballot_sync(0xffffffffu, src[w * 32 + (int)lane_id()] >= 0);
+  if (lane_id() == 0) colmask[w] = m;
+}
+
+// visited |= F_l for the vertices of level l; mark vertices reached by every
+// column that holds a source (colmask).
+__global__ void k_lvl_visit(const int32_t* __restrict__ list, uint32_t count, int W,
+                            const uint32_t* __restrict__ colmask, const uint32_t* __restrict__ Fl, uint32_t* V,
+                            uint32_t* full) {
   const unsigned lane = lane_id();
   const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
   for (uint64_t i = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < count; i += nw) {
@@ -237,7 +257,7 @@ __global__ void k_lvl_visit(const int32_t* __restrict__ list, uint32_t count, in
       const size_t r = (size_t)v * W + lane;
       const uint32_t x = V[r] | Fl[r];
       V[r] = x;
-      const uint32_t am = active_mask(lane, nactive);
+      const uint32_t am = colmask[lane];
       ok = (x & am) == am;
     }
     if (__all_sync(0xffffffffu, ok) && lane == 0) atomicOr(&full[v >> 5], 1u << (v & 31));
@@ -822,6 +842,32 @@ struct FinishSmem {
   uint8_t col[128];                          // column within the quad
 };
 
+// Finalisation of a segment whose quad holds columns of several requests
+// (packed batches): lambda terms are summed per request (runs of words) by a
+// segmented warp reduction over the compacted columns.  Kept out of line so
+// that the common single-request path keeps its registers.  Returns the
+// number of lambda updates made (on lane 0's count).
+__device__ __noinline__ int finish_mixed(const FinishSmem& fm, int total, uint64_t* row, double* lambda, int32_t n,
+                                         int32_t v, const int32_t* __restrict__ quad_words_req) {
+  const unsigned lane = lane_id();
+  int adds = 0;
+  for (int i0 = 0; i0 < total; i0 += 32) {
+    const int i = i0 + (int)lane;
+    float ls = 0.f, lc = 0.f;
+    int key = NO_REQ;
+    if (i < total) {
+      const int c = fm.col[i];
+      uint64_t* slot = row + c;
+      *slot = finish_col(acc_value(fm.s[i], fm.c[i]), *slot, ls, lc);
+      key = __ldg(&quad_words_req[c >> 5]);
+    }
+    const bool last = warp_acc_seg_sum(ls, lc, key) && key != NO_REQ && ls != 0.f;
+    if (last) atomicAdd(&lambda[(size_t)key * n + v], (double)ls + (double)lc);
+    adds += __popc(__ballot_sync(0xffffffffu, last));
+  }
+  return adds;
+}
+
 // MFBr gather of level l: zeta(s,v) = sum over the segment's pairs of the
 // successors' values (double-float, compensated).  Single-item rows are
 // finalised here: lambda(v) += zeta * sigma_bar and the slot of (s,v) takes
@@ -833,7 +879,8 @@ template <bool COUNT>
 __global__ void __launch_bounds__(256, MFBC_BWD_GATHER_MIN_BLOCKS) k_lvl_bwd_gather(
     const uint4* __restrict__ segs, const uint32_t* nseg_p, const uint32_t* __restrict__ prow,
     const uint4* __restrict__ pmask, int nb, int W, const uint32_t* __restrict__ Fl,
-    const int32_t* __restrict__ hub_of, double* svd, double* zacc, double* lambda, uint32_t* next_group,
+    const int32_t* __restrict__ hub_of, double* svd, double* zacc, double* lambda, int32_t n, int uniform_req,
+    const int32_t* __restrict__ quad_req, const int32_t* __restrict__ word_req, uint32_t* next_group,
     unsigned long long* bytes, unsigned long long* stat) {
   __shared__ GatherSmem gsm[8];
   __shared__ FinishSmem fsm[8];
@@ -872,16 +919,22 @@ __global__ void __launch_bounds__(256, MFBC_BWD_GATHER_MIN_BLOCKS) k_lvl_bwd_gat
       } else {
         // this segment is the only writer of these slots in this launch
         uint64_t* row = sv + (size_t)v * nb + 128 * d;
-        float ls = 0.f, lc = 0.f;                     // lambda(v) terms of this lane's columns
-        for (int i = (int)lane; i < total; i += 32) {
-          uint64_t* slot = row + fm.col[i];
-          *slot = finish_col(acc_value(fm.s[i], fm.c[i]), *slot, ls, lc);
-        }
+        const int rq = uniform_req >= 0 ? uniform_req : __ldg(&quad_req[d]);
         if (COUNT && lane == 0) nw += 2ull * (unsigned long long)total;
-        if (__any_sync(0xffffffffu, ls != 0.f)) {
-          const double lam = warp_acc_sum(ls, lc);
-          if (lane == 0) atomicAdd(&lambda[v], lam);
-          if (COUNT && lane == 0) nrec += 8ull;
+        if (rq >= 0) {                                // one request: one lambda(v) sum
+          float ls = 0.f, lc = 0.f;                   // lambda(v) terms of this lane's columns
+          for (int i = (int)lane; i < total; i += 32) {
+            uint64_t* slot = row + fm.col[i];
+            *slot = finish_col(acc_value(fm.s[i], fm.c[i]), *slot, ls, lc);
+          }
+          if (__any_sync(0xffffffffu, ls != 0.f)) {
+            const double lam = warp_acc_sum(ls, lc);
+            if (lane == 0) atomicAdd(&lambda[(size_t)rq * n + v], lam);
+            if (COUNT && lane == 0) nrec += 8ull;
+          }
+        } else {                                      // requests meet in this quad: sum per request
+          const int adds = finish_mixed(fm, total, row, lambda, n, v, word_req + 4 * d);
+          if (COUNT) nrec += 8ull * adds;
         }
       }
     };
@@ -914,7 +967,8 @@ __global__ void __launch_bounds__(256, MFBC_BWD_GATHER_MIN_BLOCKS) k_lvl_bwd_gat
 // into shared memory and finalised one per lane.
 __global__ void __launch_bounds__(LVL_WARPS * 32) k_lvl_hub_final(
     const int32_t* __restrict__ hubs, int32_t nhub, int W, int nb, const uint32_t* __restrict__ Fl,
-    const uint32_t* __restrict__ mem_l, double* svd, double* zacc, double* lambda, unsigned long long* bytes) {
+    const uint32_t* __restrict__ mem_l, double* svd, double* zacc, double* lambda, int32_t n, int uniform_req,
+    const int32_t* __restrict__ word_req, unsigned long long* bytes) {
   __shared__ uint16_t cols_all[LVL_WARPS][LEVEL_MAX_NB];
   uint16_t* cols = cols_all[threadIdx.x >> 5];
   const unsigned lane = lane_id();
@@ -948,14 +1002,31 @@ __global__ void __launch_bounds__(LVL_WARPS * 32) k_lvl_hub_final(
       __syncwarp();
       double* za = zacc + (size_t)h * nb;
       uint64_t* row = sv + (size_t)v * nb;
-      float ls = 0.f, lc = 0.f;
-      for (int i = (int)lane; i < total; i += 32) {
-        const int c = cols[i];
-        row[c] = finish_col(df_of_double(za[c]), row[c], ls, lc);
-        za[c] = 0.0;
+      if (uniform_req >= 0) {
+        float ls = 0.f, lc = 0.f;
+        for (int i = (int)lane; i < total; i += 32) {
+          const int c = cols[i];
+          row[c] = finish_col(df_of_double(za[c]), row[c], ls, lc);
+          za[c] = 0.0;
+        }
+        const double lam = warp_acc_sum(ls, lc);
+        if (lane == 0) lambda[(size_t)uniform_req * n + v] += lam;
+      } else {
+        // several requests in the batch: sum per request (runs of words)
+        for (int i0 = 0; i0 < total; i0 += 32) {
+          const int i = i0 + (int)lane;
+          float ls = 0.f, lc = 0.f;
+          int key = NO_REQ;
+          if (i < total) {
+            const int c = cols[i];
+            row[c] = finish_col(df_of_double(za[c]), row[c], ls, lc);
+            za[c] = 0.0;
+            key = __ldg(&word_req[c >> 5]);
+          }
+          if (warp_acc_seg_sum(ls, lc, key) && key != NO_REQ && ls != 0.f)
+            atomicAdd(&lambda[(size_t)key * n + v], (double)ls + (double)lc);
+        }
       }
-      const double lam = warp_acc_sum(ls, lc);
-      if (lane == 0) lambda[v] += lam;
       if (bytes && lane == 0) nbytes += 32ull * total + 4ull * W + 16ull;
     }
   }
@@ -1040,8 +1111,8 @@ static const unsigned kBwdGatherGrid = 152u * MFBC_BWD_GATHER_MIN_BLOCKS;
 // buffers overflow the range is split in halves; the pair kernels' side
 // effects (frontier bits, membership, list appends) are idempotent, so a
 // re-run of a range is harmless.
-static mfbc_status level_round(RunCtx& rc, LevelState& s, bool fwd, int l, int64_t ib, int64_t ie, int nactive,
-                               int64_t off_n, double* lambda) {
+static mfbc_status level_round(RunCtx& rc, LevelState& s, bool fwd, int l, int64_t ib, int64_t ie,
+                               int uniform_req, int64_t off_n, double* lambda) {
   const DevGraph& g = *rc.g;
   const int32_t n = g.n;
   const int nb = s.nb, W = s.W;
@@ -1051,7 +1122,6 @@ static mfbc_status level_round(RunCtx& rc, LevelState& s, bool fwd, int l, int64
   const uint32_t* Ml = s.member + (size_t)l * s.mw;
   uint32_t* Fn = s.F + (size_t)(l + 1) * n * W;
   uint32_t* Mn = s.member + (size_t)(l + 1) * s.mw;
-  (void)nactive;
   MFBC_CUDA_TRY(cudaMemsetAsync(s.ctr->work, 0, sizeof(uint32_t) * 4, st), rc.err);
   MFBC_CUDA_TRY(cudaMemsetAsync(&s.ctr->list_count[2], 0, sizeof(uint32_t), st), rc.err);
   const unsigned pgrid = grid_for_items(ie - ib, PAIR_GRID);
@@ -1076,9 +1146,9 @@ static mfbc_status level_round(RunCtx& rc, LevelState& s, bool fwd, int l, int64
       return MFBC_ERR_OOM;
     }
     const int64_t mid = ib + ((ie - ib) / 2 + 31) / 32 * 32;
-    mfbc_status e = level_round(rc, s, fwd, l, ib, mid, nactive, off_n, lambda);
+    mfbc_status e = level_round(rc, s, fwd, l, ib, mid, uniform_req, off_n, lambda);
     if (e) return e;
-    return level_round(rc, s, fwd, l, mid, ie, nactive, off_n, lambda);
+    return level_round(rc, s, fwd, l, mid, ie, uniform_req, off_n, lambda);
   }
   const uint32_t nseg = rc.h_ctr[6];
   if (!nseg) return MFBC_OK;
@@ -1097,11 +1167,13 @@ static mfbc_status level_round(RunCtx& rc, LevelState& s, bool fwd, int l, int64
     if (B)
       PROF(K_LVL_BWD_G, (k_lvl_bwd_gather<true><<<ggrid, 256, 0, st>>>(
                             s.segs, &s.ctr->work[1], s.prow, s.pmask, nb, W, Fl, g.items_out.hub_of, s.sv, s.zacc,
-                            lambda, &s.ctr->work[2], B + K_LVL_BWD_G, s.ctr->stat)));
+                            lambda, n, uniform_req, s.quad_req, s.word_req, &s.ctr->work[2], B + K_LVL_BWD_G,
+                            s.ctr->stat)));
     else
       PROF(K_LVL_BWD_G, (k_lvl_bwd_gather<false><<<ggrid, 256, 0, st>>>(
                             s.segs, &s.ctr->work[1], s.prow, s.pmask, nb, W, Fl, g.items_out.hub_of, s.sv, s.zacc,
-                            lambda, &s.ctr->work[2], nullptr, s.ctr->stat)));
+                            lambda, n, uniform_req, s.quad_req, s.word_req, &s.ctr->work[2], nullptr,
+                            s.ctr->stat)));
   }
   return MFBC_OK;
 }
@@ -1122,6 +1194,26 @@ mfbc_status level_batch(RunCtx& rc, LevelState& s, const int32_t* d_src_batch, i
   fill_i32(s.src, -1, (size_t)nb, st);
   if (nactive)
     MFBC_CUDA_TRY(cudaMemcpyAsync(s.src, d_src_batch, sizeof(int32_t) * nactive, cudaMemcpyDeviceToDevice, st), rc.err);
+  k_lvl_colmask<<<(unsigned)((W * 32 + 255) / 256), 256, 0, st>>>(s.src, W, s.colmask);
+  // requests packed into this batch: per-word and per-quad lambda rows
+  int uniform_req = 0;
+  if (rc.word_req && lambda) {
+    uniform_req = batch_uniform_request(rc.word_req, W);
+    if (uniform_req < 0) {
+      std::vector<int32_t> q((size_t)(W / 4));
+      for (int d = 0; d < W / 4; d++) {
+        int r = -1;
+        for (int w = 4 * d; w < 4 * d + 4; w++) {
+          const int x = rc.word_req[w];
+          if (x >= 0) r = (r == -1 || r == x) ? x : -2;
+        }
+        q[(size_t)d] = r;
+      }
+      MFBC_CUDA_TRY(cudaMemcpyAsync(s.word_req, rc.word_req, sizeof(int32_t) * W, cudaMemcpyHostToDevice, st), rc.err);
+      MFBC_CUDA_TRY(cudaMemcpyAsync(s.quad_req, q.data(), sizeof(int32_t) * q.size(), cudaMemcpyHostToDevice, st),
+                    rc.err);
+    }
+  }
   MFBC_CUDA_TRY(cudaMemsetAsync(s.ctr->list_count, 0, sizeof(uint32_t) * 4, st), rc.err);
   MFBC_CUDA_TRY(cudaMemsetAsync(s.full, 0, sizeof(uint32_t) * s.mw, st), rc.err);
   if (g.items_in.nhub)
@@ -1141,12 +1233,12 @@ mfbc_status level_batch(RunCtx& rc, LevelState& s, const int32_t* d_src_batch, i
   for (int l = 0;; l++) {
     const uint32_t cl = P.cnt[l];
     PROF(K_LVL_VISIT, (k_lvl_visit<<<grid_for_warps(cl, 152 * 16), LVL_WARPS * 32, 0, st>>>(
-                          s.lists + P.off[l], cl, W, nactive, Fl(l), s.V, s.full)));
+                          s.lists + P.off[l], cl, W, s.colmask, Fl(l), s.V, s.full)));
     rc.prof->k[K_LVL_VISIT].bytes += 12.0 * W * cl;
     if (l + 1 >= s.Lcap) { *levels_exceeded = true; level_reset(rc, s, l); return MFBC_ERR_NO_CONVERGENCE; }
     const int64_t off_n = P.off[l] + cl;
     MFBC_CUDA_TRY(cudaMemsetAsync(&s.ctr->list_count[0], 0, sizeof(uint32_t), st), rc.err);
-    mfbc_status e = level_round(rc, s, true, l, 0, g.items_in.count, nactive, off_n, nullptr);
+    mfbc_status e = level_round(rc, s, true, l, 0, g.items_in.count, uniform_req, off_n, nullptr);
     if (e) return e;
     MFBC_CUDA_TRY(cudaMemcpyAsync(rc.h_ctr, s.ctr->list_count, sizeof(uint32_t) * 5, cudaMemcpyDeviceToHost, st), rc.err);
     MFBC_CUDA_TRY(cudaStreamSynchronize(st), rc.err);
@@ -1170,12 +1262,12 @@ mfbc_status level_batch(RunCtx& rc, LevelState& s, const int32_t* d_src_batch, i
 
   // MFBr over levels L .. 1 (level L+1 is empty and all-zero)
   for (int l = L; l >= 1; l--) {
-    mfbc_status e = level_round(rc, s, false, l, 0, g.items_out.count, nactive, 0, lambda);
+    mfbc_status e = level_round(rc, s, false, l, 0, g.items_out.count, uniform_req, 0, lambda);
     if (e) return e;
     if (g.items_out.nhub)
       PROF(K_LVL_HUB, (k_lvl_hub_final<<<grid_for_items(g.items_out.nhub, 152 * 8), LVL_WARPS * 32, 0, st>>>(
-                          g.items_out.hubs, g.items_out.nhub, W, nb, Fl(l), Ml(l), s.sv, s.zacc, lambda,
-                          B ? B + K_LVL_HUB : nullptr)));
+                          g.items_out.hubs, g.items_out.nhub, W, nb, Fl(l), Ml(l), s.sv, s.zacc, lambda, n,
+                          uniform_req, s.word_req, B ? B + K_LVL_HUB : nullptr)));
     if (bwd_iters) (*bwd_iters)++;
   }
   return MFBC_OK;

@@ -132,4 +132,16 @@ void Profiler::release() {
   pool.clear();
 }
 
+int batch_uniform_request(const int32_t* word_req, int W) {
+  if (!word_req) return 0;
+  int r = -1;
+  for (int w = 0; w < W; w++) {
+    const int x = word_req[w];
+    if (x < 0) continue;
+    if (r < 0) r = x;
+    else if (r != x) return -2;
+  }
+  return r < 0 ? 0 : r;
+}
+
 }  // namespace mfbc

@@ -296,6 +296,68 @@ def test_profile_reports_kernels():
     G.close()
 
 
+def test_source_ordering_with_few_landmarks_and_duplicates():
+    # 12 non-isolated vertices (fewer than the 128 landmarks the ordering
+    # wants), 40 isolated ones, and 300 sources with repeats across 3 batches
+    edges = [(0, 1), (1, 2), (2, 3), (3, 0), (2, 4), (4, 5), (5, 6), (6, 7), (7, 4), (8, 9), (9, 10), (10, 11)]
+    g = gg.from_edges(52, edges, directed=False)
+    rng = np.random.default_rng(3)
+    srcs = rng.integers(0, 52, size=300).astype(np.int32)
+    want = oracle.bc(g, srcs)
+    G = mfbc.Graph.from_csr(g)
+    a = G.bc(srcs, n_b=128, path=mfbc.PATH_LEVEL)
+    b = G.bc(srcs, n_b=128, path=mfbc.PATH_LEVEL, keep_order=True)
+    assert_lambda_close(a, want)
+    assert_lambda_close(b, want)
+    G.close()
+
+
+def test_source_ordering_over_disconnected_components():
+    # two R-MAT components side by side: sources of the second one are
+    # unreachable from every landmark of the first and sort last
+    g1 = gg.rmat(11, 8, seed=4)
+    g2 = gg.erdos_renyi(1500, 6, seed=5)
+    e = [(int(u), int(v)) for u in range(g1.n) for v in g1.col[g1.rowptr[u]:g1.rowptr[u + 1]] if u < v]
+    e += [(int(u) + g1.n, int(v) + g1.n) for u in range(g2.n) for v in g2.col[g2.rowptr[u]:g2.rowptr[u + 1]] if u < v]
+    g = gg.from_edges(g1.n + g2.n, e, directed=False)
+    srcs = gg.sample_sources(g, 700, seed=6)
+    want = oracle.bc(g, srcs)
+    G = mfbc.Graph.from_csr(g)
+    for n_b in (128, 256):
+        assert_lambda_close(G.bc(srcs, n_b=n_b), want)
+    G.close()
+
+
+def test_l2_fetch_hint_is_restored():
+    # the calls set the context's L2 fetch granularity to 32 bytes while they
+    # run; the caller's value must be back afterwards
+    import ctypes
+    rt = None
+    for name in ("libcudart.so.13", "libcudart.so", "/usr/local/cuda/lib64/libcudart.so"):
+        try:
+            rt = ctypes.CDLL(name)
+            break
+        except OSError:
+            pass
+    if rt is None:
+        pytest.skip("no libcudart to query the limit")
+    import torch
+    torch.zeros(1, device="cuda")
+    limit = 5                                    # cudaLimitMaxL2FetchGranularity
+    v = ctypes.c_size_t(0)
+    assert rt.cudaDeviceSetLimit(limit, ctypes.c_size_t(128)) == 0
+    assert rt.cudaDeviceGetLimit(ctypes.byref(v), limit) == 0
+    before = v.value
+    g = gg.rmat(10, 8, seed=2)
+    G = mfbc.Graph.from_csr(g)
+    srcs = gg.sample_sources(g, 200, seed=1)
+    assert_lambda_close(G.bc(srcs), oracle.bc(g, srcs))
+    G.sssp(srcs[:10])
+    assert rt.cudaDeviceGetLimit(ctypes.byref(v), limit) == 0
+    assert v.value == before
+    G.close()
+
+
 def test_source_ordering_does_not_change_lambda():
     g = gg.rmat(13, 8, seed=9)
     srcs = gg.sample_sources(g, 300, seed=5)
