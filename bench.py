@@ -148,7 +148,7 @@ def serving_bench(n_requests=120, seed=5):
         return serve.make_requests(sizes, n_requests, rate, lo=64, hi=4096, seed=seed, eligible=elig)
 
     def served(rs):
-        srv = serve.Server(graphs, budget_bytes=budget, max_cols=4096, n_b=1024).start()
+        srv = serve.Server(graphs, budget_bytes=budget, max_cols=4096).start()
         try:
             serve.run_served(srv, rs, timeout=900)
         finally:

@@ -70,6 +70,44 @@ __device__ __forceinline__ void enqueue_once(uint32_t* vflag, int32_t* list, uin
     list[atomicAdd(count, 1u)] = v;
 }
 
+// The arc kernels come in two widths: ARCS = 8 walks a row's arcs eight at a
+// time with their loads issued together (rows of high-degree graphs), ARCS =
+// 1 one at a time (rows of a few arcs, e.g. grids, where the batching costs
+// more than it hides); the host picks by the average degree.
+//
+// Per-warp append buffer (shared memory, 40 entries): vertices to add to a
+// list are gathered and written 32 at a time with one atomic on the list
+// counter (a single counter shared by all warps is an L2 hot spot).
+__device__ __forceinline__ void wl_push(int32_t* buf, int& n, bool mine, int32_t v, int32_t* list,
+                                        uint32_t* count) {
+  const unsigned lane = lane_id();
+  const uint32_t m = __ballot_sync(0xffffffffu, mine);
+  if (mine) buf[n + __popc(m & ((1u << lane) - 1u))] = v;
+  n += __popc(m);
+  __syncwarp();
+  if (n >= 32) {
+    uint32_t b = 0;
+    if (lane == 0) b = atomicAdd(count, 32u);
+    b = __shfl_sync(0xffffffffu, b, 0);
+    list[b + lane] = buf[lane];
+    __syncwarp();
+    if ((int)lane < n - 32) buf[lane] = buf[32 + lane];
+    __syncwarp();
+    n -= 32;
+  }
+}
+__device__ __forceinline__ void wl_flush(int32_t* buf, int n, int32_t* list, uint32_t* count) {
+  if (!n) return;
+  uint32_t b = 0;
+  if (lane_id() == 0) b = atomicAdd(count, (uint32_t)n);
+  b = __shfl_sync(0xffffffffu, b, 0);
+  if ((int)lane_id() < n) list[b + lane_id()] = buf[lane_id()];
+}
+// true for the caller that first flags v (exactly one caller per vertex)
+__device__ __forceinline__ bool claim_vertex(uint32_t* vflag, int32_t v) {
+  return *((volatile uint32_t*)&vflag[v]) == 0 && atomicExch(&vflag[v], 1u) == 0u;
+}
+
 // Seed (Algorithm 1 start, read as T(s,s) = (0,1), frontier {(s,s)}).
 __global__ void k_gp_seed(const int32_t* __restrict__ src, int nb, int W, int32_t* dist, double* sig,
                           double* fm, uint32_t* fmask, uint32_t* vflag, int32_t* list,
@@ -91,12 +129,17 @@ __global__ void k_clear_flags(const int32_t* __restrict__ list, uint32_t count, 
   if (i < count) vflag[list[i]] = 0;
 }
 
-// MFBF product, phase 1: minimum candidate weight per (s, v).
-__global__ void __launch_bounds__(256) k_gp_relax_min(
+// MFBF product, phase 1: minimum candidate weight per (s, v).  One warp per
+// (frontier vertex u, 32-column word); the arcs of u are walked ARCS at a
+// time.
+template <int ARCS>
+__global__ void __launch_bounds__(256, ARCS > 1 ? 4 : 1) k_gp_relax_min(
     const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col, const int32_t* __restrict__ wt,
     const int32_t* __restrict__ flist, uint32_t fcount, int W, int nb,
     const uint32_t* __restrict__ fmask, const int32_t* __restrict__ dist, int32_t* cw, uint32_t* tmask,
     uint32_t* vflag, int32_t* tlist, uint32_t* tcount, unsigned long long* bytes) {
+  __shared__ int32_t qbuf[8][40];
+  int32_t* q = qbuf[threadIdx.x >> 5];
   uint64_t gw = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (gw >= (uint64_t)fcount * W) return;
   const unsigned lane = lane_id();
@@ -109,36 +152,59 @@ __global__ void __launch_bounds__(256) k_gp_relax_min(
   const int32_t du = active ? dist[(size_t)u * nb + j] : 0;
   const int64_t beg = rowptr[u], end = rowptr[u + 1];
   unsigned long long nb_bytes = 0;
+  int qn = 0;
   for (int64_t k0 = beg; k0 < end; k0 += 32) {
     const int64_t k = k0 + lane;
     const int32_t myv = k < end ? col[k] : 0;
     const int32_t myw = k < end ? (wt ? wt[k] : 1) : 0;
     const int cnt = (int)(end - k0 < 32 ? end - k0 : 32);
-    for (int t = 0; t < cnt; t++) {
-      const int32_t v = __shfl_sync(0xffffffffu, myv, t);
-      const int32_t w = __shfl_sync(0xffffffffu, myw, t);
-      bool touch = false;
-      if (active) {
-        const size_t idx = (size_t)v * nb + j;
-        const int32_t cand = du + w;
-        if (cand <= dist[idx]) {
-          if (cand < cw[idx]) atomicMin(&cw[idx], cand);
-          touch = true;
+    for (int t0 = 0; t0 < cnt; t0 += ARCS) {
+      int32_t v8[ARCS], w8[ARCS], d8[ARCS], c8[ARCS];
+#pragma unroll
+      for (int r = 0; r < ARCS; r++) {
+        v8[r] = __shfl_sync(0xffffffffu, myv, (t0 + r) & 31);
+        w8[r] = __shfl_sync(0xffffffffu, myw, (t0 + r) & 31);
+      }
+#pragma unroll
+      for (int r = 0; r < ARCS; r++) {
+        d8[r] = 0;
+        c8[r] = 0;
+        if (active && t0 + r < cnt) {
+          const size_t idx = (size_t)v8[r] * nb + j;
+          d8[r] = __ldg(&dist[idx]);
+          c8[r] = cw[idx];
         }
       }
-      const uint32_t tb = __ballot_sync(0xffffffffu, touch);
-      if (tb && lane == 0) {
-        atomicOr(&tmask[(size_t)v * W + word], tb);
-        enqueue_once(vflag, tlist, tcount, v);
+      bool mine = false;
+      int32_t mv = 0;
+#pragma unroll
+      for (int r = 0; r < ARCS; r++) {
+        if (t0 + r < cnt) {
+          const int32_t cand = du + w8[r];
+          const bool touch = active && cand <= d8[r];
+          if (touch && cand < c8[r]) atomicMin(&cw[(size_t)v8[r] * nb + j], cand);
+          const uint32_t tb = __ballot_sync(0xffffffffu, touch);
+          if (tb && (int)lane == r) {
+            atomicOr(&tmask[(size_t)v8[r] * W + word], tb);
+            if (claim_vertex(vflag, v8[r])) { mine = true; mv = v8[r]; }
+          }
+          if (bytes) nb_bytes += 4ull * __popc(m) + 8ull * __popc(tb);
+        }
       }
-      if (bytes) nb_bytes += 4ull * __popc(m) + 8ull * __popc(tb);
+      if constexpr (ARCS == 1) {
+        if (mine) tlist[atomicAdd(tcount, 1u)] = mv;
+      } else {
+        wl_push(q, qn, mine, mv, tlist, tcount);
+      }
     }
   }
+  if constexpr (ARCS > 1) wl_flush(q, qn, tlist, tcount);
   if (bytes && lane == 0) atomicAdd(bytes, nb_bytes + 8ull * (end - beg) / W + 4ull * __popc(m));
 }
 
 // MFBF product, phase 2: sum the frontier multiplicities that attain the minimum.
-__global__ void __launch_bounds__(256) k_gp_relax_tie(
+template <int ARCS>
+__global__ void __launch_bounds__(256, ARCS > 1 ? 4 : 1) k_gp_relax_tie(
     const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col, const int32_t* __restrict__ wt,
     const int32_t* __restrict__ flist, uint32_t fcount, int W, int nb,
     const uint32_t* __restrict__ fmask, const int32_t* __restrict__ dist, const double* __restrict__ fm,
@@ -161,15 +227,24 @@ __global__ void __launch_bounds__(256) k_gp_relax_tie(
     const int32_t myv = k < end ? col[k] : 0;
     const int32_t myw = k < end ? (wt ? wt[k] : 1) : 0;
     const int cnt = (int)(end - k0 < 32 ? end - k0 : 32);
-    for (int t = 0; t < cnt; t++) {
-      const int32_t v = __shfl_sync(0xffffffffu, myv, t);
-      const int32_t w = __shfl_sync(0xffffffffu, myw, t);
-      bool hit = false;
-      if (active) {
-        const size_t idx = (size_t)v * nb + j;
-        if (du + w == cw[idx]) { atomicAdd(&cm[idx], mu); hit = true; }
+    for (int t0 = 0; t0 < cnt; t0 += ARCS) {
+      int32_t v8[ARCS], w8[ARCS], c8[ARCS];
+#pragma unroll
+      for (int r = 0; r < ARCS; r++) {
+        v8[r] = __shfl_sync(0xffffffffu, myv, (t0 + r) & 31);
+        w8[r] = __shfl_sync(0xffffffffu, myw, (t0 + r) & 31);
       }
-      if (bytes) nb_bytes += 4ull * __popc(m) + 16ull * __popc(__ballot_sync(0xffffffffu, hit));
+#pragma unroll
+      for (int r = 0; r < ARCS; r++)
+        c8[r] = (active && t0 + r < cnt) ? __ldg(&cw[(size_t)v8[r] * nb + j]) : -1;
+#pragma unroll
+      for (int r = 0; r < ARCS; r++) {
+        if (t0 + r < cnt) {
+          const bool hit = active && du + w8[r] == c8[r];
+          if (hit) atomicAdd(&cm[(size_t)v8[r] * nb + j], mu);
+          if (bytes) nb_bytes += 4ull * __popc(m) + 16ull * __popc(__ballot_sync(0xffffffffu, hit));
+        }
+      }
     }
   }
   if (bytes && lane == 0) atomicAdd(bytes, nb_bytes + 8ull * (end - beg) / W + 12ull * __popc(m));
@@ -186,6 +261,9 @@ __global__ void __launch_bounds__(256) k_gp_accumulate(
     const int32_t* __restrict__ tlist, const uint32_t* tcount_p, int W, int nb, int32_t* dist,
     double* sig, int32_t* cw, double* cm, double* fm, uint32_t* fmask, uint32_t* tmask, uint32_t* vflag,
     int32_t* nlist, uint32_t* ncount, unsigned long long* bytes) {
+  __shared__ int32_t qbuf[8][40];
+  int32_t* q = qbuf[threadIdx.x >> 5];
+  int qn = 0;
   const uint32_t tcount = *tcount_p;
   const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
   for (uint64_t gw = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; gw < tcount; gw += nw) {
@@ -216,14 +294,16 @@ __global__ void __launch_bounds__(256) k_gp_accumulate(
   }
   if (lane == 0) {
     vflag[v] = 0u;
-    if (any) nlist[atomicAdd(ncount, 1u)] = v;
     if (bytes) atomicAdd(bytes, nbytes + 8ull);
   }
+  wl_push(q, qn, lane == 0 && any, v, nlist, ncount);
   }
+  wl_flush(q, qn, nlist, ncount);
 }
 
 // Algorithm 2 initialisation: successor counters and the leaf frontier.
-__global__ void __launch_bounds__(256) k_gp_counters(
+template <int ARCS>
+__global__ void __launch_bounds__(256, ARCS > 1 ? 4 : 1) k_gp_counters(
     int32_t n, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
     const int32_t* __restrict__ wt, int W, int nb, const int32_t* __restrict__ src,
     const int32_t* __restrict__ dist, const double* __restrict__ sig, int32_t* cnt, double* zp, double* fv,
@@ -249,10 +329,19 @@ __global__ void __launch_bounds__(256) k_gp_counters(
       const int32_t myu = k < end ? col[k] : 0;
       const int32_t myw = k < end ? (wt ? wt[k] : 1) : 0;
       const int cntk = (int)(end - k0 < 32 ? end - k0 : 32);
-      for (int t = 0; t < cntk; t++) {
-        const int32_t u = __shfl_sync(0xffffffffu, myu, t);
-        const int32_t w = __shfl_sync(0xffffffffu, myw, t);
-        if (reach && dist[(size_t)u * nb + j] == dv + w) c++;
+      for (int t0 = 0; t0 < cntk; t0 += ARCS) {
+        int32_t u8[ARCS], w8[ARCS], d8[ARCS];
+#pragma unroll
+        for (int r = 0; r < ARCS; r++) {
+          u8[r] = __shfl_sync(0xffffffffu, myu, (t0 + r) & 31);
+          w8[r] = __shfl_sync(0xffffffffu, myw, (t0 + r) & 31);
+        }
+#pragma unroll
+        for (int r = 0; r < ARCS; r++)
+          d8[r] = (reach && t0 + r < cntk) ? __ldg(&dist[(size_t)u8[r] * nb + j]) : -1;
+#pragma unroll
+        for (int r = 0; r < ARCS; r++)
+          if (t0 + r < cntk && d8[r] == dv + w8[r]) c++;
       }
     }
     if (reach) {
@@ -272,12 +361,16 @@ __global__ void __launch_bounds__(256) k_gp_counters(
 }
 
 // MFBr product over A^T with counter decrement and exactly-once enqueue.
-__global__ void __launch_bounds__(256) k_gp_propagate(
+template <int ARCS>
+__global__ void __launch_bounds__(256, ARCS > 1 ? 4 : 1) k_gp_propagate(
     const int64_t* __restrict__ rowptr_t, const int32_t* __restrict__ col_t,
     const int32_t* __restrict__ wt_t, const int32_t* __restrict__ flist, uint32_t fcount, int W, int nb,
     const uint32_t* __restrict__ fmask, const int32_t* __restrict__ dist, const double* __restrict__ fv,
     double* zp, int32_t* cnt, uint32_t* tmask, uint32_t* vflag, int32_t* tlist, uint32_t* tcount,
     unsigned long long* bytes) {
+  __shared__ int32_t qbuf[8][40];
+  int32_t* q = qbuf[threadIdx.x >> 5];
+  int qn = 0;
   uint64_t gw = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (gw >= (uint64_t)fcount * W) return;
   const unsigned lane = lane_id();
@@ -296,26 +389,46 @@ __global__ void __launch_bounds__(256) k_gp_propagate(
     const int32_t myv = k < end ? col_t[k] : 0;
     const int32_t myw = k < end ? (wt_t ? wt_t[k] : 1) : 0;
     const int cntk = (int)(end - k0 < 32 ? end - k0 : 32);
-    for (int t = 0; t < cntk; t++) {
-      const int32_t v = __shfl_sync(0xffffffffu, myv, t);
-      const int32_t w = __shfl_sync(0xffffffffu, myw, t);
-      bool ready = false, hit = false;
-      if (active) {
-        const size_t idx = (size_t)v * nb + j;
-        if (dist[idx] == du - w) {
+    for (int t0 = 0; t0 < cntk; t0 += ARCS) {
+      int32_t v8[ARCS], w8[ARCS], d8[ARCS], o8[ARCS];
+#pragma unroll
+      for (int r = 0; r < ARCS; r++) {
+        v8[r] = __shfl_sync(0xffffffffu, myv, (t0 + r) & 31);
+        w8[r] = __shfl_sync(0xffffffffu, myw, (t0 + r) & 31);
+      }
+#pragma unroll
+      for (int r = 0; r < ARCS; r++)
+        d8[r] = (active && t0 + r < cntk) ? __ldg(&dist[(size_t)v8[r] * nb + j]) : INT32_MIN;
+#pragma unroll
+      for (int r = 0; r < ARCS; r++) {
+        o8[r] = 0;
+        if (t0 + r < cntk && d8[r] == du - w8[r]) {
+          const size_t idx = (size_t)v8[r] * nb + j;
           atomicAdd(&zp[idx], val);
-          ready = (atomicSub(&cnt[idx], 1) == 1);
-          hit = true;
+          o8[r] = atomicSub(&cnt[idx], 1);
         }
       }
-      const uint32_t rb = __ballot_sync(0xffffffffu, ready);
-      if (rb && lane == 0) {
-        atomicOr(&tmask[(size_t)v * W + word], rb);
-        enqueue_once(vflag, tlist, tcount, v);
+      bool mine = false;
+      int32_t mv = 0;
+#pragma unroll
+      for (int r = 0; r < ARCS; r++) {
+        if (t0 + r < cntk) {
+          const uint32_t rb = __ballot_sync(0xffffffffu, o8[r] == 1);
+          if (rb && (int)lane == r) {
+            atomicOr(&tmask[(size_t)v8[r] * W + word], rb);
+            if (claim_vertex(vflag, v8[r])) { mine = true; mv = v8[r]; }
+          }
+          if (bytes) nb_bytes += 4ull * __popc(m) + 24ull * __popc(__ballot_sync(0xffffffffu, d8[r] == du - w8[r]));
+        }
       }
-      if (bytes) nb_bytes += 4ull * __popc(m) + 24ull * __popc(__ballot_sync(0xffffffffu, hit));
+      if constexpr (ARCS == 1) {
+        if (mine) tlist[atomicAdd(tcount, 1u)] = mv;
+      } else {
+        wl_push(q, qn, mine, mv, tlist, tcount);
+      }
     }
   }
+  if constexpr (ARCS > 1) wl_flush(q, qn, tlist, tcount);
   if (bytes && lane == 0) atomicAdd(bytes, nb_bytes + 8ull * (end - beg) / W + 16ull * __popc(m));
 }
 
@@ -324,6 +437,9 @@ __global__ void __launch_bounds__(256) k_gp_next_frontier(
     const int32_t* __restrict__ tlist, const uint32_t* tcount_p, int W, int nb,
     const double* __restrict__ sig, const double* __restrict__ zp, double* fv, uint32_t* fmask,
     uint32_t* tmask, uint32_t* vflag, int32_t* nlist, uint32_t* ncount, unsigned long long* bytes) {
+  __shared__ int32_t qbuf[8][40];
+  int32_t* q = qbuf[threadIdx.x >> 5];
+  int qn = 0;
   const uint32_t tcount = *tcount_p;
   const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
   for (uint64_t gw = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; gw < tcount; gw += nw) {
@@ -343,10 +459,11 @@ __global__ void __launch_bounds__(256) k_gp_next_frontier(
   }
   if (lane == 0) {
     vflag[v] = 0u;
-    nlist[atomicAdd(ncount, 1u)] = v;
     if (bytes) atomicAdd(bytes, nbytes);
   }
+  wl_push(q, qn, lane == 0, v, nlist, ncount);
   }
+  wl_flush(q, qn, nlist, ncount);
 }
 
 // Algorithm 3 accumulation, one warp per vertex, no atomics.
@@ -399,6 +516,13 @@ static mfbc_status read_counts(RunCtx& rc, Counters* ctr) {
   return MFBC_OK;
 }
 
+// arc kernels: eight arcs per step on graphs of average degree >= 8
+#define GP_LAUNCH(kern, grid, ...)                                        \
+  do {                                                                    \
+    if (wide) kern<8><<<grid, 256, 0, st>>>(__VA_ARGS__);                 \
+    else kern<1><<<grid, 256, 0, st>>>(__VA_ARGS__);                      \
+  } while (0)
+
 #define PROF(id, ...)             \
   do {                            \
     rc.prof->begin(id);           \
@@ -415,6 +539,7 @@ mfbc_status general_batch(RunCtx& rc, GeneralState& s, const int32_t* d_src_batc
   const size_t cells = (size_t)n * nb;
   unsigned long long* B = rc.prof->count_bytes ? s.ctr->bytes : nullptr;
   if (n == 0) return MFBC_OK;
+  const bool wide = g.nnz >= 8 * (int64_t)n;       // average degree >= 8: batch eight arcs per step
 
   // batch sources: active columns then padding
   fill_i32(s.src, -1, (size_t)nb, st);
@@ -451,12 +576,12 @@ mfbc_status general_batch(RunCtx& rc, GeneralState& s, const int32_t* d_src_batc
     }
     MFBC_CUDA_TRY(cudaMemsetAsync(s.ctr->list_count, 0, sizeof(uint32_t) * 4, st), rc.err);
     const uint64_t wp = (uint64_t)fcount * W;
-    PROF(K_RELAX_MIN, (k_gp_relax_min<<<warp_blocks(wp), 256, 0, st>>>(
+    PROF(K_RELAX_MIN, GP_LAUNCH(k_gp_relax_min, warp_blocks(wp),
                           g.rowptr, g.col, g.w, cur, fcount, W, nb, s.fmask, s.dist, s.cw, s.tmask,
-                          s.vflag, nxt, &s.ctr->list_count[1], B ? B + K_RELAX_MIN : nullptr)));
-    PROF(K_RELAX_TIE, (k_gp_relax_tie<<<warp_blocks(wp), 256, 0, st>>>(
+                          s.vflag, nxt, &s.ctr->list_count[1], B ? B + K_RELAX_MIN : nullptr));
+    PROF(K_RELAX_TIE, GP_LAUNCH(k_gp_relax_tie, warp_blocks(wp),
                           g.rowptr, g.col, g.w, cur, fcount, W, nb, s.fmask, s.dist, s.fm, s.cw, s.cm,
-                          B ? B + K_RELAX_TIE : nullptr)));
+                          B ? B + K_RELAX_TIE : nullptr));
     PROF(K_CLEAR, (k_clear_mask_rows<<<(unsigned)((wp + 255) / 256), 256, 0, st>>>(cur, fcount, W,
                                                                                    s.fmask)));
     // the touched list lives in nxt; compact the next frontier into cur
@@ -473,9 +598,9 @@ mfbc_status general_batch(RunCtx& rc, GeneralState& s, const int32_t* d_src_batc
 
   // ---- MFBr (Algorithm 2): cw holds the counters, cm the factors Z.p, fm the values
   MFBC_CUDA_TRY(cudaMemsetAsync(s.ctr->list_count, 0, sizeof(uint32_t) * 4, st), rc.err);
-  PROF(K_COUNTERS, (k_gp_counters<<<warp_blocks((uint64_t)n), 256, 0, st>>>(
+  PROF(K_COUNTERS, GP_LAUNCH(k_gp_counters, warp_blocks((uint64_t)n),
                        n, g.rowptr, g.col, g.w, W, nb, s.src, s.dist, s.sig, s.cw, s.cm, s.fm, s.fmask,
-                       cur, &s.ctr->list_count[0], B ? B + K_COUNTERS : nullptr)));
+                       cur, &s.ctr->list_count[0], B ? B + K_COUNTERS : nullptr));
   e = read_counts(rc, s.ctr);
   if (e) return e;
   fcount = rc.h_ctr[0];
@@ -487,10 +612,10 @@ mfbc_status general_batch(RunCtx& rc, GeneralState& s, const int32_t* d_src_batc
     }
     MFBC_CUDA_TRY(cudaMemsetAsync(s.ctr->list_count, 0, sizeof(uint32_t) * 4, st), rc.err);
     const uint64_t wp = (uint64_t)fcount * W;
-    PROF(K_PROPAGATE, (k_gp_propagate<<<warp_blocks(wp), 256, 0, st>>>(
+    PROF(K_PROPAGATE, GP_LAUNCH(k_gp_propagate, warp_blocks(wp),
                           g.rowptr_t, g.col_t, g.w_t, cur, fcount, W, nb, s.fmask, s.dist, s.fm, s.cm,
                           s.cw, s.tmask, s.vflag, nxt, &s.ctr->list_count[1],
-                          B ? B + K_PROPAGATE : nullptr)));
+                          B ? B + K_PROPAGATE : nullptr));
     PROF(K_CLEAR, (k_clear_mask_rows<<<(unsigned)((wp + 255) / 256), 256, 0, st>>>(cur, fcount, W,
                                                                                    s.fmask)));
     PROF(K_FINAL, (k_gp_next_frontier<<<stride_blocks((uint64_t)n), 256, 0, st>>>(

@@ -69,7 +69,7 @@ class Server:
     n_b, ws_bytes, stream) -> list of lambda arrays may replace the GPU call
     (host-logic tests); sizer(name, cols, nreq, n_b) -> bytes likewise."""
 
-    def __init__(self, graphs: dict, *, budget_bytes: int, max_cols: int = 4096, n_b: int = 1024,
+    def __init__(self, graphs: dict, *, budget_bytes: int, max_cols: int = 4096, n_b: int = 0,
                  executor=None, sizer=None, clock=time.perf_counter):
         self.graphs = graphs
         self.budget = int(budget_bytes)
@@ -134,10 +134,14 @@ class Server:
         return group, cols
 
     def _fit(self, key, cols, nreq):
-        """Largest n_b (multiple of 128, at most self.n_b) whose group fits the
-        budget alone; (n_b, bytes)."""
+        """The group's n_b and bytes: self.n_b (0 = the library's own choice
+        for the group's columns), lowered in steps of 128 while the group
+        alone would not fit the budget."""
         nb = self.n_b
         need = self.sizer(key, cols, nreq, nb)
+        if need > self.budget and nb == 0:
+            nb = 1024
+            need = self.sizer(key, cols, nreq, nb)
         while need > self.budget and nb > 128:
             nb -= 128
             need = self.sizer(key, cols, nreq, nb)

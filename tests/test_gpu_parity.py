@@ -136,6 +136,25 @@ def test_er_2p20_k32_sampled_sources():
     G.close()
 
 
+def test_rmat22_bench_launch_configuration():
+    # the bench's graph and sources at its batch width (n_b = 1024, level
+    # kernels, landmark ordering on): 1056 sources = two batches, lambda
+    # against the oracle element by element; then MFBF rows of sampled
+    # sources out of one full 1024-column batch, bit-exact
+    import torch
+    g = gg.rmat(22, 16, seed=1)
+    srcs = gg.sample_sources(g, 16384, seed=2)[:1056]
+    G = mfbc.Graph.from_csr(g)
+    assert_lambda_close(G.bc(srcs, n_b=1024), oracle.bc(g, srcs))
+    dist, sig = G.sssp(torch.from_numpy(srcs[:1024]).cuda(), n_b=1024)
+    pick = np.array([0, 1, 511, 1023])
+    wd, ws, _ = oracle.sssp(g, srcs[pick])
+    assert np.array_equal(dist[torch.from_numpy(pick).cuda()].cpu().numpy(), wd)
+    assert np.array_equal(sig[torch.from_numpy(pick).cuda()].cpu().numpy(), ws)
+    del dist, sig
+    G.close()
+
+
 def test_dense_weighted_er_2p16_k1024():
     g = gg.erdos_renyi(1 << 16, 1024, weights=(1, 100), seed=1)
     srcs = gg.sample_sources(g, 40, seed=3)

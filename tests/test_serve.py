@@ -98,13 +98,13 @@ def test_oversize_group_lowers_n_b_until_it_fits():
     seen = []
 
     def sizer(k, cols, nreq, nb):
-        return nb * 10
+        return (nb or 4096) * 10                  # n_b = 0: the library would take 4096 columns
 
     def ex(key, group, nb, need, stream):
         seen.append(nb)
         return [np.zeros(graphs[key].n) for _ in group]
 
-    srv = Server(graphs, budget_bytes=300 * 10, max_cols=4096, n_b=1024, executor=ex, sizer=sizer)
+    srv = Server(graphs, budget_bytes=300 * 10, max_cols=4096, n_b=0, executor=ex, sizer=sizer)
     srv.start()
     run_served(srv, [Request(0, "a", np.arange(50, dtype=np.int32), 0.0)], timeout=30)
     srv.close()
