@@ -175,6 +175,29 @@ mfbc_status mfbc_bc_multi_device(const mfbc_graph* g, const int32_t* sources, in
                                  const int32_t* req_offsets, int32_t nreq, double* lambda_out,
                                  const mfbc_options* opt);
 
+/* Result of mfbc_autotune. */
+typedef struct {
+  int32_t n_b;            /* fastest batch width found */
+  int32_t path;           /* MFBC_PATH_LEVEL or MFBC_PATH_GENERAL */
+  int32_t arcs;           /* general kernels: arcs walked per step (1 or 8); 0 on the level kernels */
+  int32_t tried;          /* configurations timed */
+  double ms_per_source;   /* wall time of the fastest configuration per source */
+} mfbc_tuning;
+
+/* Autotuner (no counterpart in the paper, whose batch width and processor
+ * grid come from its cost model, Sec. 5): times mfbc_bc on the HOST sources
+ * int32[nsrc] for each candidate configuration and keeps the fastest on the
+ * graph handle.  Candidates: n_b in {128, 256, 512, 1024} on the level kernels,
+ * or {128, 256, 512, 1024, 2048, 4096} x {1, 8} arcs per step on the general
+ * kernels, each at most nsrc rounded up; widths that do not fit the device
+ * are skipped.  Each candidate runs twice (the first call untimed).  Later
+ * calls on this handle with opt->n_b == 0 use at most the tuned width, and the
+ * general kernels use the tuned arcs per step (without tuning: 8 when the
+ * average degree is at least 8, else 1).  opt->path selects the kernel family
+ * (AUTO as in mfbc_bc); n_b in opt is ignored.  Results are unaffected. */
+mfbc_status mfbc_autotune(mfbc_graph* g, const int32_t* sources, int32_t nsrc, const mfbc_options* opt,
+                          mfbc_tuning* out);
+
 /* MFBF alone (Algorithm 1, Lemma 1): for each i < nsrc,
  *   dist_out [i*n + v] = tau(sources[i], v)        (INT32_MAX if unreachable)
  *   sigma_out[i*n + v] = sigma_bar(sources[i], v)  (0 if unreachable; sigma_bar(s,s) = 1)

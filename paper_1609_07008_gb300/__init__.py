@@ -74,6 +74,12 @@ class Options(ctypes.Structure):
                 ("flags", ctypes.c_uint32)]
 
 
+class Tuning(ctypes.Structure):
+    """mfbc_tuning (include/mfbc.h)."""
+    _fields_ = [("n_b", ctypes.c_int32), ("path", ctypes.c_int32), ("arcs", ctypes.c_int32),
+                ("tried", ctypes.c_int32), ("ms_per_source", ctypes.c_double)]
+
+
 _lib = None
 _lock = threading.Lock()
 
@@ -99,6 +105,7 @@ def load(path: str | None = None):
             "mfbc_bc": [vp, vp, i32, vp, ctypes.POINTER(Options)],
             "mfbc_bc_device": [vp, vp, i32, vp, ctypes.POINTER(Options)],
             "mfbc_bc_multi_device": [vp, vp, i32, vp, i32, vp, ctypes.POINTER(Options)],
+            "mfbc_autotune": [vp, vp, i32, ctypes.POINTER(Options), ctypes.POINTER(Tuning)],
             "mfbc_sssp_batch": [vp, vp, i32, vp, vp, ctypes.POINTER(Options)],
             "mfbc_sssp_batch_device": [vp, vp, i32, vp, vp, ctypes.POINTER(Options)],
             "mfbc_workspace_size": [vp, i32, i32, ctypes.POINTER(Options), ctypes.POINTER(ctypes.c_uint64)],
@@ -280,6 +287,17 @@ class Graph:
         _check(lib.mfbc_bc_multi_device(self._h, _dptr(src), src.numel(), _hptr(off), nreq, _dptr(lam),
                                         ctypes.byref(opt)))
         return (lam, prof.as_dict()) if profile else lam
+
+    def autotune(self, sources, *, path: int = PATH_AUTO) -> dict:
+        """Time the candidate batch widths (and, on the general kernels, arcs
+        per step) on host `sources` and keep the fastest on this handle
+        (mfbc_autotune)."""
+        lib = load()
+        src = _host(sources, np.int32)
+        t = Tuning()
+        opt = _options(0, path, None, None, None, None)
+        _check(lib.mfbc_autotune(self._h, _hptr(src), len(src), ctypes.byref(opt), ctypes.byref(t)))
+        return {"n_b": t.n_b, "path": t.path, "arcs": t.arcs, "tried": t.tried, "ms_per_source": t.ms_per_source}
 
     def sssp(self, sources, *, n_b: int = 0, path: int = PATH_AUTO, with_sigma: bool = True, stream=None,
              workspace=None, profile: bool = False, return_warn: bool = False):

@@ -2,6 +2,7 @@
 // batch width, scratch management, and the batch loop of Algorithm 3.
 #include <algorithm>
 #include <cstring>
+#include <chrono>
 #include <mutex>
 #include <string>
 
@@ -16,6 +17,12 @@ struct mfbc_graph {
   uint32_t* h_ctr = nullptr;       // pinned counter mirror
   uint32_t flags = 0;
   std::mutex mu;
+  // autotuner results (mfbc_autotune): batch width per kernel family
+  // (0 level, 1 general; 0 = not tuned) and the general kernels' arcs per
+  // step (0 = by average degree); force_arcs overrides it while tuning
+  int tuned_nb[2] = {0, 0};
+  int tuned_arcs = 0;
+  int force_arcs = 0;
 };
 
 static thread_local std::string t_err;
@@ -191,7 +198,9 @@ static mfbc_status make_plan(const mfbc_graph* G, int32_t nsrc, int mode, const 
     plan_bytes(g, path, nb, nsrc, mode, host_io, p);
     return MFBC_OK;
   }
-  // auto: widest batch (<= number of sources) whose scratch fits the budget
+  // auto: widest batch (<= number of sources, <= the tuned width) whose
+  // scratch fits the budget
+  const int tuned = G->tuned_nb[path == MFBC_PATH_LEVEL ? 0 : 1];
   size_t budget;
   if (opt && opt->workspace) budget = opt->workspace_bytes;
   else {
@@ -199,7 +208,7 @@ static mfbc_status make_plan(const mfbc_graph* G, int32_t nsrc, int mode, const 
     if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) { cudaGetLastError(); return fail(MFBC_ERR_CUDA, "cudaMemGetInfo failed"); }
     budget = (size_t)(0.80 * (double)(fr + G->ws_bytes));
   }
-  int nb = std::min(maxnb, std::max(gran, (nsrc + gran - 1) / gran * gran));
+  int nb = std::min(tuned > 0 ? tuned : maxnb, std::max(gran, (nsrc + gran - 1) / gran * gran));
   while (true) {
     plan_bytes(g, path, nb, nsrc, mode, host_io, p);
     if (p->total <= budget || nb == gran) break;
@@ -423,6 +432,7 @@ mfbc_status run(mfbc_graph* G, const int32_t* d_src, int32_t nsrc, int mode, dou
   const int nb = P.nb;
   int64_t batches = 0, fi = 0, bi = 0;
   RunCtx rc{&g, R.st, &R.prof, G->h_ctr, &R.err};
+  rc.arcs = G->force_arcs ? G->force_arcs : G->tuned_arcs;
   Carver c(R.ws, R.ws_bytes);
   GeneralState gs;
   LevelState ls;
@@ -680,6 +690,63 @@ extern "C" mfbc_status mfbc_bc_multi_device(const mfbc_graph* g, const int32_t* 
                                             const int32_t* req_offsets, int32_t nreq, double* lambda_out,
                                             const mfbc_options* opt) {
   return entry(g, sources, nsrc, 2, lambda_out, nullptr, nullptr, opt, false, req_offsets, nreq);
+}
+
+extern "C" mfbc_status mfbc_autotune(mfbc_graph* G, const int32_t* sources, int32_t nsrc, const mfbc_options* opt,
+                                     mfbc_tuning* out) {
+  if (!G || !out) return fail(MFBC_ERR_INVALID, "graph and out must not be NULL");
+  if (nsrc < 1 || !sources) return fail(MFBC_ERR_INVALID, "need at least one source");
+  int path = opt ? opt->path : MFBC_PATH_AUTO;
+  if (path == MFBC_PATH_AUTO) path = G->g.unit ? MFBC_PATH_LEVEL : MFBC_PATH_GENERAL;
+  if (path == MFBC_PATH_LEVEL && !G->g.unit) return fail(MFBC_ERR_INVALID, "MFBC_PATH_LEVEL needs unit weights");
+  if (path != MFBC_PATH_LEVEL && path != MFBC_PATH_GENERAL) return fail(MFBC_ERR_INVALID, "unknown path");
+  const bool level = path == MFBC_PATH_LEVEL;
+  std::vector<int> widths = level ? std::vector<int>{128, 256, 512, 1024}
+                                  : std::vector<int>{128, 256, 512, 1024, 2048, 4096};
+  const int gran = level ? 128 : 32;
+  const int cols = (nsrc + gran - 1) / gran * gran;
+  while (widths.size() > 1 && widths.back() > cols) widths.pop_back();
+  const std::vector<int> arcs = level ? std::vector<int>{0} : std::vector<int>{1, 8};
+  std::vector<double> lam((size_t)std::max(G->g.n, 1));
+  mfbc_options o = opt ? *opt : mfbc_options{};
+  o.path = path;
+  o.profile = nullptr;
+  o.warn_out = nullptr;
+  double best = 0.0;
+  int best_nb = 0, best_arcs = 0, tried = 0;
+  for (int nb : widths)
+    for (int a : arcs) {
+      o.n_b = nb;
+      {
+        std::lock_guard<std::mutex> lock(G->mu);
+        G->force_arcs = a;
+      }
+      // one untimed call (scratch growth, first-touch), then the timed one
+      mfbc_status s = entry(G, sources, nsrc, 0, lam.data(), nullptr, nullptr, &o, true);
+      const auto t0 = std::chrono::steady_clock::now();
+      if (s == MFBC_OK) s = entry(G, sources, nsrc, 0, lam.data(), nullptr, nullptr, &o, true);
+      const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+      if (s == MFBC_ERR_OOM) continue;             // too wide for this device: not a candidate
+      if (s != MFBC_OK) {
+        std::lock_guard<std::mutex> lock(G->mu);
+        G->force_arcs = 0;
+        return s;
+      }
+      tried++;
+      if (best_nb == 0 || ms < best) { best = ms; best_nb = nb; best_arcs = a; }
+    }
+  std::lock_guard<std::mutex> lock(G->mu);
+  G->force_arcs = 0;
+  if (!best_nb) return fail(MFBC_ERR_OOM, "no candidate batch width fits the device");
+  G->tuned_nb[level ? 0 : 1] = best_nb;
+  if (!level) G->tuned_arcs = best_arcs;
+  out->n_b = best_nb;
+  out->path = path;
+  out->arcs = best_arcs;
+  out->tried = tried;
+  out->ms_per_source = best / nsrc;
+  t_err.clear();
+  return MFBC_OK;
 }
 
 extern "C" mfbc_status mfbc_sssp_batch(const mfbc_graph* g, const int32_t* sources, int32_t nsrc,

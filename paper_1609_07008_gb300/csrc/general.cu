@@ -133,7 +133,7 @@ __global__ void k_clear_flags(const int32_t* __restrict__ list, uint32_t count, 
 // (frontier vertex u, 32-column word); the arcs of u are walked ARCS at a
 // time.
 template <int ARCS>
-__global__ void __launch_bounds__(256, ARCS > 1 ? 4 : 1) k_gp_relax_min(
+__global__ void __launch_bounds__(256, ARCS > 1 ? 4 : 8) k_gp_relax_min(
     const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col, const int32_t* __restrict__ wt,
     const int32_t* __restrict__ flist, uint32_t fcount, int W, int nb,
     const uint32_t* __restrict__ fmask, const int32_t* __restrict__ dist, int32_t* cw, uint32_t* tmask,
@@ -204,7 +204,7 @@ __global__ void __launch_bounds__(256, ARCS > 1 ? 4 : 1) k_gp_relax_min(
 
 // MFBF product, phase 2: sum the frontier multiplicities that attain the minimum.
 template <int ARCS>
-__global__ void __launch_bounds__(256, ARCS > 1 ? 4 : 1) k_gp_relax_tie(
+__global__ void __launch_bounds__(256, ARCS > 1 ? 4 : 8) k_gp_relax_tie(
     const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col, const int32_t* __restrict__ wt,
     const int32_t* __restrict__ flist, uint32_t fcount, int W, int nb,
     const uint32_t* __restrict__ fmask, const int32_t* __restrict__ dist, const double* __restrict__ fm,
@@ -303,7 +303,7 @@ __global__ void __launch_bounds__(256) k_gp_accumulate(
 
 // Algorithm 2 initialisation: successor counters and the leaf frontier.
 template <int ARCS>
-__global__ void __launch_bounds__(256, ARCS > 1 ? 4 : 1) k_gp_counters(
+__global__ void __launch_bounds__(256, ARCS > 1 ? 4 : 6) k_gp_counters(
     int32_t n, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
     const int32_t* __restrict__ wt, int W, int nb, const int32_t* __restrict__ src,
     const int32_t* __restrict__ dist, const double* __restrict__ sig, int32_t* cnt, double* zp, double* fv,
@@ -362,7 +362,7 @@ __global__ void __launch_bounds__(256, ARCS > 1 ? 4 : 1) k_gp_counters(
 
 // MFBr product over A^T with counter decrement and exactly-once enqueue.
 template <int ARCS>
-__global__ void __launch_bounds__(256, ARCS > 1 ? 4 : 1) k_gp_propagate(
+__global__ void __launch_bounds__(256, ARCS > 1 ? 4 : 6) k_gp_propagate(
     const int64_t* __restrict__ rowptr_t, const int32_t* __restrict__ col_t,
     const int32_t* __restrict__ wt_t, const int32_t* __restrict__ flist, uint32_t fcount, int W, int nb,
     const uint32_t* __restrict__ fmask, const int32_t* __restrict__ dist, const double* __restrict__ fv,
@@ -539,7 +539,8 @@ mfbc_status general_batch(RunCtx& rc, GeneralState& s, const int32_t* d_src_batc
   const size_t cells = (size_t)n * nb;
   unsigned long long* B = rc.prof->count_bytes ? s.ctr->bytes : nullptr;
   if (n == 0) return MFBC_OK;
-  const bool wide = g.nnz >= 8 * (int64_t)n;       // average degree >= 8: batch eight arcs per step
+  // eight arcs per step on graphs of average degree >= 8, unless tuned
+  const bool wide = rc.arcs ? rc.arcs > 1 : g.nnz >= 8 * (int64_t)n;
 
   // batch sources: active columns then padding
   fill_i32(s.src, -1, (size_t)nb, st);

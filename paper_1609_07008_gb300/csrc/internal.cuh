@@ -165,6 +165,8 @@ struct RunCtx {
   // Request r adds into lambda + r * n.  nullptr: the whole batch is
   // request 0.
   const int32_t* word_req = nullptr;
+  // general kernels: arcs walked per step (1 or 8); 0 = by average degree
+  int arcs = 0;
 };
 
 // Request of the batch as a whole: r >= 0 when every used word belongs to

@@ -389,3 +389,19 @@ def test_source_ordering_does_not_change_lambda():
         assert_lambda_close(b, want)
         assert_lambda_close(a, b, rtol=1e-12)
     G.close()
+
+
+@pytest.mark.parametrize("weighted", [False, True])
+def test_autotune_picks_a_candidate_and_results_are_unchanged(weighted):
+    g = gg.rmat(12, 8, directed=weighted, weights=(1, 9) if weighted else None, seed=31)
+    srcs = gg.sample_sources(g, 600, seed=1)
+    G = mfbc.Graph.from_csr(g)
+    t = G.autotune(srcs)
+    assert t["path"] == (mfbc.PATH_GENERAL if weighted else mfbc.PATH_LEVEL)
+    assert t["n_b"] in ({128, 256, 512} if not weighted else {128, 256, 512}) and t["tried"] >= 1
+    assert t["ms_per_source"] > 0
+    assert t["arcs"] == 0 if not weighted else t["arcs"] in (1, 8)
+    lam, prof = G.bc(srcs, profile=True)
+    assert prof["n_b"] <= t["n_b"]
+    assert_lambda_close(lam, oracle.bc(g, srcs))
+    G.close()
