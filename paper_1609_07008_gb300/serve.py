@@ -18,8 +18,11 @@ per graph:
   (`mfbc_workspace_size`, mode 2) plus its lambda rows; a group starts only
   when the bytes held by running groups leave room for it, and its n_b is
   lowered until a lone group fits;
-* overlap -- the workers of different graphs issue work on their own CUDA
-  streams, so groups of different graphs run on the device at once.
+* overlap -- every worker issues its work on its own CUDA stream, so groups
+  of different graphs run on the device at once; extra handles of one graph
+  (`replicas`) give it more workers, so that several of its groups overlap
+  too (a graph whose batches leave the device idle between their short
+  kernels, such as a weighted grid on the general kernels, gains most).
 
 `run_plain` is the one-request-at-a-time form (one mfbc_bc_device call per
 request, in arrival order) that the server is compared against.
@@ -70,8 +73,11 @@ class Server:
     (host-logic tests); sizer(name, cols, nreq, n_b) -> bytes likewise."""
 
     def __init__(self, graphs: dict, *, budget_bytes: int, max_cols: int = 4096, n_b: int = 0,
-                 executor=None, sizer=None, clock=time.perf_counter):
+                 executor=None, sizer=None, clock=time.perf_counter, replicas: dict | None = None):
         self.graphs = graphs
+        # extra handles of the same graphs: one more worker (and CUDA stream)
+        # each, so that several groups of one graph can run at once
+        self.handles = {k: [G] + list((replicas or {}).get(k, [])) for k, G in graphs.items()}
         self.budget = int(budget_bytes)
         self.max_cols = int(max_cols)
         self.n_b = int(n_b)
@@ -85,7 +91,8 @@ class Server:
         self._inflight = 0
         self.log: list[GroupLog] = []
         self.errors: list[BaseException] = []
-        self._threads = [threading.Thread(target=self._worker, args=(k,), daemon=True) for k in graphs]
+        self._threads = [threading.Thread(target=self._worker, args=(k, h), daemon=True)
+                         for k in graphs for h in self.handles[k]]
 
     # ------------------------------------------------------------ public
     def start(self) -> "Server":
@@ -147,7 +154,7 @@ class Server:
             need = self.sizer(key, cols, nreq, nb)
         return nb, need
 
-    def _worker(self, key):
+    def _worker(self, key, handle):
         stream = None
         try:
             import torch
@@ -173,7 +180,8 @@ class Server:
             for r in group:
                 r.start, r.group = t0, gid
             try:
-                results = self.executor(key, group, nb, need, stream)
+                results = self.executor(key, group, nb, need, stream) if self.executor != self._execute_gpu \
+                    else self._execute_gpu(key, group, nb, need, stream, handle)
             except BaseException as e:             # surface to drain()
                 with self._cv:
                     self.errors.append(e)
@@ -193,9 +201,9 @@ class Server:
         G = self.graphs[key]
         return G.workspace_size(cols, 2, n_b=nb) + 8 * nreq * G.n
 
-    def _execute_gpu(self, key, group, nb, ws_bytes, stream):
+    def _execute_gpu(self, key, group, nb, ws_bytes, stream, handle=None):
         import torch
-        G = self.graphs[key]
+        G = handle if handle is not None else self.graphs[key]
         with torch.cuda.stream(stream):
             srcs = [torch.from_numpy(np.ascontiguousarray(r.sources, dtype=np.int32)).to("cuda", non_blocking=True)
                     for r in group]

@@ -140,3 +140,21 @@ def test_make_requests_shapes_and_latency_stats():
     st = latency_stats(reqs, {"x": 10, "y": 10})
     assert st["requests"] == 200 and st["p50_ms"] <= st["p99_ms"] <= 10.0 + 1e-9
     assert align32(1) == 32 and align32(64) == 64 and align32(65) == 96
+
+
+def test_replica_handles_let_groups_of_one_graph_overlap():
+    graphs = _graphs()
+    ref = []
+    rec = Recorder(graphs, ref, delay=0.05)
+    srv = Server(graphs, budget_bytes=1 << 40, max_cols=32, executor=rec, sizer=lambda k, cols, nreq, nb: cols,
+                 replicas={"a": [object(), object()]})
+    ref.append(srv)
+    assert len(srv._threads) == 4                   # three workers for "a", one for "b"
+    reqs = [Request(i, "a", np.arange(20, dtype=np.int32), 0.0) for i in range(6)]
+    srv.start()
+    run_served(srv, reqs, timeout=60)
+    srv.close()
+    spans = [(g.t0, g.t1) for g in srv.log]
+    assert any(a[0] < b[1] and b[0] < a[1] for i, a in enumerate(spans) for b in spans[i + 1:])
+    for r in reqs:
+        np.testing.assert_allclose(r.result, oracle.bc(graphs["a"], r.sources), rtol=1e-12, atol=0)
