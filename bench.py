@@ -138,7 +138,7 @@ def serving_bench(n_requests=120, seed=5):
     host = {"rmat16": gg.rmat(16, 16, seed=1), "rmat18": gg.rmat(18, 16, seed=1), "rmat20": gg.rmat(20, 16, seed=1),
             "er16": gg.erdos_renyi(1 << 16, 16, seed=1), "grid256w": gg.grid2d(256, weights=(1, 16), seed=1)}
     graphs = {k: mfbc.Graph.from_csr(g) for k, g in host.items()}
-    replicas = {k: [mfbc.Graph.from_csr(g) for _ in range(2)] for k, g in host.items()}
+    replicas = {k: [mfbc.Graph.from_csr(g) for _ in range(3)] for k, g in host.items()}
     edges = {k: g.m for k, g in host.items()}
     elig = {k: np.flatnonzero(g.out_degree() > 0).astype(np.int32) for k, g in host.items()}
     sizes = {k: g.n for k, g in host.items()}
@@ -149,7 +149,7 @@ def serving_bench(n_requests=120, seed=5):
         return serve.make_requests(sizes, n_requests, rate, lo=64, hi=4096, seed=seed, eligible=elig)
 
     def served(rs):
-        srv = serve.Server(graphs, budget_bytes=budget, max_cols=4096, replicas=replicas).start()
+        srv = serve.Server(graphs, budget_bytes=budget, max_cols=1024, replicas=replicas).start()
         try:
             serve.run_served(srv, rs, timeout=900)
         finally:
@@ -177,7 +177,7 @@ def serving_bench(n_requests=120, seed=5):
             diff = max(diff, float(np.max(np.abs(a.result[nz] - b.result[nz]) / np.abs(b.result[nz]))))
     for G in list(graphs.values()) + [R for rs_ in replicas.values() for R in rs_]:
         G.close()
-    return {"workload": SERVE_POOL, "workers_per_graph": 3, "requests": n_requests, "budget_bytes": budget,
+    return {"workload": SERVE_POOL, "workers_per_graph": 4, "max_group_columns": 1024, "requests": n_requests, "budget_bytes": budget,
             "saturated": {"plain_gteps": sat_plain["gteps"], "served_gteps": sat_served["gteps"],
                           "plain_span_s": sat_plain["span_s"], "served_span_s": sat_served["span_s"]},
             "offered_rate_per_s": rate, "offered_load_vs_plain_capacity": 0.8,

@@ -64,9 +64,13 @@ typedef enum {
 #define MFBC_WARN_SIGMA_INEXACT 1u  /* some sigma_bar >= 2^53: FP64 counts may be rounded */
 
 /* mfbc_options.path */
-#define MFBC_PATH_AUTO    0    /* level-synchronous kernels for unit weights, general otherwise */
+#define MFBC_PATH_AUTO    0    /* level kernels for unit weights; distance kernels for weights
+                                  <= 64 with out-degrees <= 64; general kernels otherwise
+                                  (or the family mfbc_autotune chose) */
 #define MFBC_PATH_GENERAL 1    /* force the general (any integer weight) kernels */
 #define MFBC_PATH_LEVEL   2    /* require the unit-weight level kernels (INVALID if weighted) */
+#define MFBC_PATH_DIST    3    /* distance-ordered kernels for small integer weights
+                                  (INVALID when the largest weight exceeds 4096) */
 
 typedef struct mfbc_graph mfbc_graph;   /* opaque, device resident */
 
@@ -178,7 +182,7 @@ mfbc_status mfbc_bc_multi_device(const mfbc_graph* g, const int32_t* sources, in
 /* Result of mfbc_autotune. */
 typedef struct {
   int32_t n_b;            /* fastest batch width found */
-  int32_t path;           /* MFBC_PATH_LEVEL or MFBC_PATH_GENERAL */
+  int32_t path;           /* MFBC_PATH_LEVEL, MFBC_PATH_GENERAL or MFBC_PATH_DIST */
   int32_t arcs;           /* general kernels: arcs walked per step (1 or 8); 0 on the level kernels */
   int32_t tried;          /* configurations timed */
   double ms_per_source;   /* wall time of the fastest configuration per source */
@@ -187,14 +191,18 @@ typedef struct {
 /* Autotuner (no counterpart in the paper, whose batch width and processor
  * grid come from its cost model, Sec. 5): times mfbc_bc on the HOST sources
  * int32[nsrc] for each candidate configuration and keeps the fastest on the
- * graph handle.  Candidates: n_b in {128, 256, 512, 1024} on the level kernels,
- * or {128, 256, 512, 1024, 2048, 4096} x {1, 8} arcs per step on the general
- * kernels, each at most nsrc rounded up; widths that do not fit the device
- * are skipped.  Each candidate runs twice (the first call untimed).  Later
- * calls on this handle with opt->n_b == 0 use at most the tuned width, and the
- * general kernels use the tuned arcs per step (without tuning: 8 when the
- * average degree is at least 8, else 1).  opt->path selects the kernel family
- * (AUTO as in mfbc_bc); n_b in opt is ignored.  Results are unaffected. */
+ * graph handle.  Candidates: n_b in {128, 256, 512, 1024} on the level kernels;
+ * n_b in {128, 256, 512, 1024, 2048, 4096} on the general kernels (x {1, 8}
+ * arcs per step) and on the distance kernels; each at most nsrc rounded up;
+ * widths that do not fit the device are skipped.  With opt->path == AUTO a
+ * weighted graph tries both the general and (weights <= 4096) the distance
+ * kernels and later AUTO calls use the faster family; another path restricts
+ * the search to it.  Each candidate runs twice (the first call untimed).
+ * Later calls on this handle with opt->n_b == 0 use at most the tuned width
+ * (no cap when the fastest width was the widest one tried), and the general
+ * kernels use the tuned arcs per step (without tuning: 8 when the average
+ * degree is at least 8, else 1).  n_b in opt is ignored.  Results are
+ * unaffected. */
 mfbc_status mfbc_autotune(mfbc_graph* g, const int32_t* sources, int32_t nsrc, const mfbc_options* opt,
                           mfbc_tuning* out);
 

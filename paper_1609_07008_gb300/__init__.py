@@ -31,7 +31,7 @@ MFBC_ERR_TIMEOUT = 6
 MFBC_DIRECTED = 0
 MFBC_UNDIRECTED = 1
 MFBC_WARN_SIGMA_INEXACT = 1
-PATH_AUTO, PATH_GENERAL, PATH_LEVEL = 0, 1, 2
+PATH_AUTO, PATH_GENERAL, PATH_LEVEL, PATH_DIST = 0, 1, 2, 3
 MFBC_OPT_COUNT_BYTES = 1
 MFBC_OPT_KEEP_ORDER = 2
 INF = np.iinfo(np.int32).max

@@ -18,10 +18,11 @@ struct mfbc_graph {
   uint32_t flags = 0;
   std::mutex mu;
   // autotuner results (mfbc_autotune): batch width per kernel family
-  // (0 level, 1 general; 0 = not tuned) and the general kernels' arcs per
-  // step (0 = by average degree); force_arcs overrides it while tuning
-  int tuned_nb[2] = {0, 0};
+  // (0 = not tuned), the family AUTO picks, and the general kernels' arcs
+  // per step (0 = by average degree); force_arcs overrides it while tuning
+  int tuned_nb[3] = {0, 0, 0};      // level, general, distance kernels
   int tuned_arcs = 0;
+  int tuned_path = 0;               // kernel family for MFBC_PATH_AUTO (0 = by weights)
   int force_arcs = 0;
 };
 
@@ -170,6 +171,8 @@ static size_t plan_bytes(const DevGraph& g, int path, int nb, int32_t nsrc, int 
     // room for the general kernels at n_b = 32 too: the fallback used when
     // a batch is deeper than the level capacity runs in the same scratch
     p->state_bytes = std::max(level_bytes(g, nb, p->Lcap, p->list_cap), general_bytes(g.n, 32));
+  } else if (path == MFBC_PATH_DIST) {
+    p->state_bytes = dist_bytes(g.n, nb, g.wmax + 1);
   } else {
     p->state_bytes = general_bytes(g.n, nb);
   }
@@ -178,14 +181,28 @@ static size_t plan_bytes(const DevGraph& g, int path, int nb, int32_t nsrc, int 
   return p->total;
 }
 
+// Kernel family for MFBC_PATH_AUTO without tuning: level kernels for unit
+// weights; distance-ordered kernels for small weights on graphs without hubs
+// (each distance step waits for its longest adjacency list, so hubs make the
+// steps slow; grids are the case they suit); general kernels otherwise.
+static int default_path(const DevGraph& g) {
+  if (g.unit) return MFBC_PATH_LEVEL;
+  if (g.wmax <= 64 && g.max_deg <= 64 && (uint64_t)g.n * 128u <= 0xffffffffull) return MFBC_PATH_DIST;
+  return MFBC_PATH_GENERAL;
+}
+
 static mfbc_status make_plan(const mfbc_graph* G, int32_t nsrc, int mode, const mfbc_options* opt,
                              bool host_io, Plan* p) {
   const DevGraph& g = G->g;
   int path = opt ? opt->path : MFBC_PATH_AUTO;
-  if (path == MFBC_PATH_AUTO) path = g.unit ? MFBC_PATH_LEVEL : MFBC_PATH_GENERAL;
+  if (path == MFBC_PATH_AUTO) path = G->tuned_path ? G->tuned_path : default_path(g);
   else if (path == MFBC_PATH_LEVEL && !g.unit)
     return fail(MFBC_ERR_INVALID, "MFBC_PATH_LEVEL needs unit weights");
-  else if (path != MFBC_PATH_GENERAL && path != MFBC_PATH_LEVEL)
+  else if (path == MFBC_PATH_DIST && g.wmax + 1 > DIST_MAX_BUCKETS)
+    return fail(MFBC_ERR_INVALID, "MFBC_PATH_DIST needs weights <= 4096");
+  else if (path == MFBC_PATH_DIST && (uint64_t)g.n * 128u > 0xffffffffull)
+    return fail(MFBC_ERR_INVALID, "MFBC_PATH_DIST needs n < 2^25");
+  else if (path != MFBC_PATH_GENERAL && path != MFBC_PATH_LEVEL && path != MFBC_PATH_DIST)
     return fail(MFBC_ERR_INVALID, "unknown path");
   const int maxnb = path == MFBC_PATH_LEVEL ? LEVEL_MAX_NB : 4096;
   // the level kernels move 128 columns (four 32-column words) at a time
@@ -200,7 +217,7 @@ static mfbc_status make_plan(const mfbc_graph* G, int32_t nsrc, int mode, const 
   }
   // auto: widest batch (<= number of sources, <= the tuned width) whose
   // scratch fits the budget
-  const int tuned = G->tuned_nb[path == MFBC_PATH_LEVEL ? 0 : 1];
+  const int tuned = G->tuned_nb[path == MFBC_PATH_LEVEL ? 0 : (path == MFBC_PATH_GENERAL ? 1 : 2)];
   size_t budget;
   if (opt && opt->workspace) budget = opt->workspace_bytes;
   else {
@@ -436,8 +453,10 @@ mfbc_status run(mfbc_graph* G, const int32_t* d_src, int32_t nsrc, int mode, dou
   Carver c(R.ws, R.ws_bytes);
   GeneralState gs;
   LevelState ls;
+  DistState ds;
   Counters* ctr;
   if (P.path == MFBC_PATH_LEVEL) { level_carve(c, g, nb, P.Lcap, P.list_cap, ls); ctr = ls.ctr; }
+  else if (P.path == MFBC_PATH_DIST) { dist_carve(c, g.n, nb, g.wmax + 1, ds); ctr = ds.ctr; }
   else { general_carve(c, g.n, nb, gs); ctr = gs.ctr; }
   int32_t* stage_d = nullptr;
   double* stage_s = nullptr;
@@ -512,6 +531,20 @@ mfbc_status run(mfbc_graph* G, const int32_t* d_src, int32_t nsrc, int mode, dou
         level_reset(rc, ls, levels);
       } else if (exceeded) {
         fallback = true;
+      }
+    }
+    if (P.path == MFBC_PATH_DIST) {
+      s = dist_batch(rc, ds, bsrc, na, want_lambda ? d_lambda : nullptr, &fi, &bi);
+      if (s == MFBC_OK && mode == 1) {
+        int32_t* dd = out_on_host ? stage_d : dist_out + (size_t)b0 * g.n;
+        double* dsg = sigma_out ? (out_on_host ? stage_s : sigma_out + (size_t)b0 * g.n) : nullptr;
+        dist_output(rc, ds, na, dd, dsg);
+      }
+      if (s == MFBC_OK) {
+        MFBC_CUDA_TRY(cudaMemcpyAsync(G->h_ctr, &ds.ctr->flags, sizeof(uint32_t), cudaMemcpyDeviceToHost, R.st),
+                      &R.err);
+        MFBC_CUDA_TRY(cudaStreamSynchronize(R.st), &R.err);
+        if (G->h_ctr[0] & 2u) warn |= MFBC_WARN_SIGMA_INEXACT;
       }
     }
     if (P.path == MFBC_PATH_GENERAL || fallback) {
@@ -696,52 +729,74 @@ extern "C" mfbc_status mfbc_autotune(mfbc_graph* G, const int32_t* sources, int3
                                      mfbc_tuning* out) {
   if (!G || !out) return fail(MFBC_ERR_INVALID, "graph and out must not be NULL");
   if (nsrc < 1 || !sources) return fail(MFBC_ERR_INVALID, "need at least one source");
-  int path = opt ? opt->path : MFBC_PATH_AUTO;
-  if (path == MFBC_PATH_AUTO) path = G->g.unit ? MFBC_PATH_LEVEL : MFBC_PATH_GENERAL;
-  if (path == MFBC_PATH_LEVEL && !G->g.unit) return fail(MFBC_ERR_INVALID, "MFBC_PATH_LEVEL needs unit weights");
-  if (path != MFBC_PATH_LEVEL && path != MFBC_PATH_GENERAL) return fail(MFBC_ERR_INVALID, "unknown path");
-  const bool level = path == MFBC_PATH_LEVEL;
-  std::vector<int> widths = level ? std::vector<int>{128, 256, 512, 1024}
-                                  : std::vector<int>{128, 256, 512, 1024, 2048, 4096};
-  const int gran = level ? 128 : 32;
-  const int cols = (nsrc + gran - 1) / gran * gran;
-  while (widths.size() > 1 && widths.back() > cols) widths.pop_back();
-  const std::vector<int> arcs = level ? std::vector<int>{0} : std::vector<int>{1, 8};
+  const int req_path = opt ? opt->path : MFBC_PATH_AUTO;
+  const bool dist_ok = G->g.wmax + 1 <= DIST_MAX_BUCKETS;
+  std::vector<int> paths;
+  if (req_path == MFBC_PATH_AUTO) {
+    if (G->g.unit) paths = {MFBC_PATH_LEVEL};
+    else paths = dist_ok ? std::vector<int>{MFBC_PATH_GENERAL, MFBC_PATH_DIST} : std::vector<int>{MFBC_PATH_GENERAL};
+  } else if (req_path == MFBC_PATH_LEVEL) {
+    if (!G->g.unit) return fail(MFBC_ERR_INVALID, "MFBC_PATH_LEVEL needs unit weights");
+    paths = {MFBC_PATH_LEVEL};
+  } else if (req_path == MFBC_PATH_GENERAL) {
+    paths = {MFBC_PATH_GENERAL};
+  } else if (req_path == MFBC_PATH_DIST) {
+    if (!dist_ok) return fail(MFBC_ERR_INVALID, "MFBC_PATH_DIST needs weights <= 4096");
+    paths = {MFBC_PATH_DIST};
+  } else {
+    return fail(MFBC_ERR_INVALID, "unknown path");
+  }
   std::vector<double> lam((size_t)std::max(G->g.n, 1));
   mfbc_options o = opt ? *opt : mfbc_options{};
-  o.path = path;
   o.profile = nullptr;
   o.warn_out = nullptr;
   double best = 0.0;
-  int best_nb = 0, best_arcs = 0, tried = 0;
-  for (int nb : widths)
-    for (int a : arcs) {
-      o.n_b = nb;
-      {
-        std::lock_guard<std::mutex> lock(G->mu);
-        G->force_arcs = a;
+  int best_nb = 0, best_arcs = 0, best_path = 0, tried = 0;
+  bool best_widest = false;
+  for (int path : paths) {
+    const bool level = path == MFBC_PATH_LEVEL;
+    std::vector<int> widths = level ? std::vector<int>{128, 256, 512, 1024}
+                                    : std::vector<int>{128, 256, 512, 1024, 2048, 4096};
+    const int gran = level ? 128 : 32;
+    const int cols = (nsrc + gran - 1) / gran * gran;
+    while (widths.size() > 1 && widths.back() > cols) widths.pop_back();
+    const std::vector<int> arcs = path == MFBC_PATH_GENERAL ? std::vector<int>{1, 8} : std::vector<int>{0};
+    o.path = path;
+    for (int nb : widths)
+      for (int a : arcs) {
+        o.n_b = nb;
+        {
+          std::lock_guard<std::mutex> lock(G->mu);
+          G->force_arcs = a;
+        }
+        // one untimed call (scratch growth, first touch), then the timed one
+        mfbc_status s = entry(G, sources, nsrc, 0, lam.data(), nullptr, nullptr, &o, true);
+        const auto t0 = std::chrono::steady_clock::now();
+        if (s == MFBC_OK) s = entry(G, sources, nsrc, 0, lam.data(), nullptr, nullptr, &o, true);
+        const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+        if (s == MFBC_ERR_OOM) continue;           // too wide for this device: not a candidate
+        if (s != MFBC_OK) {
+          std::lock_guard<std::mutex> lock(G->mu);
+          G->force_arcs = 0;
+          return s;
+        }
+        tried++;
+        if (best_nb == 0 || ms < best) {
+          best = ms; best_nb = nb; best_arcs = a; best_path = path;
+          best_widest = nb == widths.back();
+        }
       }
-      // one untimed call (scratch growth, first-touch), then the timed one
-      mfbc_status s = entry(G, sources, nsrc, 0, lam.data(), nullptr, nullptr, &o, true);
-      const auto t0 = std::chrono::steady_clock::now();
-      if (s == MFBC_OK) s = entry(G, sources, nsrc, 0, lam.data(), nullptr, nullptr, &o, true);
-      const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
-      if (s == MFBC_ERR_OOM) continue;             // too wide for this device: not a candidate
-      if (s != MFBC_OK) {
-        std::lock_guard<std::mutex> lock(G->mu);
-        G->force_arcs = 0;
-        return s;
-      }
-      tried++;
-      if (best_nb == 0 || ms < best) { best = ms; best_nb = nb; best_arcs = a; }
-    }
+  }
   std::lock_guard<std::mutex> lock(G->mu);
   G->force_arcs = 0;
   if (!best_nb) return fail(MFBC_ERR_OOM, "no candidate batch width fits the device");
-  G->tuned_nb[level ? 0 : 1] = best_nb;
-  if (!level) G->tuned_arcs = best_arcs;
+  // a width is kept as a cap only when a wider one was tried and lost
+  G->tuned_nb[best_path == MFBC_PATH_LEVEL ? 0 : (best_path == MFBC_PATH_GENERAL ? 1 : 2)] =
+      best_widest ? 0 : best_nb;
+  if (best_path == MFBC_PATH_GENERAL) G->tuned_arcs = best_arcs;
+  if (req_path == MFBC_PATH_AUTO) G->tuned_path = best_path;
   out->n_b = best_nb;
-  out->path = path;
+  out->path = best_path;
   out->arcs = best_arcs;
   out->tried = tried;
   out->ms_per_source = best / nsrc;

@@ -184,8 +184,10 @@ mfbc_status graph_build(int32_t n, int64_t nnz, const int64_t* h_rowptr, const i
     // (degree descending, then id), isolated vertices excluded
     std::vector<int32_t> ids;
     ids.reserve((size_t)n);
-    for (int32_t v = 0; v < n; v++)
+    for (int32_t v = 0; v < n; v++) {
       if (rp[v + 1] > rp[v]) ids.push_back(v);
+      g->max_deg = std::max<int64_t>(g->max_deg, rp[v + 1] - rp[v]);
+    }
     const size_t k = std::min<size_t>(ids.size(), (size_t)ORDER_LANDMARKS);
     std::partial_sort(ids.begin(), ids.begin() + k, ids.end(), [&](int32_t a, int32_t b) {
       const int64_t da = rp[a + 1] - rp[a], db = rp[b + 1] - rp[b];

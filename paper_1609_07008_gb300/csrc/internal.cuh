@@ -40,6 +40,7 @@ struct DevGraph {
   bool unit = true;                // every arc weighs 1 (w == NULL or all ones)
   int32_t wmax = 1;
   std::vector<int32_t> landmarks;   // highest out-degree vertices, descending (source ordering)
+  int64_t max_deg = 0;             // largest out-degree
   int64_t* rowptr = nullptr;       // CSR of A (out-arcs)
   int32_t* col = nullptr;
   int32_t* w = nullptr;            // nullptr when unit
@@ -62,7 +63,7 @@ struct KStat {
 enum KId {
   K_FILL = 0, K_SEED, K_RELAX_MIN, K_RELAX_TIE, K_ACCUM, K_COUNTERS, K_PROPAGATE, K_FINAL,
   K_LAMBDA, K_CLEAR, K_LVL_FWD, K_LVL_VISIT, K_LVL_BWD, K_LVL_HUB, K_LVL_RESET, K_OUTPUT,
-  K_LVL_FWD_G, K_LVL_BWD_G, K_LVL_SPLIT, K_NUM
+  K_LVL_FWD_G, K_LVL_BWD_G, K_LVL_SPLIT, K_DP_FWD, K_DP_BWD, K_NUM
 };
 
 // Device-side counters of algorithmic bytes, one slot per kernel id.
@@ -153,6 +154,26 @@ struct LevelState {
 size_t level_bytes(const DevGraph& g, int nb, int Lcap, int64_t list_cap);
 void level_carve(Carver& c, const DevGraph& g, int nb, int Lcap, int64_t list_cap, LevelState& s);
 
+// Distance path for small integer weights: Algorithms 1 and 2 stepped in
+// order of distance value.  See dist.cu.
+constexpr int DIST_MAX_BUCKETS = 4097;   // w_max + 1 at most
+struct DistState {
+  int nb = 0, W = 0, B = 0, BW = 0;
+  int32_t* dist;      // tau  [n][nb]
+  double* sig;        // sigma_bar [n][nb]
+  double* val;        // MFBr value zeta + 1/sigma_bar [n][nb]
+  uint32_t* mlist;    // (vertex * W + word) items settled per step, concatenated
+  size_t mcap;
+  int32_t* blist;     // [B][n] ring of bucket vertex lists
+  uint32_t* bflag;    // [n][BW] bucket membership bits
+  uint32_t* bcount;   // [B + 1] bucket counts, then the settled-list count
+  int32_t* src;       // [nb]
+  int32_t* word_req;  // [W]
+  Counters* ctr;
+};
+size_t dist_bytes(int32_t n, int nb, int B);
+void dist_carve(Carver& c, int32_t n, int nb, int B, DistState& s);
+
 // --------------------------------------------------------------- drivers
 struct RunCtx {
   const DevGraph* g;
@@ -188,6 +209,11 @@ mfbc_status level_batch(RunCtx& rc, LevelState& s, const int32_t* d_src_batch, i
                         int64_t* fwd_iters, int64_t* bwd_iters);
 mfbc_status level_output(RunCtx& rc, LevelState& s, int levels, int nactive, int32_t* dist_out,
                          double* sigma_out);
+
+// One batch of the distance path (lambda != nullptr: full MFBC batch).
+mfbc_status dist_batch(RunCtx& rc, DistState& s, const int32_t* d_src_batch, int nactive, double* lambda,
+                       int64_t* fwd_iters, int64_t* bwd_iters);
+mfbc_status dist_output(RunCtx& rc, DistState& s, int nactive, int32_t* dist_out, double* sigma_out);
 void level_reset(RunCtx& rc, LevelState& s, int levels);
 
 // Graph construction helpers (graph.cu).

@@ -21,7 +21,7 @@ import paper_1609_07008_gb300 as mfbc
 
 pytestmark = pytest.mark.gpu
 RTOL = 1e-9
-PATHS = [mfbc.PATH_LEVEL, mfbc.PATH_GENERAL]
+PATHS = [mfbc.PATH_LEVEL, mfbc.PATH_GENERAL, mfbc.PATH_DIST]
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -42,7 +42,7 @@ def assert_lambda_close(got, want, rtol=RTOL):
 
 
 def paths_for(g):
-    return PATHS if g.w is None else [mfbc.PATH_GENERAL]
+    return PATHS if g.w is None else [mfbc.PATH_GENERAL, mfbc.PATH_DIST]
 
 
 def check_graph(g, srcs, n_b=0, sssp=True, paths=None):
@@ -310,7 +310,8 @@ def test_profile_reports_kernels():
         lam, prof = G.bc(srcs, n_b=64, path=p, profile=True, count_bytes=True)
         assert prof["batches"] == 1 and prof["fwd_iters"] > 0 and prof["bwd_iters"] > 0
         ks = prof["kernels"]
-        main = "level_mfbf_gather" if p == mfbc.PATH_LEVEL else "mfbf_relax_min"
+        main = {mfbc.PATH_LEVEL: "level_mfbf_gather", mfbc.PATH_GENERAL: "mfbf_relax_min",
+                mfbc.PATH_DIST: "dist_mfbf_step"}[p]
         assert ks[main]["launches"] > 0 and ks[main]["ms"] > 0 and ks[main]["bytes"] > 0
     G.close()
 
@@ -397,11 +398,16 @@ def test_autotune_picks_a_candidate_and_results_are_unchanged(weighted):
     srcs = gg.sample_sources(g, 600, seed=1)
     G = mfbc.Graph.from_csr(g)
     t = G.autotune(srcs)
-    assert t["path"] == (mfbc.PATH_GENERAL if weighted else mfbc.PATH_LEVEL)
-    assert t["n_b"] in ({128, 256, 512} if not weighted else {128, 256, 512}) and t["tried"] >= 1
-    assert t["ms_per_source"] > 0
-    assert t["arcs"] == 0 if not weighted else t["arcs"] in (1, 8)
+    if weighted:
+        # general kernels (3 widths x 2 arc steps) and distance kernels (3 widths)
+        assert t["path"] in (mfbc.PATH_GENERAL, mfbc.PATH_DIST) and t["tried"] == 9
+        assert t["arcs"] in ((1, 8) if t["path"] == mfbc.PATH_GENERAL else (0,))
+    else:
+        assert t["path"] == mfbc.PATH_LEVEL and t["tried"] == 3 and t["arcs"] == 0
+    assert t["n_b"] in {128, 256, 512} and t["ms_per_source"] > 0
     lam, prof = G.bc(srcs, profile=True)
-    assert prof["n_b"] <= t["n_b"]
+    assert prof["path"] == t["path"]
+    if t["n_b"] < 512:                      # a wider width was tried and lost: it caps later calls
+        assert prof["n_b"] <= t["n_b"]
     assert_lambda_close(lam, oracle.bc(g, srcs))
     G.close()

@@ -33,6 +33,7 @@ CASES = [
     ("level", False, mfbc.PATH_LEVEL),
     ("general-unit", False, mfbc.PATH_GENERAL),
     ("general-weighted", True, mfbc.PATH_GENERAL),
+    ("dist-weighted", True, mfbc.PATH_DIST),
 ]
 
 
