@@ -65,7 +65,7 @@ typedef enum {
 
 /* mfbc_options.path */
 #define MFBC_PATH_AUTO    0    /* level kernels for unit weights; distance kernels for weights
-                                  <= 64 with out-degrees <= 64; general kernels otherwise
+                                  <= 64 with in- and out-degrees <= 64; general kernels otherwise
                                   (or the family mfbc_autotune chose) */
 #define MFBC_PATH_GENERAL 1    /* force the general (any integer weight) kernels */
 #define MFBC_PATH_LEVEL   2    /* require the unit-weight level kernels (INVALID if weighted) */

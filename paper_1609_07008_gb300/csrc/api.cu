@@ -187,7 +187,8 @@ static size_t plan_bytes(const DevGraph& g, int path, int nb, int32_t nsrc, int 
 // steps slow; grids are the case they suit); general kernels otherwise.
 static int default_path(const DevGraph& g) {
   if (g.unit) return MFBC_PATH_LEVEL;
-  if (g.wmax <= 64 && g.max_deg <= 64 && (uint64_t)g.n * 128u <= 0xffffffffull) return MFBC_PATH_DIST;
+  if (g.wmax <= 64 && std::max(g.max_deg, g.max_in_deg) <= 64 && (uint64_t)g.n * 128u <= 0xffffffffull)
+    return MFBC_PATH_DIST;
   return MFBC_PATH_GENERAL;
 }
 

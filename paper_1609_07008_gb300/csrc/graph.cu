@@ -200,7 +200,10 @@ mfbc_status graph_build(int32_t n, int64_t nnz, const int64_t* h_rowptr, const i
     // source vertex, so the transposed graph is deterministic.
     std::vector<int64_t> rpt((size_t)n + 1, 0);
     for (int64_t k = 0; k < nnz; k++) rpt[(size_t)h_col[k] + 1]++;
-    for (int32_t v = 0; v < n; v++) rpt[v + 1] += rpt[v];
+    for (int32_t v = 0; v < n; v++) {
+      g->max_in_deg = std::max<int64_t>(g->max_in_deg, rpt[v + 1]);
+      rpt[v + 1] += rpt[v];
+    }
     std::vector<int32_t> ct((size_t)nnz), wtv(g->w ? (size_t)nnz : 0);
     std::vector<int64_t> pos(rpt.begin(), rpt.end() - 1);
     for (int32_t v = 0; v < n; v++)
@@ -219,6 +222,7 @@ mfbc_status graph_build(int32_t n, int64_t nnz, const int64_t* h_rowptr, const i
     TRY(build_items(g, rpt, &g->items_in, false, st, err));
     TRY(build_items(g, rp, &g->items_out, true, st, err));
   } else {
+    g->max_in_deg = g->max_deg;
     g->rowptr_t = g->rowptr;
     g->col_t = g->col;
     g->w_t = g->w;

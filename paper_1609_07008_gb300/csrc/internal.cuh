@@ -41,6 +41,7 @@ struct DevGraph {
   int32_t wmax = 1;
   std::vector<int32_t> landmarks;   // highest out-degree vertices, descending (source ordering)
   int64_t max_deg = 0;             // largest out-degree
+  int64_t max_in_deg = 0;          // largest in-degree
   int64_t* rowptr = nullptr;       // CSR of A (out-arcs)
   int32_t* col = nullptr;
   int32_t* w = nullptr;            // nullptr when unit
