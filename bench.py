@@ -68,7 +68,8 @@ def make_workload(name, rank=0):
 
 
 # DRAM traffic of the dominant kernel: dram__bytes_read.sum + dram__bytes_write.sum
-# per launch from one ncu capture (profiles/level_kernels_rmat22.md), expressed per
+# per launch from one ncu capture of the timed gathers on the first 2048 sources of
+# the same workload (two batches of the same width), expressed per
 # algorithmic byte so that it scales with the launches this run makes.  Each entry
 # records the SHA-1 of the kernel source it was taken on; once that source changes
 # the figure is reported as null.
