@@ -93,7 +93,7 @@ typedef struct {
   uint64_t fwd_iters;          /* MFBF products over all batches */
   uint64_t bwd_iters;          /* MFBr products over all batches */
   int32_t n_b;                 /* batch width used */
-  int32_t path;                /* MFBC_PATH_GENERAL or MFBC_PATH_LEVEL */
+  int32_t path;                /* MFBC_PATH_GENERAL, MFBC_PATH_LEVEL or MFBC_PATH_DIST */
   uint64_t stat[4];            /* with MFBC_OPT_COUNT_BYTES, level kernels: (neighbour, word)
                                   pairs gathered by MFBF / MFBr, values gathered by MFBF / MFBr */
 } mfbc_profile;

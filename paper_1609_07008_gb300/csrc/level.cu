@@ -215,11 +215,15 @@ constexpr int NO_REQ = 0x7fffffff;           // key of a lane without a column
 __global__ void k_clear_flag_bits(uint32_t* flags, uint32_t bits) { atomicAnd(flags, ~bits); }
 
 // sv rows of multi-item vertices start at zero (MFBF adds into them).
+// One warp per row, 32 bytes per lane and store (n_b is a multiple of 128).
 __global__ void k_lvl_zero_hubs(const int32_t* __restrict__ hubs, int32_t nhub, int nb, double* sv) {
-  const uint64_t total = (uint64_t)nhub * nb;
-  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
-       i += (uint64_t)gridDim.x * blockDim.x)
-    sv[(size_t)hubs[i / nb] * nb + (i % nb)] = 0.0;
+  const unsigned lane = lane_id();
+  const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  for (uint64_t h = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; h < (uint64_t)nhub; h += nw) {
+    double* row = sv + (size_t)hubs[h] * nb;
+    for (int c = 4 * (int)lane; c < nb; c += 128)
+      asm volatile("st.global.v4.u64 [%0], {%1,%1,%1,%1};" ::"l"(row + c), "l"(0ull) : "memory");
+  }
 }
 
 // Level 0: F_0(s_j) holds column j, sigma_bar(s_j, s_j) = 1.
@@ -393,7 +397,9 @@ __device__ __forceinline__ uint32_t quads_of_words(uint32_t words, int Q) {
 }
 
 // Work items are handed out in groups of 32 (hub items cost far more than
-// leaf items); the group counter is zeroed before each launch.
+// leaf items); the group counter is zeroed before each launch.  (Handing out
+// 4 to 16 groups per atomic was measured slower: balance matters more than
+// the counter.)
 #define FOR_ITEM_GROUPS(ib, ie, counter)                                                    \
   for (;;) {                                                                              \
     uint32_t grp_ = 0;                                                                    \
