@@ -18,10 +18,11 @@
 // whereas the Bellman-Ford products of the general kernels may improve a
 // pair several times (weighted grids: about 540 products per batch).
 //
-// Vertices waiting for a distance value are kept in a ring of w_max + 1
-// buckets (a vertex list and one flag bit per vertex each).  A step runs one
-// warp per (vertex, 32-column word); the items that settle pairs are appended
-// to one list with per-step offsets, which the backward pass replays in
+// (Vertex, 32-column word) items waiting for a distance value are kept in a
+// ring of w_max + 1 buckets (an item list and one flag bit per item each), so
+// a step visits only the words that received a candidate for its distance.
+// A step runs one warp per item; the items that settle pairs are appended to
+// one list with per-step offsets, which the backward pass replays in
 // reverse.
 #include <algorithm>
 
@@ -47,8 +48,9 @@ void dist_carve(Carver& c, int32_t n, int nb, int B, DistState& s) {
   s.val = c.take<double>(cells);
   s.mcap = cells + 1;                        // a (vertex, word) settles at most once per column
   s.mlist = c.take<uint32_t>(s.mcap);
-  s.blist = c.take<int32_t>((size_t)B * n);
-  s.bflag = c.take<uint32_t>((size_t)n * s.BW);
+  s.bcap = (size_t)n * s.W;                  // (vertex, word) items a bucket can hold
+  s.blist = c.take<uint32_t>((size_t)B * s.bcap);
+  s.bflag = c.take<uint32_t>(s.bcap * s.BW);
   s.bcount = c.take<uint32_t>((size_t)B + 1); // B bucket counts, then the settled-list count
   s.src = c.take<int32_t>((size_t)nb);
   s.word_req = c.take<int32_t>((size_t)s.W);
@@ -56,40 +58,42 @@ void dist_carve(Carver& c, int32_t n, int nb, int B, DistState& s) {
 }
 
 // Level 0: (s_j, s_j) at distance 0 with sigma_bar 1, in bucket 0.
-__global__ void k_dp_seed(const int32_t* __restrict__ src, int nb, int BW, int32_t n, int32_t* dist, double* sig,
-                          uint32_t* bflag, int32_t* blist, uint32_t* bcount) {
+__global__ void k_dp_seed(const int32_t* __restrict__ src, int nb, int W, int BW, int32_t* dist, double* sig,
+                          uint32_t* bflag, uint32_t* blist, uint32_t* bcount) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= nb) return;
   const int32_t s = src[j];
   if (s < 0) return;
   dist[(size_t)s * nb + j] = 0;
   sig[(size_t)s * nb + j] = 1.0;
-  if (!(atomicOr(&bflag[(size_t)s * BW], 1u) & 1u)) blist[atomicAdd(&bcount[0], 1u)] = s;
+  const uint32_t item = (uint32_t)s * (uint32_t)W + (uint32_t)(j >> 5);
+  if (!(atomicOr(&bflag[(size_t)item * BW], 1u) & 1u)) blist[atomicAdd(&bcount[0], 1u)] = item;
 }
 
-// Forward step at distance d over the vertices listed in bucket `slot`: one
-// warp per (vertex, 32-column word), lane = column.  The (vertex, word)
-// items that hold pairs at distance d are appended to the settled list, which
-// the backward pass replays.
+// Forward step at distance d over the (vertex, word) items listed in bucket
+// `slot`: one warp per item, lane = column.  The items that hold pairs at
+// distance d are appended to the settled list, which the backward pass
+// replays.
 __global__ void __launch_bounds__(256) k_dp_fwd(
-    const int32_t* __restrict__ list, uint32_t count, int32_t d, int slot, int B, int BW, int W, int nb, int32_t n,
+    const uint32_t* __restrict__ list, uint32_t count, int32_t d, int slot, int B, int BW, int W, int nb, size_t bcap,
     const int64_t* __restrict__ rp, const int32_t* __restrict__ col, const int32_t* __restrict__ wt,
     const int64_t* __restrict__ rpt, const int32_t* __restrict__ colt, const int32_t* __restrict__ wtt,
-    int32_t* dist, double* sig, uint32_t* bflag, int32_t* blist, uint32_t* bcount, uint32_t* mlist,
+    int32_t* dist, double* sig, uint32_t* bflag, uint32_t* blist, uint32_t* bcount, uint32_t* mlist,
     unsigned long long* bytes) {
   const unsigned lane = lane_id();
   const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
   unsigned long long nbytes = 0;               // algorithmic bytes of this lane (counting runs only)
-  for (uint64_t gw = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; gw < (uint64_t)count * W; gw += nw) {
-    const int32_t v = list[gw / W];
-    const int word = (int)(gw % W);
-    if (word == 0 && lane == 0) atomicAnd(&bflag[(size_t)v * BW + slot / 32], ~(1u << (slot & 31)));
+  for (uint64_t gw = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; gw < count; gw += nw) {
+    const uint32_t item = list[gw];
+    const int32_t v = (int32_t)(item / (uint32_t)W);
+    const int word = (int)(item % (uint32_t)W);
+    if (lane == 0) atomicAnd(&bflag[(size_t)item * BW + slot / 32], ~(1u << (slot & 31)));
     const int j = word * 32 + (int)lane;
     const size_t vj = (size_t)v * nb + j;
     const bool isM = dist[vj] == d;
     if (bytes) nbytes += 4;
     if (!__ballot_sync(0xffffffffu, isM)) continue;
-    if (lane == 0) mlist[atomicAdd(&bcount[B], 1u)] = (uint32_t)v * (uint32_t)W + (uint32_t)word;
+    if (lane == 0) mlist[atomicAdd(&bcount[B], 1u)] = item;
     if (d > 0) {
       // sigma_bar from the final in-neighbours one arc short of d
       double acc = 0.0;
@@ -130,8 +134,9 @@ __global__ void __launch_bounds__(256) k_dp_fwd(
         if (__ballot_sync(0xffffffffu, improved) && lane == 0) {
           const int s2 = cand % B;
           const uint32_t bit = 1u << (s2 & 31);
-          if (!(atomicOr(&bflag[(size_t)x * BW + s2 / 32], bit) & bit))
-            blist[(size_t)s2 * n + atomicAdd(&bcount[s2], 1u)] = x;
+          const uint32_t xi = (uint32_t)x * (uint32_t)W + (uint32_t)word;
+          if (!(atomicOr(&bflag[(size_t)xi * BW + s2 / 32], bit) & bit))
+            blist[(size_t)s2 * bcap + atomicAdd(&bcount[s2], 1u)] = xi;
         }
       }
     }
@@ -221,11 +226,11 @@ mfbc_status dist_batch(RunCtx& rc, DistState& s, const int32_t* d_src_batch, int
   PROF(K_FILL, {
     fill_i32(s.dist, INF, cells, st);
     cudaMemsetAsync(s.sig, 0, sizeof(double) * cells, st);
-    cudaMemsetAsync(s.bflag, 0, sizeof(uint32_t) * (size_t)n * s.BW, st);
+    cudaMemsetAsync(s.bflag, 0, sizeof(uint32_t) * s.bcap * s.BW, st);
     cudaMemsetAsync(s.bcount, 0, sizeof(uint32_t) * ((size_t)B + 1), st);
   });
-  rc.prof->k[K_FILL].bytes += 12.0 * cells + 4.0 * n * s.BW;
-  PROF(K_SEED, (k_dp_seed<<<(nb + 127) / 128, 128, 0, st>>>(s.src, nb, s.BW, n, s.dist, s.sig, s.bflag, s.blist,
+  rc.prof->k[K_FILL].bytes += 12.0 * cells + 4.0 * s.bcap * s.BW;
+  PROF(K_SEED, (k_dp_seed<<<(nb + 127) / 128, 128, 0, st>>>(s.src, nb, W, s.BW, s.dist, s.sig, s.bflag, s.blist,
                                                           s.bcount)));
 
   // ---- MFBF in increasing distance order
@@ -253,8 +258,8 @@ mfbc_status dist_batch(RunCtx& rc, DistState& s, const int32_t* d_src_batch, int
         return MFBC_ERR_NO_CONVERGENCE;
       }
       const uint32_t before = cnt[(size_t)B];
-      PROF(K_DP_FWD, (k_dp_fwd<<<dp_grid((uint64_t)c * W), 256, 0, st>>>(
-                         s.blist + (size_t)slot * n, c, d, slot, B, s.BW, W, nb, n, g.rowptr, g.col, g.w,
+      PROF(K_DP_FWD, (k_dp_fwd<<<dp_grid(c), 256, 0, st>>>(
+                         s.blist + (size_t)slot * s.bcap, c, d, slot, B, s.BW, W, nb, s.bcap, g.rowptr, g.col, g.w,
                          g.rowptr_t, g.col_t, g.w_t, s.dist, s.sig, s.bflag, s.blist, s.bcount, s.mlist,
                          B_ ? B_ + K_DP_FWD : nullptr)));
       MFBC_CUDA_TRY(cudaMemsetAsync(&s.bcount[slot], 0, sizeof(uint32_t), st), rc.err);

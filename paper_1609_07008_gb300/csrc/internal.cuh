@@ -165,8 +165,9 @@ struct DistState {
   double* val;        // MFBr value zeta + 1/sigma_bar [n][nb]
   uint32_t* mlist;    // (vertex * W + word) items settled per step, concatenated
   size_t mcap;
-  int32_t* blist;     // [B][n] ring of bucket vertex lists
-  uint32_t* bflag;    // [n][BW] bucket membership bits
+  uint32_t* blist;    // [B][bcap] ring of bucket lists of (vertex * W + word) items
+  uint32_t* bflag;    // [n * W][BW] bucket membership bits per item
+  size_t bcap;        // n * W
   uint32_t* bcount;   // [B + 1] bucket counts, then the settled-list count
   int32_t* src;       // [nb]
   int32_t* word_req;  // [W]
