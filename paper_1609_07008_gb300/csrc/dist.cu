@@ -52,6 +52,7 @@ void dist_carve(Carver& c, int32_t n, int nb, int B, DistState& s) {
   s.blist = c.take<uint32_t>((size_t)B * s.bcap);
   s.bflag = c.take<uint32_t>(s.bcap * s.BW);
   s.bcount = c.take<uint32_t>((size_t)B + 1); // B bucket counts, then the settled-list count
+  s.marks = c.take<uint32_t>(64);               // settled-list offsets of the queued steps
   s.src = c.take<int32_t>((size_t)nb);
   s.word_req = c.take<int32_t>((size_t)s.W);
   s.ctr = c.take<Counters>(1);
@@ -75,7 +76,8 @@ __global__ void k_dp_seed(const int32_t* __restrict__ src, int nb, int W, int BW
 // distance d are appended to the settled list, which the backward pass
 // replays.
 __global__ void __launch_bounds__(256) k_dp_fwd(
-    const uint32_t* __restrict__ list, uint32_t count, int32_t d, int slot, int B, int BW, int W, int nb, size_t bcap,
+    const uint32_t* __restrict__ list, const uint32_t* count_p, int32_t d, int slot, int B, int BW, int W, int nb,
+    size_t bcap,
     const int64_t* __restrict__ rp, const int32_t* __restrict__ col, const int32_t* __restrict__ wt,
     const int64_t* __restrict__ rpt, const int32_t* __restrict__ colt, const int32_t* __restrict__ wtt,
     int32_t* dist, double* sig, uint32_t* bflag, uint32_t* blist, uint32_t* bcount, uint32_t* mlist,
@@ -83,6 +85,7 @@ __global__ void __launch_bounds__(256) k_dp_fwd(
   const unsigned lane = lane_id();
   const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
   unsigned long long nbytes = 0;               // algorithmic bytes of this lane (counting runs only)
+  const uint32_t count = *count_p;             // items queued for distance d by the earlier steps
   for (uint64_t gw = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; gw < count; gw += nw) {
     const uint32_t item = list[gw];
     const int32_t v = (int32_t)(item / (uint32_t)W);
@@ -233,49 +236,43 @@ mfbc_status dist_batch(RunCtx& rc, DistState& s, const int32_t* d_src_batch, int
   PROF(K_SEED, (k_dp_seed<<<(nb + 127) / 128, 128, 0, st>>>(s.src, nb, W, s.BW, s.dist, s.sig, s.bflag, s.blist,
                                                           s.bcount)));
 
-  // ---- MFBF in increasing distance order
-  std::vector<uint32_t> cnt((size_t)B + 1);
-  std::vector<int32_t> step_d;
-  std::vector<uint32_t> step_off, step_cnt;
-  auto read_counts = [&]() -> mfbc_status {
+  // ---- MFBF in increasing distance order.  Steps are queued without waiting:
+  // each kernel reads its bucket's count on the device, and the host looks at
+  // the counts once every DP_CHECK distance values (done when every bucket is
+  // empty), collecting the settled list's offset at the start of each step.
+  constexpr int DP_CHECK = 32;
+  std::vector<uint32_t> cnt((size_t)B + 1), mk((size_t)DP_CHECK), marks;
+  const int64_t max_steps = (int64_t)n * (int64_t)std::max(1, g.wmax) + DP_CHECK + 1;
+  int64_t steps = 0;
+  int32_t d = 0;
+  while (true) {
+    for (int k = 0; k < DP_CHECK; k++, d++) {
+      const int slot = d % B;
+      MFBC_CUDA_TRY(cudaMemcpyAsync(&s.marks[k], &s.bcount[B], sizeof(uint32_t), cudaMemcpyDeviceToDevice, st),
+                    rc.err);
+      PROF(K_DP_FWD, (k_dp_fwd<<<152 * 16, 256, 0, st>>>(
+                         s.blist + (size_t)slot * s.bcap, &s.bcount[slot], d, slot, B, s.BW, W, nb, s.bcap,
+                         g.rowptr, g.col, g.w, g.rowptr_t, g.col_t, g.w_t, s.dist, s.sig, s.bflag, s.blist,
+                         s.bcount, s.mlist, B_ ? B_ + K_DP_FWD : nullptr)));
+      MFBC_CUDA_TRY(cudaMemsetAsync(&s.bcount[slot], 0, sizeof(uint32_t), st), rc.err);
+    }
+    steps += DP_CHECK;
+    MFBC_CUDA_TRY(cudaMemcpyAsync(mk.data(), s.marks, sizeof(uint32_t) * DP_CHECK, cudaMemcpyDeviceToHost, st),
+                  rc.err);
     MFBC_CUDA_TRY(cudaMemcpyAsync(cnt.data(), s.bcount, sizeof(uint32_t) * cnt.size(), cudaMemcpyDeviceToHost, st),
                   rc.err);
     MFBC_CUDA_TRY(cudaStreamSynchronize(st), rc.err);
     rc.prof->drain();
-    return MFBC_OK;
-  };
-  mfbc_status e = read_counts();
-  if (e) return e;
-  const int64_t max_steps = (int64_t)n * (int64_t)std::max(1, g.wmax) + 1;
-  int64_t steps = 0;
-  int32_t d = 0;
-  while (true) {
-    const int slot = d % B;
-    const uint32_t c = cnt[(size_t)slot];
-    if (c) {
-      if (++steps > max_steps) {
-        if (rc.err) *rc.err = "distance steps did not terminate";
-        return MFBC_ERR_NO_CONVERGENCE;
-      }
-      const uint32_t before = cnt[(size_t)B];
-      PROF(K_DP_FWD, (k_dp_fwd<<<dp_grid(c), 256, 0, st>>>(
-                         s.blist + (size_t)slot * s.bcap, c, d, slot, B, s.BW, W, nb, s.bcap, g.rowptr, g.col, g.w,
-                         g.rowptr_t, g.col_t, g.w_t, s.dist, s.sig, s.bflag, s.blist, s.bcount, s.mlist,
-                         B_ ? B_ + K_DP_FWD : nullptr)));
-      MFBC_CUDA_TRY(cudaMemsetAsync(&s.bcount[slot], 0, sizeof(uint32_t), st), rc.err);
-      e = read_counts();
-      if (e) return e;
-      step_d.push_back(d);
-      step_off.push_back(before);
-      step_cnt.push_back(cnt[(size_t)B] - before);
+    marks.insert(marks.end(), mk.begin(), mk.end());
+    bool pending = false;
+    for (int k = 0; k < B; k++) pending |= cnt[(size_t)k] != 0;
+    if (!pending) break;
+    if (steps > max_steps) {
+      if (rc.err) *rc.err = "distance steps did not terminate";
+      return MFBC_ERR_NO_CONVERGENCE;
     }
-    // next distance value with waiting vertices (all lie in d+1 .. d+B-1)
-    int next = -1;
-    for (int k = 1; k < B; k++)
-      if (cnt[(size_t)((d + k) % B)]) { next = d + k; break; }
-    if (next < 0) break;
-    d = next;
   }
+  marks.push_back(cnt[(size_t)B]);              // end of the last step's items
   if (fwd_iters) *fwd_iters += steps;
   check_sigma_exact(s.sig, cells, s.ctr, st);
   if (!lambda) return MFBC_OK;
@@ -289,11 +286,12 @@ mfbc_status dist_batch(RunCtx& rc, DistState& s, const int32_t* d_src_batch, int
     wreq = s.word_req;
   }
   double* lam0 = wreq ? lambda : lambda + (size_t)(urq < 0 ? 0 : urq) * n;
-  for (size_t i = step_d.size(); i-- > 0;) {
-    if (step_d[i] == 0 || step_cnt[i] == 0) continue;
-    PROF(K_DP_BWD, (k_dp_bwd<<<dp_grid(step_cnt[i]), 256, 0, st>>>(
-                       s.mlist + step_off[i], step_cnt[i], step_d[i], W, nb, n, g.rowptr, g.col, g.w, s.dist,
-                       s.sig, s.val, s.src, lam0, wreq, B_ ? B_ + K_DP_BWD : nullptr)));
+  for (int64_t dd = (int64_t)marks.size() - 2; dd >= 1; dd--) {
+    const uint32_t off = marks[(size_t)dd], cntd = marks[(size_t)dd + 1] - off;
+    if (!cntd) continue;
+    PROF(K_DP_BWD, (k_dp_bwd<<<dp_grid(cntd), 256, 0, st>>>(
+                       s.mlist + off, cntd, (int32_t)dd, W, nb, n, g.rowptr, g.col, g.w, s.dist, s.sig, s.val,
+                       s.src, lam0, wreq, B_ ? B_ + K_DP_BWD : nullptr)));
     if (bwd_iters) (*bwd_iters)++;
   }
   MFBC_CUDA_TRY(cudaGetLastError(), rc.err);

@@ -169,6 +169,7 @@ struct DistState {
   uint32_t* bflag;    // [n * W][BW] bucket membership bits per item
   size_t bcap;        // n * W
   uint32_t* bcount;   // [B + 1] bucket counts, then the settled-list count
+  uint32_t* marks;    // settled-list offsets of the steps queued since the last check
   int32_t* src;       // [nb]
   int32_t* word_req;  // [W]
   Counters* ctr;
