@@ -158,6 +158,19 @@ void level_carve(Carver& c, const DevGraph& g, int nb, int Lcap, int64_t list_ca
 // Distance path for small integer weights: Algorithms 1 and 2 stepped in
 // order of distance value.  See dist.cu.
 constexpr int DIST_MAX_BUCKETS = 4097;   // w_max + 1 at most
+// Grid-wide step barrier and step bookkeeping of the persistent distance
+// kernels (one per batch workspace, zeroed before a batch).
+struct DpSync {
+  uint32_t arrive, gen;  // barrier: blocks arrived at the current barrier, generation
+  int32_t d;             // distance value of the next forward step
+  uint32_t off;          // settled-list offset at the start of that step
+  uint32_t k;            // steps recorded by the current launch
+  uint32_t stop;         // 1: no pending items; 2: step records full
+  uint32_t err;          // bit 0: a barrier wait ran past its limit
+  uint32_t steps;        // forward steps processed (statistics)
+};
+constexpr int DP_STEPS = 4096;     // step records per launch of the persistent kernels
+
 struct DistState {
   int nb = 0, W = 0, B = 0, BW = 0;
   int32_t* dist;      // tau  [n][nb]
@@ -169,7 +182,10 @@ struct DistState {
   uint32_t* bflag;    // [n * W][BW] bucket membership bits per item
   size_t bcap;        // n * W
   uint32_t* bcount;   // [B + 1] bucket counts, then the settled-list count
-  uint32_t* marks;    // settled-list offsets of the steps queued since the last check
+  DpSync* sy;
+  int32_t* sd;        // [DP_STEPS] distance value of each recorded step
+  uint32_t* soff;     // [DP_STEPS] its first settled-list entry
+  uint32_t* scnt;     // [DP_STEPS] its settled-list length (backward launches)
   int32_t* src;       // [nb]
   int32_t* word_req;  // [W]
   Counters* ctr;

@@ -311,7 +311,7 @@ def test_profile_reports_kernels():
         assert prof["batches"] == 1 and prof["fwd_iters"] > 0 and prof["bwd_iters"] > 0
         ks = prof["kernels"]
         main = {mfbc.PATH_LEVEL: "level_mfbf_gather", mfbc.PATH_GENERAL: "mfbf_relax_min",
-                mfbc.PATH_DIST: "dist_mfbf_step"}[p]
+                mfbc.PATH_DIST: "dist_mfbf"}[p]
         assert ks[main]["launches"] > 0 and ks[main]["ms"] > 0 and ks[main]["bytes"] > 0
     G.close()
 
