@@ -51,6 +51,10 @@ WORKLOADS = {
                     desc="Erdos-Renyi n=2^20, k=32, undirected, unweighted, 16384 sampled sources"),
     "rmat16w": dict(kind="rmat16w", nsrc=4096,
                     desc="R-MAT scale 16, edge factor 16, directed, weights U[1,255], 4096 sources, n_b=512"),
+    "er16k1024w": dict(kind="er16k1024w", nsrc=1 << 16,
+                       desc="Erdos-Renyi n=2^16, k=1024, undirected, weights U[1,100], all 65536 sources"),
+    "grid256w": dict(kind="grid", L=256, nsrc=4096,
+                     desc="2D grid 256^2, 4-neighbour, undirected, weights U[1,16], 4096 sampled sources"),
 }
 
 
@@ -61,6 +65,11 @@ def make_workload(name, rank=0):
         g = gg.rmat(w["scale"], w["ef"], seed=1)
     elif w["kind"] == "er":
         g = gg.erdos_renyi(w["n"], w["k"], seed=1)
+    elif w["kind"] == "er16k1024w":
+        g = gg.erdos_renyi(1 << 16, 1024, weights=(1, 100), seed=1)
+        return g, np.arange(g.n, dtype=np.int32)          # all-source exact BC
+    elif w["kind"] == "grid":
+        g = gg.grid2d(w["L"], weights=(1, 16), seed=1)
     else:
         g = gg.rmat(16, 16, directed=True, weights=(1, 255), seed=1)
     srcs = gg.sample_sources(g, w["nsrc"], seed=2 + rank)
@@ -125,7 +134,7 @@ SERVE_POOL = "resident graphs R-MAT 16/18/20 (edge factor 16, undirected), Erdos
              "weighted 2D grid 256^2 w U[1,16]; requests with log-uniform [64, 4096] sampled sources"
 
 
-def serving_bench(n_requests=120, seed=5):
+def serving_bench(n_requests=120, seed=5, max_cols=1024):
     """Served (packed, continuous batching, memory-budget admission, one worker
     per graph) against plain (one mfbc_bc_device call per request, in arrival
     order) on the same requests: both saturated (every request at t = 0:
@@ -150,7 +159,7 @@ def serving_bench(n_requests=120, seed=5):
         return serve.make_requests(sizes, n_requests, rate, lo=64, hi=4096, seed=seed, eligible=elig)
 
     def served(rs):
-        srv = serve.Server(graphs, budget_bytes=budget, max_cols=1024, replicas=replicas).start()
+        srv = serve.Server(graphs, budget_bytes=budget, max_cols=max_cols, replicas=replicas).start()
         try:
             serve.run_served(srv, rs, timeout=900)
         finally:
@@ -178,7 +187,7 @@ def serving_bench(n_requests=120, seed=5):
             diff = max(diff, float(np.max(np.abs(a.result[nz] - b.result[nz]) / np.abs(b.result[nz]))))
     for G in list(graphs.values()) + [R for rs_ in replicas.values() for R in rs_]:
         G.close()
-    return {"workload": SERVE_POOL, "workers_per_graph": 4, "max_group_columns": 1024, "requests": n_requests, "budget_bytes": budget,
+    return {"workload": SERVE_POOL, "workers_per_graph": 4, "max_group_columns": max_cols, "requests": n_requests, "budget_bytes": budget,
             "saturated": {"plain_gteps": sat_plain["gteps"], "served_gteps": sat_served["gteps"],
                           "plain_span_s": sat_plain["span_s"], "served_span_s": sat_served["span_s"]},
             "offered_rate_per_s": rate, "offered_load_vs_plain_capacity": 0.8,

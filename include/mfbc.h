@@ -65,8 +65,9 @@ typedef enum {
 
 /* mfbc_options.path */
 #define MFBC_PATH_AUTO    0    /* level kernels for unit weights; distance kernels for weights
-                                  <= 64 with in- and out-degrees <= 64; general kernels otherwise
-                                  (or the family mfbc_autotune chose) */
+                                  <= 128 when no in- or out-degree exceeds max(64, 4x the
+                                  average degree); general kernels otherwise (or the family
+                                  mfbc_autotune chose) */
 #define MFBC_PATH_GENERAL 1    /* force the general (any integer weight) kernels */
 #define MFBC_PATH_LEVEL   2    /* require the unit-weight level kernels (INVALID if weighted) */
 #define MFBC_PATH_DIST    3    /* distance-ordered kernels for small integer weights

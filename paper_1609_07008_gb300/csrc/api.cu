@@ -182,12 +182,18 @@ static size_t plan_bytes(const DevGraph& g, int path, int nb, int32_t nsrc, int 
 }
 
 // Kernel family for MFBC_PATH_AUTO without tuning: level kernels for unit
-// weights; distance-ordered kernels for small weights on graphs without hubs
-// (each distance step waits for its longest adjacency list, so hubs make the
-// steps slow; grids are the case they suit); general kernels otherwise.
+// weights; distance-ordered kernels for weights <= 128 on graphs without hubs
+// (no degree above max(64, 4x the average): each distance step waits for its
+// longest adjacency list, so hubs make the steps slow -- weighted R-MAT 16,
+// 4096 sources: 3661 ms against 281 ms on the general kernels -- while grids
+// and uniform random graphs gain: weighted 256^2 grid 313 against 2883 ms,
+// Erdos-Renyi n = 2^16, k = 1024, 256 sources 153 against 326 ms); general
+// kernels otherwise.
 static int default_path(const DevGraph& g) {
   if (g.unit) return MFBC_PATH_LEVEL;
-  if (g.wmax <= 64 && std::max(g.max_deg, g.max_in_deg) <= 64 && (uint64_t)g.n * 128u <= 0xffffffffull)
+  const int64_t avg = g.n ? g.nnz / g.n : 0;
+  const int64_t deg_cap = std::max<int64_t>(64, 4 * avg);
+  if (g.wmax <= 128 && std::max(g.max_deg, g.max_in_deg) <= deg_cap && (uint64_t)g.n * 128u <= 0xffffffffull)
     return MFBC_PATH_DIST;
   return MFBC_PATH_GENERAL;
 }

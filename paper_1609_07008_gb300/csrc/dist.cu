@@ -21,9 +21,9 @@
 // (Vertex, 32-column word) items waiting for a distance value are kept in a
 // ring of w_max + 1 buckets (an item list and one flag bit per item each), so
 // a step visits only the words that received a candidate for its distance.
-// A step runs one warp per item; the items that settle pairs are appended to
-// one list with per-step offsets, which the backward pass replays in
-// reverse.
+// A step reads each item's 32 distances with one warp and works the pairs at
+// its distance one per lane; the items that settle pairs are appended to one
+// list with per-step offsets, which the backward pass replays in reverse.
 #include <algorithm>
 
 #include "internal.cuh"
@@ -51,11 +51,10 @@ void dist_carve(Carver& c, int32_t n, int nb, int B, DistState& s) {
   s.bcap = (size_t)n * s.W;                  // (vertex, word) items a bucket can hold
   s.blist = c.take<uint32_t>((size_t)B * s.bcap);
   s.bflag = c.take<uint32_t>(s.bcap * s.BW);
-  s.bcount = c.take<uint32_t>((size_t)B + 1); // B bucket counts, then the settled-list count
+  s.bcount = c.take<uint32_t>(((size_t)B + 1) * DP_CSTRIDE);  // B bucket counts, settled-list count
   s.sy = c.take<DpSync>(1);
-  s.sd = c.take<int32_t>(DP_STEPS);
-  s.soff = c.take<uint32_t>(DP_STEPS);
-  s.scnt = c.take<uint32_t>(DP_STEPS);
+  s.sd = c.take<int32_t>(DP_STEP_RECORDS);
+  s.soff = c.take<uint32_t>(DP_STEP_RECORDS);
   s.src = c.take<int32_t>((size_t)nb);
   s.word_req = c.take<int32_t>((size_t)s.W);
   s.ctr = c.take<Counters>(1);
@@ -71,69 +70,28 @@ __global__ void k_dp_seed(const int32_t* __restrict__ src, int nb, int W, int BW
   dist[(size_t)s * nb + j] = 0;
   sig[(size_t)s * nb + j] = 1.0;
   const uint32_t item = (uint32_t)s * (uint32_t)W + (uint32_t)(j >> 5);
-  if (!(atomicOr(&bflag[(size_t)item * BW], 1u) & 1u)) blist[atomicAdd(&bcount[0], 1u)] = item;
+  if (!(atomicOr(&bflag[(size_t)item * BW], 1u) & 1u)) blist[atomicAdd(&bcount[0], 1u)] = item;  // bucket 0
 }
 
-// ------------------------------------------------ persistent step kernels
-// The steps of a batch are tiny (a weighted 256^2 grid has about 2000 distance
-// values, each holding a few hundred items per 512 columns), so both passes
-// run as one cooperative launch whose resident blocks take the steps one
-// after another, separated by a grid-wide barrier, instead of one launch per
-// step.  The block that reaches a barrier last does the step's bookkeeping
-// while the others wait.  Every wait is bounded: past DP_WAIT_NS the waiting
-// block sets sy->err, every block leaves its loop, and the host reports
-// MFBC_ERR_TIMEOUT.  Buffers that other blocks write during the launch are
-// read with plain (or L2-only) loads after the barrier's fences, never through
-// the read-only data path.
-constexpr uint64_t DP_WAIT_NS = 10ull * 1000 * 1000 * 1000;
-
-__device__ __forceinline__ uint64_t dp_clock_ns() {
-  uint64_t t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-// Grid-wide barrier.  `serial` runs in all threads of the block that arrives
-// last, after every block has finished the work before the barrier and
-// before any block continues.  Returns false in every block once a wait has
-// timed out (here or in another block).
-template <class Serial>
-__device__ __forceinline__ bool dp_barrier(DpSync* sy, Serial serial) {
-  __shared__ uint32_t s_last, s_gen, s_err;
-  volatile DpSync* vs = sy;
-  __syncthreads();                             // this block's work of the step is done
-  if (threadIdx.x == 0) {
-    s_gen = vs->gen;                           // cannot advance before this block arrives
-    __threadfence();                           // publish the block's writes
-    s_last = atomicAdd(&sy->arrive, 1u) == gridDim.x - 1;
-  }
-  __syncthreads();
-  if (s_last) {
-    __threadfence();
-    serial();
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      vs->arrive = 0;
-      __threadfence();
-      vs->gen = s_gen + 1;                     // release the waiting blocks
-    }
-  } else if (threadIdx.x == 0) {
-    const uint64_t t0 = dp_clock_ns();
-    while (vs->gen == s_gen) {
-      if (dp_clock_ns() - t0 > DP_WAIT_NS) { atomicOr(&sy->err, 1u); break; }
-      __nanosleep(32);
-    }
-    __threadfence();                           // acquire what the other blocks wrote
-  }
-  if (threadIdx.x == 0) s_err = vs->err;
-  __syncthreads();
-  return s_err == 0;
-}
+// ------------------------------------------------------------ step kernels
+// The steps of a batch are small (a weighted 256^2 grid has about 2000
+// distance values, each holding a few hundred items per 512 columns), so the
+// host never waits between them.  The forward step reads its distance value
+// from sy on the device, and the last block to finish it does the step's
+// bookkeeping: it empties the bucket, records the step for MFBr, and moves
+// sy->d to the next distance value with queued items (or sets sy->stop).  A
+// round of DP_ROUND such launches is captured once per batch as a CUDA graph
+// and replayed until sy->stop; launches after the last step return at once.
+// (A persistent cooperative form with a grid barrier between steps was no
+// faster alone, and its grid, holding every SM, stopped concurrent batches of
+// other requests from overlapping.)
+constexpr int DP_ROUND = 32;
+static_assert(DP_ROUND <= DP_STEP_RECORDS, "a round records at most one step per launch");
 
 struct DpFwd {
   uint32_t* blist;       // [B][bcap] bucket item lists
   uint32_t* bflag;       // [n * W][BW] bucket membership bits
-  uint32_t* bcount;      // [B + 1] bucket counts, settled-list count
+  uint32_t* bcount;      // [B + 1] bucket counts, settled-list count (DP_CSTRIDE apart)
   uint32_t* mlist;       // settled (vertex, word) items in step order
   int32_t* dist;         // tau [n][nb]
   double* sig;           // sigma_bar [n][nb]
@@ -147,234 +105,335 @@ struct DpFwd {
   unsigned long long* bytes;  // algorithmic bytes (counting runs only)
 };
 
-// Arcs of one item taken together: their loads and atomics are issued before
+// A step's (vertex, word) items rarely have all 32 columns at its distance
+// (on a weighted grid usually one: the word's sources are at different
+// distances from the vertex).  So a warp reads an item's 32 distances, keeps
+// the columns at distance d as (vertex, column) pairs in a per-warp queue, and
+// works the queue 32 pairs at a time, one pair per lane: each lane walks its
+// own vertex's arcs.
+struct DpQueue {
+  int32_t v[64];
+  uint16_t j[64];        // column (n_b <= 4096)
+  uint32_t m[32];        // settled items waiting for one settled-list reservation
+};
+
+// Arcs of one pair taken together: their loads and atomics are issued before
 // any result is used, so a step's latency is a few memory round trips rather
 // than a few per arc (the steps of small batches are latency chains).  Four
-// arcs (58-61 registers) beat one and eight on grids and on dense graphs.
+// arcs (about 60 registers) beat one and eight on grids and on dense graphs.
 constexpr int DP_ILP = 4;
 
-// One forward item at distance d: the warp's lanes are the 32 columns of word
-// `word` of vertex v.  Pairs at distance d are final: their sigma_bar is the
-// sum over in-neighbours u one arc short of d (integers below 2^53, exact in
-// any order), and they offer d + w to their out-neighbours.
-__device__ __forceinline__ void dp_fwd_item(const DpFwd& a, uint32_t item, int32_t d, int slot, unsigned lane,
-                                            unsigned long long& nbytes) {
-  const int32_t v = (int32_t)(item / (uint32_t)a.W);
-  const int word = (int)(item % (uint32_t)a.W);
-  if (lane == 0) atomicAnd(&a.bflag[(size_t)item * a.BW + slot / 32], ~(1u << (slot & 31)));
-  const int j = word * 32 + (int)lane;
-  const size_t vj = (size_t)v * a.nb + j;
-  const bool isM = a.dist[vj] == d;
-  if (a.bytes) nbytes += 4;
-  if (!__ballot_sync(0xffffffffu, isM)) return;
-  if (lane == 0) a.mlist[atomicAdd(&a.bcount[a.B], 1u)] = item;
+// Appends the lanes with isM, as (v, column) pairs, to the warp's queue (whole warp).
+__device__ __forceinline__ void dp_enqueue(DpQueue& q, int& qn, int32_t v, int j, bool isM, unsigned lane) {
+  const uint32_t bal = __ballot_sync(0xffffffffu, isM);
+  const int at = qn + __popc(bal & ((1u << lane) - 1u));
+  __syncwarp();
+  if (isM) { q.v[at] = v; q.j[at] = (uint16_t)j; }
+  qn += __popc(bal);
+  __syncwarp();
+}
+
+// Drops the first 32 entries of the queue (whole warp).
+__device__ __forceinline__ void dp_shift(DpQueue& q, int& qn, unsigned lane) {
+  int32_t v = 0;
+  uint16_t j = 0;
+  const bool keep = (int)lane < qn - 32;
+  if (keep) { v = q.v[32 + lane]; j = q.j[32 + lane]; }
+  __syncwarp();
+  if (keep) { q.v[lane] = v; q.j[lane] = j; }
+  qn -= 32;
+  __syncwarp();
+}
+
+// Appends the warp's buffered settled items to the settled list with one
+// reservation (whole warp).
+__device__ __forceinline__ void dp_flush_settled(const DpFwd& a, DpQueue& q, int& mn, unsigned lane) {
+  __syncwarp();
+  uint32_t at = 0;
+  if (lane == 0) at = atomicAdd(&a.bcount[(size_t)a.B * DP_CSTRIDE], (uint32_t)mn);
+  at = __shfl_sync(0xffffffffu, at, 0);
+  if ((int)lane < mn) a.mlist[at + lane] = q.m[lane];
+  mn = 0;
+  __syncwarp();
+}
+
+// Items are read SCAN at a time per warp, with their 32 distances each
+// loaded before any is used.  Four suit graphs of small degree, where an item
+// costs little more than these loads; one suits dense graphs, where the
+// items' arc walks dominate and are better spread over more warps (weighted
+// 256^2 grid, 4096 sources: 353 ms with one, 313 with four; Erdos-Renyi
+// n = 2^16, k = 1024, 256 sources: 154 ms with one, 186 with four).
+constexpr uint32_t DP_NO_ITEM = 0xffffffffu;   // items are < n * W <= 2^32 / 4
+
+template <int SCAN>
+__device__ __forceinline__ void dp_scan_load(const uint32_t* list, uint64_t count, uint64_t base, int W, int nb,
+                                             const int32_t* dist, unsigned lane, uint32_t (&it)[SCAN],
+                                             int32_t (&dv)[SCAN]) {
+  const uint32_t mine = lane < (unsigned)SCAN && base + lane < count ? list[base + lane] : DP_NO_ITEM;
+#pragma unroll
+  for (int t = 0; t < SCAN; t++) {
+    it[t] = __shfl_sync(0xffffffffu, mine, t);
+    const int32_t v = (int32_t)(it[t] / (uint32_t)W);
+    const int j = (int)(it[t] % (uint32_t)W) * 32 + (int)lane;
+    dv[t] = it[t] != DP_NO_ITEM ? dist[(size_t)v * nb + j] : -1;
+  }
+}
+
+// Forward pairs at distance d, lane i < cnt takes queue entry i.  The pair is
+// final: sigma_bar is the sum over in-neighbours u one arc short of d
+// (integers below 2^53, exact in any order), and it offers d + w to its
+// out-neighbours; an out-neighbour's (vertex, word) item joins the bucket of
+// d + w unless it is there already.
+__device__ __forceinline__ void dp_fwd_pairs(const DpFwd& a, const DpQueue& q, int cnt, int32_t d, unsigned lane,
+                                             unsigned long long& nbytes) {
+  if ((int)lane >= cnt) return;
+  const int32_t v = q.v[lane];
+  const int j = q.j[lane];
   if (d > 0) {
     double acc = 0.0;
     const int64_t b = __ldg(&a.rpt[v]), e = __ldg(&a.rpt[v + 1]);
-    for (int64_t k0 = b; k0 < e; k0 += 32) {
-      const int64_t k = k0 + lane;
-      const int32_t myu = k < e ? __ldg(&a.colt[k]) : 0;
-      const int32_t myw = k < e ? (a.wtt ? __ldg(&a.wtt[k]) : 1) : INF;
-      const int cnt = (int)(e - k0 < 32 ? e - k0 : 32);
-      for (int t0 = 0; t0 < cnt; t0 += DP_ILP) {
-        size_t uj[DP_ILP];
-        int32_t du[DP_ILP], want[DP_ILP];
+    for (int64_t k0 = b; k0 < e; k0 += DP_ILP) {
+      size_t uj[DP_ILP];
+      int32_t du[DP_ILP], want[DP_ILP];
 #pragma unroll
-        for (int q = 0; q < DP_ILP; q++) {
-          const int32_t u = __shfl_sync(0xffffffffu, myu, (t0 + q) & 31);
-          const int32_t w = __shfl_sync(0xffffffffu, myw, (t0 + q) & 31);
-          const bool ok = isM && t0 + q < cnt && w <= d;
-          uj[q] = (size_t)u * a.nb + j;
-          want[q] = d - w;
-          du[q] = ok ? a.dist[uj[q]] : INF;      // want[q] < INF: never matches
-          if (a.bytes && ok) nbytes += 4;
-        }
-#pragma unroll
-        for (int q = 0; q < DP_ILP; q++)
-          if (du[q] == want[q]) { acc += a.sig[uj[q]]; if (a.bytes) nbytes += 8; }
-      }
-    }
-    if (isM) { a.sig[vj] = acc; if (a.bytes) nbytes += 8; }
-  }
-  const int64_t b = __ldg(&a.rp[v]), e = __ldg(&a.rp[v + 1]);
-  for (int64_t k0 = b; k0 < e; k0 += 32) {
-    const int64_t k = k0 + lane;
-    const int32_t myx = k < e ? __ldg(&a.col[k]) : 0;
-    const int32_t myw = k < e ? (a.wt ? __ldg(&a.wt[k]) : 1) : 0;
-    const int cnt = (int)(e - k0 < 32 ? e - k0 : 32);
-    for (int t0 = 0; t0 < cnt; t0 += DP_ILP) {
-      int32_t x[DP_ILP], cand[DP_ILP], cur[DP_ILP];
-#pragma unroll
-      for (int q = 0; q < DP_ILP; q++) {
-        x[q] = __shfl_sync(0xffffffffu, myx, (t0 + q) & 31);
-        cand[q] = d + __shfl_sync(0xffffffffu, myw, (t0 + q) & 31);
-        const bool ok = isM && t0 + q < cnt;
-        cur[q] = ok ? a.dist[(size_t)x[q] * a.nb + j] : -1;  // cand[q] >= 1: never better
+      for (int t = 0; t < DP_ILP; t++) {
+        const bool in = k0 + t < e;
+        const int32_t u = in ? __ldg(&a.colt[k0 + t]) : 0;
+        const int32_t w = in ? (a.wtt ? __ldg(&a.wtt[k0 + t]) : 1) : INF;
+        const bool ok = in && w <= d;
+        uj[t] = (size_t)u * a.nb + j;
+        want[t] = d - w;
+        du[t] = ok ? a.dist[uj[t]] : INF;       // want[t] < INF: never matches
         if (a.bytes && ok) nbytes += 4;
       }
-      unsigned imp = 0;                        // bit q: arc t0 + q improved some column
 #pragma unroll
-      for (int q = 0; q < DP_ILP; q++) {
-        const bool better = cand[q] < cur[q] && atomicMin(&a.dist[(size_t)x[q] * a.nb + j], cand[q]) > cand[q];
-        if (a.bytes && cand[q] < cur[q]) nbytes += 4;
-        if (__ballot_sync(0xffffffffu, better)) imp |= 1u << q;
-      }
-      // lane q queues (x, word) of arc t0 + q for distance cand
-      int32_t xq = 0, cq = 0;
+      for (int t = 0; t < DP_ILP; t++)
+        if (du[t] == want[t]) { acc += a.sig[uj[t]]; if (a.bytes) nbytes += 8; }
+    }
+    a.sig[(size_t)v * a.nb + j] = acc;
+    if (a.bytes) nbytes += 8;
+  }
+  const uint32_t word = (uint32_t)j >> 5;
+  const int64_t b = __ldg(&a.rp[v]), e = __ldg(&a.rp[v + 1]);
+  for (int64_t k0 = b; k0 < e; k0 += DP_ILP) {
+    int32_t x[DP_ILP], cand[DP_ILP], cur[DP_ILP];
 #pragma unroll
-      for (int q = 0; q < DP_ILP; q++)
-        if ((int)lane == q) { xq = x[q]; cq = cand[q]; }
-      if (lane < (unsigned)DP_ILP && ((imp >> lane) & 1u)) {
-        const int s2 = cq % a.B;
-        const uint32_t bit = 1u << (s2 & 31);
-        const uint32_t xi = (uint32_t)xq * (uint32_t)a.W + (uint32_t)word;
-        if (!(atomicOr(&a.bflag[(size_t)xi * a.BW + s2 / 32], bit) & bit))
-          a.blist[(size_t)s2 * a.bcap + atomicAdd(&a.bcount[s2], 1u)] = xi;
+    for (int t = 0; t < DP_ILP; t++) {
+      const bool in = k0 + t < e;
+      x[t] = in ? __ldg(&a.col[k0 + t]) : 0;
+      cand[t] = d + (in ? (a.wt ? __ldg(&a.wt[k0 + t]) : 1) : 0);
+      cur[t] = in ? a.dist[(size_t)x[t] * a.nb + j] : -1;  // cand[t] >= 0: never better
+      if (a.bytes && in) nbytes += 4;
+    }
+#pragma unroll
+    for (int t = 0; t < DP_ILP; t++) {
+      if (cand[t] < cur[t]) {
+        if (a.bytes) nbytes += 4;
+        if (atomicMin(&a.dist[(size_t)x[t] * a.nb + j], cand[t]) > cand[t]) {
+          const int s2 = cand[t] % a.B;
+          const uint32_t bit = 1u << (s2 & 31);
+          const uint32_t xi = (uint32_t)x[t] * (uint32_t)a.W + word;
+          if (!(atomicOr(&a.bflag[(size_t)xi * a.BW + s2 / 32], bit) & bit)) {
+            // one reservation per bucket among the lanes here
+            const unsigned act = __activemask();
+            const unsigned grp = __match_any_sync(act, s2);
+            const int leader = __ffs(grp) - 1;
+            uint32_t at = 0;
+            if ((int)lane == leader) at = atomicAdd(&a.bcount[(size_t)s2 * DP_CSTRIDE], (uint32_t)__popc(grp));
+            at = __shfl_sync(grp, at, leader) + __popc(grp & ((1u << lane) - 1u));
+            a.blist[(size_t)s2 * a.bcap + at] = xi;
+          }
+        }
       }
     }
   }
 }
 
-// MFBF: steps d = sy->d, then the next distance value with queued items, ...
-// until no bucket holds items (stop 1) or DP_STEPS steps with settled items
-// have been recorded (stop 2; the host launches again from sy->d).  The
-// candidates of step d land on d + 1 .. d + w_max, i.e. never in bucket d, so
-// the last block to finish step d can empty that bucket and look for the next
-// non-empty one among the other w_max.
-__global__ void __launch_bounds__(256) k_dp_fwd(DpFwd a) {
+// MFBF step at distance sy->d.  The candidates of step d land on d + 1 ..
+// d + w_max, never in bucket d, so the last block can empty that bucket and
+// look for the next non-empty one among the other w_max.
+template <int SCAN>
+__global__ void __launch_bounds__(256, 4) k_dp_fwd(DpFwd a) {
   __shared__ int32_t s_d;
-  __shared__ uint32_t s_cnt, s_stop, s_j;
+  __shared__ uint32_t s_cnt, s_stop, s_last, s_j;
   const unsigned lane = lane_id();
-  const uint64_t nw = (gridDim.x * blockDim.x) >> 5;
-  const uint64_t w0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  unsigned long long nbytes = 0;
   volatile DpSync* vs = a.sy;
-  for (;;) {
-    if (threadIdx.x == 0) {
-      s_stop = vs->stop | vs->err;
-      s_d = vs->d;
-      s_cnt = s_stop ? 0u : __ldcg(&a.bcount[s_d % a.B]);
-    }
-    __syncthreads();
-    if (s_stop) break;
-    const int32_t d = s_d;
-    const int slot = d % a.B;
-    const uint32_t count = s_cnt;
-    const uint32_t* list = a.blist + (size_t)slot * a.bcap;
-    for (uint64_t gw = w0; gw < count; gw += nw) dp_fwd_item(a, list[gw], d, slot, lane, nbytes);
-    const bool ok = dp_barrier(a.sy, [&] {
-      if (threadIdx.x == 0) s_j = 0xffffffffu;
-      __syncthreads();
-      for (uint32_t j = 1 + threadIdx.x; j < (uint32_t)a.B; j += blockDim.x)
-        if (__ldcg(&a.bcount[(d + (int32_t)j) % a.B])) atomicMin(&s_j, j);
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        a.bcount[slot] = 0;
-        const uint32_t end = __ldcg(&a.bcount[a.B]);
-        const uint32_t k = vs->k;
-        vs->steps = vs->steps + 1;
-        if (end != vs->off) {                  // the step settled pairs: record it
-          a.sd[k] = d;
-          a.soff[k] = vs->off;
-          vs->k = k + 1;
-          vs->off = end;
-        }
-        if (s_j == 0xffffffffu) vs->stop = 1;
-        else {
-          vs->d = d + (int32_t)s_j;
-          if (vs->k == (uint32_t)DP_STEPS) vs->stop = 2;
-        }
-      }
-    });
-    if (!ok) break;
+  if (threadIdx.x == 0) {
+    s_stop = vs->stop;
+    s_d = vs->d;
+    s_cnt = s_stop ? 0u : __ldcg(&a.bcount[(size_t)(s_d % a.B) * DP_CSTRIDE]);
   }
+  __syncthreads();
+  if (s_stop) return;
+  const int32_t d = s_d;
+  const int slot = d % a.B;
+  const uint32_t count = s_cnt;
+  const uint32_t* list = a.blist + (size_t)slot * a.bcap;
+  const uint64_t nw = (gridDim.x * blockDim.x) >> 5;
+  unsigned long long nbytes = 0;
+  __shared__ DpQueue dq[8];
+  DpQueue& q = dq[threadIdx.x >> 5];
+  int qn = 0;                                  // warp-uniform queue length (< 32 between items)
+  int mn = 0;                                  // warp-uniform count of settled items not yet listed
+  for (uint64_t base = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * SCAN; base < count;
+       base += nw * SCAN) {
+    uint32_t it[SCAN];
+    int32_t dv[SCAN];
+    dp_scan_load(list, count, base, a.W, a.nb, a.dist, lane, it, dv);
+#pragma unroll
+    for (int t = 0; t < SCAN; t++) {
+      if (it[t] == DP_NO_ITEM) break;
+      const int32_t v = (int32_t)(it[t] / (uint32_t)a.W);
+      const int j = (int)(it[t] % (uint32_t)a.W) * 32 + (int)lane;
+      if (lane == 0) atomicAnd(&a.bflag[(size_t)it[t] * a.BW + slot / 32], ~(1u << (slot & 31)));
+      const bool isM = dv[t] == d;
+      if (a.bytes) nbytes += 4;
+      if (!__any_sync(0xffffffffu, isM)) continue;
+      if (lane == 0) q.m[mn] = it[t];
+      if (++mn == 32) dp_flush_settled(a, q, mn, lane);
+      dp_enqueue(q, qn, v, j, isM, lane);
+      if (qn >= 32) {
+        dp_fwd_pairs(a, q, 32, d, lane, nbytes);
+        __syncwarp();
+        dp_shift(q, qn, lane);
+      }
+    }
+  }
+  if (qn > 0) dp_fwd_pairs(a, q, qn, d, lane, nbytes);
+  __syncwarp();
+  if (mn > 0) dp_flush_settled(a, q, mn, lane);
   if (a.bytes) {
     for (int o = 16; o; o >>= 1) nbytes += __shfl_xor_sync(0xffffffffu, nbytes, o);
-    if (lane == 0) atomicAdd(a.bytes, nbytes);
+    if (lane == 0 && nbytes) atomicAdd(a.bytes, nbytes);
+  }
+  // the last block to finish the step does its bookkeeping
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();                           // publish this block's writes
+    s_last = atomicAdd(&a.sy->done, 1u) == gridDim.x - 1;
+    s_j = 0xffffffffu;
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();                             // see every block's writes
+  for (uint32_t j = 1 + threadIdx.x; j < (uint32_t)a.B; j += blockDim.x)
+    if (__ldcg(&a.bcount[(size_t)((d + (int32_t)j) % a.B) * DP_CSTRIDE])) atomicMin(&s_j, j);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    a.bcount[(size_t)slot * DP_CSTRIDE] = 0;
+    const uint32_t end = __ldcg(&a.bcount[(size_t)a.B * DP_CSTRIDE]);
+    const uint32_t k = vs->k;
+    vs->steps = vs->steps + 1;
+    if (end != vs->off && k < (uint32_t)DP_STEP_RECORDS) {  // the step settled pairs: record it
+      a.sd[k] = d;
+      a.soff[k] = vs->off;
+      vs->k = k + 1;
+      vs->off = end;
+    }
+    if (s_j == 0xffffffffu) vs->stop = 1;
+    else vs->d = d + (int32_t)s_j;
+    vs->done = 0;
   }
 }
 
 struct DpBwd {
-  const uint32_t* mlist;
-  const int32_t* sd;     // [nsteps] distance values, decreasing
-  const uint32_t* soff;  // [nsteps] first settled-list entry of each step
-  const uint32_t* scnt;  // [nsteps] its length
-  int nsteps;
+  const uint32_t* items;  // the step's settled (vertex, word) items
+  uint32_t count;
+  int32_t d;
   const int64_t* rp; const int32_t* col; const int32_t* wt;
-  const int32_t* dist; const double* sig;  // final, read-only during the launch
+  const int32_t* dist; const double* sig;  // final, read-only in MFBr
   double* val;           // zeta + 1/sigma_bar [n][nb]
   const int32_t* src;
   double* lambda;
   const int32_t* word_req;
   int W, nb;
   int32_t n;
-  DpSync* sy;
   unsigned long long* bytes;
 };
 
-// One backward item at distance d: zeta of the pairs settled at d is the sum
-// over out-neighbours x at d + w of their value zeta + 1/sigma_bar (Sec.
-// 4.2.1); lambda(v) += zeta * sigma_bar over the word's columns (Algorithm 3).
-__device__ __forceinline__ void dp_bwd_item(const DpBwd& a, uint32_t it, int32_t d, unsigned lane,
-                                            unsigned long long& nbytes) {
-  const int32_t v = (int32_t)(it / (uint32_t)a.W);
-  const int word = (int)(it % (uint32_t)a.W);
-  const int r = a.word_req ? __ldg(&a.word_req[word]) : 0;
-  const int j = word * 32 + (int)lane;
-  const size_t vj = (size_t)v * a.nb + j;
-  const bool isM = __ldg(&a.dist[vj]) == d;
-  double acc = 0.0;
-  const int64_t b = __ldg(&a.rp[v]), e = __ldg(&a.rp[v + 1]);
-  for (int64_t k0 = b; k0 < e; k0 += 32) {
-    const int64_t k = k0 + lane;
-    const int32_t myx = k < e ? __ldg(&a.col[k]) : 0;
-    const int32_t myw = k < e ? (a.wt ? __ldg(&a.wt[k]) : 1) : 0;
-    const int cnt = (int)(e - k0 < 32 ? e - k0 : 32);
-    for (int t0 = 0; t0 < cnt; t0 += DP_ILP) {
+// Backward pairs at distance d, lane i < cnt takes queue entry i: zeta is
+// the sum over out-neighbours x at d + w of their value zeta + 1/sigma_bar
+// (Sec. 4.2.1), the slot takes zeta + 1/sigma_bar, and lambda(v) gains
+// zeta * sigma_bar (Algorithm 3), summed over each item's pairs (they sit
+// next to each other in the queue, and an item occurs once per step).
+__device__ __forceinline__ void dp_bwd_pairs(const DpBwd& a, const DpQueue& q, int cnt, int32_t d, unsigned lane,
+                                             unsigned long long& nbytes) {
+  const bool has = (int)lane < cnt;
+  const int32_t v = has ? q.v[lane] : -1;
+  const int j = has ? q.j[lane] : 0;
+  const int r = has ? (a.word_req ? __ldg(&a.word_req[j >> 5]) : 0) : -1;
+  double lam = 0.0;
+  if (has) {
+    double acc = 0.0;
+    const int64_t b = __ldg(&a.rp[v]), e = __ldg(&a.rp[v + 1]);
+    for (int64_t k0 = b; k0 < e; k0 += DP_ILP) {
       size_t xj[DP_ILP];
       int32_t dx[DP_ILP], want[DP_ILP];
 #pragma unroll
-      for (int q = 0; q < DP_ILP; q++) {
-        const int32_t x = __shfl_sync(0xffffffffu, myx, (t0 + q) & 31);
-        const int32_t w = __shfl_sync(0xffffffffu, myw, (t0 + q) & 31);
-        const bool ok = isM && t0 + q < cnt;
-        xj[q] = (size_t)x * a.nb + j;
-        want[q] = d + w;
-        dx[q] = ok ? __ldg(&a.dist[xj[q]]) : -1;  // want[q] >= 1: never matches
-        if (a.bytes && ok) nbytes += 4;
+      for (int t = 0; t < DP_ILP; t++) {
+        const bool in = k0 + t < e;
+        const int32_t x = in ? __ldg(&a.col[k0 + t]) : 0;
+        want[t] = d + (in ? (a.wt ? __ldg(&a.wt[k0 + t]) : 1) : 0);
+        xj[t] = (size_t)x * a.nb + j;
+        dx[t] = in ? __ldg(&a.dist[xj[t]]) : -1;  // want[t] >= 1: never matches
+        if (a.bytes && in) nbytes += 4;
       }
 #pragma unroll
-      for (int q = 0; q < DP_ILP; q++)
-        if (dx[q] == want[q]) { acc += a.val[xj[q]]; if (a.bytes) nbytes += 8; }
+      for (int t = 0; t < DP_ILP; t++)
+        if (dx[t] == want[t]) { acc += a.val[xj[t]]; if (a.bytes) nbytes += 8; }
     }
-  }
-  double lam = 0.0;
-  if (isM) {
+    const size_t vj = (size_t)v * a.nb + j;
     const double sg = __ldg(&a.sig[vj]);
     if (__ldg(&a.src[j]) != v) lam = acc * sg;
     a.val[vj] = acc + 1.0 / sg;
     if (a.bytes) nbytes += 20;
   }
-  for (int o = 16; o; o >>= 1) lam += __shfl_xor_sync(0xffffffffu, lam, o);
-  if (lane == 0 && r >= 0 && lam != 0.0) atomicAdd(&a.lambda[(size_t)r * a.n + v], lam);
+  // segmented sum over runs of one item (vertex, word); the run's last lane
+  // adds it
+  const int wd = j >> 5;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const double y = __shfl_up_sync(0xffffffffu, lam, o);
+    const int32_t vo = __shfl_up_sync(0xffffffffu, v, o);
+    const int wo = __shfl_up_sync(0xffffffffu, wd, o);
+    if ((int)lane >= o && vo == v && wo == wd) lam += y;
+  }
+  const int32_t vn = __shfl_down_sync(0xffffffffu, v, 1);
+  const int wn = __shfl_down_sync(0xffffffffu, wd, 1);
+  const bool last = lane == 31 || vn != v || wn != wd;
+  if (has && last && r >= 0 && lam != 0.0) atomicAdd(&a.lambda[(size_t)r * a.n + v], lam);
 }
 
-// MFBr: the recorded steps in decreasing distance order, one barrier apart.
-__global__ void __launch_bounds__(256) k_dp_bwd(DpBwd a) {
+// MFBr step at distance a.d over the items that settled there.
+template <int SCAN>
+__global__ void __launch_bounds__(256, 4) k_dp_bwd(DpBwd a) {
+  __shared__ DpQueue dq[8];
+  DpQueue& q = dq[threadIdx.x >> 5];
   const unsigned lane = lane_id();
   const uint64_t nw = (gridDim.x * blockDim.x) >> 5;
-  const uint64_t w0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   unsigned long long nbytes = 0;
-  for (int k = 0; k < a.nsteps; k++) {
-    const int32_t d = __ldg(&a.sd[k]);
-    const uint32_t* items = a.mlist + __ldg(&a.soff[k]);
-    const uint32_t count = __ldg(&a.scnt[k]);
-    for (uint64_t gw = w0; gw < count; gw += nw) dp_bwd_item(a, __ldg(&items[gw]), d, lane, nbytes);
-    if (k + 1 < a.nsteps && !dp_barrier(a.sy, [] {})) break;
+  int qn = 0;
+  for (uint64_t base = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * SCAN; base < a.count;
+       base += nw * SCAN) {
+    uint32_t it[SCAN];
+    int32_t dv[SCAN];
+    dp_scan_load(a.items, a.count, base, a.W, a.nb, a.dist, lane, it, dv);
+#pragma unroll
+    for (int t = 0; t < SCAN; t++) {
+      if (it[t] == DP_NO_ITEM) break;
+      const int32_t v = (int32_t)(it[t] / (uint32_t)a.W);
+      const int j = (int)(it[t] % (uint32_t)a.W) * 32 + (int)lane;
+      dp_enqueue(q, qn, v, j, dv[t] == a.d, lane);
+      if (qn >= 32) {
+        dp_bwd_pairs(a, q, 32, a.d, lane, nbytes);
+        dp_shift(q, qn, lane);
+      }
+    }
   }
+  if (qn > 0) dp_bwd_pairs(a, q, qn, a.d, lane, nbytes);
   if (a.bytes) {
     for (int o = 16; o; o >>= 1) nbytes += __shfl_xor_sync(0xffffffffu, nbytes, o);
-    if (lane == 0) atomicAdd(a.bytes, nbytes);
+    if (lane == 0 && nbytes) atomicAdd(a.bytes, nbytes);
   }
 }
 
@@ -385,16 +444,44 @@ __global__ void __launch_bounds__(256) k_dp_bwd(DpBwd a) {
     rc.prof->end(id);             \
   } while (0)
 
-// Blocks of a cooperative launch: as many as the SMs hold at once (each item
-// is a chain of dependent loads, so the steps need every resident warp; two
-// blocks per SM made small batches 1.3x and dense graphs 2.5x slower).
+// One wave of blocks: each item is a chain of dependent loads, so a step
+// wants every warp the SMs hold, and blocks beyond one wave would only read
+// the count and leave.
 static unsigned dp_blocks(const void* kern) {
   int dev = 0, sms = 0, per_sm = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return 0;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, 0) != cudaSuccess) return 0;
-  return (unsigned)(sms * per_sm);
+  return (unsigned)(sms * std::max(per_sm, 1));
 }
+
+static inline unsigned dp_grid(uint64_t warps, unsigned cap) {
+  const uint64_t b = (warps + 7) / 8;
+  return (unsigned)(b < 1 ? 1 : (b > cap ? cap : b));
+}
+
+// A round of DP_ROUND forward step launches as an executable CUDA graph,
+// captured on a private stream of the calling thread (capture is not
+// possible on the legacy default stream, which callers may pass).
+struct DpRound {
+  cudaGraphExec_t exec = nullptr;
+  ~DpRound() { if (exec) cudaGraphExecDestroy(exec); }
+  cudaError_t build(const void* kern, const DpFwd& fa, unsigned grid) {
+    static thread_local cudaStream_t cap = nullptr;
+    cudaError_t e = cudaSuccess;
+    if (!cap && (e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking)) != cudaSuccess) return e;
+    if ((e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) return e;
+    void* args[] = {const_cast<DpFwd*>(&fa)};
+    cudaError_t le = cudaSuccess;
+    for (int k = 0; k < DP_ROUND && le == cudaSuccess; k++) le = cudaLaunchKernel(kern, grid, 256, args, 0, cap);
+    cudaGraph_t gr = nullptr;
+    e = cudaStreamEndCapture(cap, &gr);         // ends the capture in every case
+    if (le != cudaSuccess) e = le;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, gr, 0);
+    if (gr) cudaGraphDestroy(gr);
+    return e;
+  }
+};
 
 mfbc_status dist_batch(RunCtx& rc, DistState& s, const int32_t* d_src_batch, int nactive, double* lambda,
                        int64_t* fwd_iters, int64_t* bwd_iters) {
@@ -414,46 +501,47 @@ mfbc_status dist_batch(RunCtx& rc, DistState& s, const int32_t* d_src_batch, int
     fill_i32(s.dist, INF, cells, st);
     cudaMemsetAsync(s.sig, 0, sizeof(double) * cells, st);
     cudaMemsetAsync(s.bflag, 0, sizeof(uint32_t) * s.bcap * s.BW, st);
-    cudaMemsetAsync(s.bcount, 0, sizeof(uint32_t) * ((size_t)B + 1), st);
+    cudaMemsetAsync(s.bcount, 0, sizeof(uint32_t) * ((size_t)B + 1) * DP_CSTRIDE, st);
     cudaMemsetAsync(s.sy, 0, sizeof(DpSync), st);
   });
   rc.prof->k[K_FILL].bytes += 12.0 * cells + 4.0 * s.bcap * s.BW;
   PROF(K_SEED, (k_dp_seed<<<(nb + 127) / 128, 128, 0, st>>>(s.src, nb, W, s.BW, s.dist, s.sig, s.bflag, s.blist,
                                                           s.bcount)));
 
-  // ---- MFBF in increasing distance order, DP_STEPS recorded steps per launch
-  DpFwd fa{s.blist, s.bflag, s.bcount, s.mlist, s.dist, s.sig, g.rowptr, g.col, g.w, g.rowptr_t, g.col_t, g.w_t,
-           s.bcap, B, s.BW, W, nb, s.sy, s.sd, s.soff, B_ ? B_ + K_DP_FWD : nullptr};
-  const unsigned fgrid = dp_blocks((const void*)k_dp_fwd);
+  // ---- MFBF in increasing distance order, DP_ROUND steps between host reads
+  const DpFwd fa{s.blist, s.bflag, s.bcount, s.mlist, s.dist, s.sig, g.rowptr, g.col, g.w, g.rowptr_t, g.col_t,
+                 g.w_t, s.bcap, B, s.BW, W, nb, s.sy, s.sd, s.soff, B_ ? B_ + K_DP_FWD : nullptr};
+  const bool dense = g.nnz >= 32 * (int64_t)n;  // scan one item at a time (see SCAN)
+  const void* fk = dense ? (const void*)k_dp_fwd<1> : (const void*)k_dp_fwd<4>;
+  const unsigned fgrid = dp_blocks(fk);
   if (!fgrid) return cuda_fail(rc.err, "occupancy of the distance kernels", cudaGetLastError());
-  std::vector<int32_t> hd, kd((size_t)DP_STEPS);
-  std::vector<uint32_t> hoff, koff((size_t)DP_STEPS);
+  DpRound round;
+  MFBC_CUDA_TRY(round.build(fk, fa, fgrid), rc.err);
+  std::vector<int32_t> hd, kd((size_t)DP_STEP_RECORDS);
+  std::vector<uint32_t> hoff, koff((size_t)DP_STEP_RECORDS);
   DpSync hs{};
-  const int64_t max_launches = (int64_t)n * (int64_t)std::max(1, g.wmax) / DP_STEPS + 2;
-  for (int64_t launch = 0;; launch++) {
-    void* args[] = {&fa};
+  const int64_t max_rounds = (int64_t)n * (int64_t)std::max(1, g.wmax) / DP_ROUND + 2;
+  for (int64_t r = 0;; r++) {
     cudaError_t e;
-    PROF(K_DP_FWD, e = cudaLaunchCooperativeKernel((const void*)k_dp_fwd, fgrid, 256, args, 0, st));
+    PROF(K_DP_FWD, e = cudaGraphLaunch(round.exec, st));
     MFBC_CUDA_TRY(e, rc.err);
+    rc.prof->k[K_DP_FWD].launches += DP_ROUND - 1;   // kernels, not graph launches
     MFBC_CUDA_TRY(cudaMemcpyAsync(&hs, s.sy, sizeof(DpSync), cudaMemcpyDeviceToHost, st), rc.err);
-    MFBC_CUDA_TRY(cudaMemcpyAsync(kd.data(), s.sd, sizeof(int32_t) * DP_STEPS, cudaMemcpyDeviceToHost, st), rc.err);
-    MFBC_CUDA_TRY(cudaMemcpyAsync(koff.data(), s.soff, sizeof(uint32_t) * DP_STEPS, cudaMemcpyDeviceToHost, st),
+    MFBC_CUDA_TRY(cudaMemcpyAsync(kd.data(), s.sd, sizeof(int32_t) * DP_STEP_RECORDS, cudaMemcpyDeviceToHost, st),
                   rc.err);
+    MFBC_CUDA_TRY(
+        cudaMemcpyAsync(koff.data(), s.soff, sizeof(uint32_t) * DP_STEP_RECORDS, cudaMemcpyDeviceToHost, st),
+        rc.err);
     MFBC_CUDA_TRY(cudaStreamSynchronize(st), rc.err);
     rc.prof->drain();
-    if (hs.err) {
-      if (rc.err) *rc.err = "a grid barrier of the distance kernels waited past its limit";
-      return MFBC_ERR_TIMEOUT;
-    }
     hd.insert(hd.end(), kd.begin(), kd.begin() + hs.k);
     hoff.insert(hoff.end(), koff.begin(), koff.begin() + hs.k);
-    if (hs.stop == 1) break;
-    if (hs.stop != 2 || launch >= max_launches) {
+    if (hs.stop) break;
+    if (r >= max_rounds) {
       if (rc.err) *rc.err = "distance steps did not terminate";
       return MFBC_ERR_NO_CONVERGENCE;
     }
-    hs.k = 0;                                  // continue from hs.d with empty step records
-    hs.stop = 0;
+    hs.k = 0;                                  // the next round records from the start
     MFBC_CUDA_TRY(cudaMemcpyAsync(s.sy, &hs, sizeof(DpSync), cudaMemcpyHostToDevice, st), rc.err);
   }
   if (fwd_iters) *fwd_iters += hs.steps;
@@ -469,40 +557,24 @@ mfbc_status dist_batch(RunCtx& rc, DistState& s, const int32_t* d_src_batch, int
     wreq = s.word_req;
   }
   double* lam0 = wreq ? lambda : lambda + (size_t)(urq < 0 ? 0 : urq) * n;
-  std::vector<int32_t> bd;
-  std::vector<uint32_t> boff, bcnt;
+  const void* bk = dense ? (const void*)k_dp_bwd<1> : (const void*)k_dp_bwd<4>;
+  const unsigned bcap = dp_blocks(bk);
+  if (!bcap) return cuda_fail(rc.err, "occupancy of the distance kernels", cudaGetLastError());
+  DpBwd ba{nullptr, 0, 0, g.rowptr, g.col, g.w, s.dist, s.sig, s.val, s.src, lam0, wreq, W, nb, n,
+           B_ ? B_ + K_DP_BWD : nullptr};
   for (int64_t i = (int64_t)hd.size() - 1; i >= 0; i--) {
     if (hd[(size_t)i] <= 0) continue;
     const uint32_t end = (size_t)i + 1 < hoff.size() ? hoff[(size_t)i + 1] : hs.off;
-    bd.push_back(hd[(size_t)i]);
-    boff.push_back(hoff[(size_t)i]);
-    bcnt.push_back(end - hoff[(size_t)i]);
-  }
-  DpBwd ba{s.mlist, s.sd, s.soff, s.scnt, 0, g.rowptr, g.col, g.w, s.dist, s.sig, s.val, s.src, lam0, wreq, W, nb,
-           n, s.sy, B_ ? B_ + K_DP_BWD : nullptr};
-  const unsigned bgrid = dp_blocks((const void*)k_dp_bwd);
-  if (!bgrid) return cuda_fail(rc.err, "occupancy of the distance kernels", cudaGetLastError());
-  for (size_t c0 = 0; c0 < bd.size(); c0 += DP_STEPS) {
-    const size_t c = std::min(bd.size() - c0, (size_t)DP_STEPS);
-    MFBC_CUDA_TRY(cudaMemcpyAsync(s.sd, bd.data() + c0, sizeof(int32_t) * c, cudaMemcpyHostToDevice, st), rc.err);
-    MFBC_CUDA_TRY(cudaMemcpyAsync(s.soff, boff.data() + c0, sizeof(uint32_t) * c, cudaMemcpyHostToDevice, st),
-                  rc.err);
-    MFBC_CUDA_TRY(cudaMemcpyAsync(s.scnt, bcnt.data() + c0, sizeof(uint32_t) * c, cudaMemcpyHostToDevice, st),
-                  rc.err);
-    ba.nsteps = (int)c;
+    ba.items = s.mlist + hoff[(size_t)i];
+    ba.count = end - hoff[(size_t)i];
+    ba.d = hd[(size_t)i];
     void* args[] = {&ba};
     cudaError_t e;
-    PROF(K_DP_BWD, e = cudaLaunchCooperativeKernel((const void*)k_dp_bwd, bgrid, 256, args, 0, st));
+    PROF(K_DP_BWD, e = cudaLaunchKernel(bk, dp_grid(ba.count, bcap), 256, args, 0, st));
     MFBC_CUDA_TRY(e, rc.err);
-    if (bwd_iters) *bwd_iters += (int64_t)c;
+    if (bwd_iters) (*bwd_iters)++;
   }
-  MFBC_CUDA_TRY(cudaMemcpyAsync(&hs, s.sy, sizeof(DpSync), cudaMemcpyDeviceToHost, st), rc.err);
-  MFBC_CUDA_TRY(cudaStreamSynchronize(st), rc.err);
-  rc.prof->drain();
-  if (hs.err) {
-    if (rc.err) *rc.err = "a grid barrier of the distance kernels waited past its limit";
-    return MFBC_ERR_TIMEOUT;
-  }
+  MFBC_CUDA_TRY(cudaGetLastError(), rc.err);
   return MFBC_OK;
 }
 

@@ -158,18 +158,19 @@ void level_carve(Carver& c, const DevGraph& g, int nb, int Lcap, int64_t list_ca
 // Distance path for small integer weights: Algorithms 1 and 2 stepped in
 // order of distance value.  See dist.cu.
 constexpr int DIST_MAX_BUCKETS = 4097;   // w_max + 1 at most
-// Grid-wide step barrier and step bookkeeping of the persistent distance
-// kernels (one per batch workspace, zeroed before a batch).
+// Step bookkeeping of the distance kernels (one per batch workspace, zeroed
+// before a batch): the forward step kernels read the distance value to
+// process here, and the last block of each step advances it.
 struct DpSync {
-  uint32_t arrive, gen;  // barrier: blocks arrived at the current barrier, generation
+  uint32_t done;         // blocks finished with the current step
   int32_t d;             // distance value of the next forward step
   uint32_t off;          // settled-list offset at the start of that step
-  uint32_t k;            // steps recorded by the current launch
-  uint32_t stop;         // 1: no pending items; 2: step records full
-  uint32_t err;          // bit 0: a barrier wait ran past its limit
+  uint32_t k;            // steps recorded since the host last read them
+  uint32_t stop;         // 1: no bucket holds items
   uint32_t steps;        // forward steps processed (statistics)
 };
-constexpr int DP_STEPS = 4096;     // step records per launch of the persistent kernels
+constexpr int DP_STEP_RECORDS = 32; // >= the forward steps of one round between host reads
+constexpr int DP_CSTRIDE = 32;      // uint32 per bucket counter: one 128-byte line each
 
 struct DistState {
   int nb = 0, W = 0, B = 0, BW = 0;
@@ -181,11 +182,10 @@ struct DistState {
   uint32_t* blist;    // [B][bcap] ring of bucket lists of (vertex * W + word) items
   uint32_t* bflag;    // [n * W][BW] bucket membership bits per item
   size_t bcap;        // n * W
-  uint32_t* bcount;   // [B + 1] bucket counts, then the settled-list count
+  uint32_t* bcount;   // [B + 1] bucket counts, then the settled-list count, DP_CSTRIDE apart
   DpSync* sy;
-  int32_t* sd;        // [DP_STEPS] distance value of each recorded step
-  uint32_t* soff;     // [DP_STEPS] its first settled-list entry
-  uint32_t* scnt;     // [DP_STEPS] its settled-list length (backward launches)
+  int32_t* sd;        // [DP_STEP_RECORDS] distance value of each recorded step
+  uint32_t* soff;     // [DP_STEP_RECORDS] its first settled-list entry
   int32_t* src;       // [nb]
   int32_t* word_req;  // [W]
   Counters* ctr;
