@@ -74,9 +74,10 @@ __global__ void k_dp_seed(const int32_t* __restrict__ src, int nb, int W, int BW
 }
 
 // ------------------------------------------------------------ step kernels
-// The steps of a batch are small (a weighted 256^2 grid has about 2000
-// distance values, each holding a few hundred items per 512 columns), so the
-// host never waits between them.  The forward step reads its distance value
+// The steps of a batch are small (a weighted 256^2 grid has about 2200
+// distance values, each settling about 15 000 pairs at 512 columns: under 500
+// passes of 32 pairs over the whole GPU), so the host never waits between
+// them.  The forward step reads its distance value
 // from sy on the device, and the last block to finish it does the step's
 // bookkeeping: it empties the bucket, records the step for MFBr, and moves
 // sy->d to the next distance value with queued items (or sets sy->stop).  A
@@ -120,7 +121,8 @@ struct DpQueue {
 // Arcs of one pair taken together: their loads and atomics are issued before
 // any result is used, so a step's latency is a few memory round trips rather
 // than a few per arc (the steps of small batches are latency chains).  Four
-// arcs (about 60 registers) beat one and eight on grids and on dense graphs.
+// arcs beat one and eight on grids and on dense graphs (measured when a warp
+// still took one item, 32 columns, per pass).
 constexpr int DP_ILP = 4;
 
 // Appends the lanes with isM, as (v, column) pairs, to the warp's queue (whole warp).
