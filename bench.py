@@ -297,10 +297,22 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+L2_BYTES = 129 << 20
+
+
+def l2_note(n, n_b):
+    """How the timed steps relate to the L2: the smallest per-pair state of any
+    kernel family (8 bytes per (source, vertex)) against the L2 size."""
+    state = 8 * int(n) * int(n_b or 0)
+    if state > 2 * L2_BYTES:
+        return "state much larger than L2 (no flush)"
+    return f"state of {state / 2**20:.0f} MB may stay in L2 (no flush: a probe, not a bench line)"
+
+
 def config_of(args, g, nsrc, n_b):
     return {"workload": WORKLOADS[args.workload]["desc"], "name": args.workload, "n": g.n, "nnz": g.nnz,
             "m": g.m, "sources": nsrc, "n_b": n_b, "parallelism": f"sources sharded x{args.gpus}",
-            "l2": "state much larger than L2 (no flush)"}
+            "l2": l2_note(g.n, n_b if n_b else min(nsrc, 1024))}   # the reference arm has no n_b
 
 
 def main():
