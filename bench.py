@@ -300,19 +300,23 @@ def run_reference(args):
 L2_BYTES = 129 << 20
 
 
-def l2_note(n, n_b):
-    """How the timed steps relate to the L2: the smallest per-pair state of any
-    kernel family (8 bytes per (source, vertex)) against the L2 size."""
-    state = 8 * int(n) * int(n_b or 0)
+STATE_BYTES_PER_PAIR = {1: 32, 2: 8, 3: 20}   # general, level, distance kernels
+
+
+def l2_note(n, n_b, path=None):
+    """How the timed steps relate to the L2: the kernel family's state per
+    (source, vertex) pair (the smallest, 8 bytes, when the family is not
+    known) times n * n_b, against the L2 size."""
+    state = STATE_BYTES_PER_PAIR.get(path, 8) * int(n) * int(n_b or 0)
     if state > 2 * L2_BYTES:
         return "state much larger than L2 (no flush)"
     return f"state of {state / 2**20:.0f} MB may stay in L2 (no flush: a probe, not a bench line)"
 
 
-def config_of(args, g, nsrc, n_b):
+def config_of(args, g, nsrc, n_b, path=None):
     return {"workload": WORKLOADS[args.workload]["desc"], "name": args.workload, "n": g.n, "nnz": g.nnz,
             "m": g.m, "sources": nsrc, "n_b": n_b, "parallelism": f"sources sharded x{args.gpus}",
-            "l2": l2_note(g.n, n_b if n_b else min(nsrc, 1024))}   # the reference arm has no n_b
+            "l2": l2_note(g.n, n_b if n_b else min(nsrc, 1024), path)}   # the reference arm has no n_b
 
 
 def main():
@@ -439,7 +443,7 @@ def main():
             "metric": "BC GTEPS", "value": value, "unit": "GTEPS", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t / args.steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": config_of(args, g, len(srcs), prof_bytes["n_b"]),
+            "config": config_of(args, g, len(srcs), prof_bytes["n_b"], prof_bytes.get("path")),
             "clocks": clk,
             "e2e": {"value": e2e, "unit": "GTEPS", "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(hl.nbytes)},

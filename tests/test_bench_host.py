@@ -55,6 +55,9 @@ def test_model_roofline_terms_on_a_small_graph():
 def test_l2_note_follows_the_state_size():
     assert bench.l2_note(1 << 22, 1024).startswith("state much larger than L2")
     assert "may stay in L2" in bench.l2_note(1 << 16, 64)
+    # the general kernels keep 32 bytes per pair: R-MAT 16 at n_b = 512 is 1 GiB
+    assert bench.l2_note(1 << 16, 512, path=1).startswith("state much larger than L2")
+    assert "may stay in L2" in bench.l2_note(1 << 16, 512)
 
 
 def test_grid_workload_shape():
