@@ -63,3 +63,26 @@ def test_sample_sources():
     assert np.array_equal(s, gg.sample_sources(g, 100, seed=2))
     with pytest.raises(ValueError):
         gg.sample_sources(g, g.n + 1)
+
+
+def test_grid_is_four_neighbour_with_the_weight_range():
+    L = 20
+    g = gg.grid2d(L, weights=(1, 16), seed=1)
+    assert g.n == L * L and g.nnz == 2 * 2 * L * (L - 1)          # 2L(L-1) edges, both arcs
+    deg = g.out_degree()
+    assert deg.min() == 2 and deg.max() == 4 and np.sum(deg == 2) == 4
+    src = np.repeat(np.arange(g.n), np.diff(g.rowptr))
+    dx = np.abs(src % L - g.col % L)
+    dy = np.abs(src // L - g.col // L)
+    assert np.all(dx + dy == 1)                                      # only lattice neighbours
+    assert g.w.min() == 1 and g.w.max() == 16
+    assert len(np.unique(g.w)) == 16                                 # every weight occurs
+
+
+def test_dense_er_degree_spread_suits_the_distance_kernels():
+    # the automatic choice takes the distance kernels when no degree exceeds
+    # max(64, 4x the average): true of uniform random graphs, false of R-MAT
+    er = gg.erdos_renyi(1 << 12, 256, weights=(1, 100), seed=1)
+    assert er.out_degree().max() <= 4 * er.nnz / er.n
+    rm = gg.rmat(12, 16, directed=True, weights=(1, 255), seed=1)
+    assert rm.out_degree().max() > max(64, 4 * rm.nnz / rm.n)
