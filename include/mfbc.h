@@ -85,14 +85,17 @@ typedef struct {
   uint64_t launches;
   double ms;
   double bytes;
-} mfbc_kernel_stat;
+} mfbc_kernel_stat;              /* launches counts kernels, also those run inside the
+                                     CUDA graphs of the distance kernels' forward steps */
 
 typedef struct {
   int32_t nkernels;
   mfbc_kernel_stat k[MFBC_MAX_KSTATS];
   uint64_t batches;
-  uint64_t fwd_iters;          /* MFBF products over all batches */
-  uint64_t bwd_iters;          /* MFBr products over all batches */
+  uint64_t fwd_iters;          /* MFBF products over all batches (distance kernels: distance
+                                  steps, including those that settle no pair) */
+  uint64_t bwd_iters;          /* MFBr products over all batches (distance kernels: steps that
+                                  settled pairs, distance 0 excepted) */
   int32_t n_b;                 /* batch width used */
   int32_t path;                /* MFBC_PATH_GENERAL, MFBC_PATH_LEVEL or MFBC_PATH_DIST */
   uint64_t stat[4];            /* with MFBC_OPT_COUNT_BYTES, level kernels: (neighbour, word)
