@@ -21,10 +21,18 @@ Printed JSON line (rank 0):
               steps), against the measured HBM copy bandwidth;
   cpu_baseline  the CPU oracle (plain C Brandes) on a bounded sample of the
               same workload on all host cores, rank 0 only.
-Multi-GPU (torchrun): each rank runs its own sample of sources (weak scaling)
-and lambda is summed across ranks with one all-reduce per step.
-The state (n x n_b x 8 bytes and more) is far larger than the 129 MB L2, so no
-explicit L2 flush is done between steps.
+  workloads   the other benchmark configurations (Erdos-Renyi n=1024 all
+              sources; weighted directed R-MAT 16; Erdos-Renyi n=2^20 k=32;
+              dense weighted Erdos-Renyi n=2^16 k=1024 on its first 4096
+              sources), one short measurement each with its own roofline
+              and oracle baseline (all cores and one thread).
+Multi-GPU (torchrun): each rank runs its own sample of sources (weak scaling),
+or with --shard one contiguous part of the same list (strong scaling); lambda
+is summed across ranks with one all-reduce per step.
+The headline state (n x n_b x 8 bytes and more) is far larger than the 129 MB
+L2, so no explicit L2 flush is done between its steps; configurations whose
+state could stay in L2 are timed step by step with an L2-sized buffer
+overwritten between steps.
 """
 from __future__ import annotations
 
@@ -45,6 +53,8 @@ sys.path.insert(0, ROOT)
 WORKLOADS = {
     "rmat22": dict(kind="rmat", scale=22, ef=16, nsrc=16384,
                    desc="R-MAT scale 22, edge factor 16, undirected, unweighted, 16384 sampled sources"),
+    "er1024": dict(kind="er1024", nsrc=1024,
+                   desc="Erdos-Renyi n=1024, k=8, undirected, unweighted, all 1024 sources, n_b=128"),
     "rmat20": dict(kind="rmat", scale=20, ef=16, nsrc=4096,
                    desc="R-MAT scale 20, edge factor 16, undirected, unweighted, 4096 sampled sources (profiling size)"),
     "er20k32": dict(kind="er", n=1 << 20, k=32, nsrc=16384,
@@ -65,6 +75,9 @@ def make_workload(name, rank=0):
         g = gg.rmat(w["scale"], w["ef"], seed=1)
     elif w["kind"] == "er":
         g = gg.erdos_renyi(w["n"], w["k"], seed=1)
+    elif w["kind"] == "er1024":
+        g = gg.erdos_renyi(1024, 8, seed=1)
+        return g, np.arange(g.n, dtype=np.int32)          # all-source exact BC
     elif w["kind"] == "er16k1024w":
         g = gg.erdos_renyi(1 << 16, 1024, weights=(1, 100), seed=1)
         return g, np.arange(g.n, dtype=np.int32)          # all-source exact BC
@@ -99,9 +112,13 @@ def traffic_per_launch(workload, kernel, alg_bytes):
     return t["per_alg_byte"] * alg_bytes
 
 
-def model_roofline(g, srcs, prof_bytes, step_s, peak_gbs):
-    """Whole-step roofline of the traffic model for MFBF + counters + MFBr + lambda
-    (unweighted graphs, 4-byte arcs): per step
+def survey_model(g, srcs, prof_bytes, step_s, peak_gbs):
+    """The survey's per-TEP byte model for MFBF + counters + MFBr + lambda
+    (unweighted graphs, 4-byte arcs).  It is an algorithmic-byte model of the
+    paper's products with stored distances and counters, not a ceiling of the
+    level kernels: those replace the 4-byte distance check per arc visit by
+    frontier bit rows shared by 32 columns per word and keep no counters, so
+    a run can exceed the model's rate (`measured_over_model` > 1).  Per step
       B_fwd = 12 R + 4 F + 16 D + 24 G,  B_cnt = 4 R + 4 nnz + 4 F + 8 D,
       B_bwd = 12 R + 4 F + 24 D,         B_acc = 16 R + 16 n,
     with R reachable (source, vertex) pairs, F arc visits from reachable pairs
@@ -126,8 +143,9 @@ def model_roofline(g, srcs, prof_bytes, step_s, peak_gbs):
         + (16 * R + 16 * g.n)
     teps = len(srcs) * g.m
     at_peak = peak_gbs * 1e9 / (total / teps) / 1e9
-    return {"bytes_per_step": total, "bytes_per_tep": total / teps, "gteps_at_peak": at_peak,
-            "frac": (total / (peak_gbs * 1e9)) / step_s, "reachable_pairs": R, "arc_visits": F, "tight_arcs": D}
+    return {"bytes_per_step": total, "bytes_per_tep": total / teps, "gteps_if_model_bytes_at_peak": at_peak,
+            "measured_over_model": (total / (peak_gbs * 1e9)) / step_s, "reachable_pairs": R, "arc_visits": F,
+            "tight_arcs": D}
 
 
 SERVE_POOL = "resident graphs R-MAT 16/18/20 (edge factor 16, undirected), Erdos-Renyi n=2^16 k=16, " \
@@ -252,8 +270,9 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def cpu_baseline(g, srcs, budget_s=15.0):
-    """The oracle as it stands, on all host cores, on a bounded sample of sources."""
+def cpu_baseline(g, srcs, budget_s=15.0, single_budget_s=5.0):
+    """The oracle as it stands on a bounded sample of sources: on all host
+    cores (the line's value) and on one thread (single_thread)."""
     import oracle
     nth = oracle.default_threads()
     k = max(nth, 1)
@@ -267,8 +286,19 @@ def cpu_baseline(g, srcs, budget_s=15.0):
         oracle.bc(g, srcs[:k2], nthreads=nth)
         dt = time.perf_counter() - t0
         k = k2
-    return {"value": k * g.m / dt / 1e9, "unit": "GTEPS", "cores": nth, "kind": "oracle",
-            "sample": f"first {k} of the {len(srcs)} sources, {dt:.1f} s"}
+    out = {"value": k * g.m / dt / 1e9, "unit": "GTEPS", "cores": nth, "kind": "oracle",
+           "sample": f"first {k} of the {len(srcs)} sources, {dt:.1f} s"}
+    t0 = time.perf_counter()
+    oracle.bc(g, srcs[:1], nthreads=1)
+    d1 = time.perf_counter() - t0
+    k1 = int(min(len(srcs), max(1, single_budget_s / max(d1, 1e-6))))
+    if k1 > 1:
+        t0 = time.perf_counter()
+        oracle.bc(g, srcs[:k1], nthreads=1)
+        d1 = time.perf_counter() - t0
+    out["single_thread"] = {"value": k1 * g.m / d1 / 1e9, "unit": "GTEPS", "cores": 1,
+                            "sample": f"first {k1} of the {len(srcs)} sources, {d1:.1f} s"}
+    return out
 
 
 def run_reference(args):
@@ -289,8 +319,8 @@ def run_reference(args):
     val = args.steps * per_step * g.m / dt / 1e9
     line = {"impl": "reference", "metric": "BC GTEPS", "value": val, "unit": "GTEPS", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": config_of(args, g, len(srcs), None),
+            "higher_is_better": True, "scaling": "strong" if args.shard else "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic", "config": config_of(args, g, len(srcs), None),
             "cpu_baseline": {"value": val, "unit": "GTEPS", "cores": nth, "kind": "oracle",
                              "sample": f"{per_step} sources per step of the {len(srcs)}-source workload"},
             "e2e": {"value": val, "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -313,10 +343,100 @@ def l2_note(n, n_b, path=None):
     return f"state of {state / 2**20:.0f} MB may stay in L2 (no flush: a probe, not a bench line)"
 
 
+def needs_flush(n, n_b, path):
+    return STATE_BYTES_PER_PAIR.get(path, 8) * int(n) * int(n_b or 0) <= 2 * L2_BYTES
+
+
 def config_of(args, g, nsrc, n_b, path=None):
+    par = f"one source list sharded x{args.gpus}" if args.shard else f"sources sampled per rank x{args.gpus}"
     return {"workload": WORKLOADS[args.workload]["desc"], "name": args.workload, "n": g.n, "nnz": g.nnz,
-            "m": g.m, "sources": nsrc, "n_b": n_b, "parallelism": f"sources sharded x{args.gpus}",
+            "m": g.m, "sources": nsrc, "n_b": n_b, "parallelism": par,
             "l2": l2_note(g.n, n_b if n_b else min(nsrc, 1024), path)}   # the reference arm has no n_b
+
+
+DTYPE = {1: "f64 (sigma, zeta, lambda)", 2: "u64 sigma / fp32x2 zeta / f64 lambda", 3: "f64 (sigma, zeta, lambda)"}
+
+
+def roofline_of(kstats, prof_bytes, peak, peak_kind, workload, step_s):
+    """Dominant kernel's algorithmic bytes per launch over its mean launch time,
+    plus the whole step: every kernel's device-counted bytes over the step time."""
+    dom = max(kstats.items(), key=lambda kv: kv[1]["ms"])[0]
+    kb = prof_bytes["kernels"].get(dom, {})
+    per_launch_bytes = kb.get("bytes", 0.0) / max(kb.get("launches", 1), 1)
+    avg_ms = kstats[dom]["ms"] / kstats[dom]["launches"]
+    achieved = per_launch_bytes / (avg_ms / 1e3) / 1e9 if avg_ms > 0 else 0.0
+    step_bytes = sum(v.get("bytes", 0.0) for v in prof_bytes["kernels"].values())
+    traffic = {}
+    for k, v in prof_bytes["kernels"].items():
+        t = traffic_per_launch(workload, k, v.get("bytes", 0.0) / max(v.get("launches", 1), 1))
+        if t is not None:
+            traffic[k] = t
+    roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
+            "peak_kind": f"{peak_kind} copy bandwidth", "unit": "GB/s", "frac": achieved / peak,
+            "traffic": traffic.get(dom), "bytes_per_launch": per_launch_bytes, "avg_launch_ms": avg_ms,
+            "whole_step": {"bytes": step_bytes, "achieved": step_bytes / step_s / 1e9,
+                           "frac": step_bytes / step_s / 1e9 / peak}}
+    if len(traffic) > 1 or (traffic and dom not in traffic):
+        roof["traffic_other_kernels"] = {k: v for k, v in traffic.items() if k != dom}
+    return roof
+
+
+def time_steps(step, steps, stream, flush=None):
+    """K timed steps with CUDA events on the launching stream; with flush, an
+    L2-sized buffer is overwritten between steps (outside the timed spans)."""
+    import torch
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    kstats = {}
+    for a, b in ev:
+        if flush is not None:
+            flush.fill_(1)
+        a.record(stream)
+        prof = step()
+        b.record(stream)
+        for k, v in prof["kernels"].items():
+            x = kstats.setdefault(k, {"launches": 0, "ms": 0.0})
+            x["launches"] += v["launches"]
+            x["ms"] += v["ms"]
+    torch.cuda.synchronize()
+    return sum(a.elapsed_time(b) for a, b in ev) / 1e3, kstats
+
+
+# The benchmark configurations besides the headline, one short measurement
+# each on the default run (name, batch width, timed steps, source cap).
+EXTRA_WORKLOADS = [("er1024", 128, 20, None), ("rmat16w", 512, 2, None), ("er20k32", 0, 1, None),
+                   ("er16k1024w", 0, 1, 4096)]
+
+
+def extra_workload(name, n_b, steps, cap, peak, peak_kind, args):
+    """One configuration: untimed byte-counting pass, one warm-up step, then
+    `steps` timed steps (L2 flushed between steps when the state could stay
+    in L2), its roofline and the oracle on the host cores."""
+    import torch
+    import paper_1609_07008_gb300 as mfbc
+    g, srcs = make_workload(name)
+    if cap:
+        srcs = srcs[:cap]
+    G = mfbc.Graph.from_csr(g)
+    d_src = torch.from_numpy(srcs).cuda()
+    lam = torch.empty(g.n, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+    _, prof_bytes = G.bc(d_src, n_b=n_b, out=lam, count_bytes=True)
+    G.bc(d_src, n_b=n_b, out=lam)
+    flush = torch.empty(2 * L2_BYTES, dtype=torch.uint8, device="cuda") \
+        if needs_flush(g.n, prof_bytes["n_b"], prof_bytes["path"]) else None
+    t, kstats = time_steps(lambda: G.bc(d_src, n_b=n_b, out=lam, profile=True)[1], steps, stream, flush)
+    G.close()
+    del flush
+    torch.cuda.empty_cache()
+    desc = WORKLOADS[name]["desc"] + (f" (first {cap} of them)" if cap else "")
+    return {"value": steps * len(srcs) * g.m / t / 1e9, "unit": "GTEPS", "steps": steps,
+            "ms_per_step": t / steps * 1e3, "dtype": DTYPE.get(prof_bytes["path"], "f64"),
+            "config": {"workload": desc, "name": name, "n": g.n, "nnz": g.nnz, "m": g.m, "sources": len(srcs),
+                       "n_b": prof_bytes["n_b"], "path": prof_bytes["path"],
+                       "l2": "L2 flushed between steps (2x L2 buffer written)" if flush is not None
+                       else l2_note(g.n, prof_bytes["n_b"], prof_bytes["path"])},
+            "roofline": roofline_of(kstats, prof_bytes, peak, peak_kind, name, t / steps),
+            "cpu_baseline": None if args.no_cpu_baseline else cpu_baseline(g, srcs, budget_s=4.0, single_budget_s=2.0)}
 
 
 def main():
@@ -329,8 +449,11 @@ def main():
     ap.add_argument("--n-b", type=int, default=0)
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--ref-sources", type=int, default=64)
+    ap.add_argument("--shard", action="store_true",
+                    help="split the one source list across ranks (strong scaling) instead of a sample per rank")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
+    ap.add_argument("--no-workloads", action="store_true", help="skip the other benchmark configurations")
     ap.add_argument("--sources", type=int, default=0, help="use only the first N sources (probing)")
     ap.add_argument("--keep-order", action="store_true", help="batch sources in the given order")
     args = ap.parse_args()
@@ -340,6 +463,7 @@ def main():
     import torch
     import paper_1609_07008_gb300 as mfbc
     from paper_1609_07008_gb300 import build as mbuild
+    from paper_1609_07008_gb300.shard import shard_sources
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -357,12 +481,14 @@ def main():
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
 
-    g, srcs = make_workload(args.workload, rank)
+    # weak scaling: every rank its own sample; --shard: one list split across ranks
+    g, srcs_all = make_workload(args.workload, 0 if args.shard else rank)
     if args.sources:
-        srcs = srcs[:args.sources]
+        srcs_all = srcs_all[:args.sources]
+    srcs = shard_sources(srcs_all, rank, world) if args.shard else srcs_all
     nb_req = args.n_b or (512 if args.workload == "rmat16w" else 0)
     G = mfbc.Graph.from_csr(g)
-    d_src = torch.from_numpy(srcs).to(dev)
+    d_src = torch.from_numpy(np.ascontiguousarray(srcs)).to(dev)
     lam = torch.empty(g.n, dtype=torch.float64, device=dev)
 
     def step(profile=False):
@@ -401,14 +527,15 @@ def main():
         tt = torch.tensor([t], dtype=torch.float64, device=dev)
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         t = float(tt.item())
-    units = args.steps * len(srcs) * g.m * world
+    total_sources = len(srcs_all) if args.shard else len(srcs_all) * world
+    units = args.steps * total_sources * g.m
     value = units / t / 1e9
 
     # end to end through the host-buffer C ABI
     rp = torch.from_numpy(g.rowptr).pin_memory().numpy()
     cl = torch.from_numpy(g.col).pin_memory().numpy()
     wt = torch.from_numpy(g.w).pin_memory().numpy() if g.w is not None else None
-    hs = torch.from_numpy(srcs).pin_memory().numpy()
+    hs = torch.from_numpy(np.ascontiguousarray(srcs)).pin_memory().numpy()
     hl = torch.empty(g.n, dtype=torch.float64).pin_memory().numpy()
     h2d = rp.nbytes + cl.nbytes + hs.nbytes + (wt.nbytes if wt is not None else 0)
     G.close()
@@ -429,35 +556,31 @@ def main():
         tt = torch.tensor([te], dtype=torch.float64, device=dev)
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         te = float(tt.item())
-    e2e = args.e2e_steps * len(srcs) * g.m * world / te / 1e9 if args.e2e_steps else None
+    e2e = args.e2e_steps * total_sources * g.m / te / 1e9 if args.e2e_steps else None
 
     if rank == 0:
         peak, peak_kind = load_peaks()
-        dom = max(kstats.items(), key=lambda kv: kv[1]["ms"])[0]
-        kb = prof_bytes["kernels"].get(dom, {})
-        per_launch_bytes = kb.get("bytes", 0.0) / max(kb.get("launches", 1), 1)
-        avg_ms = kstats[dom]["ms"] / kstats[dom]["launches"]
-        achieved = per_launch_bytes / (avg_ms / 1e3) / 1e9 if avg_ms > 0 else 0.0
         launches = sum(v["launches"] for v in kstats.values())
         line = {
             "metric": "BC GTEPS", "value": value, "unit": "GTEPS", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t / args.steps * 1e3, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": config_of(args, g, len(srcs), prof_bytes["n_b"], prof_bytes.get("path")),
+            "scaling": "strong" if args.shard else "weak", "vs_baseline": None,
+            "dtype": DTYPE.get(prof_bytes.get("path"), "f64"), "data": "synthetic",
+            "config": config_of(args, g, total_sources, prof_bytes["n_b"], prof_bytes.get("path")),
             "clocks": clk,
             "e2e": {"value": e2e, "unit": "GTEPS", "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(hl.nbytes)},
             "gpu_launches": int(launches),
-            "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
-                         "peak_kind": f"{peak_kind} copy bandwidth", "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": traffic_per_launch(args.workload, dom, per_launch_bytes),
-                         "bytes_per_launch": per_launch_bytes, "avg_launch_ms": avg_ms},
-            "model_roofline": model_roofline(g, srcs, prof_bytes, t / args.steps, peak),
+            "roofline": roofline_of(kstats, prof_bytes, peak, peak_kind, args.workload, t / args.steps),
+            "survey_model": survey_model(g, srcs, prof_bytes, t / args.steps, peak),
             "gather_stats": {k: prof_bytes.get(k) for k in ("pairs_fwd", "pairs_bwd", "values_fwd", "values_bwd",
                                                             "fwd_iters", "bwd_iters", "batches")},
             "kernels_ms_share": {k: round(v["ms"] / sum(x["ms"] for x in kstats.values()), 4)
                                  for k, v in sorted(kstats.items(), key=lambda kv: -kv[1]["ms"])},
         }
+        if world == 1 and not args.no_workloads:
+            line["workloads"] = {name: extra_workload(name, nb, k, cap, peak, peak_kind, args)
+                                 for name, nb, k, cap in EXTRA_WORKLOADS}
         if world == 1 and not args.no_serve:
             line["serving"] = serving_bench()
         if world == 1 and not args.no_cpu_baseline:

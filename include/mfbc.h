@@ -15,10 +15,11 @@
  *         over batches of sources.
  *
  * Conventions shared by every call
- *  - Graphs are CSR over the adjacency matrix A of Sec. 2.1: row v lists the
- *    arcs v -> col[k] with integer weight w[k] >= 1 (w == NULL: every arc
- *    weighs 1).  Vertex ids are 0..n-1.  Rows must be sorted by column with
- *    no duplicate arcs and no self-loops.
+ *  - Graphs are compressed rows of the adjacency matrix A of Sec. 2.1 (CSR:
+ *    row v lists the arcs v -> col[k]) or of its transpose (CSC: row v lists
+ *    the arcs col[k] -> v), with integer weights w[k] >= 1 (w == NULL: every
+ *    arc weighs 1).  Vertex ids are 0..n-1.  Rows must be sorted by column
+ *    with no duplicate arcs and no self-loops.
  *  - Distances are int32 with INT32_MAX meaning "unreachable" (the infinity
  *    of Sec. 2.1); path multiplicities and centralities are IEEE FP64.
  *    Multiplicities are exact integers while below 2^53.
@@ -56,9 +57,13 @@ typedef enum {
   MFBC_ERR_TIMEOUT = 6         /* reserved: a bounded device-side wait gave up */
 } mfbc_status;
 
-/* mfbc_graph_create flags */
+/* mfbc_graph_create flags: bit 0 = orientation of the arrays, bit 1 = symmetry */
+#define MFBC_CSR        0u     /* row v of the arrays lists the out-arcs v -> col[k]: the adjacency
+                                  matrix A itself, A(v, col[k]) = w[k] (Sec. 2.1) */
+#define MFBC_CSC        1u     /* row v lists the in-arcs col[k] -> v: the arrays hold A^T, the
+                                  operand of Algorithm 2's products (Sec. 4.2); A is built from it */
 #define MFBC_DIRECTED   0u
-#define MFBC_UNDIRECTED 1u     /* A is symmetric with symmetric weights (checked) */
+#define MFBC_UNDIRECTED 2u     /* A is symmetric with symmetric weights (checked) */
 
 /* bits written to *mfbc_options.warn_out */
 #define MFBC_WARN_SIGMA_INEXACT 1u  /* some sigma_bar >= 2^53: FP64 counts may be rounded */
@@ -118,20 +123,32 @@ typedef struct {
 #define MFBC_OPT_COUNT_BYTES 1u  /* with profile: count algorithmic bytes on the device (slower) */
 #define MFBC_OPT_KEEP_ORDER  2u  /* mfbc_bc*: batch the sources in the given order (see below) */
 
-/* Build a device-resident graph from HOST CSR arrays (Sec. 2.1: A(i,j) = w(i,j)
- * for (i,j) in E; the paper's Tensor::write of the input, Sec. 6.1).
+/* Build a device-resident graph from HOST compressed-row arrays (Sec. 2.1:
+ * A(i,j) = w(i,j) for (i,j) in E; the paper's Tensor::write of the input,
+ * Sec. 6.1).
  *   n       vertices (0 <= n < 2^31);  nnz = rowptr[n] arcs
  *   rowptr  int64[n+1], col int32[nnz], w int32[nnz] or NULL (unweighted)
- *   flags   MFBC_DIRECTED or MFBC_UNDIRECTED
- *   stream  cudaStream_t or NULL; the call is complete on return
- * The arrays are copied; the transposed adjacency needed by MFBr (A^T in
- * Algorithm 2) is built for directed graphs.  Returns INVALID for unsorted
- * or out-of-range columns, duplicates, self-loops, weights < 1, or an
- * asymmetric UNDIRECTED graph; OVERFLOW if (n-1)*max_w + max_w >= 2^31-1. */
+ *   flags   (MFBC_CSR or MFBC_CSC) | (MFBC_DIRECTED or MFBC_UNDIRECTED).
+ *           MFBC_CSR: the arrays are the rows of A (out-arcs); MFBC_CSC: they
+ *           are the rows of A^T (row v lists the tails u of the arcs u -> v,
+ *           with their weights).  Both describe the same graph; for an
+ *           UNDIRECTED graph A = A^T and the two are the same arrays.
+ *   stream  cudaStream_t or NULL; the construction (copies, validation
+ *           kernels) is queued on it, and the call is complete on return.
+ *           The paper's interface has no stream; it lets a caller keep the
+ *           upload off the legacy default stream.
+ * The arrays are copied; the library keeps both A and A^T (Algorithm 1's
+ * products read in-arcs, Algorithm 2's out-arcs), building the one not given
+ * (for directed graphs) by a stable counting sort, so rows stay sorted and the
+ * result does not depend on the orientation passed.  Returns INVALID for
+ * unsorted or out-of-range columns, duplicates, self-loops, weights < 1, an
+ * asymmetric UNDIRECTED graph or unknown flag bits; OVERFLOW if
+ * (n-1)*max_w + max_w >= 2^31-1. */
 mfbc_status mfbc_graph_create(int32_t n, int64_t nnz, const int64_t* rowptr, const int32_t* col,
                               const int32_t* w, uint32_t flags, void* stream, mfbc_graph** out);
 
-/* Same as mfbc_graph_create, from DEVICE arrays (copied; caller keeps ownership). */
+/* Same as mfbc_graph_create (either orientation), from DEVICE arrays (copied;
+ * caller keeps ownership). */
 mfbc_status mfbc_graph_create_device(int32_t n, int64_t nnz, const int64_t* rowptr,
                                      const int32_t* col, const int32_t* w, uint32_t flags,
                                      void* stream, mfbc_graph** out);
@@ -247,10 +264,12 @@ mfbc_status mfbc_workspace_size(const mfbc_graph* g, int32_t nsrc, int32_t mode,
  * mfbc_static_max_vertices() vertices are rejected with MFBC_ERR_INVALID.
  * All calls share the array and it keeps the last call's contents (each call
  * clears what must start at zero); calls that overlap on the GPU race.  The
- * call returns once lambda_out is complete on the stream. */
+ * call returns once lambda_out is complete on the stream.  warn_out (HOST,
+ * may be NULL) receives the same MFBC_WARN_* bits as mfbc_options.warn_out:
+ * MFBC_WARN_SIGMA_INEXACT when some sigma_bar reached 2^53. */
 #define MFBC_STATIC_SCRATCH_BYTES (32u << 20)
 mfbc_status mfbc_bc_static(const mfbc_graph* g, const int32_t* sources, int32_t nsrc,
-                           double* lambda_out, void* stream);
+                           double* lambda_out, void* stream, uint32_t* warn_out);
 
 /* Largest vertex count mfbc_bc_static accepts. */
 uint64_t mfbc_static_max_vertices(void);

@@ -28,8 +28,10 @@ MFBC_ERR_CUDA = 3
 MFBC_ERR_OVERFLOW = 4
 MFBC_ERR_NO_CONVERGENCE = 5
 MFBC_ERR_TIMEOUT = 6
+MFBC_CSR = 0
+MFBC_CSC = 1
 MFBC_DIRECTED = 0
-MFBC_UNDIRECTED = 1
+MFBC_UNDIRECTED = 2
 MFBC_WARN_SIGMA_INEXACT = 1
 PATH_AUTO, PATH_GENERAL, PATH_LEVEL, PATH_DIST = 0, 1, 2, 3
 MFBC_OPT_COUNT_BYTES = 1
@@ -184,12 +186,14 @@ class Graph:
     """A device-resident graph (CSR of the adjacency matrix A, Sec. 2.1).
 
     rowptr/col/w are numpy arrays (host) or torch CUDA tensors (device);
-    w None means unit weights.  directed=False asserts A is symmetric."""
+    w None means unit weights.  directed=False asserts A is symmetric.
+    csc=True: the arrays are the rows of A^T (row v lists the tails of the
+    arcs into v) instead of the rows of A."""
 
-    def __init__(self, rowptr, col, w=None, *, directed: bool, stream=None):
+    def __init__(self, rowptr, col, w=None, *, directed: bool, stream=None, csc: bool = False):
         lib = load()
         self._h = ctypes.c_void_p()
-        flags = MFBC_DIRECTED if directed else MFBC_UNDIRECTED
+        flags = (MFBC_DIRECTED if directed else MFBC_UNDIRECTED) | (MFBC_CSC if csc else MFBC_CSR)
         if _is_torch(rowptr):
             n = rowptr.numel() - 1
             nnz = col.numel()

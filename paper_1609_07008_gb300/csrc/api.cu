@@ -51,8 +51,49 @@ extern "C" const char* mfbc_last_error(void) { return t_err.c_str(); }
 extern "C" const char* mfbc_version(void) { return "mfbc-gb300 0.1 (sm_103a)"; }
 
 // ------------------------------------------------------------------ graphs
+// Arrays given in CSC orientation hold the rows of A^T (row v lists the tails
+// of the arcs into v).  For a directed graph they are checked as rows
+// (row pointers, column range, strictly increasing columns: the checks that
+// the transposition itself relies on) and turned into the rows of A by a
+// stable counting sort, which leaves every row of A sorted; graph_build then
+// validates A as usual.  An undirected A equals A^T: nothing to do.
+static mfbc_status csc_to_csr(int32_t n, int64_t nnz, const int64_t* rp, const int32_t* col, const int32_t* w,
+                              std::vector<int64_t>& orp, std::vector<int32_t>& ocol, std::vector<int32_t>& ow) {
+  for (int32_t v = 0; v < n; v++)
+    if (rp[v + 1] < rp[v] || rp[v + 1] > nnz)
+      return fail(MFBC_ERR_INVALID, "rowptr must start at 0, be non-decreasing and end at nnz");
+  orp.assign((size_t)n + 1, 0);
+  for (int32_t v = 0; v < n; v++)
+    for (int64_t k = rp[v]; k < rp[v + 1]; k++) {
+      const int32_t u = col[k];
+      if (u < 0 || u >= n) return fail(MFBC_ERR_INVALID, "column index out of range [0, n)");
+      if (k > rp[v] && col[k - 1] >= u) return fail(MFBC_ERR_INVALID, "rows must be sorted by column without duplicate arcs");
+      orp[(size_t)u + 1]++;
+    }
+  for (int32_t u = 0; u < n; u++) orp[(size_t)u + 1] += orp[(size_t)u];
+  ocol.resize((size_t)nnz);
+  if (w) ow.resize((size_t)nnz);
+  std::vector<int64_t> pos(orp.begin(), orp.end() - 1);
+  for (int32_t v = 0; v < n; v++)            // rows of A^T in order: each row of A receives its heads sorted
+    for (int64_t k = rp[v]; k < rp[v + 1]; k++) {
+      const int64_t p = pos[(size_t)col[k]]++;
+      ocol[(size_t)p] = v;
+      if (w) ow[(size_t)p] = w[k];
+    }
+  return MFBC_OK;
+}
+
 static mfbc_status create_common(int32_t n, int64_t nnz, const int64_t* rowptr, const int32_t* col,
                                  const int32_t* w, uint32_t flags, void* stream, mfbc_graph** out) {
+  std::vector<int64_t> trp;
+  std::vector<int32_t> tcol, tw;
+  if ((flags & MFBC_CSC) && !(flags & MFBC_UNDIRECTED)) {
+    mfbc_status s = csc_to_csr(n, nnz, rowptr, col, w, trp, tcol, tw);
+    if (s) return s;
+    rowptr = trp.data();
+    col = tcol.data();
+    w = w ? tw.data() : nullptr;
+  }
   auto* G = new (std::nothrow) mfbc_graph();
   if (!G) return fail(MFBC_ERR_OOM, "host allocation of the graph handle failed");
   std::string err;
@@ -82,7 +123,7 @@ static mfbc_status check_create_args(int32_t n, int64_t nnz, const void* rowptr,
   if (nnz < 0) return fail(MFBC_ERR_INVALID, "nnz must be >= 0");
   if (!rowptr) return fail(MFBC_ERR_INVALID, "rowptr must not be NULL");
   if (nnz > 0 && !col) return fail(MFBC_ERR_INVALID, "col must not be NULL when nnz > 0");
-  if (flags & ~1u) return fail(MFBC_ERR_INVALID, "unknown flag bits");
+  if (flags & ~(MFBC_CSC | MFBC_UNDIRECTED)) return fail(MFBC_ERR_INVALID, "unknown flag bits");
   return MFBC_OK;
 }
 
@@ -551,7 +592,7 @@ mfbc_status run(mfbc_graph* G, const int32_t* d_src, int32_t nsrc, int mode, dou
         MFBC_CUDA_TRY(cudaMemcpyAsync(G->h_ctr, &ds.ctr->flags, sizeof(uint32_t), cudaMemcpyDeviceToHost, R.st),
                       &R.err);
         MFBC_CUDA_TRY(cudaStreamSynchronize(R.st), &R.err);
-        if (G->h_ctr[0] & 2u) warn |= MFBC_WARN_SIGMA_INEXACT;
+        if (G->h_ctr[0] & FLAG_SIGMA_INEXACT) warn |= MFBC_WARN_SIGMA_INEXACT;
       }
     }
     if (P.path == MFBC_PATH_GENERAL || fallback) {
@@ -584,7 +625,7 @@ mfbc_status run(mfbc_graph* G, const int32_t* d_src, int32_t nsrc, int mode, dou
         }
         MFBC_CUDA_TRY(cudaMemcpyAsync(G->h_ctr, &gp->ctr->flags, sizeof(uint32_t), cudaMemcpyDeviceToHost, R.st), &R.err);
         MFBC_CUDA_TRY(cudaStreamSynchronize(R.st), &R.err);
-        if (G->h_ctr[0] & 2u) warn |= MFBC_WARN_SIGMA_INEXACT;
+        if (G->h_ctr[0] & FLAG_SIGMA_INEXACT) warn |= MFBC_WARN_SIGMA_INEXACT;
       }
       if (fallback && s == MFBC_OK) {
         // restore the level masks for the next batch
@@ -609,7 +650,7 @@ mfbc_status run(mfbc_graph* G, const int32_t* d_src, int32_t nsrc, int mode, dou
   }
   MFBC_CUDA_TRY(cudaMemcpyAsync(G->h_ctr, &ctr->flags, sizeof(uint32_t), cudaMemcpyDeviceToHost, R.st), &R.err);
   MFBC_CUDA_TRY(cudaStreamSynchronize(R.st), &R.err);
-  if (G->h_ctr[0] & 2u) warn |= MFBC_WARN_SIGMA_INEXACT;
+  if (G->h_ctr[0] & FLAG_SIGMA_INEXACT) warn |= MFBC_WARN_SIGMA_INEXACT;
   MFBC_CUDA_TRY(cudaGetLastError(), &R.err);
   if (R.opt && R.opt->warn_out) *R.opt->warn_out = warn;
   if (R.opt && R.opt->profile) finish_profile(R, R.opt->profile, batches, fi, bi, ctr);

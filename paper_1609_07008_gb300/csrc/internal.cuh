@@ -67,12 +67,18 @@ enum KId {
   K_LVL_FWD_G, K_LVL_BWD_G, K_LVL_SPLIT, K_DP_FWD, K_DP_BWD, K_NUM
 };
 
+// Bits of Counters::flags, set by kernels and read by the host drivers.
+constexpr uint32_t FLAG_LEVEL_LIST = 1u;     // level kernels: a per-level vertex list overflowed
+constexpr uint32_t FLAG_SIGMA_INEXACT = 2u;  // some sigma_bar >= 2^53 (FP64 output may be rounded)
+constexpr uint32_t FLAG_BAD_SOURCE = 4u;     // mfbc_bc_static: a source id outside [0, n)
+constexpr uint32_t FLAG_COUNT_WRAP = 8u;     // level kernels: a path count reached 2^58 (batch redone)
+
 // Device-side counters of algorithmic bytes, one slot per kernel id.
 struct Counters {
   unsigned long long bytes[K_NUM];
   unsigned long long stat[4];      // (counting pass) pairs fwd/bwd, gathered values fwd/bwd
   uint32_t list_count[4];          // frontier / touched list sizes
-  uint32_t flags;                  // bit0: level capacity exceeded, bit1: sigma >= 2^53
+  uint32_t flags;                  // FLAG_* bits
   uint32_t work[4];                // level kernels: pairs, segments, gather group counter, overflow
 };
 

@@ -434,7 +434,7 @@ __global__ void __launch_bounds__(LVL_WARPS * 32, MFBC_PAIR_MIN_BLOCKS) k_lvl_fw
     if ((int)lane < nnew) {
       const uint32_t pos = b + lane;
       if ((int64_t)pos < cap_n) list_n[pos] = sm.newv[lane];
-      else atomicOr(flags, 1u);
+      else atomicOr(flags, FLAG_LEVEL_LIST);
     }
     __syncwarp();
     nnew = 0;
@@ -677,8 +677,27 @@ __device__ __forceinline__ void stage_chunk(const uint4& myseg, int excl, int in
   __syncwarp();
 }
 
+// Gather load of one 32-byte sector (four columns of one vertex row of sv).
+//
+// The gathers read sv through the non-coherent path while other warps of the
+// same launch write sv.  This is correct because no element is both read and
+// written by one launch: the MFBF gather of level l reads sigma_bar of
+// level-l pairs and writes those of level-(l+1) pairs; the MFBr gather of
+// level l reads the values of level-(l+1) pairs and overwrites level-l pairs
+// (a pair has one level).  A loaded sector may still hold a column that the
+// launch writes (a vertex has columns at several levels), but the gathers use
+// only the columns named by the pair's mask, which are never written during
+// the launch; the stale copy of a written neighbour column is never consumed.
+// Building with -DMFBC_GATHER_NC=0 selects coherent loads (same result).
+#ifndef MFBC_GATHER_NC
+#define MFBC_GATHER_NC 1
+#endif
 __device__ __forceinline__ void ld4u(const uint64_t* p, uint64_t& a, uint64_t& b, uint64_t& c, uint64_t& d) {
+#if MFBC_GATHER_NC
   asm volatile("ld.global.nc.L1::no_allocate.v4.u64 {%0,%1,%2,%3}, [%4];" : "=l"(a), "=l"(b), "=l"(c), "=l"(d) : "l"(p));
+#else
+  asm volatile("ld.global.L1::no_allocate.v4.u64 {%0,%1,%2,%3}, [%4];" : "=l"(a), "=l"(b), "=l"(c), "=l"(d) : "l"(p));
+#endif
 }
 
 // Gather over a group of up to 32 segments (lane k holds segment k's header).
@@ -827,8 +846,8 @@ __global__ void __launch_bounds__(256, MFBC_GATHER_MIN_BLOCKS) k_lvl_fwd_gather(
       }
     });
   }
-  if (__any_sync(0xffffffffu, big != 0u) && lane == 0) atomicOr(flags, 2u);
-  if (__any_sync(0xffffffffu, ovf != 0u) && lane == 0) atomicOr(flags, 8u);
+  if (__any_sync(0xffffffffu, big != 0u) && lane == 0) atomicOr(flags, FLAG_SIGMA_INEXACT);
+  if (__any_sync(0xffffffffu, ovf != 0u) && lane == 0) atomicOr(flags, FLAG_COUNT_WRAP);
   if (COUNT) {
     for (int o = 16; o; o >>= 1) {
       nvals += __shfl_xor_sync(0xffffffffu, nvals, o);
@@ -1249,10 +1268,10 @@ mfbc_status level_batch(RunCtx& rc, LevelState& s, const int32_t* d_src_batch, i
     MFBC_CUDA_TRY(cudaMemcpyAsync(rc.h_ctr, s.ctr->list_count, sizeof(uint32_t) * 5, cudaMemcpyDeviceToHost, st), rc.err);
     MFBC_CUDA_TRY(cudaStreamSynchronize(st), rc.err);
     rc.prof->drain();
-    if (rc.h_ctr[4] & 9u) {
+    if (rc.h_ctr[4] & (FLAG_LEVEL_LIST | FLAG_COUNT_WRAP)) {
       // list capacity exceeded (bit 0) or a path count passed 2^64 (bit 3):
       // the general kernels redo this batch
-      k_clear_flag_bits<<<1, 1, 0, st>>>(&s.ctr->flags, 9u);
+      k_clear_flag_bits<<<1, 1, 0, st>>>(&s.ctr->flags, FLAG_LEVEL_LIST | FLAG_COUNT_WRAP);
       *levels_exceeded = true;
       level_reset(rc, s, l + 1);
       return MFBC_ERR_NO_CONVERGENCE;

@@ -55,7 +55,7 @@ static mfbc_status static_scratch_ptr(void** out, std::string* err) {
 
 __global__ void k_check_sources(const int32_t* __restrict__ src, int32_t nsrc, int32_t n, Counters* ctr) {
   int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < nsrc && (src[i] < 0 || src[i] >= n)) atomicOr(&ctr->flags, 4u);
+  if (i < nsrc && (src[i] < 0 || src[i] >= n)) atomicOr(&ctr->flags, FLAG_BAD_SOURCE);
 }
 
 }  // namespace mfbc
@@ -74,7 +74,8 @@ extern "C" uint64_t mfbc_static_max_vertices(void) {
 }
 
 extern "C" mfbc_status mfbc_bc_static(const mfbc_graph* G, const int32_t* sources, int32_t nsrc,
-                                      double* lambda_out, void* stream) {
+                                      double* lambda_out, void* stream, uint32_t* warn_out) {
+  if (warn_out) *warn_out = 0;
   if (!G) { set_last_error("graph must not be NULL"); return MFBC_ERR_INVALID; }
   if (nsrc < 0) { set_last_error("nsrc must be >= 0"); return MFBC_ERR_INVALID; }
   if (nsrc > 0 && !sources) { set_last_error("sources must not be NULL"); return MFBC_ERR_INVALID; }
@@ -112,16 +113,20 @@ extern "C" mfbc_status mfbc_bc_static(const mfbc_graph* G, const int32_t* source
       e = cudaMemcpyAsync(h_ctr, &gs.ctr->flags, sizeof(uint32_t), cudaMemcpyDeviceToHost, st);
       if (e == cudaSuccess) e = cudaStreamSynchronize(st);
       if (e != cudaSuccess) { s = cuda_fail(&err, "checking sources", e); break; }
-      if (h_ctr[0] & 4u) { s = MFBC_ERR_INVALID; err = "source id out of range"; break; }
+      if (h_ctr[0] & FLAG_BAD_SOURCE) { s = MFBC_ERR_INVALID; err = "source id out of range"; break; }
     }
     for (int32_t b0 = 0; b0 < nsrc && s == MFBC_OK; b0 += kStaticNb) {
       const int na = nsrc - b0 < kStaticNb ? nsrc - b0 : kStaticNb;
       s = general_batch(rc, gs, sources + b0, na, lambda_out, nullptr, nullptr);
     }
     if (s) break;
-    e = cudaStreamSynchronize(st);
+    // the general batches raise FLAG_SIGMA_INEXACT when a path count reaches
+    // 2^53; report it like mfbc_bc_device does through warn_out
+    e = cudaMemcpyAsync(h_ctr, &gs.ctr->flags, sizeof(uint32_t), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e == cudaSuccess) e = cudaGetLastError();
-    if (e != cudaSuccess) s = cuda_fail(&err, "mfbc_bc_static", e);
+    if (e != cudaSuccess) { s = cuda_fail(&err, "mfbc_bc_static", e); break; }
+    if (warn_out && (h_ctr[0] & FLAG_SIGMA_INEXACT)) *warn_out |= MFBC_WARN_SIGMA_INEXACT;
   } while (0);
   graph_unlock(G);
   if (s) { set_last_error(err.empty() ? mfbc_status_string(s) : err); cudaGetLastError(); }

@@ -41,7 +41,7 @@ __global__ void k_sigma_exact(const double* __restrict__ s, size_t count, Counte
   size_t stride = (size_t)gridDim.x * blockDim.x;
   bool big = false;
   for (size_t k = i; k < count; k += stride) big |= (s[k] >= 9007199254740992.0);
-  if (__syncthreads_or(big) && threadIdx.x == 0) atomicOr(&ctr->flags, 2u);
+  if (__syncthreads_or(big) && threadIdx.x == 0) atomicOr(&ctr->flags, FLAG_SIGMA_INEXACT);
 }
 
 void check_sigma_exact(const double* sig, size_t count, Counters* ctr, cudaStream_t st) {

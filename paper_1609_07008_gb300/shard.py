@@ -26,20 +26,29 @@ def shard_sources(sources, rank: int, world: int) -> np.ndarray:
 
 
 def allreduce_lambda(lam, group=None):
-    """Sum a per-rank lambda (torch tensor) over the process group in place."""
+    """Sum a per-rank lambda (torch tensor) over the process group in place
+    (a no-op without an initialised process group)."""
     import torch.distributed as dist
-    if dist.is_available() and dist.is_initialized() and dist.get_world_size(group) > 1:
+    if dist.is_available() and dist.is_initialized():
         dist.all_reduce(lam, op=dist.ReduceOp.SUM, group=group)
     return lam
 
 
-def sharded_bc(graph, sources, rank: int, world: int, *, group=None, **kw):
+def _device_bc(graph, shard, **kw):
+    """This rank's lambda on its GPU: mfbc_bc_device over the shard."""
+    import torch
+    dev = torch.device("cuda", torch.cuda.current_device())
+    return graph.bc(torch.from_numpy(np.ascontiguousarray(shard, dtype=np.int32)).to(dev), **kw)
+
+
+def sharded_bc(graph, sources, rank: int, world: int, *, group=None, compute=None, **kw):
     """lambda over all `sources`, computed as this rank's shard plus an all-reduce.
 
-    `graph` is a paper_1609_07008_gb300.Graph replica on this rank's GPU;
-    `sources` is the full list (host array); returns a torch CUDA tensor."""
-    import torch
+    `graph` is this rank's replica of the graph (a paper_1609_07008_gb300.Graph
+    on its GPU); `sources` is the full list (host array), the same on every
+    rank.  `compute(graph, shard, **kw)` returns the shard's lambda as a torch
+    tensor; by default it is the library's device call.  Returns the summed
+    lambda (a torch tensor on the compute's device)."""
     mine = shard_sources(sources, rank, world)
-    dev = torch.device("cuda", torch.cuda.current_device())
-    lam = graph.bc(torch.from_numpy(np.ascontiguousarray(mine, dtype=np.int32)).to(dev), **kw)
+    lam = (compute or _device_bc)(graph, mine, **kw)
     return allreduce_lambda(lam, group)

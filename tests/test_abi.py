@@ -74,8 +74,18 @@ def test_host_side_argument_checks(lib):
     assert st == mfbc.MFBC_ERR_INVALID and b"rowptr" in lib.mfbc_last_error()
     st, h = _create(lib, 2, [1, 1, 2], [1, 0])          # rowptr[0] != 0
     assert st == mfbc.MFBC_ERR_INVALID
-    st, h = _create(lib, 2, [0, 1, 2], [1, 0], flags=8)  # unknown flag
-    assert st == mfbc.MFBC_ERR_INVALID
+    for bad_flags in (4, 8, 0x80000000):                   # unknown flag bits
+        st, h = _create(lib, 2, [0, 1, 2], [1, 0], flags=bad_flags)
+        assert st == mfbc.MFBC_ERR_INVALID and b"flag" in lib.mfbc_last_error()
+    # CSC arrays (rows of A^T) are checked as rows before they are transposed,
+    # on the host
+    csc = mfbc.MFBC_CSC | mfbc.MFBC_DIRECTED
+    st, h = _create(lib, 3, [0, 2, 3, 4], [2, 1, 0, 0], flags=csc)
+    assert st == mfbc.MFBC_ERR_INVALID and b"sorted" in lib.mfbc_last_error()
+    st, h = _create(lib, 3, [0, 1, 2, 3], [1, 7, 0], flags=csc)
+    assert st == mfbc.MFBC_ERR_INVALID and b"range" in lib.mfbc_last_error()
+    st, h = _create(lib, 3, [0, 2, 1, 3], [1, 2, 0], flags=csc)
+    assert st == mfbc.MFBC_ERR_INVALID and b"rowptr" in lib.mfbc_last_error()
     assert lib.mfbc_bc(None, None, 0, None, None) == mfbc.MFBC_ERR_INVALID
     assert lib.mfbc_sssp_batch(None, None, 0, None, None, None) == mfbc.MFBC_ERR_INVALID
     out = ctypes.c_uint64()

@@ -32,12 +32,12 @@ def test_committed_traffic_entries_name_existing_sources():
         assert t["per_alg_byte"] >= 1.0                 # DRAM traffic cannot undercut the compulsory bytes
 
 
-def test_model_roofline_terms_on_a_small_graph():
+def test_survey_model_terms_on_a_small_graph():
     # two components: a path 0-1-2-3 and an edge 4-5
     g = gg.from_edges(6, [(0, 1), (1, 2), (2, 3), (4, 5)], directed=False)
     srcs = np.array([0, 4], np.int32)
     prof = {"values_bwd": 7}
-    m = bench.model_roofline(g, srcs, prof, step_s=1.0, peak_gbs=1.0)
+    m = bench.survey_model(g, srcs, prof, step_s=1.0, peak_gbs=1.0)
     R = 4 + 2                                            # reachable pairs, sources included
     F = 6 + 2                                            # arcs in each source's component
     D = 7
@@ -47,9 +47,9 @@ def test_model_roofline_terms_on_a_small_graph():
     assert m["reachable_pairs"] == R and m["arc_visits"] == F and m["tight_arcs"] == D
     assert m["bytes_per_step"] == pytest.approx(total)
     assert m["bytes_per_tep"] == pytest.approx(total / (len(srcs) * g.m))
-    assert m["frac"] == pytest.approx(total / 1e9)
+    assert m["measured_over_model"] == pytest.approx(total / 1e9)
     w = gg.from_edges(3, [(0, 1), (1, 2)], directed=False, weights=[1, 2])
-    assert bench.model_roofline(w, srcs[:1], prof, 1.0, 1.0) is None
+    assert bench.survey_model(w, srcs[:1], prof, 1.0, 1.0) is None
 
 
 def test_l2_note_follows_the_state_size():

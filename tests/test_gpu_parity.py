@@ -139,19 +139,24 @@ def test_er_2p20_k32_sampled_sources():
 def test_rmat22_bench_launch_configuration():
     # the bench's graph and sources at its batch width (n_b = 1024, level
     # kernels, landmark ordering on): 1056 sources = two batches, lambda
-    # against the oracle element by element; then MFBF rows of sampled
-    # sources out of one full 1024-column batch, bit-exact
+    # against the oracle element by element; then MFBF of the same 1056
+    # sources (a full 1024-column batch and a ragged 32-column one) with 40
+    # rows spread over both batches compared bit-exactly
     import torch
     g = gg.rmat(22, 16, seed=1)
     srcs = gg.sample_sources(g, 16384, seed=2)[:1056]
     G = mfbc.Graph.from_csr(g)
     assert_lambda_close(G.bc(srcs, n_b=1024), oracle.bc(g, srcs))
-    dist, sig = G.sssp(torch.from_numpy(srcs[:1024]).cuda(), n_b=1024)
-    pick = np.array([0, 1, 511, 1023])
-    wd, ws, _ = oracle.sssp(g, srcs[pick])
-    assert np.array_equal(dist[torch.from_numpy(pick).cuda()].cpu().numpy(), wd)
-    assert np.array_equal(sig[torch.from_numpy(pick).cuda()].cpu().numpy(), ws)
+    dist, sig = G.sssp(torch.from_numpy(srcs).cuda(), n_b=1024)
+    pick = np.concatenate([np.linspace(0, 1023, 24).astype(np.int64), np.arange(1024, 1056, 2)])
+    assert len(np.unique(pick)) == 40
+    idx = torch.from_numpy(pick).cuda()
+    got_d, got_s = dist[idx].cpu().numpy(), sig[idx].cpu().numpy()
     del dist, sig
+    torch.cuda.empty_cache()
+    wd, ws, _ = oracle.sssp(g, srcs[pick])
+    assert np.array_equal(got_d, wd)
+    assert np.array_equal(got_s, ws)
     G.close()
 
 

@@ -1,6 +1,8 @@
-"""Multi-rank host logic on CPU: world_size-2 gloo ranks shard the sources,
-compute their partial lambda (the oracle stands in for the per-rank GPU
-call), and sum them with the all-reduce used by the multi-GPU path."""
+"""Multi-rank host logic on CPU: world_size-2 gloo ranks run the product's
+sharded_bc (shard the source list, compute the shard's lambda, sum by one
+all-reduce).  Only the per-rank computation is replaced, through sharded_bc's
+`compute` argument, by the oracle on the CPU; the sharding and the reduction
+are the code a multi-GPU run executes."""
 import os
 
 import numpy as np
@@ -11,7 +13,7 @@ import torch.multiprocessing as mp
 
 import graphgen as gg
 import oracle
-from paper_1609_07008_gb300.shard import allreduce_lambda, shard_sources
+from paper_1609_07008_gb300.shard import shard_sources, sharded_bc
 
 
 def test_shards_partition_the_list():
@@ -30,8 +32,14 @@ def _rank(rank, world, port, out):
     dist.init_process_group("gloo", rank=rank, world_size=world)
     g = gg.rmat(9, 8, directed=True, weights=(1, 5), seed=3)
     src = gg.sample_sources(g, 77, seed=4)
-    lam = torch.from_numpy(oracle.bc(g, shard_sources(src, rank, world), nthreads=1))
-    allreduce_lambda(lam)
+    seen = []
+
+    def on_cpu(graph, shard):
+        seen.append(len(shard))
+        return torch.from_numpy(oracle.bc(graph, shard, nthreads=1))
+
+    lam = sharded_bc(g, src, rank, world, compute=on_cpu)
+    assert seen == [len(shard_sources(src, rank, world))]
     if rank == 0:
         np.save(out, lam.numpy())
     dist.barrier()
