@@ -426,6 +426,7 @@ def extra_workload(name, n_b, steps, cap, peak, peak_kind, args):
         if needs_flush(g.n, prof_bytes["n_b"], prof_bytes["path"]) else None
     t, kstats = time_steps(lambda: G.bc(d_src, n_b=n_b, out=lam, profile=True)[1], steps, stream, flush)
     G.close()
+    flushed = flush is not None
     del flush
     torch.cuda.empty_cache()
     desc = WORKLOADS[name]["desc"] + (f" (first {cap} of them)" if cap else "")
@@ -433,7 +434,7 @@ def extra_workload(name, n_b, steps, cap, peak, peak_kind, args):
             "ms_per_step": t / steps * 1e3, "dtype": DTYPE.get(prof_bytes["path"], "f64"),
             "config": {"workload": desc, "name": name, "n": g.n, "nnz": g.nnz, "m": g.m, "sources": len(srcs),
                        "n_b": prof_bytes["n_b"], "path": prof_bytes["path"],
-                       "l2": "L2 flushed between steps (2x L2 buffer written)" if flush is not None
+                       "l2": "L2 flushed between steps (2x L2 buffer written)" if flushed
                        else l2_note(g.n, prof_bytes["n_b"], prof_bytes["path"])},
             "roofline": roofline_of(kstats, prof_bytes, peak, peak_kind, name, t / steps),
             "cpu_baseline": None if args.no_cpu_baseline else cpu_baseline(g, srcs, budget_s=4.0, single_budget_s=2.0)}

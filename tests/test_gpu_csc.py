@@ -3,8 +3,8 @@
 The arrays may hold the rows of A (MFBC_CSR, Sec. 2.1) or of A^T (MFBC_CSC:
 row v lists the tails of the arcs into v, the operand of Algorithm 2's
 products, Sec. 4.2).  A graph built from each, through the C ABI, must give
-bit-identical tau and sigma_bar and identical lambda on every kernel family,
-and match the oracle.
+bit-identical tau and sigma_bar on every kernel family, lambda equal up to the
+order of floating-point atomic sums (1e-12 relative), and match the oracle.
 """
 import numpy as np
 import pytest
@@ -54,7 +54,9 @@ def test_csc_and_csr_inputs_agree(kind):
         la = A.bc(srcs, n_b=128, path=p)
         for H in (At, At_dev):
             lb = H.bc(srcs, n_b=128, path=p)
-            assert np.array_equal(la, lb), f"lambda differs between orientations (path {p})"
+            nz = la != 0
+            assert np.array_equal(la[~nz], lb[~nz]), f"exact zeros differ between orientations (path {p})"
+            assert np.max(np.abs(la[nz] - lb[nz]) / la[nz]) <= 1e-12, f"lambda differs (path {p})"
             d, s = H.sssp(srcs[:40], n_b=64, path=p)
             assert np.array_equal(d, wd) and np.array_equal(s, ws)
         nz = want != 0
