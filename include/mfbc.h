@@ -54,7 +54,9 @@ typedef enum {
   MFBC_ERR_CUDA = 3,           /* a CUDA runtime call failed */
   MFBC_ERR_OVERFLOW = 4,       /* (n-1) * max weight could overflow int32 distances */
   MFBC_ERR_NO_CONVERGENCE = 5, /* an MFBF/MFBr loop exceeded its iteration bound */
-  MFBC_ERR_TIMEOUT = 6         /* reserved: a bounded device-side wait gave up */
+  MFBC_ERR_TIMEOUT = 6         /* a bounded device-side wait ran out of its budget (the
+                                  persistent small-graph kernel's group barriers); the
+                                  outputs are unspecified, the context stays usable */
 } mfbc_status;
 
 /* mfbc_graph_create flags: bit 0 = orientation of the arrays, bit 1 = symmetry */
@@ -69,7 +71,8 @@ typedef enum {
 #define MFBC_WARN_SIGMA_INEXACT 1u  /* some sigma_bar >= 2^53: FP64 counts may be rounded */
 
 /* mfbc_options.path */
-#define MFBC_PATH_AUTO    0    /* level kernels for unit weights; distance kernels for weights
+#define MFBC_PATH_AUTO    0    /* unit weights: the persistent small-graph kernel when n <= 2^15
+                                  and nnz <= 2^19, else the level kernels; distance kernels for weights
                                   <= 128 when no in- or out-degree exceeds max(64, 4x the
                                   average degree); general kernels otherwise (or the family
                                   mfbc_autotune chose) */
@@ -77,6 +80,9 @@ typedef enum {
 #define MFBC_PATH_LEVEL   2    /* require the unit-weight level kernels (INVALID if weighted) */
 #define MFBC_PATH_DIST    3    /* distance-ordered kernels for small integer weights
                                   (INVALID when the largest weight exceeds 4096) */
+#define MFBC_PATH_SMALL   4    /* persistent kernel for small unit-weight graphs: every batch
+                                  of the call in one launch (INVALID if weighted or when
+                                  n * n_b * 9 bytes per group does not fit; see below) */
 
 typedef struct mfbc_graph mfbc_graph;   /* opaque, device resident */
 
@@ -117,11 +123,21 @@ typedef struct {
   uint32_t* warn_out;          /* optional host pointer, receives MFBC_WARN_* bits */
   mfbc_profile* profile;       /* optional host pointer; enables per-kernel event timing */
   uint32_t flags;              /* MFBC_OPT_* bits */
+  const int32_t* lambda_rows;  /* mfbc_bc_multi_device only, optional HOST int32[nreq]: the row of
+                                  lambda_out that receives request r (NULL: row r); rows >= 0 */
 } mfbc_options;                /* zero-initialised = all defaults */
 
 /* mfbc_options.flags */
 #define MFBC_OPT_COUNT_BYTES 1u  /* with profile: count algorithmic bytes on the device (slower) */
 #define MFBC_OPT_KEEP_ORDER  2u  /* mfbc_bc*: batch the sources in the given order (see below) */
+#define MFBC_OPT_ACCUMULATE  8u  /* mfbc_bc* and mfbc_bc_multi_device: add the result to the values
+                                    already in lambda_out (its rows) instead of overwriting them;
+                                    lambda is linear in the source list, so a request split over
+                                    several calls accumulates to its whole answer */
+#define MFBC_OPT_TEST_STALL  4u  /* test hook, MFBC_PATH_SMALL only: every group barrier waits
+                                    for one arrival more than the group has, so each wait runs
+                                    out of its (shortened, 20 ms) budget and the call returns
+                                    MFBC_ERR_TIMEOUT; nothing faults and the context stays usable */
 
 /* Build a device-resident graph from HOST compressed-row arrays (Sec. 2.1:
  * A(i,j) = w(i,j) for (i,j) in E; the paper's Tensor::write of the input,
@@ -190,12 +206,15 @@ mfbc_status mfbc_bc_device(const mfbc_graph* g, const int32_t* sources, int32_t 
  * Algorithm 3's loop.  DEVICE sources int32[nsrc] hold the requests' lists
  * back to back; HOST req_offsets int32[nreq+1] (req_offsets[0] = 0,
  * non-decreasing, req_offsets[nreq] = nsrc) delimit them: request r owns
- * sources[req_offsets[r] .. req_offsets[r+1]).  DEVICE lambda_out
- * double[nreq*n] is overwritten; row r (lambda_out + r*n) receives request
- * r's lambda exactly as mfbc_bc_device would compute it for that list alone,
- * up to the floating-point summation order.  Each request starts on a
- * 32-column boundary of a batch and may continue into the next batch; sources
- * are not reordered.  Returns once lambda_out is complete on opt->stream. */
+ * sources[req_offsets[r] .. req_offsets[r+1]).  DEVICE lambda_out: row
+ * lambda_rows[r] (row r when opt->lambda_rows is NULL; a row is n doubles at
+ * lambda_out + row*n) receives request r's lambda exactly as mfbc_bc_device
+ * would compute it for that list alone, up to the floating-point summation
+ * order; the rows are overwritten, or added to with MFBC_OPT_ACCUMULATE (a
+ * serving loop that splits a request over several calls keeps one row per
+ * request and accumulates into it).  Each request starts on a 32-column
+ * boundary of a batch and may continue into the next batch; sources are not
+ * reordered.  Returns once lambda_out is complete on opt->stream. */
 mfbc_status mfbc_bc_multi_device(const mfbc_graph* g, const int32_t* sources, int32_t nsrc,
                                  const int32_t* req_offsets, int32_t nreq, double* lambda_out,
                                  const mfbc_options* opt);
@@ -212,7 +231,9 @@ typedef struct {
 /* Autotuner (no counterpart in the paper, whose batch width and processor
  * grid come from its cost model, Sec. 5): times mfbc_bc on the HOST sources
  * int32[nsrc] for each candidate configuration and keeps the fastest on the
- * graph handle.  Candidates: n_b in {128, 256, 512, 1024} on the level kernels;
+ * graph handle.  Candidates: n_b in {128, 256, 512, 1024} on the level kernels
+ * and, for unit-weight graphs of at most 2^15 vertices and 2^19 arcs, n_b in
+ * {32, 64, 128, 256} on the persistent small-graph kernel;
  * n_b in {128, 256, 512, 1024, 2048, 4096} on the general kernels (x {1, 8}
  * arcs per step) and on the distance kernels; each at most nsrc rounded up;
  * widths that do not fit the device are skipped.  With opt->path == AUTO a

@@ -33,9 +33,11 @@ MFBC_CSC = 1
 MFBC_DIRECTED = 0
 MFBC_UNDIRECTED = 2
 MFBC_WARN_SIGMA_INEXACT = 1
-PATH_AUTO, PATH_GENERAL, PATH_LEVEL, PATH_DIST = 0, 1, 2, 3
+PATH_AUTO, PATH_GENERAL, PATH_LEVEL, PATH_DIST, PATH_SMALL = 0, 1, 2, 3, 4
 MFBC_OPT_COUNT_BYTES = 1
 MFBC_OPT_KEEP_ORDER = 2
+MFBC_OPT_TEST_STALL = 4
+MFBC_OPT_ACCUMULATE = 8
 INF = np.iinfo(np.int32).max
 MAX_KSTATS = 24
 
@@ -73,7 +75,7 @@ class Options(ctypes.Structure):
     _fields_ = [("n_b", ctypes.c_int32), ("path", ctypes.c_int32), ("stream", ctypes.c_void_p),
                 ("workspace", ctypes.c_void_p), ("workspace_bytes", ctypes.c_uint64),
                 ("warn_out", ctypes.POINTER(ctypes.c_uint32)), ("profile", ctypes.POINTER(Profile)),
-                ("flags", ctypes.c_uint32)]
+                ("flags", ctypes.c_uint32), ("lambda_rows", ctypes.c_void_p)]
 
 
 class Tuning(ctypes.Structure):
@@ -166,9 +168,11 @@ def _stream_handle(stream) -> ctypes.c_void_p | None:
     return ctypes.c_void_p(stream.cuda_stream)
 
 
-def _options(n_b, path, stream, workspace, warn, profile, count_bytes=False, keep_order=False) -> Options:
+def _options(n_b, path, stream, workspace, warn, profile, count_bytes=False, keep_order=False,
+             test_stall=False) -> Options:
     o = Options()
-    o.flags = (MFBC_OPT_COUNT_BYTES if count_bytes else 0) | (MFBC_OPT_KEEP_ORDER if keep_order else 0)
+    o.flags = (MFBC_OPT_COUNT_BYTES if count_bytes else 0) | (MFBC_OPT_KEEP_ORDER if keep_order else 0) | \
+        (MFBC_OPT_TEST_STALL if test_stall else 0)
     o.n_b = int(n_b)
     o.path = int(path)
     o.stream = _stream_handle(stream)
@@ -239,15 +243,16 @@ class Graph:
     # ----------------------------------------------------------- entry points
     def bc(self, sources, *, n_b: int = 0, path: int = PATH_AUTO, out=None, stream=None, workspace=None,
            profile: bool = False, count_bytes: bool = False, keep_order: bool = False,
-           return_warn: bool = False):
+           return_warn: bool = False, test_stall: bool = False):
         """Betweenness centrality summed over `sources` (Algorithm 3).
 
         Host (numpy) sources -> numpy lambda via mfbc_bc; torch CUDA sources
-        -> torch CUDA lambda via mfbc_bc_device (into `out` when given)."""
+        -> torch CUDA lambda via mfbc_bc_device (into `out` when given).
+        test_stall sets the MFBC_OPT_TEST_STALL test hook."""
         lib = load()
         warn = ctypes.c_uint32(0)
         prof = Profile() if (profile or count_bytes) else None
-        opt = _options(n_b, path, stream, workspace, warn, prof, count_bytes, keep_order)
+        opt = _options(n_b, path, stream, workspace, warn, prof, count_bytes, keep_order, test_stall)
         if _is_torch(sources):
             import torch
             src = sources.to(dtype=torch.int32).contiguous()
@@ -266,11 +271,13 @@ class Graph:
         return res[0] if len(res) == 1 else tuple(res)
 
     def bc_multi(self, source_lists, *, n_b: int = 0, path: int = PATH_AUTO, out=None, stream=None,
-                 workspace=None, profile: bool = False):
+                 workspace=None, profile: bool = False, rows=None, accumulate: bool = False):
         """One lambda row per request: `source_lists` is a sequence of torch
         CUDA int tensors (or one concatenated tensor with a host `offsets`
         pair: (sources, offsets)).  Returns a [nreq, n] float64 CUDA tensor
-        (mfbc_bc_multi_device)."""
+        (mfbc_bc_multi_device), or `out` ([rows, n]) when given.  rows: the
+        row of `out` for each request (default: request r -> row r);
+        accumulate: add into those rows instead of overwriting them."""
         import torch
         lib = load()
         if isinstance(source_lists, tuple) and len(source_lists) == 2 and not _is_torch(source_lists[1]):
@@ -288,6 +295,14 @@ class Graph:
         lam = out if out is not None else torch.empty((nreq, self.n), dtype=torch.float64, device=src.device)
         prof = Profile() if profile else None
         opt = _options(n_b, path, stream, workspace, None, prof)
+        rws = None
+        if rows is not None:
+            rws = np.ascontiguousarray(rows, dtype=np.int32)
+            if len(rws) != nreq or (len(rws) and (rws.min() < 0 or rws.max() >= lam.shape[0])):
+                raise ValueError("rows must name one row of out per request")
+            opt.lambda_rows = ctypes.c_void_p(rws.ctypes.data)
+        if accumulate:
+            opt.flags |= MFBC_OPT_ACCUMULATE
         _check(lib.mfbc_bc_multi_device(self._h, _dptr(src), src.numel(), _hptr(off), nreq, _dptr(lam),
                                         ctypes.byref(opt)))
         return (lam, prof.as_dict()) if profile else lam

@@ -20,7 +20,7 @@ struct mfbc_graph {
   // autotuner results (mfbc_autotune): batch width per kernel family
   // (0 = not tuned), the family AUTO picks, and the general kernels' arcs
   // per step (0 = by average degree); force_arcs overrides it while tuning
-  int tuned_nb[3] = {0, 0, 0};      // level, general, distance kernels
+  int tuned_nb[4] = {0, 0, 0, 0};   // level, general, distance, persistent small-graph kernels
   int tuned_arcs = 0;
   int tuned_path = 0;               // kernel family for MFBC_PATH_AUTO (0 = by weights)
   int force_arcs = 0;
@@ -177,6 +177,8 @@ extern "C" mfbc_status mfbc_graph_info(const mfbc_graph* G, int32_t* n, int64_t*
 struct Plan {
   int path = MFBC_PATH_GENERAL;
   int nb = 32;
+  int groups = 0;                  // persistent small-graph kernel: block groups
+  int64_t table_batches = 1;       //   and the batches its table holds
   int Lcap = 0;
   int64_t list_cap = 0;
   size_t state_bytes = 0;          // kernel-family state
@@ -186,8 +188,12 @@ struct Plan {
 
 static inline size_t al256(size_t b) { return (b + 255) & ~size_t(255); }
 
-static size_t extras(const DevGraph& g, int32_t nsrc, int mode, int nb, bool host_io) {
+static size_t extras(const DevGraph& g, int32_t nsrc, int mode, int nb, bool host_io, int path) {
   size_t b = 0;
+  if (path == MFBC_PATH_SMALL) {             // the call's batch table: sources, lambda rows, packed columns
+    const size_t nbatch = std::max<size_t>(1, ((size_t)nsrc + nb - 1) / nb);
+    b += 2 * al256(sizeof(int32_t) * nbatch * nb) + al256(sizeof(int32_t) * nbatch * (nb / 32));
+  }
   if (mode == 0) b += al256(sizeof(double) * (size_t)std::max(g.n, 1));        // device lambda
   if (host_io) b += al256(sizeof(int32_t) * (size_t)std::max(nsrc, 1));        // device sources
   if (mode == 0) b += al256(sizeof(int32_t) * (size_t)std::max(nsrc, 1));      // reordered sources
@@ -214,10 +220,17 @@ static size_t plan_bytes(const DevGraph& g, int path, int nb, int32_t nsrc, int 
     p->state_bytes = std::max(level_bytes(g, nb, p->Lcap, p->list_cap), general_bytes(g.n, 32));
   } else if (path == MFBC_PATH_DIST) {
     p->state_bytes = dist_bytes(g.n, nb, g.wmax + 1);
+  } else if (path == MFBC_PATH_SMALL) {
+    // batches too deep for the kernel's byte levels are redone by the general
+    // kernels at n_b = 32 in the same scratch
+    const int nbatch = (int)std::max<int64_t>(1, ((int64_t)nsrc + nb - 1) / nb);
+    p->table_batches = nbatch;
+    p->groups = small_groups(g.n, nb, mode == 1 ? 1 : nbatch);
+    p->state_bytes = std::max(small_bytes(g.n, nb, p->groups), general_bytes(g.n, 32));
   } else {
     p->state_bytes = general_bytes(g.n, nb);
   }
-  p->extra_bytes = extras(g, nsrc, mode, nb, host_io);
+  p->extra_bytes = extras(g, nsrc, mode, nb, host_io, path);
   p->total = p->state_bytes + p->extra_bytes;
   return p->total;
 }
@@ -230,8 +243,14 @@ static size_t plan_bytes(const DevGraph& g, int path, int nb, int32_t nsrc, int 
 // and uniform random graphs gain: weighted 256^2 grid 313 against 2883 ms,
 // Erdos-Renyi n = 2^16, k = 1024, 256 sources 153 against 326 ms); general
 // kernels otherwise.
+// Unit-weight graphs small enough for the persistent kernel to win: its
+// levels scan every (vertex, word) and every in-arc of an open vertex, which
+// costs more than the per-product kernels once the graph has a few hundred
+// thousand arcs, while below that the per-product kernels wait on launches.
+static bool small_graph(const DevGraph& g) { return g.n <= (1 << 15) && g.nnz <= (1 << 19); }
+
 static int default_path(const DevGraph& g) {
-  if (g.unit) return MFBC_PATH_LEVEL;
+  if (g.unit) return small_graph(g) ? MFBC_PATH_SMALL : MFBC_PATH_LEVEL;
   const int64_t avg = g.n ? g.nnz / g.n : 0;
   const int64_t deg_cap = std::max<int64_t>(64, 4 * avg);
   if (g.wmax <= 128 && std::max(g.max_deg, g.max_in_deg) <= deg_cap && (uint64_t)g.n * 128u <= 0xffffffffull)
@@ -239,20 +258,26 @@ static int default_path(const DevGraph& g) {
   return MFBC_PATH_GENERAL;
 }
 
+static int tuned_slot(int path) {
+  return path == MFBC_PATH_LEVEL ? 0 : path == MFBC_PATH_GENERAL ? 1 : path == MFBC_PATH_DIST ? 2 : 3;
+}
+
 static mfbc_status make_plan(const mfbc_graph* G, int32_t nsrc, int mode, const mfbc_options* opt,
                              bool host_io, Plan* p) {
   const DevGraph& g = G->g;
   int path = opt ? opt->path : MFBC_PATH_AUTO;
   if (path == MFBC_PATH_AUTO) path = G->tuned_path ? G->tuned_path : default_path(g);
-  else if (path == MFBC_PATH_LEVEL && !g.unit)
-    return fail(MFBC_ERR_INVALID, "MFBC_PATH_LEVEL needs unit weights");
+  else if ((path == MFBC_PATH_LEVEL || path == MFBC_PATH_SMALL) && !g.unit)
+    return fail(MFBC_ERR_INVALID, path == MFBC_PATH_LEVEL ? "MFBC_PATH_LEVEL needs unit weights"
+                                                          : "MFBC_PATH_SMALL needs unit weights");
   else if (path == MFBC_PATH_DIST && g.wmax + 1 > DIST_MAX_BUCKETS)
     return fail(MFBC_ERR_INVALID, "MFBC_PATH_DIST needs weights <= 4096");
   else if (path == MFBC_PATH_DIST && (uint64_t)g.n * 128u > 0xffffffffull)
     return fail(MFBC_ERR_INVALID, "MFBC_PATH_DIST needs n < 2^25");
-  else if (path != MFBC_PATH_GENERAL && path != MFBC_PATH_LEVEL && path != MFBC_PATH_DIST)
+  else if (path != MFBC_PATH_GENERAL && path != MFBC_PATH_LEVEL && path != MFBC_PATH_DIST &&
+           path != MFBC_PATH_SMALL)
     return fail(MFBC_ERR_INVALID, "unknown path");
-  const int maxnb = path == MFBC_PATH_LEVEL ? LEVEL_MAX_NB : 4096;
+  const int maxnb = path == MFBC_PATH_LEVEL ? LEVEL_MAX_NB : (path == MFBC_PATH_SMALL ? 1024 : 4096);
   // the level kernels move 128 columns (four 32-column words) at a time
   const int gran = path == MFBC_PATH_LEVEL ? 128 : 32;
   int req = opt ? opt->n_b : 0;
@@ -265,7 +290,7 @@ static mfbc_status make_plan(const mfbc_graph* G, int32_t nsrc, int mode, const 
   }
   // auto: widest batch (<= number of sources, <= the tuned width) whose
   // scratch fits the budget
-  const int tuned = G->tuned_nb[path == MFBC_PATH_LEVEL ? 0 : (path == MFBC_PATH_GENERAL ? 1 : 2)];
+  const int tuned = G->tuned_nb[tuned_slot(path)];
   size_t budget;
   if (opt && opt->workspace) budget = opt->workspace_bytes;
   else {
@@ -273,7 +298,10 @@ static mfbc_status make_plan(const mfbc_graph* G, int32_t nsrc, int mode, const 
     if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) { cudaGetLastError(); return fail(MFBC_ERR_CUDA, "cudaMemGetInfo failed"); }
     budget = (size_t)(0.80 * (double)(fr + G->ws_bytes));
   }
-  int nb = std::min(tuned > 0 ? tuned : maxnb, std::max(gran, (nsrc + gran - 1) / gran * gran));
+  // the persistent small-graph kernel runs batches side by side: 128 columns
+  // per batch leave it several batches to spread over its block groups
+  const int widest = tuned > 0 ? tuned : (path == MFBC_PATH_SMALL ? 128 : maxnb);
+  int nb = std::min(widest, std::max(gran, (nsrc + gran - 1) / gran * gran));
   while (true) {
     plan_bytes(g, path, nb, nsrc, mode, host_io, p);
     if (p->total <= budget || nb == gran) break;
@@ -459,7 +487,7 @@ struct Packing {
   std::vector<int32_t> colidx, wreq, used;
   int64_t batches = 0;
 };
-static Packing pack_requests(const int32_t* off, int32_t nreq, int nb) {
+static Packing pack_requests(const int32_t* off, int32_t nreq, int nb, const int32_t* rows) {
   Packing p;
   const int W = nb / 32;
   auto open_batch = [&]() {
@@ -479,13 +507,109 @@ static Packing pack_requests(const int32_t* off, int32_t nreq, int nb) {
       const int64_t b = p.batches - 1;
       const int take = (int)std::min<int64_t>(e - i, nb - col);
       for (int t = 0; t < take; t++) p.colidx[(size_t)b * nb + col + t] = (int32_t)(i + t);
-      for (int w = col / 32; w <= (col + take - 1) / 32; w++) p.wreq[(size_t)b * W + w] = r;
+      for (int w = col / 32; w <= (col + take - 1) / 32; w++) p.wreq[(size_t)b * W + w] = rows ? rows[r] : r;
       col += take;
       i += take;
       p.used[(size_t)b] = col;
     }
   }
   return p;
+}
+
+// Every batch of the call on the persistent small-graph kernel (one launch
+// for modes 0 and 2; mode 1 launches per batch so that host outputs go
+// through the one-batch staging rows).  Batches the kernel hands back (deeper
+// than its byte levels, or path counts >= 2^58) are recomputed by the
+// general kernels at n_b = 32 in the same scratch.
+mfbc_status small_path(mfbc_graph* G, Run& R, RunCtx& rc, SmallState& ss, const int32_t* d_src, int32_t nsrc,
+                       int mode, double* d_lambda, int32_t* dist_out, double* sigma_out, bool out_on_host,
+                       const Packing& pk, int64_t nbatches, char* tab, int32_t* stage_d, double* stage_s,
+                       uint32_t* warn, int64_t* fi, int64_t* bi) {
+  const DevGraph& g = G->g;
+  const Plan& P = R.plan;
+  const int nb = P.nb, W = nb / 32;
+  const bool multi = mode == 2;
+  const size_t nbt = (size_t)P.table_batches;
+  int32_t* d_all = (int32_t*)tab;
+  int32_t* d_col = (int32_t*)(tab + al256(sizeof(int32_t) * nbt * nb));
+  int32_t* d_wreq = (int32_t*)(tab + 2 * al256(sizeof(int32_t) * nbt * nb));
+  if ((size_t)nbatches > nbt) { *rc.err = "packed batches exceed the batch table"; return MFBC_ERR_INVALID; }
+  if (multi) {
+    MFBC_CUDA_TRY(cudaMemcpyAsync(d_col, pk.colidx.data(), sizeof(int32_t) * pk.colidx.size(), cudaMemcpyHostToDevice,
+                                  R.st), rc.err);
+    const size_t cols = (size_t)nbatches * nb;
+    k_gather_sources<<<(unsigned)((cols + 255) / 256), 256, 0, R.st>>>(d_src, d_col, (int)cols, d_all);
+    MFBC_CUDA_TRY(cudaMemcpyAsync(d_wreq, pk.wreq.data(), sizeof(int32_t) * pk.wreq.size(), cudaMemcpyHostToDevice,
+                                  R.st), rc.err);
+  } else {
+    fill_i32(d_all, -1, (size_t)nbatches * nb, R.st);
+    if (nsrc)
+      MFBC_CUDA_TRY(cudaMemcpyAsync(d_all, d_src, sizeof(int32_t) * (size_t)nsrc, cudaMemcpyDeviceToDevice, R.st),
+                    rc.err);
+  }
+  const uint32_t oflags = R.opt ? R.opt->flags : 0u;
+  std::vector<int32_t> redo, part;
+  if (mode == 1) {
+    for (int64_t b = 0; b < nbatches; b++) {
+      const int32_t b0 = (int32_t)(b * nb);
+      const int na = std::min(nb, nsrc - b0);
+      int32_t* dd = out_on_host ? stage_d : dist_out + (size_t)b0 * g.n;
+      double* dsg = sigma_out ? (out_on_host ? stage_s : sigma_out + (size_t)b0 * g.n) : nullptr;
+      mfbc_status s = small_run(rc, ss, d_all + (size_t)b * nb, nullptr, 1, nullptr, dd, dsg, na, oflags, &part);
+      if (s) return s;
+      if (!part.empty()) redo.push_back((int32_t)b);
+      else if (out_on_host) {
+        MFBC_CUDA_TRY(cudaMemcpyAsync(dist_out + (size_t)b0 * g.n, stage_d, sizeof(int32_t) * (size_t)na * g.n,
+                                      cudaMemcpyDeviceToHost, R.st), rc.err);
+        if (sigma_out)
+          MFBC_CUDA_TRY(cudaMemcpyAsync(sigma_out + (size_t)b0 * g.n, stage_s, sizeof(double) * (size_t)na * g.n,
+                                        cudaMemcpyDeviceToHost, R.st), rc.err);
+        MFBC_CUDA_TRY(cudaStreamSynchronize(R.st), rc.err);
+      }
+    }
+  } else {
+    mfbc_status s = small_run(rc, ss, d_all, multi ? d_wreq : nullptr, (int)nbatches, d_lambda, nullptr, nullptr, 0,
+                              oflags, &redo);
+    if (s) return s;
+  }
+  if (fi) *fi += nbatches - (int64_t)redo.size();
+  if (bi) *bi += nbatches - (int64_t)redo.size();
+  if (redo.empty()) return MFBC_OK;
+  // general kernels for the batches handed back
+  Carver c2(R.ws, P.state_bytes);
+  GeneralState gs;
+  general_carve(c2, g.n, 32, gs);
+  MFBC_CUDA_TRY(cudaMemsetAsync(gs.ctr, 0, sizeof(Counters), R.st), rc.err);
+  for (int32_t b : redo) {
+    const int32_t b0 = (int32_t)((int64_t)b * nb);
+    const int na = multi ? nb : std::min(nb, nsrc - b0);
+    for (int sb = 0; sb < na; sb += 32) {
+      const int nsa = std::min(32, na - sb);
+      rc.word_req = multi ? &pk.wreq[(size_t)b * W + sb / 32] : nullptr;
+      mfbc_status s = general_batch(rc, gs, d_all + (size_t)b * nb + sb, nsa, mode == 1 ? nullptr : d_lambda, fi, bi);
+      if (s) return s;
+      if (mode == 1) {
+        int32_t* dd = out_on_host ? stage_d + (size_t)sb * g.n : dist_out + (size_t)(b0 + sb) * g.n;
+        double* dsg = sigma_out ? (out_on_host ? stage_s + (size_t)sb * g.n : sigma_out + (size_t)(b0 + sb) * g.n)
+                                : nullptr;
+        general_output(rc, gs, nsa, dd, dsg);
+      }
+    }
+    if (mode == 1 && out_on_host) {
+      MFBC_CUDA_TRY(cudaMemcpyAsync(dist_out + (size_t)b0 * g.n, stage_d, sizeof(int32_t) * (size_t)na * g.n,
+                                    cudaMemcpyDeviceToHost, R.st), rc.err);
+      if (sigma_out)
+        MFBC_CUDA_TRY(cudaMemcpyAsync(sigma_out + (size_t)b0 * g.n, stage_s, sizeof(double) * (size_t)na * g.n,
+                                      cudaMemcpyDeviceToHost, R.st), rc.err);
+      MFBC_CUDA_TRY(cudaStreamSynchronize(R.st), rc.err);
+    }
+  }
+  rc.word_req = nullptr;
+  // the general batches flag inexact counts in their own counters
+  MFBC_CUDA_TRY(cudaMemcpyAsync(G->h_ctr, &gs.ctr->flags, sizeof(uint32_t), cudaMemcpyDeviceToHost, R.st), rc.err);
+  MFBC_CUDA_TRY(cudaStreamSynchronize(R.st), rc.err);
+  if (G->h_ctr[0] & FLAG_SIGMA_INEXACT) *warn |= MFBC_WARN_SIGMA_INEXACT;
+  return MFBC_OK;
 }
 
 // mode 0: lambda (d_lambda device, n doubles, overwritten); mode 1: sssp rows;
@@ -503,11 +627,18 @@ mfbc_status run(mfbc_graph* G, const int32_t* d_src, int32_t nsrc, int mode, dou
   LevelState ls;
   DistState ds;
   Counters* ctr;
+  SmallState ss;
   if (P.path == MFBC_PATH_LEVEL) { level_carve(c, g, nb, P.Lcap, P.list_cap, ls); ctr = ls.ctr; }
   else if (P.path == MFBC_PATH_DIST) { dist_carve(c, g.n, nb, g.wmax + 1, ds); ctr = ds.ctr; }
+  else if (P.path == MFBC_PATH_SMALL) { small_carve(c, g.n, nb, P.groups, ss); ctr = ss.ctr; }
   else { general_carve(c, g.n, nb, gs); ctr = gs.ctr; }
   int32_t* stage_d = nullptr;
   double* stage_s = nullptr;
+  char* small_tab = extra;
+  if (P.path == MFBC_PATH_SMALL) {          // batch table first (see extras)
+    const size_t nbatch = (size_t)P.table_batches;
+    extra += 2 * al256(sizeof(int32_t) * nbatch * nb) + al256(sizeof(int32_t) * nbatch * (nb / 32));
+  }
   if (mode == 1 && out_on_host) {
     stage_d = (int32_t*)extra;
     stage_s = (double*)(extra + al256(sizeof(int32_t) * (size_t)nb * std::max(g.n, 1)));
@@ -515,19 +646,33 @@ mfbc_status run(mfbc_graph* G, const int32_t* d_src, int32_t nsrc, int mode, dou
   MFBC_CUDA_TRY(cudaMemsetAsync(ctr, 0, sizeof(Counters), R.st), &R.err);
   const bool multi = mode == 2;
   const bool want_lambda = mode != 1;
-  if (want_lambda && g.n) {
-    const size_t rows = multi ? (size_t)R.nreq : 1;
-    MFBC_CUDA_TRY(cudaMemsetAsync(d_lambda, 0, sizeof(double) * rows * (size_t)g.n, R.st), &R.err);
+  const int32_t* lrows = multi && R.opt ? R.opt->lambda_rows : nullptr;
+  if (want_lambda && g.n && !(R.opt && (R.opt->flags & MFBC_OPT_ACCUMULATE))) {
+    if (lrows) {
+      for (int32_t r = 0; r < R.nreq; r++)
+        MFBC_CUDA_TRY(cudaMemsetAsync(d_lambda + (size_t)lrows[r] * g.n, 0, sizeof(double) * (size_t)g.n, R.st),
+                      &R.err);
+    } else {
+      const size_t rows = multi ? (size_t)R.nreq : 1;
+      MFBC_CUDA_TRY(cudaMemsetAsync(d_lambda, 0, sizeof(double) * rows * (size_t)g.n, R.st), &R.err);
+    }
   }
   Packing pk;
   int32_t* d_colidx = nullptr;
   int32_t* d_batch = nullptr;
   if (multi) {
-    pk = pack_requests(R.req_off, R.nreq, nb);
+    pk = pack_requests(R.req_off, R.nreq, nb, lrows);
     d_colidx = (int32_t*)extra;
     d_batch = (int32_t*)(extra + al256(sizeof(int32_t) * (size_t)nb));
   }
   const int64_t nbatches = multi ? pk.batches : ((int64_t)nsrc + nb - 1) / nb;
+  uint32_t warn = 0;
+  if (P.path == MFBC_PATH_SMALL) {
+    mfbc_status s = small_path(G, R, rc, ss, d_src, nsrc, mode, d_lambda, dist_out, sigma_out, out_on_host, pk,
+                               nbatches, small_tab, stage_d, stage_s, &warn, &fi, &bi);
+    if (s) return fail(s, R.err.empty() ? std::string(mfbc_status_string(s)) : R.err);
+    batches = nbatches;
+  }
   if (P.path == MFBC_PATH_LEVEL && g.n) {
     // masks start clean; each batch returns them to zero
     MFBC_CUDA_TRY(cudaMemsetAsync(ls.V, 0, sizeof(uint32_t) * (size_t)g.n * ls.W, R.st), &R.err);
@@ -536,14 +681,13 @@ mfbc_status run(mfbc_graph* G, const int32_t* d_src, int32_t nsrc, int mode, dou
     if (g.items_out.nhub)
       MFBC_CUDA_TRY(cudaMemsetAsync(ls.zacc, 0, sizeof(double) * (size_t)g.items_out.nhub * nb, R.st), &R.err);
   }
-  uint32_t warn = 0;
   if (mode == 0 && P.path == MFBC_PATH_LEVEL && nsrc > nb && !(R.opt && (R.opt->flags & MFBC_OPT_KEEP_ORDER))) {
     bool applied = false;
     mfbc_status so = order_sources(rc, ls, d_src, nsrc, d_sorted, &applied);
     if (so) return fail(so, R.err.empty() ? std::string(mfbc_status_string(so)) : R.err);
     if (applied) d_src = d_sorted;
   }
-  for (int64_t bx = 0; bx < nbatches; bx++) {
+  for (int64_t bx = 0; bx < (P.path == MFBC_PATH_SMALL ? 0 : nbatches); bx++) {
     const int32_t b0 = multi ? 0 : (int32_t)(bx * nb);
     int na;
     const int32_t* bsrc;
@@ -690,6 +834,9 @@ mfbc_status entry(const mfbc_graph* Gc, const int32_t* sources, int32_t nsrc, in
       return fail(MFBC_ERR_INVALID, "req_offsets must start at 0 and end at nsrc");
     for (int32_t r = 0; r < nreq; r++)
       if (req_off[r + 1] < req_off[r]) return fail(MFBC_ERR_INVALID, "req_offsets must be non-decreasing");
+    if (opt && opt->lambda_rows)
+      for (int32_t r = 0; r < nreq; r++)
+        if (opt->lambda_rows[r] < 0) return fail(MFBC_ERR_INVALID, "lambda_rows must be >= 0");
   }
   if (mode == 1 && nsrc > 0 && Gc->g.n > 0 && !dist_out) return fail(MFBC_ERR_INVALID, "dist_out must not be NULL");
   mfbc_graph* G = const_cast<mfbc_graph*>(Gc);
@@ -708,7 +855,13 @@ mfbc_status entry(const mfbc_graph* Gc, const int32_t* sources, int32_t nsrc, in
   R.req_off = req_off;
   R.nreq = nreq;
   R.st = opt ? (cudaStream_t)opt->stream : nullptr;
-  mfbc_status s = make_plan(G, nsrc, mode, opt, host_io, &R.plan);
+  int32_t plan_cols = nsrc;                  // mode 2: each request rounded up to 32 columns
+  if (mode == 2) {
+    int64_t cols = 0;
+    for (int32_t r = 0; r < nreq; r++) cols += (req_off[r + 1] - req_off[r] + 31) / 32 * 32;
+    plan_cols = (int32_t)std::min<int64_t>(cols, 0x7fffffff);
+  }
+  mfbc_status s = make_plan(G, plan_cols, mode, opt, host_io, &R.plan);
   if (s) return s;
   s = get_workspace(R);
   if (s) return s;
@@ -720,6 +873,10 @@ mfbc_status entry(const mfbc_graph* Gc, const int32_t* sources, int32_t nsrc, in
   const int32_t* d_src = sources;
   if (mode == 0 && host_io) { d_lambda = (double*)extra; extra += al256(sizeof(double) * (size_t)std::max(n, 1)); }
   else if (mode == 0) extra += al256(sizeof(double) * (size_t)std::max(n, 1));
+  if (mode == 0 && host_io && n > 0 && opt && (opt->flags & MFBC_OPT_ACCUMULATE)) {
+    cudaError_t e = cudaMemcpyAsync(d_lambda, lambda_out, sizeof(double) * (size_t)n, cudaMemcpyHostToDevice, R.st);
+    if (e != cudaSuccess) { cudaGetLastError(); return fail(MFBC_ERR_CUDA, "copying lambda failed"); }
+  }
   if (host_io) {
     int32_t* ds = (int32_t*)extra;
     extra += al256(sizeof(int32_t) * (size_t)std::max(nsrc, 1));
@@ -781,7 +938,8 @@ extern "C" mfbc_status mfbc_autotune(mfbc_graph* G, const int32_t* sources, int3
   const bool dist_ok = G->g.wmax + 1 <= DIST_MAX_BUCKETS;
   std::vector<int> paths;
   if (req_path == MFBC_PATH_AUTO) {
-    if (G->g.unit) paths = {MFBC_PATH_LEVEL};
+    if (G->g.unit) paths = small_graph(G->g) ? std::vector<int>{MFBC_PATH_LEVEL, MFBC_PATH_SMALL}
+                                             : std::vector<int>{MFBC_PATH_LEVEL};
     else paths = dist_ok ? std::vector<int>{MFBC_PATH_GENERAL, MFBC_PATH_DIST} : std::vector<int>{MFBC_PATH_GENERAL};
   } else if (req_path == MFBC_PATH_LEVEL) {
     if (!G->g.unit) return fail(MFBC_ERR_INVALID, "MFBC_PATH_LEVEL needs unit weights");
@@ -791,6 +949,9 @@ extern "C" mfbc_status mfbc_autotune(mfbc_graph* G, const int32_t* sources, int3
   } else if (req_path == MFBC_PATH_DIST) {
     if (!dist_ok) return fail(MFBC_ERR_INVALID, "MFBC_PATH_DIST needs weights <= 4096");
     paths = {MFBC_PATH_DIST};
+  } else if (req_path == MFBC_PATH_SMALL) {
+    if (!G->g.unit) return fail(MFBC_ERR_INVALID, "MFBC_PATH_SMALL needs unit weights");
+    paths = {MFBC_PATH_SMALL};
   } else {
     return fail(MFBC_ERR_INVALID, "unknown path");
   }
@@ -804,7 +965,8 @@ extern "C" mfbc_status mfbc_autotune(mfbc_graph* G, const int32_t* sources, int3
   for (int path : paths) {
     const bool level = path == MFBC_PATH_LEVEL;
     std::vector<int> widths = level ? std::vector<int>{128, 256, 512, 1024}
-                                    : std::vector<int>{128, 256, 512, 1024, 2048, 4096};
+                              : path == MFBC_PATH_SMALL ? std::vector<int>{32, 64, 128, 256}
+                                                        : std::vector<int>{128, 256, 512, 1024, 2048, 4096};
     const int gran = level ? 128 : 32;
     const int cols = (nsrc + gran - 1) / gran * gran;
     while (widths.size() > 1 && widths.back() > cols) widths.pop_back();
@@ -839,8 +1001,7 @@ extern "C" mfbc_status mfbc_autotune(mfbc_graph* G, const int32_t* sources, int3
   G->force_arcs = 0;
   if (!best_nb) return fail(MFBC_ERR_OOM, "no candidate batch width fits the device");
   // a width is kept as a cap only when a wider one was tried and lost
-  G->tuned_nb[best_path == MFBC_PATH_LEVEL ? 0 : (best_path == MFBC_PATH_GENERAL ? 1 : 2)] =
-      best_widest ? 0 : best_nb;
+  G->tuned_nb[tuned_slot(best_path)] = best_widest ? 0 : best_nb;
   if (best_path == MFBC_PATH_GENERAL) G->tuned_arcs = best_arcs;
   if (req_path == MFBC_PATH_AUTO) G->tuned_path = best_path;
   out->n_b = best_nb;

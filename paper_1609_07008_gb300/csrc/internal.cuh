@@ -64,7 +64,7 @@ struct KStat {
 enum KId {
   K_FILL = 0, K_SEED, K_RELAX_MIN, K_RELAX_TIE, K_ACCUM, K_COUNTERS, K_PROPAGATE, K_FINAL,
   K_LAMBDA, K_CLEAR, K_LVL_FWD, K_LVL_VISIT, K_LVL_BWD, K_LVL_HUB, K_LVL_RESET, K_OUTPUT,
-  K_LVL_FWD_G, K_LVL_BWD_G, K_LVL_SPLIT, K_DP_FWD, K_DP_BWD, K_NUM
+  K_LVL_FWD_G, K_LVL_BWD_G, K_LVL_SPLIT, K_DP_FWD, K_DP_BWD, K_SMALL, K_NUM
 };
 
 // Bits of Counters::flags, set by kernels and read by the host drivers.
@@ -72,6 +72,7 @@ constexpr uint32_t FLAG_LEVEL_LIST = 1u;     // level kernels: a per-level verte
 constexpr uint32_t FLAG_SIGMA_INEXACT = 2u;  // some sigma_bar >= 2^53 (FP64 output may be rounded)
 constexpr uint32_t FLAG_BAD_SOURCE = 4u;     // mfbc_bc_static: a source id outside [0, n)
 constexpr uint32_t FLAG_COUNT_WRAP = 8u;     // level kernels: a path count reached 2^58 (batch redone)
+constexpr uint32_t FLAG_TIMEOUT = 16u;       // a bounded device-side wait ran out (MFBC_ERR_TIMEOUT)
 
 // Device-side counters of algorithmic bytes, one slot per kernel id.
 struct Counters {
@@ -199,6 +200,30 @@ struct DistState {
 size_t dist_bytes(int32_t n, int nb, int B);
 void dist_carve(Carver& c, int32_t n, int nb, int B, DistState& s);
 
+// Persistent path for small unit-weight graphs: whole batches inside one
+// cooperative launch, block groups taking batches from a device queue.  See
+// small.cu.
+struct SmallGroupCtl {  // one per block group, on its own 128-byte line
+  uint32_t arrive;      // barrier arrivals of the group's blocks (monotonic)
+  uint32_t batch;       // batch the group works on
+  uint32_t wrap;        // a path count of the batch reached 2^58
+  uint32_t any[3];      // a pair entered level l + 1 during product l (slot l % 3)
+  uint32_t pad[26];
+};
+struct SmallState {
+  int nb = 0, W = 0, G = 0;
+  uint8_t* lvl;         // [G][n][nb] tau, 255 = unreached
+  uint64_t* sv;         // [G][n][nb] sigma_bar, then zeta + 1/sigma_bar (double-float)
+  SmallGroupCtl* ctl;   // [G]
+  uint32_t* head;       // [0] batch queue head, [1] batches listed in redo
+  int32_t* redo;        // batches left to the general kernels (too deep or counts >= 2^58)
+  Counters* ctr;
+};
+size_t small_bytes(int32_t n, int nb, int groups);
+void small_carve(Carver& c, int32_t n, int nb, int groups, SmallState& s);
+// groups a call launches for nbatch batches (bounded by a quarter of the co-resident blocks)
+int small_groups(int32_t n, int nb, int nbatch);
+
 // --------------------------------------------------------------- drivers
 struct RunCtx {
   const DevGraph* g;
@@ -239,6 +264,15 @@ mfbc_status level_output(RunCtx& rc, LevelState& s, int levels, int nactive, int
 mfbc_status dist_batch(RunCtx& rc, DistState& s, const int32_t* d_src_batch, int nactive, double* lambda,
                        int64_t* fwd_iters, int64_t* bwd_iters);
 mfbc_status dist_output(RunCtx& rc, DistState& s, int nactive, int32_t* dist_out, double* sigma_out);
+
+// All batches of a call on the persistent small-graph kernel.  d_src_all:
+// [nbatch][nb] columns' sources (-1 padding); d_wreq: [nbatch][W] lambda row
+// of each word or null (row 0).  lambda null: MFBF only, writing sssp rows
+// b*nb + j < out_rows of dist_out / sigma_out.  Batches the kernel could not
+// finish (too deep, or counts >= 2^58) are returned in redo, untouched.
+mfbc_status small_run(RunCtx& rc, SmallState& s, const int32_t* d_src_all, const int32_t* d_wreq, int nbatch,
+                      double* lambda, int32_t* dist_out, double* sigma_out, int32_t out_rows, uint32_t opt_flags,
+                      std::vector<int32_t>* redo);
 void level_reset(RunCtx& rc, LevelState& s, int levels);
 
 // Graph construction helpers (graph.cu).

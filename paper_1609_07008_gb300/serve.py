@@ -6,23 +6,27 @@ server receives many independent lists and can pack their columns into the
 same MFBF/MFBr batches (Algorithm 3's batch dimension), which amortises the
 per-level costs of small requests.
 
-`Server` keeps the graphs resident on the device and runs one worker thread
-per graph:
+`Server` keeps the graphs resident on the device and runs workers (one CUDA
+stream each; `replicas` gives a graph more of them):
 
-* continuous batching -- a worker takes, in arrival order, the pending
-  requests of its graph up to `max_cols` packed columns (each request rounded
-  up to 32) and runs them in one `mfbc_bc_multi_device` call, which returns
-  one lambda row per request; requests that arrive meanwhile wait for the
-  worker's next group;
-* memory-budget admission -- a group holds the device bytes of its scratch
-  (`mfbc_workspace_size`, mode 2) plus its lambda rows; a group starts only
-  when the bytes held by running groups leave room for it, and its n_b is
-  lowered until a lone group fits;
-* overlap -- every worker issues its work on its own CUDA stream, so groups
-  of different graphs run on the device at once; extra handles of one graph
-  (`replicas`) give it more workers, so that several of its groups overlap
-  too (a graph whose batches leave the device idle between their short
-  kernels, such as a weighted grid on the general kernels, gains most).
+* continuous batching at batch granularity -- a worker runs one batch of
+  n_b columns at a time.  Before each batch it fills the columns, in arrival
+  order, first with the next sources of the requests it already serves, then
+  with newly arrived requests of its graph (each request's part starts on a
+  32-column word).  A request that arrives while a batch runs joins the next
+  batch; a large request is spread over several batches and shares them
+  with others.  Each batch is one `mfbc_bc_multi_device` call that adds
+  every part's lambda into its request's row of the worker's lambda pool
+  (lambda is linear in the source list, MFBC_OPT_ACCUMULATE); a request is
+  answered when the batch holding its last sources completes;
+* memory-budget admission -- a worker holds its batch scratch
+  (`mfbc_workspace_size`, mode 2) and one lambda row per request it can
+  serve at once (n_b / 32 rows); it takes this memory from the budget when
+  it has work and gives it back when idle, so the workers of other graphs
+  wait while the budget is spent; n_b is lowered until one worker fits;
+* overlap -- every worker issues its work on its own CUDA stream, so the
+  batches of different graphs (and of one graph's replicas) run on the device
+  at once.
 
 `run_plain` is the one-request-at-a-time form (one mfbc_bc_device call per
 request, in arrival order) that the server is compared against.
@@ -33,7 +37,7 @@ import collections
 import math
 import threading
 import time
-from dataclasses import dataclass, field
+from dataclasses import dataclass
 
 import numpy as np
 
@@ -48,14 +52,18 @@ class Request:
     graph: str
     sources: np.ndarray                  # int32 vertex ids
     arrival: float = 0.0                 # seconds, on the run's clock
-    start: float = math.nan
+    start: float = math.nan              # its first batch began
     done: float = math.nan
     result: np.ndarray | None = None     # lambda, float64[n]
-    group: int = -1
+    group: int = -1                      # index of its first batch in Server.log
+    placed: int = 0                      # sources already given to batches
+    slot: int = -1                       # its row in the worker's lambda pool
 
 
 @dataclass
 class GroupLog:
+    """One batch: the requests it held (nreq), how many of them started in it
+    (new), the columns used, its width and the bytes its worker held."""
     graph: str
     nreq: int
     cols: int
@@ -63,27 +71,43 @@ class GroupLog:
     bytes: int
     t0: float
     t1: float
+    new: int = 0
+    worker: int = 0
+
+
+class _Worker:
+    def __init__(self, wid, key, handle):
+        self.wid, self.key, self.handle = wid, key, handle
+        self.bound: collections.deque = collections.deque()   # requests served, arrival order
+        self.free_slots: list[int] = []
+        self.active = False
+        self.nb = 0
+        self.need = 0
+        self.pool = None                   # [slots, n] lambda rows
+        self.ws = None                     # batch scratch (GPU)
+        self.stream = None
 
 
 class Server:
     """Resident graphs, memory-budget admission, continuous batching.
 
-    graphs: name -> paper_1609_07008_gb300.Graph.  executor(name, group,
-    n_b, ws_bytes, stream) -> list of lambda arrays may replace the GPU call
-    (host-logic tests); sizer(name, cols, nreq, n_b) -> bytes likewise."""
+    graphs: name -> paper_1609_07008_gb300.Graph.  For host-logic tests,
+    executor(key, parts, n_b, pool, rows, stream, handle) may replace the GPU
+    call (it must add each part's lambda into pool[row]; parts are (request,
+    first source, count)), and sizer(key, n_b, slots) -> bytes the
+    library's scratch size; the pool is then a numpy array."""
 
-    def __init__(self, graphs: dict, *, budget_bytes: int, max_cols: int = 4096, n_b: int = 0,
+    def __init__(self, graphs: dict, *, budget_bytes: int, max_cols: int = 1024, n_b: int = 0,
                  executor=None, sizer=None, clock=time.perf_counter, replicas: dict | None = None):
         self.graphs = graphs
-        # extra handles of the same graphs: one more worker (and CUDA stream)
-        # each, so that several groups of one graph can run at once
         self.handles = {k: [G] + list((replicas or {}).get(k, [])) for k, G in graphs.items()}
         self.budget = int(budget_bytes)
         self.max_cols = int(max_cols)
         self.n_b = int(n_b)
         self.clock = clock
+        self._gpu = executor is None
         self.executor = executor or self._execute_gpu
-        self.sizer = sizer or self._group_bytes
+        self.sizer = sizer or self._worker_bytes
         self._cv = threading.Condition()
         self._pending = {k: collections.deque() for k in graphs}
         self._held = 0
@@ -91,8 +115,9 @@ class Server:
         self._inflight = 0
         self.log: list[GroupLog] = []
         self.errors: list[BaseException] = []
-        self._threads = [threading.Thread(target=self._worker, args=(k, h), daemon=True)
-                         for k in graphs for h in self.handles[k]]
+        self._workers = [_Worker(i, k, h) for i, (k, h) in
+                         enumerate((k, h) for k in graphs for h in self.handles[k])]
+        self._threads = [threading.Thread(target=self._run, args=(w,), daemon=True) for w in self._workers]
 
     # ------------------------------------------------------------ public
     def start(self) -> "Server":
@@ -128,89 +153,182 @@ class Server:
         for t in self._threads:
             t.join()
 
-    # ------------------------------------------------------------ internals
-    def _take_group(self, key):
-        q = self._pending[key]
-        group, cols = [], 0
-        while q:
-            c = align32(len(q[0].sources))
-            if group and cols + c > self.max_cols:
-                break
-            group.append(q.popleft())
-            cols += c
-        return group, cols
+    def stats(self) -> dict:
+        """Packing of the batches run so far: requests per batch, columns
+        used per batch, batches that held several requests."""
+        if not self.log:
+            return {"batches": 0}
+        nreq = np.array([g.nreq for g in self.log])
+        cols = np.array([g.cols / g.n_b for g in self.log])
+        return {"batches": len(self.log), "requests_per_batch_mean": float(nreq.mean()),
+                "requests_per_batch_max": int(nreq.max()),
+                "batches_with_several_requests": float((nreq > 1).mean()),
+                "columns_used_mean": float(cols.mean())}
 
-    def _fit(self, key, cols, nreq):
-        """The group's n_b and bytes: self.n_b (0 = the library's own choice
-        for the group's columns), lowered in steps of 128 while the group
-        alone would not fit the budget."""
-        nb = self.n_b
-        need = self.sizer(key, cols, nreq, nb)
-        if need > self.budget and nb == 0:
-            nb = 1024
-            need = self.sizer(key, cols, nreq, nb)
+    # ------------------------------------------------------------ internals
+    def _width(self, key):
+        """The worker's n_b and bytes: n_b (or max_cols), lowered in steps of
+        128 while one worker would not fit the budget."""
+        nb = self.n_b or self.max_cols
+        need = self.sizer(key, nb, max(1, nb // 32))
         while need > self.budget and nb > 128:
-            nb -= 128
-            need = self.sizer(key, cols, nreq, nb)
+            nb = max(128, nb - 128)
+            need = self.sizer(key, nb, max(1, nb // 32))
         return nb, need
 
-    def _worker(self, key, handle):
-        stream = None
+    def _fill(self, w: _Worker):
+        """Columns of the next batch.  The requests the worker serves that
+        still have sources, then newly arrived ones (while pool rows and
+        32-column words are free), share the batch's words equally as far as
+        each needs them (water filling), so a request that arrives while a
+        large one runs gets its share of the very next batch."""
+        words = max(1, w.nb // 32)
+        cands = [r for r in w.bound if len(r.sources) > r.placed]
+        new = 0
+        q = self._pending[w.key]
+        while q and w.free_slots and len(cands) < words:
+            r = q.popleft()
+            r.slot = w.free_slots.pop()
+            r.start, r.group = self.clock(), len(self.log)
+            w.bound.append(r)
+            new += 1
+            if len(r.sources):
+                cands.append(r)
+        need = [-(-(len(r.sources) - r.placed) // 32) for r in cands]
+        alloc = [0] * len(cands)
+        left = words
+        order = sorted(range(len(cands)), key=lambda i: need[i])
+        for k, i in enumerate(order):           # smallest needs first, the rest share what remains
+            share = min(need[i], left // (len(order) - k))
+            alloc[i] = share
+            left -= share
+        for i in order[::-1]:                   # words left by rounding go to the largest needs
+            extra = min(left, need[i] - alloc[i])
+            alloc[i] += extra
+            left -= extra
+        parts, cols = [], 0
+        for r, a in zip(cands, alloc):
+            if a:
+                take = min(len(r.sources) - r.placed, 32 * a)
+                parts.append((r, r.placed, take))
+                r.placed += take
+                cols += align32(take)
+        for r in w.bound:                       # requests without sources are answered with this batch
+            if len(r.sources) == 0 and r.group == len(self.log):
+                parts.append((r, 0, 0))
+        return parts, cols, new
+
+    def _has_work(self, w: _Worker) -> bool:
+        if any(len(r.sources) > r.placed for r in w.bound):
+            return True
+        return bool(self._pending[w.key]) and (not w.active or bool(w.free_slots))
+
+    def _run(self, w: _Worker):
         try:
             import torch
-            if torch.cuda.is_available() and self.executor == self._execute_gpu:
-                stream = torch.cuda.Stream()
+            if self._gpu and torch.cuda.is_available():
+                w.stream = torch.cuda.Stream()
         except ImportError:
             pass
         while True:
             with self._cv:
-                while not self._pending[key] and not self._stop:
+                while True:
+                    if self._has_work(w):
+                        if w.active:
+                            break
+                        nb, need = self._width(w.key)
+                        # admission: start when the active workers leave room
+                        if not self._held or self._held + need <= self.budget:
+                            w.active, w.nb, w.need = True, nb, need
+                            w.free_slots = list(range(max(1, nb // 32)))[::-1]
+                            self._held += need
+                            break
+                    elif w.active and not w.bound:
+                        # idle: give the memory back to the budget
+                        w.active = False
+                        self._held -= w.need
+                        w.pool = w.ws = None
+                        self._cv.notify_all()
+                    elif self._stop and not w.bound and not self._pending[w.key]:
+                        return
                     self._cv.wait()
-                if not self._pending[key]:
-                    return
-                group, cols = self._take_group(key)
-                nb, need = self._fit(key, cols, len(group))
-                # admission: wait until the running groups leave room
-                while self._held and self._held + need > self.budget:
-                    self._cv.wait()
-                self._held += need
+                parts, cols, new = self._fill(w)
                 gid = len(self.log)
-                self.log.append(GroupLog(key, len(group), cols, nb, need, self.clock(), math.nan))
-            t0 = self.clock()
-            for r in group:
-                r.start, r.group = t0, gid
+                self.log.append(GroupLog(w.key, len({id(p[0]) for p in parts}), cols, w.nb, w.need,
+                                         self.clock(), math.nan, new, w.wid))
             try:
-                results = self.executor(key, group, nb, need, stream) if self.executor != self._execute_gpu \
-                    else self._execute_gpu(key, group, nb, need, stream, handle)
+                self._ensure_memory(w)
+                for r, first, _ in parts:
+                    if first == 0:
+                        self._zero_row(w, r.slot)
+                rows = [r.slot for r, _, _ in parts]
+                if self._gpu:
+                    self._execute_gpu(w, parts, rows)
+                else:
+                    self.executor(w.key, parts, w.nb, w.pool, rows, None, None)
+                finished = [r for r in w.bound if r.placed >= len(r.sources)]
+                results = [self._read_row(w, r.slot) for r in finished]
             except BaseException as e:             # surface to drain()
                 with self._cv:
                     self.errors.append(e)
-                    self._held -= need
+                    if w.active:
+                        self._held -= w.need
+                    w.active = False
                     self._cv.notify_all()
                 return
             t1 = self.clock()
             with self._cv:
-                for r, lam in zip(group, results):
+                for r, lam in zip(finished, results):
                     r.result, r.done = lam, t1
+                    w.bound.remove(r)
+                    w.free_slots.append(r.slot)
                 self.log[gid].t1 = t1
-                self._held -= need
-                self._inflight -= len(group)
+                self._inflight -= len(finished)
                 self._cv.notify_all()
 
-    def _group_bytes(self, key, cols, nreq, nb):
-        G = self.graphs[key]
-        return G.workspace_size(cols, 2, n_b=nb) + 8 * nreq * G.n
-
-    def _execute_gpu(self, key, group, nb, ws_bytes, stream, handle=None):
+    def _ensure_memory(self, w: _Worker):
+        n = self.graphs[w.key].n
+        slots = max(1, w.nb // 32)
+        if w.pool is not None and w.pool.shape[0] == slots:
+            return
+        if not self._gpu:
+            w.pool = np.zeros((slots, n))
+            return
         import torch
-        G = handle if handle is not None else self.graphs[key]
-        with torch.cuda.stream(stream):
-            srcs = [torch.from_numpy(np.ascontiguousarray(r.sources, dtype=np.int32)).to("cuda", non_blocking=True)
-                    for r in group]
-            ws = torch.empty(ws_bytes - 8 * len(group) * G.n, dtype=torch.uint8, device="cuda")
-            lam = G.bc_multi(srcs, n_b=nb, stream=stream, workspace=ws)
-            host = lam.to("cpu")
-        return [host[i].numpy() for i in range(len(group))]
+        G = self.graphs[w.key]
+        with torch.cuda.stream(w.stream):
+            w.pool = torch.zeros((slots, n), dtype=torch.float64, device="cuda")
+            w.ws = torch.empty(max(1, G.workspace_size(w.nb, 2, n_b=w.nb)), dtype=torch.uint8, device="cuda")
+
+    def _zero_row(self, w: _Worker, slot: int):
+        if self._gpu:
+            import torch
+            with torch.cuda.stream(w.stream):
+                w.pool[slot].zero_()
+        else:
+            w.pool[slot] = 0.0
+
+    def _read_row(self, w: _Worker, slot: int):
+        if self._gpu:
+            import torch
+            with torch.cuda.stream(w.stream):
+                return w.pool[slot].to("cpu").numpy()
+        return w.pool[slot].copy()
+
+    def _worker_bytes(self, key, nb, slots):
+        G = self.graphs[key]
+        return G.workspace_size(nb, 2, n_b=nb) + 8 * slots * G.n
+
+    def _execute_gpu(self, w: _Worker, parts, rows):
+        """One batch: every part's lambda added into its request's pool row."""
+        import torch
+        src = np.concatenate([r.sources[a:a + k] for r, a, k in parts]).astype(np.int32)
+        off = np.zeros(len(parts) + 1, dtype=np.int32)
+        off[1:] = np.cumsum([k for _, _, k in parts])
+        with torch.cuda.stream(w.stream):
+            d_src = torch.from_numpy(src).to("cuda")
+            w.handle.bc_multi((d_src, off), n_b=w.nb, stream=w.stream, workspace=w.ws, out=w.pool, rows=rows,
+                              accumulate=True)
 
 
 def run_served(server: Server, requests: list[Request], clock=time.perf_counter, timeout=None):

@@ -21,7 +21,7 @@ import paper_1609_07008_gb300 as mfbc
 
 pytestmark = pytest.mark.gpu
 RTOL = 1e-9
-PATHS = [mfbc.PATH_LEVEL, mfbc.PATH_GENERAL, mfbc.PATH_DIST]
+PATHS = [mfbc.PATH_LEVEL, mfbc.PATH_GENERAL, mfbc.PATH_DIST, mfbc.PATH_SMALL]
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -222,7 +222,7 @@ def test_long_path_exceeds_level_capacity_and_falls_back():
     n = 300                                  # depth 299 > the level kernels' 64-level capacity
     g = gg.from_edges(n, [(i, i + 1) for i in range(n - 1)], directed=False)
     srcs = np.arange(0, n, 7, dtype=np.int32)
-    check_graph(g, srcs, n_b=32, paths=[mfbc.PATH_LEVEL])
+    check_graph(g, srcs, n_b=32, paths=[mfbc.PATH_LEVEL, mfbc.PATH_SMALL])
 
 
 def _grid(L):
@@ -316,7 +316,7 @@ def test_profile_reports_kernels():
         assert prof["batches"] == 1 and prof["fwd_iters"] > 0 and prof["bwd_iters"] > 0
         ks = prof["kernels"]
         main = {mfbc.PATH_LEVEL: "level_mfbf_gather", mfbc.PATH_GENERAL: "mfbf_relax_min",
-                mfbc.PATH_DIST: "dist_mfbf"}[p]
+                mfbc.PATH_DIST: "dist_mfbf", mfbc.PATH_SMALL: "small_persistent"}[p]
         assert ks[main]["launches"] > 0 and ks[main]["ms"] > 0 and ks[main]["bytes"] > 0
     G.close()
 
@@ -408,11 +408,13 @@ def test_autotune_picks_a_candidate_and_results_are_unchanged(weighted):
         assert t["path"] in (mfbc.PATH_GENERAL, mfbc.PATH_DIST) and t["tried"] == 9
         assert t["arcs"] in ((1, 8) if t["path"] == mfbc.PATH_GENERAL else (0,))
     else:
-        assert t["path"] == mfbc.PATH_LEVEL and t["tried"] == 3 and t["arcs"] == 0
-    assert t["n_b"] in {128, 256, 512} and t["ms_per_source"] > 0
+        # level kernels (3 widths) and the persistent small-graph kernel (4 widths)
+        assert t["path"] in (mfbc.PATH_LEVEL, mfbc.PATH_SMALL) and t["tried"] == 7 and t["arcs"] == 0
+    assert t["n_b"] in {32, 64, 128, 256, 512} and t["ms_per_source"] > 0
     lam, prof = G.bc(srcs, profile=True)
     assert prof["path"] == t["path"]
-    if t["n_b"] < 512:                      # a wider width was tried and lost: it caps later calls
+    widest = 256 if t["path"] == mfbc.PATH_SMALL else 512
+    if t["n_b"] < widest:                   # a wider width was tried and lost: it caps later calls
         assert prof["n_b"] <= t["n_b"]
     assert_lambda_close(lam, oracle.bc(g, srcs))
     G.close()

@@ -1,6 +1,6 @@
-"""Host logic of the serving loop, without a GPU: a fake executor answers
-each request with the CPU oracle, so grouping, admission and the latency
-bookkeeping are checked on their own."""
+"""Host logic of the serving loop, without a GPU: a fake executor adds each
+batch part's oracle lambda into its request's pool row, so batching,
+admission and the latency bookkeeping are checked on their own."""
 import threading
 import time
 
@@ -25,12 +25,15 @@ class Recorder:
         self.held_seen = []
         self.lock = threading.Lock()
 
-    def __call__(self, key, group, nb, need, stream):
+    def __call__(self, key, parts, nb, pool, rows, stream, handle):
         with self.lock:
             self.held_seen.append(self.server_ref[0]._held)
+        assert sum(align32(k) for _, _, k in parts) <= nb
         if self.delay:
             time.sleep(self.delay)
-        return [oracle.bc(self.graphs[key], r.sources, nthreads=1) for r in group]
+        for (r, a, k), row in zip(parts, rows):
+            if k:
+                pool[row] += oracle.bc(self.graphs[key], r.sources[a:a + k], nthreads=1)
 
 
 def test_groups_respect_columns_and_results_match_the_oracle():
@@ -38,7 +41,7 @@ def test_groups_respect_columns_and_results_match_the_oracle():
     ref = []
     rec = Recorder(graphs, ref)
     srv = Server(graphs, budget_bytes=1 << 40, max_cols=256, executor=rec,
-                 sizer=lambda k, cols, nreq, nb: cols * 100)
+                 sizer=lambda k, nb, slots: nb * 100)
     ref.append(srv)
     reqs = make_requests({k: g.n for k, g in graphs.items()}, 40, rate=0, lo=5, hi=200, seed=3)
     srv.start()
@@ -47,22 +50,24 @@ def test_groups_respect_columns_and_results_match_the_oracle():
     for r in reqs:
         np.testing.assert_allclose(r.result, oracle.bc(graphs[r.graph], r.sources), rtol=1e-12, atol=0)
         assert r.arrival <= r.start <= r.done
-    # every group fits max_cols unless it is a single oversize request
+    # every batch fits its columns (requests larger than a batch are split)
     for g in srv.log:
-        assert g.cols <= 256 or g.nreq == 1
-    # all requests arrived at once: several share a group (continuous batching)
+        assert g.cols <= 256
+    # all requests arrived at once: several share a batch (continuous batching)
     assert max(g.nreq for g in srv.log) > 1
-    assert sum(g.nreq for g in srv.log) == len(reqs)
+    assert sum(g.new for g in srv.log) == len(reqs)
+    st = srv.stats()
+    assert st["batches"] == len(srv.log) and st["batches_with_several_requests"] > 0
 
 
 def test_admission_never_exceeds_the_budget():
     graphs = _graphs()
     ref = []
     rec = Recorder(graphs, ref, delay=0.02)
-    # each group holds 1000 bytes per column; the budget lets one group of at
-    # most 1024 columns run, so the two graphs' workers must take turns
+    # a worker holds 1000 bytes per column; the budget lets one worker of
+    # 1024 columns run, so the two graphs' workers must take turns
     srv = Server(graphs, budget_bytes=1024 * 1000, max_cols=1024, executor=rec,
-                 sizer=lambda k, cols, nreq, nb: cols * 1000)
+                 sizer=lambda k, nb, slots: nb * 1000)
     ref.append(srv)
     reqs = make_requests({k: g.n for k, g in graphs.items()}, 30, rate=0, lo=200, hi=300, seed=4)
     srv.start()
@@ -82,7 +87,7 @@ def test_groups_run_concurrently_when_the_budget_allows():
     ref = []
     rec = Recorder(graphs, ref, delay=0.05)
     srv = Server(graphs, budget_bytes=1 << 40, max_cols=64, executor=rec,
-                 sizer=lambda k, cols, nreq, nb: cols)
+                 sizer=lambda k, nb, slots: nb)
     ref.append(srv)
     reqs = [Request(i, "a" if i % 2 else "b", np.arange(10, dtype=np.int32), 0.0) for i in range(8)]
     srv.start()
@@ -93,16 +98,15 @@ def test_groups_run_concurrently_when_the_budget_allows():
     assert overlap
 
 
-def test_oversize_group_lowers_n_b_until_it_fits():
+def test_oversize_worker_lowers_n_b_until_it_fits():
     graphs = _graphs()
     seen = []
 
-    def sizer(k, cols, nreq, nb):
-        return (nb or 4096) * 10                  # n_b = 0: the library would take 4096 columns
+    def sizer(k, nb, slots):
+        return nb * 10
 
-    def ex(key, group, nb, need, stream):
+    def ex(key, parts, nb, pool, rows, stream, handle):
         seen.append(nb)
-        return [np.zeros(graphs[key].n) for _ in group]
 
     srv = Server(graphs, budget_bytes=300 * 10, max_cols=4096, n_b=0, executor=ex, sizer=sizer)
     srv.start()
@@ -146,7 +150,7 @@ def test_replica_handles_let_groups_of_one_graph_overlap():
     graphs = _graphs()
     ref = []
     rec = Recorder(graphs, ref, delay=0.05)
-    srv = Server(graphs, budget_bytes=1 << 40, max_cols=32, executor=rec, sizer=lambda k, cols, nreq, nb: cols,
+    srv = Server(graphs, budget_bytes=1 << 40, max_cols=32, executor=rec, sizer=lambda k, nb, slots: nb,
                  replicas={"a": [object(), object()]})
     ref.append(srv)
     assert len(srv._threads) == 4                   # three workers for "a", one for "b"
@@ -157,4 +161,25 @@ def test_replica_handles_let_groups_of_one_graph_overlap():
     spans = [(g.t0, g.t1) for g in srv.log]
     assert any(a[0] < b[1] and b[0] < a[1] for i, a in enumerate(spans) for b in spans[i + 1:])
     for r in reqs:
+        np.testing.assert_allclose(r.result, oracle.bc(graphs["a"], r.sources), rtol=1e-12, atol=0)
+
+
+def test_request_arriving_during_a_batch_joins_the_next_one():
+    # one worker, 256-column batches: a 1000-source request needs four; a
+    # small request arriving while the first runs is admitted into the
+    # second and answered long before the large one
+    graphs = {"a": gg.rmat(9, 8, seed=5)}
+    ref = []
+    rec = Recorder(graphs, ref, delay=0.1)
+    srv = Server(graphs, budget_bytes=1 << 40, max_cols=256, executor=rec, sizer=lambda k, nb, slots: nb)
+    ref.append(srv)
+    big = Request(0, "a", gg.sample_sources(graphs["a"], 300, seed=1).repeat(4)[:1000].astype(np.int32), 0.0)
+    small = Request(1, "a", np.arange(40, dtype=np.int32), 0.05)
+    srv.start()
+    run_served(srv, [big, small], timeout=60)
+    srv.close()
+    assert len(srv.log) == 5                         # 4 batches of the big one; the small shares the 2nd
+    assert small.group == 1 and srv.log[1].nreq == 2 and srv.log[1].new == 1
+    assert small.done < big.done
+    for r in (big, small):
         np.testing.assert_allclose(r.result, oracle.bc(graphs["a"], r.sources), rtol=1e-12, atol=0)

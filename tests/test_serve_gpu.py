@@ -88,3 +88,31 @@ def test_server_answers_each_request_as_if_alone():
     assert st["p50_ms"] > 0 and st["p99_ms"] >= st["p50_ms"] and st["gteps"] > 0
     for G in graphs.values():
         G.close()
+
+
+@pytest.mark.parametrize("path", [mfbc.PATH_LEVEL, mfbc.PATH_SMALL, mfbc.PATH_GENERAL])
+def test_requests_split_over_calls_accumulate_into_their_rows(path):
+    # the serving loop's use of mfbc_bc_multi_device: each request owns a row
+    # of a pool (lambda_rows, in any order), and a request split over several
+    # calls (MFBC_OPT_ACCUMULATE) sums to its answer alone
+    import torch
+    g = gg.rmat(11, 8, seed=31)
+    lists = _lists(g, [300, 45, 128, 7], seed=6)
+    G = mfbc.Graph.from_csr(g)
+    pool = torch.full((6, g.n), 123.0, dtype=torch.float64, device="cuda")
+    rows = [4, 0, 2, 5]
+    pool[rows] = 0.0
+    cuts = [(0, 100), (100, 300)]
+    for lo, hi in cuts:
+        parts = [torch.from_numpy(x[min(lo, len(x)):min(hi, len(x))]).cuda() for x in lists]
+        G.bc_multi(parts, n_b=128, path=path, out=pool, rows=rows, accumulate=True)
+    got = pool.cpu().numpy()
+    for r, x in zip(rows, lists):
+        _close(got[r], oracle.bc(g, x))
+    assert np.all(got[[1, 3]] == 123.0)                # rows no request names are untouched
+    # without accumulate the named rows are overwritten
+    G.bc_multi([torch.from_numpy(x).cuda() for x in lists], n_b=128, path=path, out=pool, rows=rows)
+    got = pool.cpu().numpy()
+    for r, x in zip(rows, lists):
+        _close(got[r], oracle.bc(g, x))
+    G.close()
