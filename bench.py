@@ -457,6 +457,7 @@ def main():
     ap.add_argument("--no-workloads", action="store_true", help="skip the other benchmark configurations")
     ap.add_argument("--sources", type=int, default=0, help="use only the first N sources (probing)")
     ap.add_argument("--keep-order", action="store_true", help="batch sources in the given order")
+    ap.add_argument("--accumulator", type=int, default=0, help="general kernels: MFBC_ACCUM_* (0 = auto)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -493,7 +494,8 @@ def main():
     lam = torch.empty(g.n, dtype=torch.float64, device=dev)
 
     def step(profile=False):
-        out = G.bc(d_src, n_b=nb_req, out=lam, profile=profile, keep_order=args.keep_order)
+        out = G.bc(d_src, n_b=nb_req, out=lam, profile=profile, keep_order=args.keep_order,
+                   accumulator=args.accumulator)
         if dist:
             dist.all_reduce(lam)
         return out
@@ -505,7 +507,8 @@ def main():
         torch.cuda.synchronize()
 
     # untimed pass that counts algorithmic bytes per kernel on the device
-    _, prof_bytes = G.bc(d_src, n_b=nb_req, out=lam, count_bytes=True, keep_order=args.keep_order)
+    _, prof_bytes = G.bc(d_src, n_b=nb_req, out=lam, count_bytes=True, keep_order=args.keep_order,
+                         accumulator=args.accumulator)
     for _ in range(args.warmup):
         step()
     clocks = ClockSampler(local)

@@ -125,7 +125,21 @@ typedef struct {
   uint32_t flags;              /* MFBC_OPT_* bits */
   const int32_t* lambda_rows;  /* mfbc_bc_multi_device only, optional HOST int32[nreq]: the row of
                                   lambda_out that receives request r (NULL: row r); rows >= 0 */
+  int32_t accumulator;         /* general kernels: MFBC_ACCUM_*, how a product reduces the
+                                  candidates that meet at one (vertex, column) */
 } mfbc_options;                /* zero-initialised = all defaults */
+
+/* mfbc_options.accumulator (general kernels; the monoid reduction inside the
+ * products of Algorithms 1 and 2, Sec. 3's generalised product) */
+#define MFBC_ACCUM_AUTO      0   /* per product: segmented when the frontier holds at least
+                                    1/64 of the vertices, else atomic (or what mfbc_autotune chose) */
+#define MFBC_ACCUM_ATOMIC    1   /* push from the frontier: atomicMin on the distance, then an
+                                    atomic add of the tied multiplicities (MFBr: atomic adds
+                                    and counter decrements at the predecessors) */
+#define MFBC_ACCUM_SEGMENTED 2   /* pull by target: the candidates of one (vertex, 32-column word)
+                                    form one segment -- the vertex's arcs to the frontier -- and
+                                    are reduced in registers by the warp that owns it (a block
+                                    for rows of more than 256 arcs); no same-address atomics */
 
 /* mfbc_options.flags */
 #define MFBC_OPT_COUNT_BYTES 1u  /* with profile: count algorithmic bytes on the device (slower) */
@@ -226,6 +240,7 @@ typedef struct {
   int32_t arcs;           /* general kernels: arcs walked per step (1 or 8); 0 on the level kernels */
   int32_t tried;          /* configurations timed */
   double ms_per_source;   /* wall time of the fastest configuration per source */
+  int32_t accumulator;    /* general kernels: MFBC_ACCUM_* chosen; 0 on the other families */
 } mfbc_tuning;
 
 /* Autotuner (no counterpart in the paper, whose batch width and processor
@@ -234,8 +249,10 @@ typedef struct {
  * graph handle.  Candidates: n_b in {128, 256, 512, 1024} on the level kernels
  * and, for unit-weight graphs of at most 2^15 vertices and 2^19 arcs, n_b in
  * {32, 64, 128, 256} on the persistent small-graph kernel;
- * n_b in {128, 256, 512, 1024, 2048, 4096} on the general kernels (x {1, 8}
- * arcs per step) and on the distance kernels; each at most nsrc rounded up;
+ * n_b in {128, 256, 512, 1024, 2048, 4096} on the general kernels (x the
+ * atomic accumulator walking 1 or 8 arcs per step, the segmented accumulator,
+ * and the per-product choice) and on the distance kernels; each at most nsrc
+ * rounded up;
  * widths that do not fit the device are skipped.  With opt->path == AUTO a
  * weighted graph tries both the general and (weights <= 4096) the distance
  * kernels and later AUTO calls use the faster family; another path restricts
@@ -243,7 +260,8 @@ typedef struct {
  * Later calls on this handle with opt->n_b == 0 use at most the tuned width
  * (no cap when the fastest width was the widest one tried), and the general
  * kernels use the tuned arcs per step (without tuning: 8 when the average
- * degree is at least 8, else 1).  n_b in opt is ignored.  Results are
+ * degree is at least 8, else 1) and, with opt->accumulator == AUTO, the tuned
+ * accumulator.  n_b and accumulator in opt are ignored.  Results are
  * unaffected. */
 mfbc_status mfbc_autotune(mfbc_graph* g, const int32_t* sources, int32_t nsrc, const mfbc_options* opt,
                           mfbc_tuning* out);

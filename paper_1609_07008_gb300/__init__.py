@@ -38,6 +38,7 @@ MFBC_OPT_COUNT_BYTES = 1
 MFBC_OPT_KEEP_ORDER = 2
 MFBC_OPT_TEST_STALL = 4
 MFBC_OPT_ACCUMULATE = 8
+ACCUM_AUTO, ACCUM_ATOMIC, ACCUM_SEGMENTED = 0, 1, 2
 INF = np.iinfo(np.int32).max
 MAX_KSTATS = 24
 
@@ -75,13 +76,13 @@ class Options(ctypes.Structure):
     _fields_ = [("n_b", ctypes.c_int32), ("path", ctypes.c_int32), ("stream", ctypes.c_void_p),
                 ("workspace", ctypes.c_void_p), ("workspace_bytes", ctypes.c_uint64),
                 ("warn_out", ctypes.POINTER(ctypes.c_uint32)), ("profile", ctypes.POINTER(Profile)),
-                ("flags", ctypes.c_uint32), ("lambda_rows", ctypes.c_void_p)]
+                ("flags", ctypes.c_uint32), ("lambda_rows", ctypes.c_void_p), ("accumulator", ctypes.c_int32)]
 
 
 class Tuning(ctypes.Structure):
     """mfbc_tuning (include/mfbc.h)."""
     _fields_ = [("n_b", ctypes.c_int32), ("path", ctypes.c_int32), ("arcs", ctypes.c_int32),
-                ("tried", ctypes.c_int32), ("ms_per_source", ctypes.c_double)]
+                ("tried", ctypes.c_int32), ("ms_per_source", ctypes.c_double), ("accumulator", ctypes.c_int32)]
 
 
 _lib = None
@@ -169,8 +170,9 @@ def _stream_handle(stream) -> ctypes.c_void_p | None:
 
 
 def _options(n_b, path, stream, workspace, warn, profile, count_bytes=False, keep_order=False,
-             test_stall=False) -> Options:
+             test_stall=False, accumulator=ACCUM_AUTO) -> Options:
     o = Options()
+    o.accumulator = int(accumulator)
     o.flags = (MFBC_OPT_COUNT_BYTES if count_bytes else 0) | (MFBC_OPT_KEEP_ORDER if keep_order else 0) | \
         (MFBC_OPT_TEST_STALL if test_stall else 0)
     o.n_b = int(n_b)
@@ -243,7 +245,7 @@ class Graph:
     # ----------------------------------------------------------- entry points
     def bc(self, sources, *, n_b: int = 0, path: int = PATH_AUTO, out=None, stream=None, workspace=None,
            profile: bool = False, count_bytes: bool = False, keep_order: bool = False,
-           return_warn: bool = False, test_stall: bool = False):
+           return_warn: bool = False, test_stall: bool = False, accumulator: int = ACCUM_AUTO):
         """Betweenness centrality summed over `sources` (Algorithm 3).
 
         Host (numpy) sources -> numpy lambda via mfbc_bc; torch CUDA sources
@@ -252,7 +254,7 @@ class Graph:
         lib = load()
         warn = ctypes.c_uint32(0)
         prof = Profile() if (profile or count_bytes) else None
-        opt = _options(n_b, path, stream, workspace, warn, prof, count_bytes, keep_order, test_stall)
+        opt = _options(n_b, path, stream, workspace, warn, prof, count_bytes, keep_order, test_stall, accumulator)
         if _is_torch(sources):
             import torch
             src = sources.to(dtype=torch.int32).contiguous()
@@ -316,15 +318,16 @@ class Graph:
         t = Tuning()
         opt = _options(0, path, None, None, None, None)
         _check(lib.mfbc_autotune(self._h, _hptr(src), len(src), ctypes.byref(opt), ctypes.byref(t)))
-        return {"n_b": t.n_b, "path": t.path, "arcs": t.arcs, "tried": t.tried, "ms_per_source": t.ms_per_source}
+        return {"n_b": t.n_b, "path": t.path, "arcs": t.arcs, "tried": t.tried, "ms_per_source": t.ms_per_source,
+                "accumulator": t.accumulator}
 
     def sssp(self, sources, *, n_b: int = 0, path: int = PATH_AUTO, with_sigma: bool = True, stream=None,
-             workspace=None, profile: bool = False, return_warn: bool = False):
+             workspace=None, profile: bool = False, return_warn: bool = False, accumulator: int = ACCUM_AUTO):
         """MFBF alone (Algorithm 1): (dist [nsrc, n] int32, sigma [nsrc, n] f64 or None)."""
         lib = load()
         warn = ctypes.c_uint32(0)
         prof = Profile() if profile else None
-        opt = _options(n_b, path, stream, workspace, warn, prof)
+        opt = _options(n_b, path, stream, workspace, warn, prof, accumulator=accumulator)
         if _is_torch(sources):
             import torch
             src = sources.to(dtype=torch.int32).contiguous()

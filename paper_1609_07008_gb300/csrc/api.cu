@@ -4,6 +4,7 @@
 #include <cstring>
 #include <chrono>
 #include <mutex>
+#include <optional>
 #include <string>
 
 #include "internal.cuh"
@@ -24,6 +25,7 @@ struct mfbc_graph {
   int tuned_arcs = 0;
   int tuned_path = 0;               // kernel family for MFBC_PATH_AUTO (0 = by weights)
   int force_arcs = 0;
+  int tuned_accum = 0;              // general kernels' accumulator for MFBC_ACCUM_AUTO (0 = per product)
 };
 
 static thread_local std::string t_err;
@@ -516,6 +518,16 @@ static Packing pack_requests(const int32_t* off, int32_t nreq, int nb, const int
   return p;
 }
 
+// Sources outside [0, n) in the batch table become padding (-1) and raise
+// FLAG_BAD_SOURCE, so no kernel indexes with them.
+__global__ void k_check_table(int32_t* tab, size_t count, int32_t n, Counters* ctr) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < count && (tab[i] < -1 || tab[i] >= n)) {
+    tab[i] = -1;
+    atomicOr(&ctr->flags, FLAG_BAD_SOURCE);
+  }
+}
+
 // Every batch of the call on the persistent small-graph kernel (one launch
 // for modes 0 and 2; mode 1 launches per batch so that host outputs go
 // through the one-batch staging rows).  Batches the kernel hands back (deeper
@@ -547,6 +559,9 @@ mfbc_status small_path(mfbc_graph* G, Run& R, RunCtx& rc, SmallState& ss, const 
       MFBC_CUDA_TRY(cudaMemcpyAsync(d_all, d_src, sizeof(int32_t) * (size_t)nsrc, cudaMemcpyDeviceToDevice, R.st),
                     rc.err);
   }
+  // sources out of [0, n) become padding and fail the call after the launch
+  k_check_table<<<(unsigned)(((size_t)nbatches * nb + 255) / 256), 256, 0, R.st>>>(d_all, (size_t)nbatches * nb,
+                                                                                  g.n, ss.ctr);
   const uint32_t oflags = R.opt ? R.opt->flags : 0u;
   std::vector<int32_t> redo, part;
   if (mode == 1) {
@@ -572,6 +587,8 @@ mfbc_status small_path(mfbc_graph* G, Run& R, RunCtx& rc, SmallState& ss, const 
                               oflags, &redo);
     if (s) return s;
   }
+  if (rc.h_ctr[0] & FLAG_BAD_SOURCE) { *rc.err = "source id out of range"; return MFBC_ERR_INVALID; }
+  if (rc.h_ctr[0] & FLAG_SIGMA_INEXACT) *warn |= MFBC_WARN_SIGMA_INEXACT;
   if (fi) *fi += nbatches - (int64_t)redo.size();
   if (bi) *bi += nbatches - (int64_t)redo.size();
   if (redo.empty()) return MFBC_OK;
@@ -622,6 +639,7 @@ mfbc_status run(mfbc_graph* G, const int32_t* d_src, int32_t nsrc, int mode, dou
   int64_t batches = 0, fi = 0, bi = 0;
   RunCtx rc{&g, R.st, &R.prof, G->h_ctr, &R.err};
   rc.arcs = G->force_arcs ? G->force_arcs : G->tuned_arcs;
+  rc.accum = R.opt && R.opt->accumulator ? R.opt->accumulator : G->tuned_accum;
   Carver c(R.ws, R.ws_bytes);
   GeneralState gs;
   LevelState ls;
@@ -792,9 +810,11 @@ mfbc_status run(mfbc_graph* G, const int32_t* d_src, int32_t nsrc, int mode, dou
                                       cudaMemcpyDeviceToHost, R.st), &R.err);
     }
   }
-  MFBC_CUDA_TRY(cudaMemcpyAsync(G->h_ctr, &ctr->flags, sizeof(uint32_t), cudaMemcpyDeviceToHost, R.st), &R.err);
-  MFBC_CUDA_TRY(cudaStreamSynchronize(R.st), &R.err);
-  if (G->h_ctr[0] & FLAG_SIGMA_INEXACT) warn |= MFBC_WARN_SIGMA_INEXACT;
+  if (P.path != MFBC_PATH_SMALL) {            // the small path read its flags already
+    MFBC_CUDA_TRY(cudaMemcpyAsync(G->h_ctr, &ctr->flags, sizeof(uint32_t), cudaMemcpyDeviceToHost, R.st), &R.err);
+    MFBC_CUDA_TRY(cudaStreamSynchronize(R.st), &R.err);
+    if (G->h_ctr[0] & FLAG_SIGMA_INEXACT) warn |= MFBC_WARN_SIGMA_INEXACT;
+  }
   MFBC_CUDA_TRY(cudaGetLastError(), &R.err);
   if (R.opt && R.opt->warn_out) *R.opt->warn_out = warn;
   if (R.opt && R.opt->profile) finish_profile(R, R.opt->profile, batches, fi, bi, ctr);
@@ -846,9 +866,10 @@ mfbc_status entry(const mfbc_graph* Gc, const int32_t* sources, int32_t nsrc, in
     for (int32_t i = 0; i < nsrc; i++)
       if (sources[i] < 0 || sources[i] >= n) return fail(MFBC_ERR_INVALID, "source id out of range");
   }
+  if (opt && (opt->accumulator < MFBC_ACCUM_AUTO || opt->accumulator > MFBC_ACCUM_SEGMENTED))
+    return fail(MFBC_ERR_INVALID, "unknown accumulator");
   if (opt && opt->warn_out) *opt->warn_out = 0;
   t_err.clear();
-  L2FetchHint l2hint;
   Run R;
   R.G = G;
   R.opt = opt;
@@ -865,6 +886,10 @@ mfbc_status entry(const mfbc_graph* Gc, const int32_t* sources, int32_t nsrc, in
   if (s) return s;
   s = get_workspace(R);
   if (s) return s;
+  // only the level kernels' gathers gain from the 32-byte fetch hint; setting
+  // and restoring it costs two driver calls that small calls would feel
+  std::optional<L2FetchHint> l2hint;
+  if (R.plan.path == MFBC_PATH_LEVEL) l2hint.emplace();
   R.prof.on = opt && opt->profile;
   R.prof.count_bytes = R.prof.on && (opt->flags & MFBC_OPT_COUNT_BYTES);
   R.prof.stream = R.st;
@@ -885,8 +910,9 @@ mfbc_status entry(const mfbc_graph* Gc, const int32_t* sources, int32_t nsrc, in
       if (e != cudaSuccess) { cudaGetLastError(); return fail(MFBC_ERR_CUDA, "copying sources failed"); }
     }
     d_src = ds;
-  } else if (nsrc > 0) {
-    // device sources: validate the range on the host copy
+  } else if (nsrc > 0 && R.plan.path != MFBC_PATH_SMALL) {
+    // device sources: validate the range on the host copy (the persistent
+    // small-graph path checks them on the device, without a round trip)
     std::vector<int32_t> hs((size_t)nsrc);
     if (cudaMemcpyAsync(hs.data(), sources, sizeof(int32_t) * (size_t)nsrc, cudaMemcpyDeviceToHost, R.st) != cudaSuccess ||
         cudaStreamSynchronize(R.st) != cudaSuccess) {
@@ -960,7 +986,7 @@ extern "C" mfbc_status mfbc_autotune(mfbc_graph* G, const int32_t* sources, int3
   o.profile = nullptr;
   o.warn_out = nullptr;
   double best = 0.0;
-  int best_nb = 0, best_arcs = 0, best_path = 0, tried = 0;
+  int best_nb = 0, best_arcs = 0, best_path = 0, best_accum = 0, tried = 0;
   bool best_widest = false;
   for (int path : paths) {
     const bool level = path == MFBC_PATH_LEVEL;
@@ -970,11 +996,18 @@ extern "C" mfbc_status mfbc_autotune(mfbc_graph* G, const int32_t* sources, int3
     const int gran = level ? 128 : 32;
     const int cols = (nsrc + gran - 1) / gran * gran;
     while (widths.size() > 1 && widths.back() > cols) widths.pop_back();
-    const std::vector<int> arcs = path == MFBC_PATH_GENERAL ? std::vector<int>{1, 8} : std::vector<int>{0};
+    // general kernels: atomic products walking 1 or 8 arcs per step, the
+    // segmented products, and the per-product choice between them
+    struct Var { int arcs, accum; };
+    const std::vector<Var> vars = path == MFBC_PATH_GENERAL
+        ? std::vector<Var>{{1, MFBC_ACCUM_ATOMIC}, {8, MFBC_ACCUM_ATOMIC}, {0, MFBC_ACCUM_SEGMENTED}, {0, MFBC_ACCUM_AUTO}}
+        : std::vector<Var>{{0, MFBC_ACCUM_AUTO}};
     o.path = path;
     for (int nb : widths)
-      for (int a : arcs) {
+      for (const Var& var : vars) {
+        const int a = var.arcs;
         o.n_b = nb;
+        o.accumulator = var.accum;
         {
           std::lock_guard<std::mutex> lock(G->mu);
           G->force_arcs = a;
@@ -992,7 +1025,7 @@ extern "C" mfbc_status mfbc_autotune(mfbc_graph* G, const int32_t* sources, int3
         }
         tried++;
         if (best_nb == 0 || ms < best) {
-          best = ms; best_nb = nb; best_arcs = a; best_path = path;
+          best = ms; best_nb = nb; best_arcs = a; best_path = path; best_accum = var.accum;
           best_widest = nb == widths.back();
         }
       }
@@ -1002,13 +1035,17 @@ extern "C" mfbc_status mfbc_autotune(mfbc_graph* G, const int32_t* sources, int3
   if (!best_nb) return fail(MFBC_ERR_OOM, "no candidate batch width fits the device");
   // a width is kept as a cap only when a wider one was tried and lost
   G->tuned_nb[tuned_slot(best_path)] = best_widest ? 0 : best_nb;
-  if (best_path == MFBC_PATH_GENERAL) G->tuned_arcs = best_arcs;
+  if (best_path == MFBC_PATH_GENERAL) {
+    G->tuned_arcs = best_arcs;
+    G->tuned_accum = best_accum;
+  }
   if (req_path == MFBC_PATH_AUTO) G->tuned_path = best_path;
   out->n_b = best_nb;
   out->path = best_path;
   out->arcs = best_arcs;
   out->tried = tried;
   out->ms_per_source = best / nsrc;
+  out->accumulator = best_path == MFBC_PATH_GENERAL ? best_accum : 0;
   t_err.clear();
   return MFBC_OK;
 }

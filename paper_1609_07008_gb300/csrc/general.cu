@@ -56,6 +56,7 @@ void general_carve(Carver& c, int32_t n, int nb, GeneralState& s) {
   s.fmask = c.take<uint32_t>((size_t)n * s.W);
   s.tmask = c.take<uint32_t>((size_t)n * s.W);
   s.vflag = c.take<uint32_t>((size_t)n);
+  s.fmem = c.take<uint32_t>(((size_t)n + 31) / 32);
   s.listA = c.take<int32_t>((size_t)n);
   s.listB = c.take<int32_t>((size_t)n);
   s.src = c.take<int32_t>((size_t)nb);
@@ -110,7 +111,7 @@ __device__ __forceinline__ bool claim_vertex(uint32_t* vflag, int32_t v) {
 
 // Seed (Algorithm 1 start, read as T(s,s) = (0,1), frontier {(s,s)}).
 __global__ void k_gp_seed(const int32_t* __restrict__ src, int nb, int W, int32_t* dist, double* sig,
-                          double* fm, uint32_t* fmask, uint32_t* vflag, int32_t* list,
+                          double* fm, uint32_t* fmask, uint32_t* fmem, uint32_t* vflag, int32_t* list,
                           uint32_t* count) {
   int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= nb) return;
@@ -121,6 +122,7 @@ __global__ void k_gp_seed(const int32_t* __restrict__ src, int nb, int W, int32_
   sig[idx] = 1.0;
   fm[idx] = 1.0;
   atomicOr(&fmask[(size_t)s * W + (j >> 5)], 1u << (j & 31));
+  atomicOr(&fmem[s >> 5], 1u << (s & 31));
   enqueue_once(vflag, list, count, s);
 }
 
@@ -250,17 +252,21 @@ __global__ void __launch_bounds__(256, ARCS > 1 ? 4 : 8) k_gp_relax_tie(
   if (bytes && lane == 0) atomicAdd(bytes, nb_bytes + 8ull * (end - beg) / W + 12ull * __popc(m));
 }
 
-__global__ void k_clear_mask_rows(const int32_t* __restrict__ list, uint32_t count, int W, uint32_t* mask) {
+// Zero the frontier rows of the listed vertices and their membership bits.
+__global__ void k_clear_mask_rows(const int32_t* __restrict__ list, uint32_t count, int W, uint32_t* mask,
+                                  uint32_t* mem) {
   uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= (uint64_t)count * W) return;
-  mask[(size_t)list[i / W] * W + (i % W)] = 0u;
+  const int32_t v = list[i / W];
+  mask[(size_t)v * W + (i % W)] = 0u;
+  if (mem && i % W == 0) atomicAnd(&mem[v >> 5], ~(1u << (v & 31)));
 }
 
 // T := T (+) product, frontier filter, compaction of the next frontier.
 __global__ void __launch_bounds__(256) k_gp_accumulate(
     const int32_t* __restrict__ tlist, const uint32_t* tcount_p, int W, int nb, int32_t* dist,
     double* sig, int32_t* cw, double* cm, double* fm, uint32_t* fmask, uint32_t* tmask, uint32_t* vflag,
-    int32_t* nlist, uint32_t* ncount, unsigned long long* bytes) {
+    uint32_t* fmem, int32_t* nlist, uint32_t* ncount, unsigned long long* bytes) {
   __shared__ int32_t qbuf[8][40];
   int32_t* q = qbuf[threadIdx.x >> 5];
   int qn = 0;
@@ -294,6 +300,7 @@ __global__ void __launch_bounds__(256) k_gp_accumulate(
   }
   if (lane == 0) {
     vflag[v] = 0u;
+    if (any) atomicOr(&fmem[v >> 5], 1u << (v & 31));
     if (bytes) atomicAdd(bytes, nbytes + 8ull);
   }
   wl_push(q, qn, lane == 0 && any, v, nlist, ncount);
@@ -307,7 +314,7 @@ __global__ void __launch_bounds__(256, ARCS > 1 ? 4 : 6) k_gp_counters(
     int32_t n, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
     const int32_t* __restrict__ wt, int W, int nb, const int32_t* __restrict__ src,
     const int32_t* __restrict__ dist, const double* __restrict__ sig, int32_t* cnt, double* zp, double* fv,
-    uint32_t* fmask, int32_t* flist, uint32_t* fcount, unsigned long long* bytes) {
+    uint32_t* fmask, uint32_t* fmem, int32_t* flist, uint32_t* fcount, unsigned long long* bytes) {
   uint64_t gw = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (gw >= (uint64_t)n) return;
   const unsigned lane = lane_id();
@@ -355,7 +362,10 @@ __global__ void __launch_bounds__(256, ARCS > 1 ? 4 : 6) k_gp_counters(
     nbytes += 4ull * __popc(rb) * (end - beg) + 24ull * __popc(rb);
   }
   if (lane == 0) {
-    if (any) flist[atomicAdd(fcount, 1u)] = v;
+    if (any) {
+      flist[atomicAdd(fcount, 1u)] = v;
+      atomicOr(&fmem[v >> 5], 1u << (v & 31));
+    }
     if (bytes) atomicAdd(bytes, nbytes + 8ull * (end - beg));
   }
 }
@@ -436,7 +446,7 @@ __global__ void __launch_bounds__(256, ARCS > 1 ? 4 : 6) k_gp_propagate(
 __global__ void __launch_bounds__(256) k_gp_next_frontier(
     const int32_t* __restrict__ tlist, const uint32_t* tcount_p, int W, int nb,
     const double* __restrict__ sig, const double* __restrict__ zp, double* fv, uint32_t* fmask,
-    uint32_t* tmask, uint32_t* vflag, int32_t* nlist, uint32_t* ncount, unsigned long long* bytes) {
+    uint32_t* tmask, uint32_t* vflag, uint32_t* fmem, int32_t* nlist, uint32_t* ncount, unsigned long long* bytes) {
   __shared__ int32_t qbuf[8][40];
   int32_t* q = qbuf[threadIdx.x >> 5];
   int qn = 0;
@@ -459,6 +469,7 @@ __global__ void __launch_bounds__(256) k_gp_next_frontier(
   }
   if (lane == 0) {
     vflag[v] = 0u;
+    atomicOr(&fmem[v >> 5], 1u << (v & 31));
     if (bytes) atomicAdd(bytes, nbytes);
   }
   wl_push(q, qn, lane == 0, v, nlist, ncount);
@@ -500,12 +511,243 @@ __global__ void __launch_bounds__(256) k_gp_lambda(int32_t n, int W, int nb, con
   if (lane == 0 && cur >= 0) lambda[(size_t)cur * n + v] += acc;
 }
 
+// ------------------------------------------------------ segmented (pull) products
+// The same products as the push kernels above, with the roles reversed: the
+// candidates that meet at one (vertex v, 32-column word) -- those of v's arcs
+// whose other end is in the frontier -- form one segment, and the warp that
+// owns (v, word) reduces it in registers, so no two threads update one
+// (vertex, column) and no atomics are needed.  Frontier membership is one bit
+// per vertex (fmem), so a vertex with no frontier neighbour costs a row of
+// bit tests.  Rows of more than PULL_ROW_MAX arcs (hubs) are reduced by a
+// block: its warps split the row and combine their partial results through
+// shared memory.
+//
+// FWD (MFBF, Algorithm 1's product over A^T rows = in-arcs): per column the
+// minimum of tau(s,u) + A(u,v) over frontier (s,u), and the sum of the
+// frontier multiplicities that attain it (the multpath monoid, Sec. 4.1.1);
+// a minimum <= T(s,v).w is written to cw / cm and its bit to tmask, for
+// k_gp_accumulate.
+// BWD (MFBr, over A rows = out-arcs): for columns whose counter is still
+// positive, the sum of the frontier values of successors u with
+// tau(s,u) = tau(s,v) + A(v,u) (the centpath monoid, Sec. 4.2) and their
+// number; zeta += sum, counter -= number; a counter reaching zero puts (s,v)
+// in the next frontier (tmask), for k_gp_next_frontier.
+constexpr int PULL_ROW_MAX = 256;
+
+struct PullArgs {
+  const int64_t* rowptr;   // FWD: A^T rows (in-arcs); BWD: A rows (out-arcs)
+  const int32_t* col;
+  const int32_t* wt;       // nullptr: unit weights
+  int32_t n;
+  int W, nb;
+  const uint32_t* fmem;    // frontier membership bits
+  const uint32_t* fmask;   // frontier columns [n][W]
+  const int32_t* dist;     // T.w
+  const double* fval;      // FWD: frontier multiplicities; BWD: frontier values zeta + 1/sigma_bar
+  int32_t* cw;             // FWD: product weight out;  BWD: counters (in/out)
+  double* cm;              // FWD: product multiplicity out;  BWD: zeta (in/out)
+  uint32_t* tmask;
+  uint32_t* vflag;
+  int32_t* tlist;
+  uint32_t* tcount;
+  const int32_t* hubs;     // vertices whose row may exceed PULL_ROW_MAX (the block kernel's list)
+  int32_t nhub;
+  unsigned long long* bytes;
+};
+
+// Per-lane reduction state of one column.
+template <bool FWD> struct PullAcc;
+template <> struct PullAcc<true> {
+  int32_t best = INF;
+  double sum = 0.0;
+  __device__ __forceinline__ void add(int32_t c, double m) {
+    if (c < best) { best = c; sum = m; }
+    else if (c == best) sum += m;
+  }
+  __device__ __forceinline__ void merge(const PullAcc& o) { add(o.best, o.sum); }
+};
+template <> struct PullAcc<false> {
+  double sum = 0.0;
+  int32_t hits = 0;
+  __device__ __forceinline__ void merge(const PullAcc& o) { sum += o.sum; hits += o.hits; }
+};
+
+// Reduce the arcs [k0, k1) of v's row into this lane's column j.  FWD: act is
+// "the column holds a source"; BWD: "the counter of (s,v) is positive", dv =
+// tau(s,v).
+template <bool FWD>
+__device__ __forceinline__ void pull_span(const PullArgs& a, int64_t k0, int64_t k1, int word, int j, bool act,
+                                          int32_t dv, PullAcc<FWD>& acc, unsigned long long& nbytes) {
+  const unsigned lane = threadIdx.x & 31u;
+  for (int64_t c0 = k0; c0 < k1; c0 += 32) {
+    const int64_t k = c0 + lane;
+    const int32_t myu = k < k1 ? __ldg(&a.col[k]) : -1;
+    const int32_t myw = k < k1 ? (a.wt ? __ldg(&a.wt[k]) : 1) : 0;
+    const bool mem = myu >= 0 && ((__ldg(&a.fmem[myu >> 5]) >> (myu & 31)) & 1u);
+    uint32_t mm = __ballot_sync(0xffffffffu, mem);
+    if (a.bytes && lane == 0) nbytes += 8ull * (uint64_t)(k1 - c0 < 32 ? k1 - c0 : 32);
+    while (mm) {                                   // four frontier neighbours in flight
+      int q[4];
+#pragma unroll
+      for (int r = 0; r < 4; r++) {
+        q[r] = mm ? __ffs(mm) - 1 : -1;
+        mm &= mm ? mm - 1 : 0u;
+      }
+      int32_t u[4], w[4];
+      uint32_t fw[4];
+#pragma unroll
+      for (int r = 0; r < 4; r++) {
+        u[r] = __shfl_sync(0xffffffffu, myu, q[r] & 31);
+        w[r] = __shfl_sync(0xffffffffu, myw, q[r] & 31);
+        fw[r] = q[r] >= 0 ? __ldg(&a.fmask[(size_t)u[r] * a.W + word]) : 0u;
+      }
+      int32_t d[4];
+      double x[4];
+      bool on[4];
+#pragma unroll
+      for (int r = 0; r < 4; r++) {
+        on[r] = act && ((fw[r] >> lane) & 1u);
+        d[r] = on[r] ? __ldg(&a.dist[(size_t)u[r] * a.nb + j]) : 0;
+      }
+#pragma unroll
+      for (int r = 0; r < 4; r++) {
+        if (!FWD) on[r] = on[r] && d[r] == dv + w[r];      // arc v -> u on a shortest path
+        x[r] = on[r] ? __ldg(&a.fval[(size_t)u[r] * a.nb + j]) : 0.0;
+      }
+#pragma unroll
+      for (int r = 0; r < 4; r++) {
+        if (on[r]) {
+          if constexpr (FWD) acc.add(d[r] + w[r], x[r]);
+          else { acc.sum += x[r]; acc.hits++; }
+        }
+        if (a.bytes && q[r] >= 0) nbytes += 4ull * (lane == 0) + 12ull * on[r];
+      }
+    }
+  }
+}
+
+// Write the reduced segment of (v, word): FWD the product entry, BWD the
+// counter and zeta; set the touched bits and list v once.
+template <bool FWD>
+__device__ __forceinline__ void pull_finish(const PullArgs& a, int32_t v, int word, int j, int32_t dv,
+                                            const PullAcc<FWD>& acc, bool& mine, unsigned long long& nbytes) {
+  const unsigned lane = threadIdx.x & 31u;
+  const size_t idx = (size_t)v * a.nb + j;
+  bool touch;
+  if constexpr (FWD) {
+    touch = acc.best != INF && acc.best <= dv;     // heavier candidates cannot pass the filter
+    if (touch) { a.cw[idx] = acc.best; a.cm[idx] = acc.sum; }
+  } else {
+    touch = false;
+    if (acc.hits) {
+      a.cm[idx] += acc.sum;
+      const int32_t c = a.cw[idx] - acc.hits;
+      a.cw[idx] = c;
+      touch = c == 0;
+    }
+  }
+  const uint32_t tb = __ballot_sync(0xffffffffu, touch);
+  if (a.bytes && lane == 0) nbytes += 4ull + (FWD ? 12ull : 24ull) * __popc(tb);
+  if (tb && lane == 0) {
+    atomicOr(&a.tmask[(size_t)v * a.W + word], tb);
+    if (claim_vertex(a.vflag, v)) mine = true;
+  }
+}
+
+// One warp per (vertex, word) for rows of at most PULL_ROW_MAX arcs.
+template <bool FWD>
+__global__ void __launch_bounds__(256) k_gp_pull_rows(PullArgs a) {
+  __shared__ int32_t qbuf[8][40];
+  int32_t* q = qbuf[threadIdx.x >> 5];
+  int qn = 0;
+  const unsigned lane = threadIdx.x & 31u;
+  const uint64_t tasks = (uint64_t)a.n * a.W;
+  const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  unsigned long long nbytes = 0;
+  for (uint64_t t = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < tasks; t += nw) {
+    const int32_t v = (int32_t)(t / a.W);
+    const int word = (int)(t % a.W);
+    const int64_t k0 = __ldg(&a.rowptr[v]), k1 = __ldg(&a.rowptr[v + 1]);
+    bool mine = false;
+    if (k1 > k0 && k1 - k0 <= PULL_ROW_MAX) {
+      const int j = word * 32 + (int)lane;
+      const int32_t dv = __ldg(&a.dist[(size_t)v * a.nb + j]);
+      const bool act = FWD ? true : (dv != INF && a.cw[(size_t)v * a.nb + j] > 0);
+      if (__any_sync(0xffffffffu, act)) {
+        PullAcc<FWD> acc;
+        pull_span<FWD>(a, k0, k1, word, j, act, dv, acc, nbytes);
+        pull_finish<FWD>(a, v, word, j, dv, acc, mine, nbytes);
+      }
+    }
+    wl_push(q, qn, mine, v, a.tlist, a.tcount);
+  }
+  wl_flush(q, qn, a.tlist, a.tcount);
+  if (a.bytes) {
+    for (int o = 16; o; o >>= 1) nbytes += __shfl_xor_sync(0xffffffffu, nbytes, o);
+    if (lane == 0 && nbytes) atomicAdd(a.bytes, nbytes);
+  }
+}
+
+// One block of 8 warps per (hub, word) for rows of more than PULL_ROW_MAX arcs.
+template <bool FWD>
+__global__ void __launch_bounds__(256) k_gp_pull_hubs(PullArgs a) {
+  __shared__ PullAcc<FWD> part[8][32];
+  const unsigned lane = threadIdx.x & 31u;
+  const int wid = (int)(threadIdx.x >> 5);
+  unsigned long long nbytes = 0;
+  const uint64_t tasks = (uint64_t)a.nhub * a.W;
+  for (uint64_t t = blockIdx.x; t < tasks; t += gridDim.x) {
+    const int32_t v = __ldg(&a.hubs[t / a.W]);
+    const int word = (int)(t % a.W);
+    const int64_t k0 = __ldg(&a.rowptr[v]), k1 = __ldg(&a.rowptr[v + 1]);
+    if (k1 - k0 <= PULL_ROW_MAX) continue;         // uniform over the block
+    const int j = word * 32 + (int)lane;
+    const int32_t dv = __ldg(&a.dist[(size_t)v * a.nb + j]);
+    const bool act = FWD ? true : (dv != INF && a.cw[(size_t)v * a.nb + j] > 0);
+    PullAcc<FWD> acc;
+    if (__syncthreads_or(act)) {
+      // warp w takes the 32-arc chunks w, w + 8, ...
+      for (int64_t c0 = k0 + 32 * wid; c0 < k1; c0 += 32 * 8)
+        pull_span<FWD>(a, c0, c0 + 32 < k1 ? c0 + 32 : k1, word, j, act, dv, acc, nbytes);
+      part[wid][lane] = acc;
+      __syncthreads();
+      if (wid == 0) {
+        for (int r = 1; r < 8; r++) acc.merge(part[r][lane]);
+        bool mine = false;
+        pull_finish<FWD>(a, v, word, j, dv, acc, mine, nbytes);
+        if (mine) a.tlist[atomicAdd(a.tcount, 1u)] = v;
+      }
+    }
+    __syncthreads();
+  }
+  if (a.bytes) {
+    for (int o = 16; o; o >>= 1) nbytes += __shfl_xor_sync(0xffffffffu, nbytes, o);
+    if (lane == 0 && nbytes) atomicAdd(a.bytes, nbytes);
+  }
+}
+
 // ------------------------------------------------------------------ driver
 static inline unsigned warp_blocks(uint64_t warps) { return (unsigned)((warps + 7) / 8); }
 // grid for kernels whose item count is only known on the device (grid-stride)
 static inline unsigned stride_blocks(uint64_t max_warps) {
   uint64_t b = (max_warps + 7) / 8;
   return (unsigned)(b < 1 ? 1 : (b > 152 * 16 ? 152 * 16 : b));
+}
+
+// blocks of the hub kernels: one per (hub, word) task, at most 8 per SM
+static inline unsigned hub_blocks(int32_t nhub, int W) {
+  const uint64_t t = (uint64_t)nhub * W;
+  return (unsigned)(t < 152 * 8 ? (t ? t : 1) : 152 * 8);
+}
+
+// Segmented (pull) or atomic (push) reduction for a product whose frontier
+// holds fcount vertices: MFBC_ACCUM_AUTO pulls once the frontier holds 1/64 of
+// the vertices (the pull kernels visit every vertex; the push kernels only
+// the frontier's arcs, but meet in atomics at hub columns).
+static inline bool use_pull(const RunCtx& rc, uint32_t fcount, int32_t n) {
+  if (rc.accum == MFBC_ACCUM_SEGMENTED) return true;
+  if (rc.accum == MFBC_ACCUM_ATOMIC) return false;
+  return (uint64_t)fcount * 64 >= (uint64_t)n;
 }
 
 static mfbc_status read_counts(RunCtx& rc, Counters* ctr) {
@@ -555,6 +797,7 @@ mfbc_status general_batch(RunCtx& rc, GeneralState& s, const int32_t* d_src_batc
     cudaMemsetAsync(s.fmask, 0, sizeof(uint32_t) * (size_t)n * W, st);
     cudaMemsetAsync(s.tmask, 0, sizeof(uint32_t) * (size_t)n * W, st);
     cudaMemsetAsync(s.vflag, 0, sizeof(uint32_t) * (size_t)n, st);
+    cudaMemsetAsync(s.fmem, 0, sizeof(uint32_t) * (((size_t)n + 31) / 32), st);
     cudaMemsetAsync(s.ctr->list_count, 0, sizeof(uint32_t) * 4, st);
   });
   rc.prof->k[K_FILL].bytes += 24.0 * cells + 8.0 * n * W + 4.0 * n;
@@ -562,7 +805,7 @@ mfbc_status general_batch(RunCtx& rc, GeneralState& s, const int32_t* d_src_batc
   int32_t* cur = s.listA;
   int32_t* nxt = s.listB;
   PROF(K_SEED, (k_gp_seed<<<(nb + 127) / 128, 128, 0, st>>>(s.src, nb, W, s.dist, s.sig, s.fm, s.fmask,
-                                                          s.vflag, cur, &s.ctr->list_count[0])));
+                                                          s.fmem, s.vflag, cur, &s.ctr->list_count[0])));
   mfbc_status e = read_counts(rc, s.ctr);
   if (e) return e;
   uint32_t fcount = rc.h_ctr[0];
@@ -577,18 +820,28 @@ mfbc_status general_batch(RunCtx& rc, GeneralState& s, const int32_t* d_src_batc
     }
     MFBC_CUDA_TRY(cudaMemsetAsync(s.ctr->list_count, 0, sizeof(uint32_t) * 4, st), rc.err);
     const uint64_t wp = (uint64_t)fcount * W;
-    PROF(K_RELAX_MIN, GP_LAUNCH(k_gp_relax_min, warp_blocks(wp),
-                          g.rowptr, g.col, g.w, cur, fcount, W, nb, s.fmask, s.dist, s.cw, s.tmask,
-                          s.vflag, nxt, &s.ctr->list_count[1], B ? B + K_RELAX_MIN : nullptr));
-    PROF(K_RELAX_TIE, GP_LAUNCH(k_gp_relax_tie, warp_blocks(wp),
-                          g.rowptr, g.col, g.w, cur, fcount, W, nb, s.fmask, s.dist, s.fm, s.cw, s.cm,
-                          B ? B + K_RELAX_TIE : nullptr));
+    if (use_pull(rc, fcount, n)) {
+      const PullArgs pa{g.rowptr_t, g.col_t, g.w_t, n, W, nb, s.fmem, s.fmask, s.dist, s.fm, s.cw, s.cm,
+                        s.tmask, s.vflag, nxt, &s.ctr->list_count[1], g.items_in.hubs, g.items_in.nhub,
+                        B ? B + K_PULL_FWD : nullptr};
+      PROF(K_PULL_FWD, {
+        k_gp_pull_rows<true><<<stride_blocks((uint64_t)n * W), 256, 0, st>>>(pa);
+        if (g.items_in.nhub) k_gp_pull_hubs<true><<<hub_blocks(g.items_in.nhub, W), 256, 0, st>>>(pa);
+      });
+    } else {
+      PROF(K_RELAX_MIN, GP_LAUNCH(k_gp_relax_min, warp_blocks(wp),
+                            g.rowptr, g.col, g.w, cur, fcount, W, nb, s.fmask, s.dist, s.cw, s.tmask,
+                            s.vflag, nxt, &s.ctr->list_count[1], B ? B + K_RELAX_MIN : nullptr));
+      PROF(K_RELAX_TIE, GP_LAUNCH(k_gp_relax_tie, warp_blocks(wp),
+                            g.rowptr, g.col, g.w, cur, fcount, W, nb, s.fmask, s.dist, s.fm, s.cw, s.cm,
+                            B ? B + K_RELAX_TIE : nullptr));
+    }
     PROF(K_CLEAR, (k_clear_mask_rows<<<(unsigned)((wp + 255) / 256), 256, 0, st>>>(cur, fcount, W,
-                                                                                   s.fmask)));
+                                                                                   s.fmask, s.fmem)));
     // the touched list lives in nxt; compact the next frontier into cur
     PROF(K_ACCUM, (k_gp_accumulate<<<stride_blocks((uint64_t)n), 256, 0, st>>>(
                       nxt, &s.ctr->list_count[1], W, nb, s.dist, s.sig, s.cw, s.cm, s.fm, s.fmask,
-                      s.tmask, s.vflag, cur, &s.ctr->list_count[0], B ? B + K_ACCUM : nullptr)));
+                      s.tmask, s.vflag, s.fmem, cur, &s.ctr->list_count[0], B ? B + K_ACCUM : nullptr)));
     e = read_counts(rc, s.ctr);
     if (e) return e;
     fcount = rc.h_ctr[0];
@@ -601,7 +854,7 @@ mfbc_status general_batch(RunCtx& rc, GeneralState& s, const int32_t* d_src_batc
   MFBC_CUDA_TRY(cudaMemsetAsync(s.ctr->list_count, 0, sizeof(uint32_t) * 4, st), rc.err);
   PROF(K_COUNTERS, GP_LAUNCH(k_gp_counters, warp_blocks((uint64_t)n),
                        n, g.rowptr, g.col, g.w, W, nb, s.src, s.dist, s.sig, s.cw, s.cm, s.fm, s.fmask,
-                       cur, &s.ctr->list_count[0], B ? B + K_COUNTERS : nullptr));
+                       s.fmem, cur, &s.ctr->list_count[0], B ? B + K_COUNTERS : nullptr));
   e = read_counts(rc, s.ctr);
   if (e) return e;
   fcount = rc.h_ctr[0];
@@ -613,15 +866,25 @@ mfbc_status general_batch(RunCtx& rc, GeneralState& s, const int32_t* d_src_batc
     }
     MFBC_CUDA_TRY(cudaMemsetAsync(s.ctr->list_count, 0, sizeof(uint32_t) * 4, st), rc.err);
     const uint64_t wp = (uint64_t)fcount * W;
-    PROF(K_PROPAGATE, GP_LAUNCH(k_gp_propagate, warp_blocks(wp),
-                          g.rowptr_t, g.col_t, g.w_t, cur, fcount, W, nb, s.fmask, s.dist, s.fm, s.cm,
-                          s.cw, s.tmask, s.vflag, nxt, &s.ctr->list_count[1],
-                          B ? B + K_PROPAGATE : nullptr));
+    if (use_pull(rc, fcount, n)) {
+      const PullArgs pb{g.rowptr, g.col, g.w, n, W, nb, s.fmem, s.fmask, s.dist, s.fm, s.cw, s.cm,
+                        s.tmask, s.vflag, nxt, &s.ctr->list_count[1], g.items_out.hubs, g.items_out.nhub,
+                        B ? B + K_PULL_BWD : nullptr};
+      PROF(K_PULL_BWD, {
+        k_gp_pull_rows<false><<<stride_blocks((uint64_t)n * W), 256, 0, st>>>(pb);
+        if (g.items_out.nhub) k_gp_pull_hubs<false><<<hub_blocks(g.items_out.nhub, W), 256, 0, st>>>(pb);
+      });
+    } else {
+      PROF(K_PROPAGATE, GP_LAUNCH(k_gp_propagate, warp_blocks(wp),
+                            g.rowptr_t, g.col_t, g.w_t, cur, fcount, W, nb, s.fmask, s.dist, s.fm, s.cm,
+                            s.cw, s.tmask, s.vflag, nxt, &s.ctr->list_count[1],
+                            B ? B + K_PROPAGATE : nullptr));
+    }
     PROF(K_CLEAR, (k_clear_mask_rows<<<(unsigned)((wp + 255) / 256), 256, 0, st>>>(cur, fcount, W,
-                                                                                   s.fmask)));
+                                                                                   s.fmask, s.fmem)));
     PROF(K_FINAL, (k_gp_next_frontier<<<stride_blocks((uint64_t)n), 256, 0, st>>>(
                       nxt, &s.ctr->list_count[1], W, nb, s.sig, s.cm, s.fm, s.fmask, s.tmask, s.vflag,
-                      cur, &s.ctr->list_count[0], B ? B + K_FINAL : nullptr)));
+                      s.fmem, cur, &s.ctr->list_count[0], B ? B + K_FINAL : nullptr)));
     e = read_counts(rc, s.ctr);
     if (e) return e;
     fcount = rc.h_ctr[0];

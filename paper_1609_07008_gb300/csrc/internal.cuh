@@ -64,7 +64,7 @@ struct KStat {
 enum KId {
   K_FILL = 0, K_SEED, K_RELAX_MIN, K_RELAX_TIE, K_ACCUM, K_COUNTERS, K_PROPAGATE, K_FINAL,
   K_LAMBDA, K_CLEAR, K_LVL_FWD, K_LVL_VISIT, K_LVL_BWD, K_LVL_HUB, K_LVL_RESET, K_OUTPUT,
-  K_LVL_FWD_G, K_LVL_BWD_G, K_LVL_SPLIT, K_DP_FWD, K_DP_BWD, K_SMALL, K_NUM
+  K_LVL_FWD_G, K_LVL_BWD_G, K_LVL_SPLIT, K_DP_FWD, K_DP_BWD, K_SMALL, K_PULL_FWD, K_PULL_BWD, K_NUM
 };
 
 // Bits of Counters::flags, set by kernels and read by the host drivers.
@@ -125,6 +125,7 @@ struct GeneralState {
   uint32_t* fmask;    // frontier bits  [n][W]
   uint32_t* tmask;    // touched bits   [n][W]
   uint32_t* vflag;    // per-vertex enqueue flags [n]
+  uint32_t* fmem;     // frontier membership bits, one per vertex [n/32] (pull products)
   int32_t* listA;     // frontier vertex lists [n]
   int32_t* listB;
   int32_t* src;       // [nb]
@@ -238,6 +239,8 @@ struct RunCtx {
   const int32_t* word_req = nullptr;
   // general kernels: arcs walked per step (1 or 8); 0 = by average degree
   int arcs = 0;
+  // general kernels: how a product reduces its candidates (MFBC_ACCUM_*)
+  int accum = 0;
 };
 
 // Request of the batch as a whole: r >= 0 when every used word belongs to

@@ -276,19 +276,35 @@ __global__ void __launch_bounds__(SMALL_THREADS, 4) k_small_bc(SmallArgs a) {
     for (size_t i = (size_t)gt; i < cells / 2; i += (size_t)GT) reinterpret_cast<uint4*>(sv)[i] = make_uint4(0, 0, 0, 0);
     if (a.bytes && gt == 0) nbytes += 9ull * cells;
     if (!group_barrier(a, c, epoch, s_ok)) break;
-    // seed: T(s_j, s_j) = (0, 1), frontier {(s_j, s_j)} (Algorithm 1's start)
-    for (int j = gt; j < a.nb; j += GT) {
-      const int32_t s = src[j];
-      if (s >= 0) {
+    // seed: T(s_j, s_j) = (0, 1), frontier {(s_j, s_j)} (Algorithm 1's start);
+    // the first product is pushed from the seed by the column's thread: every
+    // out-neighbour of s_j is at level 1 with one path (no self-loops, so
+    // the two levels never meet in one column)
+    {
+      bool any1 = false;
+      for (int j = gt; j < a.nb; j += GT) {
+        const int32_t s = src[j];
+        if (s < 0) continue;
         lvl[(size_t)s * a.nb + j] = 0;
         sv[(size_t)s * a.nb + j] = 1ull;
+        for (int64_t k = __ldg(&a.rp_out[s]); k < __ldg(&a.rp_out[s + 1]); k++) {
+          const int32_t v = __ldg(&a.col_out[k]);
+          lvl[(size_t)v * a.nb + j] = 1;
+          sv[(size_t)v * a.nb + j] = 1ull;
+          any1 = true;
+          if (a.bytes) nbytes += 13;
+        }
       }
+      if (__syncthreads_or(any1) && threadIdx.x == 0) atomicOr(&c->any[0], 1u);
     }
     if (!group_barrier(a, c, epoch, s_ok)) break;
-    // MFBF, level by level until a product adds no pair
+    // MFBF, level by level until a product adds no pair (slot 0 holds the
+    // seed's flag; every block reads it here, before the barrier after which
+    // block 0 may clear that slot for level 3)
     int deepest = 0;
     bool redo = false, quit = false;
-    for (int l = 0;; l++) {
+    const bool level1 = ld_relaxed(&c->any[0]) != 0u;
+    for (int l = 1; level1; l++) {
       if (l >= SMALL_MAX_LEVEL) { redo = true; break; }
       // the flag of level l + 1 shares its slot with level l - 2, which every
       // block has read before arriving at the barrier of level l - 1
@@ -342,18 +358,27 @@ static int small_group_blocks(int32_t n, int W) {
   return (int)std::max<int64_t>(1, std::min<int64_t>(32, p));
 }
 
-int small_groups(int32_t n, int nb, int nbatch) {
-  int per_sm = 0, sms = 0, dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess ||
-      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+// Co-resident blocks of k_small_bc on the current device (looked up once per device).
+static int small_resident_blocks() {
+  static int cache[64];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) { cudaGetLastError(); return 1; }
+  if (dev < 64 && cache[dev]) return cache[dev];
+  int per_sm = 0, sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_small_bc, SMALL_THREADS, 0) != cudaSuccess) {
     cudaGetLastError();
-    per_sm = 1;
-    sms = 1;
+    return 1;
   }
+  const int r = std::max(1, per_sm * sms);
+  if (dev < 64) cache[dev] = r;
+  return r;
+}
+
+int small_groups(int32_t n, int nb, int nbatch) {
   const int P = small_group_blocks(n, nb / 32);
-  // a quarter of the co-resident blocks at most: other streams keep the rest
-  const int cap = std::max(1, per_sm * sms / 4 / P);
+  // half of the co-resident blocks at most: other streams keep the rest
+  const int cap = std::max(1, small_resident_blocks() / 2 / P);
   return std::max(1, std::min(nbatch, cap));
 }
 
@@ -387,9 +412,14 @@ mfbc_status small_run(RunCtx& rc, SmallState& s, const int32_t* d_src_all, const
   a.redo = s.redo;
   a.redo_cap = 4096;
   a.flags = &s.ctr->flags;
+  static int khz_cache[64];
   int khz = 0, dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev) != cudaSuccess)
+  if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); dev = -1; }
+  if (dev >= 0 && dev < 64 && khz_cache[dev]) khz = khz_cache[dev];
+  else if (dev < 0 || cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev) != cudaSuccess || khz <= 0) {
+    cudaGetLastError();
     khz = 2000000;
+  } else if (dev < 64) khz_cache[dev] = khz;
   // a wait ends when the group's slowest block finishes its level; one
   // second is far beyond any level of a graph this path takes.  The test
   // hook makes every wait run out, and a short budget keeps that test quick.
