@@ -71,8 +71,8 @@ typedef enum {
 #define MFBC_WARN_SIGMA_INEXACT 1u  /* some sigma_bar >= 2^53: FP64 counts may be rounded */
 
 /* mfbc_options.path */
-#define MFBC_PATH_AUTO    0    /* unit weights: the persistent small-graph kernel when n <= 2^15
-                                  and nnz <= 2^19, else the level kernels; distance kernels for weights
+#define MFBC_PATH_AUTO    0    /* unit weights: the persistent small-graph kernel when n <= 2^13
+                                  and nnz <= 2^18, else the level kernels; distance kernels for weights
                                   <= 128 when no in- or out-degree exceeds max(64, 4x the
                                   average degree); general kernels otherwise (or the family
                                   mfbc_autotune chose) */
@@ -248,7 +248,8 @@ typedef struct {
  * int32[nsrc] for each candidate configuration and keeps the fastest on the
  * graph handle.  Candidates: n_b in {128, 256, 512, 1024} on the level kernels
  * and, for unit-weight graphs of at most 2^15 vertices and 2^19 arcs, n_b in
- * {32, 64, 128, 256} on the persistent small-graph kernel;
+ * {32, 64, 128, 256} on the persistent small-graph kernel (AUTO itself takes
+ * it up to 2^13 vertices and 2^18 arcs);
  * n_b in {128, 256, 512, 1024, 2048, 4096} on the general kernels (x the
  * atomic accumulator walking 1 or 8 arcs per step, the segmented accumulator,
  * and the per-product choice) and on the distance kernels; each at most nsrc

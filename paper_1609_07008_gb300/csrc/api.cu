@@ -247,9 +247,13 @@ static size_t plan_bytes(const DevGraph& g, int path, int nb, int32_t nsrc, int 
 // kernels otherwise.
 // Unit-weight graphs small enough for the persistent kernel to win: its
 // levels scan every (vertex, word) and every in-arc of an open vertex, which
-// costs more than the per-product kernels once the graph has a few hundred
-// thousand arcs, while below that the per-product kernels wait on launches.
-static bool small_graph(const DevGraph& g) { return g.n <= (1 << 15) && g.nnz <= (1 << 19); }
+// costs more than the per-product kernels as the graph grows (R-MAT 14,
+// 16384 vertices, 4096 sources: 45 ms), while on small graphs the
+// per-product kernels wait on launches (Erdos-Renyi n = 1024, all sources:
+// 0.75 ms here against 14.7 ms).  mfbc_autotune compares the two.
+static bool small_graph(const DevGraph& g) { return g.n <= (1 << 13) && g.nnz <= (1 << 18); }
+// graphs on which mfbc_autotune also times the persistent kernel
+static bool small_tunable(const DevGraph& g) { return g.n <= (1 << 15) && g.nnz <= (1 << 19); }
 
 static int default_path(const DevGraph& g) {
   if (g.unit) return small_graph(g) ? MFBC_PATH_SMALL : MFBC_PATH_LEVEL;
@@ -546,6 +550,7 @@ mfbc_status small_path(mfbc_graph* G, Run& R, RunCtx& rc, SmallState& ss, const 
   int32_t* d_col = (int32_t*)(tab + al256(sizeof(int32_t) * nbt * nb));
   int32_t* d_wreq = (int32_t*)(tab + 2 * al256(sizeof(int32_t) * nbt * nb));
   if ((size_t)nbatches > nbt) { *rc.err = "packed batches exceed the batch table"; return MFBC_ERR_INVALID; }
+  if (nbatches == 0) return MFBC_OK;       // no sources: nothing to launch
   if (multi) {
     MFBC_CUDA_TRY(cudaMemcpyAsync(d_col, pk.colidx.data(), sizeof(int32_t) * pk.colidx.size(), cudaMemcpyHostToDevice,
                                   R.st), rc.err);
@@ -964,7 +969,7 @@ extern "C" mfbc_status mfbc_autotune(mfbc_graph* G, const int32_t* sources, int3
   const bool dist_ok = G->g.wmax + 1 <= DIST_MAX_BUCKETS;
   std::vector<int> paths;
   if (req_path == MFBC_PATH_AUTO) {
-    if (G->g.unit) paths = small_graph(G->g) ? std::vector<int>{MFBC_PATH_LEVEL, MFBC_PATH_SMALL}
+    if (G->g.unit) paths = small_tunable(G->g) ? std::vector<int>{MFBC_PATH_LEVEL, MFBC_PATH_SMALL}
                                              : std::vector<int>{MFBC_PATH_LEVEL};
     else paths = dist_ok ? std::vector<int>{MFBC_PATH_GENERAL, MFBC_PATH_DIST} : std::vector<int>{MFBC_PATH_GENERAL};
   } else if (req_path == MFBC_PATH_LEVEL) {
