@@ -148,68 +148,99 @@ def survey_model(g, srcs, prof_bytes, step_s, peak_gbs):
             "tight_arcs": D}
 
 
-SERVE_POOL = "resident graphs R-MAT 16/18/20 (edge factor 16, undirected), Erdos-Renyi n=2^16 k=16, " \
-             "weighted 2D grid 256^2 w U[1,16]; requests with log-uniform [64, 4096] sampled sources"
+# The serving pool of the request-loop configuration: R-MAT scales 10-20 (edge
+# factor 16, undirected, unweighted), Erdos-Renyi n = 2^14..2^20 (k = 16,
+# undirected, unweighted), weighted 2D grids 256^2..2048^2 (w U[1,16]).
+SERVE_FULL = ["rmat10", "rmat12", "rmat14", "rmat16", "rmat18", "rmat20", "er14", "er16", "er18", "er20",
+              "grid256w", "grid512w", "grid1024w", "grid2048w"]
+# the default bench line's pool: the same families up to about 2^18 vertices
+SERVE_DEFAULT = ["rmat10", "rmat12", "rmat14", "rmat16", "rmat18", "er14", "er16", "er18", "grid256w", "grid512w"]
 
 
-def serving_bench(n_requests=120, seed=5, max_cols=1024):
-    """Served (packed, continuous batching, memory-budget admission, one worker
-    per graph) against plain (one mfbc_bc_device call per request, in arrival
-    order) on the same requests: both saturated (every request at t = 0:
-    capacity) and at an offered Poisson rate of 0.8x the plain capacity
-    (latency).  Also the largest relative difference between the two forms'
-    lambdas (equal accuracy)."""
-    import torch
+def serve_graph(name):
     import graphgen as gg
+    if name.startswith("rmat"):
+        return gg.rmat(int(name[4:]), 16, seed=1)
+    if name.startswith("er"):
+        return gg.erdos_renyi(1 << int(name[2:]), 16, seed=1)
+    return gg.grid2d(int(name[4:-1]), weights=(1, 16), seed=1)
+
+
+def serving_bench(pool=SERVE_DEFAULT, n_requests=300, seed=5, max_cols=1024, loads=(0.5, 0.8, 1.2)):
+    """Served (continuous batching at batch granularity, memory-budget
+    admission, several workers and CUDA streams per graph) against plain (one
+    mfbc_bc_device call per request, in arrival order) on the same requests:
+    saturated (every request at t = 0: capacity), then Poisson arrivals at
+    each offered load (a multiple of the plain form's capacity): p50/p99
+    latency, throughput, the batches' packing, and the largest relative
+    difference between the two forms' lambdas (equal accuracy).  A request
+    picks graph g with probability proportional to 1/sqrt(n_g) (small graphs
+    are asked more often) and log-uniform [64, 4096] sources (at most the
+    graph's vertices of degree >= 1)."""
+    import torch
     import paper_1609_07008_gb300 as mfbc
     from paper_1609_07008_gb300 import serve
-    host = {"rmat16": gg.rmat(16, 16, seed=1), "rmat18": gg.rmat(18, 16, seed=1), "rmat20": gg.rmat(20, 16, seed=1),
-            "er16": gg.erdos_renyi(1 << 16, 16, seed=1), "grid256w": gg.grid2d(256, weights=(1, 16), seed=1)}
+    host = {k: serve_graph(k) for k in pool}
     graphs = {k: mfbc.Graph.from_csr(g) for k, g in host.items()}
-    replicas = {k: [mfbc.Graph.from_csr(g) for _ in range(3)] for k, g in host.items()}
+    # three more workers (handles, streams) per graph up to 2^18 vertices, one more above
+    replicas = {k: [mfbc.Graph.from_csr(g) for _ in range(3 if g.n <= (1 << 18) else 1)] for k, g in host.items()}
     edges = {k: g.m for k, g in host.items()}
     elig = {k: np.flatnonzero(g.out_degree() > 0).astype(np.int32) for k, g in host.items()}
     sizes = {k: g.n for k, g in host.items()}
+    weights = {k: 1.0 / np.sqrt(g.n) for k, g in host.items()}
     free, _ = torch.cuda.mem_get_info()
     budget = int(0.6 * free)
 
-    def reqs(rate):
-        return serve.make_requests(sizes, n_requests, rate, lo=64, hi=4096, seed=seed, eligible=elig)
+    def reqs(rate, count=n_requests, lo=64, hi=4096, sd=seed):
+        return serve.make_requests(sizes, count, rate, lo=lo, hi=hi, seed=sd, eligible=elig, weights=weights)
 
     def served(rs):
         srv = serve.Server(graphs, budget_bytes=budget, max_cols=max_cols, replicas=replicas).start()
         try:
-            serve.run_served(srv, rs, timeout=900)
+            serve.run_served(srv, rs, timeout=3600)
         finally:
             srv.close()
-        return serve.latency_stats(rs, edges), len(srv.log)
+        return dict(serve.latency_stats(rs, edges), **srv.stats())
+
+    def diff(a_list, b_list):
+        d = 0.0
+        for a, b in zip(sorted(a_list, key=lambda r: r.rid), sorted(b_list, key=lambda r: r.rid)):
+            nz = b.result != 0
+            if np.any(a.result[~nz] != 0):
+                return float("inf")
+            if nz.any():
+                d = max(d, float(np.max(np.abs(a.result[nz] - b.result[nz]) / np.abs(b.result[nz]))))
+        return d
 
     # warm both forms once (library scratch, torch allocator, module load)
-    w = serve.make_requests(sizes, 10, 0, lo=64, hi=256, seed=seed + 1, eligible=elig)
-    serve.run_plain(graphs, w)
-    served(serve.make_requests(sizes, 10, 0, lo=64, hi=256, seed=seed + 1, eligible=elig))
-    sat_plain = serve.latency_stats(serve.run_plain(graphs, reqs(0)), edges)
-    sat_served, _ = served(reqs(0))
+    serve.run_plain(graphs, reqs(0, count=2 * len(pool), hi=256, sd=seed + 1))
+    served(reqs(0, count=2 * len(pool), hi=256, sd=seed + 1))
+    sat_plain_reqs = serve.run_plain(graphs, reqs(0))
+    sat_plain = serve.latency_stats(sat_plain_reqs, edges)
+    sat_served_reqs = reqs(0)
+    sat_served = served(sat_served_reqs)
+    worst = diff(sat_plain_reqs, sat_served_reqs)
     cap = n_requests / sat_plain["span_s"]
-    rate = 0.8 * cap
-    rp = serve.run_plain(graphs, reqs(rate))
-    plain = serve.latency_stats(rp, edges)
-    rs = reqs(rate)
-    srv_stats, groups = served(rs)
-    diff = 0.0
-    for a, b in zip(sorted(rp, key=lambda r: r.rid), sorted(rs, key=lambda r: r.rid)):
-        nz = b.result != 0
-        if np.any(a.result[~nz] != 0):
-            diff = float("inf")
-        if nz.any():
-            diff = max(diff, float(np.max(np.abs(a.result[nz] - b.result[nz]) / np.abs(b.result[nz]))))
+    rows = []
+    for load in loads:
+        rp = serve.run_plain(graphs, reqs(load * cap))
+        rs = reqs(load * cap)
+        row = {"offered_load_vs_plain_capacity": load, "rate_per_s": load * cap,
+               "plain": serve.latency_stats(rp, edges), "served": served(rs)}
+        worst = max(worst, diff(rp, rs))
+        rows.append(row)
     for G in list(graphs.values()) + [R for rs_ in replicas.values() for R in rs_]:
         G.close()
-    return {"workload": SERVE_POOL, "workers_per_graph": 4, "max_group_columns": max_cols, "requests": n_requests, "budget_bytes": budget,
+    return {"pool": {k: {"n": host[k].n, "m": int(host[k].m), "weighted": host[k].w is not None} for k in pool},
+            "graph_choice": "probability proportional to 1/sqrt(n)", "sources_per_request": "log-uniform [64, 4096]",
+            "requests": n_requests, "workers_per_graph": {k: 1 + len(v) for k, v in replicas.items()},
+            "batch_columns": max_cols, "budget_bytes": budget,
             "saturated": {"plain_gteps": sat_plain["gteps"], "served_gteps": sat_served["gteps"],
-                          "plain_span_s": sat_plain["span_s"], "served_span_s": sat_served["span_s"]},
-            "offered_rate_per_s": rate, "offered_load_vs_plain_capacity": 0.8,
-            "plain": plain, "served": dict(srv_stats, groups=groups), "max_rel_diff": diff}
+                          "plain_span_s": sat_plain["span_s"], "served_span_s": sat_served["span_s"],
+                          "served_packing": {k: sat_served[k] for k in sat_served if k.startswith(("batches",
+                                                                                                     "requests_per",
+                                                                                                     "columns"))}},
+            "plain_capacity_per_s": cap, "loads": rows, "max_rel_diff": worst}
 
 
 def load_peaks():
@@ -430,13 +461,17 @@ def extra_workload(name, n_b, steps, cap, peak, peak_kind, args):
     del flush
     torch.cuda.empty_cache()
     desc = WORKLOADS[name]["desc"] + (f" (first {cap} of them)" if cap else "")
+    roof = roofline_of(kstats, prof_bytes, peak, peak_kind, name, t / steps)
+    if flushed:
+        roof["note"] = ("the state fits in the L2: after the flush the kernel's per-use bytes are served mostly by "
+                        "the L2, so the fraction of the HBM copy bandwidth can pass 1")
     return {"value": steps * len(srcs) * g.m / t / 1e9, "unit": "GTEPS", "steps": steps,
             "ms_per_step": t / steps * 1e3, "dtype": DTYPE.get(prof_bytes["path"], "f64"),
             "config": {"workload": desc, "name": name, "n": g.n, "nnz": g.nnz, "m": g.m, "sources": len(srcs),
                        "n_b": prof_bytes["n_b"], "path": prof_bytes["path"],
                        "l2": "L2 flushed between steps (2x L2 buffer written)" if flushed
                        else l2_note(g.n, prof_bytes["n_b"], prof_bytes["path"])},
-            "roofline": roofline_of(kstats, prof_bytes, peak, peak_kind, name, t / steps),
+            "roofline": roof,
             "cpu_baseline": None if args.no_cpu_baseline else cpu_baseline(g, srcs, budget_s=4.0, single_budget_s=2.0)}
 
 
@@ -455,12 +490,29 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
     ap.add_argument("--no-workloads", action="store_true", help="skip the other benchmark configurations")
+    ap.add_argument("--serve-only", action="store_true", help="print only the serving measurement")
+    ap.add_argument("--serve-full", action="store_true",
+                    help="serving over the whole pool (R-MAT 10-20, ER 2^14-2^20, grids 256^2-2048^2)")
+    ap.add_argument("--serve-requests", type=int, default=0)
+    ap.add_argument("--serve-loads", default="0.5,0.8,1.2", help="offered loads (x plain capacity) to measure")
     ap.add_argument("--sources", type=int, default=0, help="use only the first N sources (probing)")
     ap.add_argument("--keep-order", action="store_true", help="batch sources in the given order")
     ap.add_argument("--accumulator", type=int, default=0, help="general kernels: MFBC_ACCUM_* (0 = auto)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.serve_only:
+        import torch
+        import paper_1609_07008_gb300 as mfbc
+        from paper_1609_07008_gb300 import build as mbuild
+        torch.cuda.set_device(0)
+        mbuild.build()
+        mfbc.load()
+        pool = SERVE_FULL if args.serve_full else SERVE_DEFAULT
+        res = serving_bench(pool, n_requests=args.serve_requests or (2000 if args.serve_full else 300),
+                            loads=tuple(float(x) for x in args.serve_loads.split(",")))
+        print(json.dumps({"serving": res}), flush=True)
+        return
 
     import torch
     import paper_1609_07008_gb300 as mfbc

@@ -73,7 +73,6 @@ constexpr uint32_t FLAG_SIGMA_INEXACT = 2u;  // some sigma_bar >= 2^53 (FP64 out
 constexpr uint32_t FLAG_BAD_SOURCE = 4u;     // mfbc_bc_static: a source id outside [0, n)
 constexpr uint32_t FLAG_COUNT_WRAP = 8u;     // level kernels: a path count reached 2^58 (batch redone)
 constexpr uint32_t FLAG_TIMEOUT = 16u;       // a bounded device-side wait ran out (MFBC_ERR_TIMEOUT)
-constexpr uint32_t FLAG_COUNT32 = 32u;       // level kernels: a 32-bit path count overflowed (batch redone)
 
 // Device-side counters of algorithmic bytes, one slot per kernel id.
 struct Counters {
@@ -142,9 +141,7 @@ constexpr int LEVEL_MAX_NB = 1024;   // widest batch of the level kernels
 constexpr int ORDER_LANDMARKS = 128; // distance profile length used to order sources
 struct LevelState {
   int nb = 0, W = 0, Lcap = 0;
-  bool c32 = true;    // MFBF path counts in sc (32-bit) rather than sv (64-bit)
-  double* sv;         // 64-bit sigma_bar (when !c32), then zeta + 1/sigma_bar  [n][nb]
-  uint32_t* sc;       // 32-bit sigma_bar (when c32)  [n][nb]
+  double* sv;         // sigma_bar, then zeta + 1/sigma_bar (in place)  [n][nb]
   uint32_t* V;        // visited bits [n][W]
   uint32_t* F;        // per-level frontier bits, level l at F + l*n*W
   uint32_t* member;   // per-level vertex bitmaps, level l at member + l*mw

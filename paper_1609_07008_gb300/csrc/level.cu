@@ -68,7 +68,6 @@ void level_carve(Carver& c, const DevGraph& g, int nb, int Lcap, int64_t list_ca
   s.Lcap = Lcap;
   s.mw = ((int64_t)n + 31) / 32;
   s.sv = c.take<double>((size_t)n * nb);
-  s.sc = c.take<uint32_t>((size_t)n * nb);
   s.V = c.take<uint32_t>((size_t)n * s.W);
   s.F = c.take<uint32_t>((size_t)Lcap * n * s.W);
   s.member = c.take<uint32_t>((size_t)Lcap * s.mw);
@@ -106,34 +105,26 @@ constexpr int NO_REQ = 0x7fffffff;           // key of a lane without a column
 
 __global__ void k_clear_flag_bits(uint32_t* flags, uint32_t bits) { atomicAnd(flags, ~bits); }
 
-// Path-count rows of multi-item vertices start at zero (MFBF adds into
-// them): sc (32-bit counts) when given, else sv (64-bit counts).  One warp
-// per row, 16 or 32 bytes per lane and store (n_b is a multiple of 128).
-__global__ void k_lvl_zero_hubs(const int32_t* __restrict__ hubs, int32_t nhub, int nb, double* sv, uint32_t* sc) {
+// sv rows of multi-item vertices start at zero (MFBF adds into them).
+// One warp per row, 32 bytes per lane and store (n_b is a multiple of 128).
+__global__ void k_lvl_zero_hubs(const int32_t* __restrict__ hubs, int32_t nhub, int nb, double* sv) {
   const unsigned lane = lane_id();
   const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
   for (uint64_t h = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; h < (uint64_t)nhub; h += nw) {
-    if (sc) {
-      uint32_t* row = sc + (size_t)hubs[h] * nb;
-      for (int c = 4 * (int)lane; c < nb; c += 128)
-        asm volatile("st.global.v4.u32 [%0], {%1,%1,%1,%1};" ::"l"(row + c), "r"(0u) : "memory");
-    } else {
-      double* row = sv + (size_t)hubs[h] * nb;
-      for (int c = 4 * (int)lane; c < nb; c += 128)
-        asm volatile("st.global.v4.u64 [%0], {%1,%1,%1,%1};" ::"l"(row + c), "l"(0ull) : "memory");
-    }
+    double* row = sv + (size_t)hubs[h] * nb;
+    for (int c = 4 * (int)lane; c < nb; c += 128)
+      asm volatile("st.global.v4.u64 [%0], {%1,%1,%1,%1};" ::"l"(row + c), "l"(0ull) : "memory");
   }
 }
 
 // Level 0: F_0(s_j) holds column j, sigma_bar(s_j, s_j) = 1.
-__global__ void k_lvl_seed(const int32_t* __restrict__ src, int nb, int W, double* sv, uint32_t* sc, uint32_t* F0,
+__global__ void k_lvl_seed(const int32_t* __restrict__ src, int nb, int W, double* sv, uint32_t* F0,
                            uint32_t* member0, int32_t* list0, uint32_t* count) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= nb) return;
   const int32_t s = src[j];
   if (s < 0) return;
-  if (sc) sc[(size_t)s * nb + j] = 1u;                               // sigma_bar as an exact integer
-  else reinterpret_cast<uint64_t*>(sv)[(size_t)s * nb + j] = 1ull;
+  reinterpret_cast<uint64_t*>(sv)[(size_t)s * nb + j] = 1ull;   // sigma_bar as an exact integer
   atomicOr(&F0[(size_t)s * W + (j >> 5)], 1u << (j & 31));
   const uint32_t bit = 1u << (s & 31);
   if (!(atomicOr(&member0[s >> 5], bit) & bit)) list0[atomicAdd(count, 1u)] = s;
@@ -607,19 +598,11 @@ __device__ __forceinline__ void ld4u(const uint64_t* p, uint64_t& a, uint64_t& b
 // values with compensation.  FLUSH(k, ...) is called once per segment with
 // pairs, in order, by the whole warp, with the lane's four column sums and
 // the OR of its 4-bit slices.
-__device__ __forceinline__ void ld4u32(const uint32_t* p, uint64_t& a, uint64_t& b, uint64_t& c, uint64_t& d) {
-  uint32_t x, y, z, w;
-  asm volatile("ld.global.L1::no_allocate.v4.u32 {%0,%1,%2,%3}, [%4];" : "=r"(x), "=r"(y), "=r"(z), "=r"(w) : "l"(p));
-  a = x; b = y; c = z; d = w;
-}
-
-// C32 (MFBF only): the gathered path counts are 32-bit (sc, 16 bytes per lane
-// and pair, so two lanes share one 32-byte sector), else 64-bit (sv).
-template <bool COUNT, bool INT, bool C32, class Flush>
+template <bool COUNT, bool INT, class Flush>
 __device__ __forceinline__ void gather_group(const uint4& myseg, int nin, const uint32_t* __restrict__ prow,
                                              const uint4* __restrict__ pmask, GatherSmem& gs, const uint64_t* sv,
-                                             const uint32_t* sc, unsigned long long& nvals,
-                                             unsigned long long& nvals_rec, uint32_t& ovf, Flush flush) {
+                                             unsigned long long& nvals, unsigned long long& nvals_rec, uint32_t& ovf,
+                                             Flush flush) {
   const unsigned lane = lane_id();
   const int mycnt = (int)lane < nin ? (int)(myseg.z & 0xffu) : 0;
   int incl = mycnt;
@@ -657,8 +640,7 @@ __device__ __forceinline__ void gather_group(const uint4& myseg, int nin, const 
           const uint32_t mw = reinterpret_cast<const uint32_t*>(&gs.mask[q])[mword];
           sl[r] = (mw >> shift) & 0xfu;
           if (sl[r]) {
-            if (C32) ld4u32(sc + (size_t)gs.row[q] * 128 + 4 * lane, x[r][0], x[r][1], x[r][2], x[r][3]);
-            else ld4u(sv + (size_t)gs.row[q] * 128 + 4 * lane, x[r][0], x[r][1], x[r][2], x[r][3]);
+            ld4u(sv + (size_t)gs.row[q] * 128 + 4 * lane, x[r][0], x[r][1], x[r][2], x[r][3]);
             if (COUNT) nvals += __popc(sl[r]);
           }
         }
@@ -704,14 +686,12 @@ __device__ __forceinline__ void gather_group(const uint4& myseg, int nin, const 
     const int nin = (uint64_t)(nseg) - base < 32 ? (int)((uint64_t)(nseg) - base) : 32;
 
 // MFBF gather of level l: sigma_bar(s,v) = sum over the segment's pairs
-// (exact integers).  flags: FLAG_SIGMA_INEXACT some sigma_bar >= 2^53;
-// FLAG_COUNT_WRAP a 64-bit count reached 2^58 (the batch is then recomputed
-// by the general kernels); FLAG_COUNT32 (C32) a count reached 2^32 (the batch
-// is then recomputed with 64-bit counts).
-template <bool COUNT, bool C32>
+// (exact 64-bit integers).  flags: bit 1 some sigma_bar >= 2^53, bit 3 a sum
+// passed 2^64 (the batch is then recomputed by the general kernels).
+template <bool COUNT>
 __global__ void __launch_bounds__(256, MFBC_GATHER_MIN_BLOCKS) k_lvl_fwd_gather(
     const uint4* __restrict__ segs, const uint32_t* nseg_p, const uint32_t* __restrict__ prow,
-    const uint4* __restrict__ pmask, int nb, double* svd, uint32_t* sc, uint32_t* flags, uint32_t* next_group,
+    const uint4* __restrict__ pmask, int nb, double* svd, uint32_t* flags, uint32_t* next_group,
     unsigned long long* bytes, unsigned long long* stat) {
   __shared__ GatherSmem gsm[8];
   GatherSmem& gs = gsm[threadIdx.x >> 5];
@@ -721,36 +701,13 @@ __global__ void __launch_bounds__(256, MFBC_GATHER_MIN_BLOCKS) k_lvl_fwd_gather(
   unsigned long long nvals = 0, nw = 0, nrec = 0;
   uint32_t ovf = 0, big = 0;
   FOR_SEGMENT_GROUPS(nseg, next_group)
-    gather_group<COUNT, true, C32>(myseg, nin, prow, pmask, gs, sv, sc, nvals, nrec, ovf,
+    gather_group<COUNT, true>(myseg, nin, prow, pmask, gs, sv, nvals, nrec, ovf,
         [&](int k, uint64_t a0, uint64_t a1, uint64_t a2, uint64_t a3, float, float, float, float, float, float,
             float, float, uint32_t cs) {
       const int32_t v = (int32_t)__shfl_sync(0xffffffffu, myseg.x, k);
       const uint32_t z = __shfl_sync(0xffffffffu, myseg.z, k);
       const int d = (int)((z >> 8) & 0xffu);
-      if (C32 && cs) {
-        uint32_t* dst = sc + (size_t)v * nb + 128 * d + 4 * lane;
-        uint64_t t0 = a0, t1 = a1, t2 = a2, t3 = a3;
-        if ((z >> 16) & 1u) {
-          if (cs & 1u) t0 += atomicAdd(dst + 0, (uint32_t)a0);
-          if (cs & 2u) t1 += atomicAdd(dst + 1, (uint32_t)a1);
-          if (cs & 4u) t2 += atomicAdd(dst + 2, (uint32_t)a2);
-          if (cs & 8u) t3 += atomicAdd(dst + 3, (uint32_t)a3);
-        } else if (cs == 0xfu) {
-          asm volatile("st.global.v4.u32 [%0], {%1,%2,%3,%4};" ::"l"(dst), "r"((uint32_t)a0), "r"((uint32_t)a1),
-                       "r"((uint32_t)a2), "r"((uint32_t)a3) : "memory");
-        } else {
-          if (cs & 1u) dst[0] = (uint32_t)a0;
-          if (cs & 2u) dst[1] = (uint32_t)a1;
-          if (cs & 4u) dst[2] = (uint32_t)a2;
-          if (cs & 8u) dst[3] = (uint32_t)a3;
-        }
-        // a segment adds at most 32 counts below 2^32, so the 64-bit sums are
-        // exact; one at or above 2^32 did not fit (the sum or the stored value)
-        const uint64_t m = ((cs & 1u) ? t0 : 0ull) | ((cs & 2u) ? t1 : 0ull) | ((cs & 4u) ? t2 : 0ull) |
-                           ((cs & 8u) ? t3 : 0ull);
-        ovf |= (uint32_t)(m >> 32 != 0ull);
-        if (COUNT) nw += __popc(cs);
-      } else if (cs) {
+      if (cs) {
         uint64_t* dst = sv + (size_t)v * nb + 128 * d + 4 * lane;
         uint64_t t0 = a0, t1 = a1, t2 = a2, t3 = a3;
         if ((z >> 16) & 1u) {
@@ -780,7 +737,7 @@ __global__ void __launch_bounds__(256, MFBC_GATHER_MIN_BLOCKS) k_lvl_fwd_gather(
     });
   }
   if (__any_sync(0xffffffffu, big != 0u) && lane == 0) atomicOr(flags, FLAG_SIGMA_INEXACT);
-  if (__any_sync(0xffffffffu, ovf != 0u) && lane == 0) atomicOr(flags, C32 ? FLAG_COUNT32 : FLAG_COUNT_WRAP);
+  if (__any_sync(0xffffffffu, ovf != 0u) && lane == 0) atomicOr(flags, FLAG_COUNT_WRAP);
   if (COUNT) {
     for (int o = 16; o; o >>= 1) {
       nvals += __shfl_xor_sync(0xffffffffu, nvals, o);
@@ -788,7 +745,7 @@ __global__ void __launch_bounds__(256, MFBC_GATHER_MIN_BLOCKS) k_lvl_fwd_gather(
     }
     for (int o = 16; o; o >>= 1) nrec += __shfl_xor_sync(0xffffffffu, nrec, o);
     if (lane == 0) {
-      atomicAdd(bytes, (C32 ? 4ull : 8ull) * (nvals + nw) + nrec);
+      atomicAdd(bytes, 8ull * (nvals + nw) + nrec);
       atomicAdd(&stat[2], nvals);
     }
   }
@@ -805,9 +762,8 @@ struct FinishSmem {
 // segmented warp reduction over the compacted columns.  Kept out of line so
 // that the common single-request path keeps its registers.  Returns the
 // number of lambda updates made (on lane 0's count).
-__device__ __noinline__ int finish_mixed(const FinishSmem& fm, int total, uint64_t* row, const uint32_t* srow,
-                                         double* lambda, int32_t n, int32_t v,
-                                         const int32_t* __restrict__ quad_words_req) {
+__device__ __noinline__ int finish_mixed(const FinishSmem& fm, int total, uint64_t* row, double* lambda, int32_t n,
+                                         int32_t v, const int32_t* __restrict__ quad_words_req) {
   const unsigned lane = lane_id();
   int adds = 0;
   for (int i0 = 0; i0 < total; i0 += 32) {
@@ -817,7 +773,7 @@ __device__ __noinline__ int finish_mixed(const FinishSmem& fm, int total, uint64
     if (i < total) {
       const int c = fm.col[i];
       uint64_t* slot = row + c;
-      *slot = finish_col(acc_value(fm.s[i], fm.c[i]), srow ? (uint64_t)srow[c] : *slot, ls, lc);
+      *slot = finish_col(acc_value(fm.s[i], fm.c[i]), *slot, ls, lc);
       key = __ldg(&quad_words_req[c >> 5]);
     }
     const bool last = warp_acc_seg_sum(ls, lc, key) && key != NO_REQ && ls != 0.f;
@@ -834,14 +790,11 @@ __device__ __noinline__ int finish_mixed(const FinishSmem& fm, int total, uint64
 // the row's FP64 accumulator.  Only the columns of v's level-l frontier are
 // finalised (about one in six of the quad on R-MAT inputs), so they are
 // first compacted through shared memory and then finalised one per lane.
-// With C32 the path counts sigma_bar are read from the 32-bit array sc; the
-// values zeta + 1/sigma_bar are always written to sv.
-template <bool COUNT, bool C32>
+template <bool COUNT>
 __global__ void __launch_bounds__(256, MFBC_BWD_GATHER_MIN_BLOCKS) k_lvl_bwd_gather(
     const uint4* __restrict__ segs, const uint32_t* nseg_p, const uint32_t* __restrict__ prow,
     const uint4* __restrict__ pmask, int nb, int W, const uint32_t* __restrict__ Fl,
-    const int32_t* __restrict__ hub_of, double* svd, const uint32_t* sc, double* zacc, double* lambda, int32_t n,
-    int uniform_req,
+    const int32_t* __restrict__ hub_of, double* svd, double* zacc, double* lambda, int32_t n, int uniform_req,
     const int32_t* __restrict__ quad_req, const int32_t* __restrict__ word_req, uint32_t* next_group,
     unsigned long long* bytes, unsigned long long* stat) {
   __shared__ GatherSmem gsm[8];
@@ -881,18 +834,13 @@ __global__ void __launch_bounds__(256, MFBC_BWD_GATHER_MIN_BLOCKS) k_lvl_bwd_gat
       } else {
         // this segment is the only writer of these slots in this launch
         uint64_t* row = sv + (size_t)v * nb + 128 * d;
-        const uint32_t* srow = C32 ? sc + (size_t)v * nb + 128 * d : nullptr;
         const int rq = uniform_req >= 0 ? uniform_req : __ldg(&quad_req[d]);
-        // sigma_bar read (4 or 8 bytes) and the value written (8 bytes) per column
-        if (COUNT && lane == 0) {
-          if (C32) nrec += 12ull * (unsigned long long)total;
-          else nw += 2ull * (unsigned long long)total;
-        }
+        if (COUNT && lane == 0) nw += 2ull * (unsigned long long)total;
         if (rq >= 0) {                                // one request: one lambda(v) sum
           float ls = 0.f, lc = 0.f;                   // lambda(v) terms of this lane's columns
           for (int i = (int)lane; i < total; i += 32) {
-            const int c = fm.col[i];
-            row[c] = finish_col(acc_value(fm.s[i], fm.c[i]), C32 ? (uint64_t)srow[c] : row[c], ls, lc);
+            uint64_t* slot = row + fm.col[i];
+            *slot = finish_col(acc_value(fm.s[i], fm.c[i]), *slot, ls, lc);
           }
           if (__any_sync(0xffffffffu, ls != 0.f)) {
             const double lam = warp_acc_sum(ls, lc);
@@ -900,12 +848,12 @@ __global__ void __launch_bounds__(256, MFBC_BWD_GATHER_MIN_BLOCKS) k_lvl_bwd_gat
             if (COUNT && lane == 0) nrec += 8ull;
           }
         } else {                                      // requests meet in this quad: sum per request
-          const int adds = finish_mixed(fm, total, row, srow, lambda, n, v, word_req + 4 * d);
+          const int adds = finish_mixed(fm, total, row, lambda, n, v, word_req + 4 * d);
           if (COUNT) nrec += 8ull * adds;
         }
       }
     };
-    gather_group<COUNT, false, false>(myseg, nin, prow, pmask, gs, sv, nullptr, nvals, nrec, ovf, finish);
+    gather_group<COUNT, false>(myseg, nin, prow, pmask, gs, sv, nvals, nrec, ovf, finish);
     // segments without successor pairs: zeta = 0
     uint32_t empty = __ballot_sync(0xffffffffu, (int)lane < nin && (myseg.z & 0xffu) == 0u && myseg.x != SEG_DUMMY);
     while (empty) {
@@ -934,8 +882,8 @@ __global__ void __launch_bounds__(256, MFBC_BWD_GATHER_MIN_BLOCKS) k_lvl_bwd_gat
 // into shared memory and finalised one per lane.
 __global__ void __launch_bounds__(LVL_WARPS * 32) k_lvl_hub_final(
     const int32_t* __restrict__ hubs, int32_t nhub, int W, int nb, const uint32_t* __restrict__ Fl,
-    const uint32_t* __restrict__ mem_l, double* svd, const uint32_t* sc, double* zacc, double* lambda, int32_t n,
-    int uniform_req, const int32_t* __restrict__ word_req, unsigned long long* bytes) {
+    const uint32_t* __restrict__ mem_l, double* svd, double* zacc, double* lambda, int32_t n, int uniform_req,
+    const int32_t* __restrict__ word_req, unsigned long long* bytes) {
   __shared__ uint16_t cols_all[LVL_WARPS][LEVEL_MAX_NB];
   uint16_t* cols = cols_all[threadIdx.x >> 5];
   const unsigned lane = lane_id();
@@ -969,12 +917,11 @@ __global__ void __launch_bounds__(LVL_WARPS * 32) k_lvl_hub_final(
       __syncwarp();
       double* za = zacc + (size_t)h * nb;
       uint64_t* row = sv + (size_t)v * nb;
-      const uint32_t* srow = sc ? sc + (size_t)v * nb : nullptr;   // 32-bit path counts, else in row
       if (uniform_req >= 0) {
         float ls = 0.f, lc = 0.f;
         for (int i = (int)lane; i < total; i += 32) {
           const int c = cols[i];
-          row[c] = finish_col(df_of_double(za[c]), srow ? (uint64_t)srow[c] : row[c], ls, lc);
+          row[c] = finish_col(df_of_double(za[c]), row[c], ls, lc);
           za[c] = 0.0;
         }
         const double lam = warp_acc_sum(ls, lc);
@@ -987,7 +934,7 @@ __global__ void __launch_bounds__(LVL_WARPS * 32) k_lvl_hub_final(
           int key = NO_REQ;
           if (i < total) {
             const int c = cols[i];
-            row[c] = finish_col(df_of_double(za[c]), srow ? (uint64_t)srow[c] : row[c], ls, lc);
+            row[c] = finish_col(df_of_double(za[c]), row[c], ls, lc);
             za[c] = 0.0;
             key = __ldg(&word_req[c >> 5]);
           }
@@ -995,7 +942,7 @@ __global__ void __launch_bounds__(LVL_WARPS * 32) k_lvl_hub_final(
             atomicAdd(&lambda[(size_t)key * n + v], (double)ls + (double)lc);
         }
       }
-      if (bytes && lane == 0) nbytes += (sc ? 28ull : 32ull) * total + 4ull * W + 16ull;
+      if (bytes && lane == 0) nbytes += 32ull * total + 4ull * W + 16ull;
     }
   }
   if (bytes) {
@@ -1019,8 +966,7 @@ __global__ void k_lvl_clear_rows(const int32_t* __restrict__ list, uint32_t coun
 // Per-source rows of tau and sigma_bar from the level masks (sssp output).
 __global__ void k_lvl_output(const int32_t* __restrict__ list, uint32_t count, int level, int W, int nb,
                              int nactive, int32_t n, const uint32_t* __restrict__ Fl,
-                             const double* __restrict__ sv, const uint32_t* __restrict__ sc, int32_t* dist_out,
-                             double* sigma_out) {
+                             const double* __restrict__ sv, int32_t* dist_out, double* sigma_out) {
   const unsigned lane = lane_id();
   const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
   for (uint64_t i = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < count; i += nw) {
@@ -1030,9 +976,7 @@ __global__ void k_lvl_output(const int32_t* __restrict__ list, uint32_t count, i
       const int c = j * 32 + lane;
       if (((fj >> lane) & 1u) && c < nactive) {
         dist_out[(size_t)c * n + v] = level;
-        if (sigma_out)
-          sigma_out[(size_t)c * n + v] = sc ? (double)sc[(size_t)v * nb + c]
-                                            : (double)reinterpret_cast<const uint64_t*>(sv)[(size_t)v * nb + c];
+        if (sigma_out) sigma_out[(size_t)c * n + v] = (double)reinterpret_cast<const uint64_t*>(sv)[(size_t)v * nb + c];
       }
     }
   }
@@ -1126,22 +1070,25 @@ static mfbc_status level_round(RunCtx& rc, LevelState& s, bool fwd, int l, int64
   MFBC_CUDA_TRY(cudaMemsetAsync(&s.ctr->work[2], 0, sizeof(uint32_t), st), rc.err);
   const unsigned ggrid = grid_for_items(nseg, fwd ? kGatherGrid : kBwdGatherGrid);
   if (fwd) {
-#define FWDG(CNT, C32)                                                                                          \
-  PROF(K_LVL_FWD_G, (k_lvl_fwd_gather<CNT, C32><<<ggrid, 256, 0, st>>>(                                         \
-                        s.segs, &s.ctr->work[1], s.prow, s.pmask, nb, s.sv, s.sc, &s.ctr->flags, &s.ctr->work[2], \
-                        CNT ? B + K_LVL_FWD_G : nullptr, s.ctr->stat)))
-    if (B) { if (s.c32) FWDG(true, true); else FWDG(true, false); }
-    else { if (s.c32) FWDG(false, true); else FWDG(false, false); }
-#undef FWDG
+    if (B)
+      PROF(K_LVL_FWD_G, (k_lvl_fwd_gather<true><<<ggrid, 256, 0, st>>>(
+                            s.segs, &s.ctr->work[1], s.prow, s.pmask, nb, s.sv, &s.ctr->flags, &s.ctr->work[2],
+                            B + K_LVL_FWD_G, s.ctr->stat)));
+    else
+      PROF(K_LVL_FWD_G, (k_lvl_fwd_gather<false><<<ggrid, 256, 0, st>>>(
+                            s.segs, &s.ctr->work[1], s.prow, s.pmask, nb, s.sv, &s.ctr->flags, &s.ctr->work[2],
+                            nullptr, s.ctr->stat)));
   } else {
-#define BWDG(CNT, C32)                                                                                          \
-  PROF(K_LVL_BWD_G, (k_lvl_bwd_gather<CNT, C32><<<ggrid, 256, 0, st>>>(                                         \
-                        s.segs, &s.ctr->work[1], s.prow, s.pmask, nb, W, Fl, g.items_out.hub_of, s.sv, s.sc,      \
-                        s.zacc, lambda, n, uniform_req, s.quad_req, s.word_req, &s.ctr->work[2],                  \
-                        CNT ? B + K_LVL_BWD_G : nullptr, s.ctr->stat)))
-    if (B) { if (s.c32) BWDG(true, true); else BWDG(true, false); }
-    else { if (s.c32) BWDG(false, true); else BWDG(false, false); }
-#undef BWDG
+    if (B)
+      PROF(K_LVL_BWD_G, (k_lvl_bwd_gather<true><<<ggrid, 256, 0, st>>>(
+                            s.segs, &s.ctr->work[1], s.prow, s.pmask, nb, W, Fl, g.items_out.hub_of, s.sv, s.zacc,
+                            lambda, n, uniform_req, s.quad_req, s.word_req, &s.ctr->work[2], B + K_LVL_BWD_G,
+                            s.ctr->stat)));
+    else
+      PROF(K_LVL_BWD_G, (k_lvl_bwd_gather<false><<<ggrid, 256, 0, st>>>(
+                            s.segs, &s.ctr->work[1], s.prow, s.pmask, nb, W, Fl, g.items_out.hub_of, s.sv, s.zacc,
+                            lambda, n, uniform_req, s.quad_req, s.word_req, &s.ctr->work[2], nullptr,
+                            s.ctr->stat)));
   }
   return MFBC_OK;
 }
@@ -1185,11 +1132,9 @@ mfbc_status level_batch(RunCtx& rc, LevelState& s, const int32_t* d_src_batch, i
   MFBC_CUDA_TRY(cudaMemsetAsync(s.ctr->list_count, 0, sizeof(uint32_t) * 4, st), rc.err);
   MFBC_CUDA_TRY(cudaMemsetAsync(s.full, 0, sizeof(uint32_t) * s.mw, st), rc.err);
   if (g.items_in.nhub)
-    PROF(K_FILL, (k_lvl_zero_hubs<<<152 * 4, 256, 0, st>>>(g.items_in.hubs, g.items_in.nhub, nb, s.sv,
-                                                           s.c32 ? s.sc : nullptr)));
+    PROF(K_FILL, (k_lvl_zero_hubs<<<152 * 4, 256, 0, st>>>(g.items_in.hubs, g.items_in.nhub, nb, s.sv)));
   rc.prof->k[K_FILL].bytes += 8.0 * g.items_in.nhub * nb;
-  PROF(K_SEED, (k_lvl_seed<<<(nb + 127) / 128, 128, 0, st>>>(s.src, nb, W, s.sv, s.c32 ? s.sc : nullptr, s.F,
-                                                           s.member, s.lists,
+  PROF(K_SEED, (k_lvl_seed<<<(nb + 127) / 128, 128, 0, st>>>(s.src, nb, W, s.sv, s.F, s.member, s.lists,
                                                            &s.ctr->list_count[0])));
   MFBC_CUDA_TRY(cudaMemcpyAsync(rc.h_ctr, s.ctr->list_count, sizeof(uint32_t) * 5, cudaMemcpyDeviceToHost, st), rc.err);
   MFBC_CUDA_TRY(cudaStreamSynchronize(st), rc.err);
@@ -1213,15 +1158,6 @@ mfbc_status level_batch(RunCtx& rc, LevelState& s, const int32_t* d_src_batch, i
     MFBC_CUDA_TRY(cudaMemcpyAsync(rc.h_ctr, s.ctr->list_count, sizeof(uint32_t) * 5, cudaMemcpyDeviceToHost, st), rc.err);
     MFBC_CUDA_TRY(cudaStreamSynchronize(st), rc.err);
     rc.prof->drain();
-    if (rc.h_ctr[4] & FLAG_COUNT32) {
-      // a count reached 2^32: this batch and the rest of the call count in
-      // 64 bits (nothing has been added to lambda yet)
-      k_clear_flag_bits<<<1, 1, 0, st>>>(&s.ctr->flags, FLAG_COUNT32);
-      level_reset(rc, s, l + 1);
-      s.c32 = false;
-      return level_batch(rc, s, d_src_batch, nactive, lambda, backward, levels_out, levels_exceeded, fwd_iters,
-                         bwd_iters);
-    }
     if (rc.h_ctr[4] & (FLAG_LEVEL_LIST | FLAG_COUNT_WRAP)) {
       // list capacity exceeded (bit 0) or a path count passed 2^64 (bit 3):
       // the general kernels redo this batch
@@ -1245,8 +1181,7 @@ mfbc_status level_batch(RunCtx& rc, LevelState& s, const int32_t* d_src_batch, i
     if (e) return e;
     if (g.items_out.nhub)
       PROF(K_LVL_HUB, (k_lvl_hub_final<<<grid_for_items(g.items_out.nhub, 152 * 8), LVL_WARPS * 32, 0, st>>>(
-                          g.items_out.hubs, g.items_out.nhub, W, nb, Fl(l), Ml(l), s.sv, s.c32 ? s.sc : nullptr,
-                          s.zacc, lambda, n,
+                          g.items_out.hubs, g.items_out.nhub, W, nb, Fl(l), Ml(l), s.sv, s.zacc, lambda, n,
                           uniform_req, s.word_req, B ? B + K_LVL_HUB : nullptr)));
     if (bwd_iters) (*bwd_iters)++;
   }
@@ -1280,8 +1215,7 @@ mfbc_status level_output(RunCtx& rc, LevelState& s, int levels, int nactive, int
       const uint32_t c = P.cnt[l];
       if (!c) continue;
       k_lvl_output<<<grid_for_warps(c, 152 * 16), LVL_WARPS * 32, 0, rc.stream>>>(
-          s.lists + P.off[l], c, l, s.W, s.nb, nactive, n, s.F + (size_t)l * n * s.W, s.sv,
-          s.c32 ? s.sc : nullptr, dist_out,
+          s.lists + P.off[l], c, l, s.W, s.nb, nactive, n, s.F + (size_t)l * n * s.W, s.sv, dist_out,
           sigma_out);
     }
   });

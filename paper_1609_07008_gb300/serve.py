@@ -366,17 +366,22 @@ def run_plain(graphs: dict, requests: list[Request], clock=time.perf_counter, n_
 
 
 def make_requests(graph_sizes: dict, count: int, rate: float, *, lo: int = 64, hi: int = 4096,
-                  seed: int = 0, eligible: dict | None = None) -> list[Request]:
+                  seed: int = 0, eligible: dict | None = None, weights: dict | None = None) -> list[Request]:
     """Poisson arrivals at `rate` per second; each request picks a graph
-    uniformly and log-uniform [lo, hi] sources (at most the graph's eligible
-    vertices), sampled without replacement."""
+    (uniformly, or with probability proportional to `weights`) and
+    log-uniform [lo, hi] sources (at most the graph's eligible vertices),
+    sampled without replacement."""
     rng = np.random.default_rng(seed)
     names = sorted(graph_sizes)
+    p = None
+    if weights:
+        p = np.array([float(weights[k]) for k in names])
+        p = p / p.sum()
     t = 0.0
     out = []
     for i in range(count):
         t += rng.exponential(1.0 / rate) if rate > 0 else 0.0
-        name = names[int(rng.integers(len(names)))]
+        name = names[int(rng.choice(len(names), p=p))] if p is not None else names[int(rng.integers(len(names)))]
         pool = eligible[name] if eligible else np.arange(graph_sizes[name], dtype=np.int32)
         k = int(round(math.exp(rng.uniform(math.log(lo), math.log(hi)))))
         k = max(1, min(k, len(pool)))
