@@ -166,7 +166,7 @@ def serve_graph(name):
     return gg.grid2d(int(name[4:-1]), weights=(1, 16), seed=1)
 
 
-def serving_bench(pool=SERVE_DEFAULT, n_requests=300, seed=5, max_cols=1024, loads=(0.5, 0.8, 1.2)):
+def serving_bench(pool=SERVE_DEFAULT, n_requests=300, seed=5, loads=(0.5, 0.8, 1.2)):
     """Served (continuous batching at batch granularity, memory-budget
     admission, several workers and CUDA streams per graph) against plain (one
     mfbc_bc_device call per request, in arrival order) on the same requests:
@@ -188,6 +188,10 @@ def serving_bench(pool=SERVE_DEFAULT, n_requests=300, seed=5, max_cols=1024, loa
     elig = {k: np.flatnonzero(g.out_degree() > 0).astype(np.int32) for k, g in host.items()}
     sizes = {k: g.n for k, g in host.items()}
     weights = {k: 1.0 / np.sqrt(g.n) for k, g in host.items()}
+    # batch width per graph: the level kernels take at most 1024 columns; the
+    # distance kernels (weighted grids) pay per distance step whatever the
+    # width, so their batches are as wide as a request gets
+    max_cols = {k: 4096 if g.w is not None else 1024 for k, g in host.items()}
     free, _ = torch.cuda.mem_get_info()
     budget = int(0.6 * free)
 

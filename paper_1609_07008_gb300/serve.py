@@ -97,12 +97,13 @@ class Server:
     first source, count)), and sizer(key, n_b, slots) -> bytes the
     library's scratch size; the pool is then a numpy array."""
 
-    def __init__(self, graphs: dict, *, budget_bytes: int, max_cols: int = 1024, n_b: int = 0,
+    def __init__(self, graphs: dict, *, budget_bytes: int, max_cols=1024, n_b: int = 0,
                  executor=None, sizer=None, clock=time.perf_counter, replicas: dict | None = None):
         self.graphs = graphs
         self.handles = {k: [G] + list((replicas or {}).get(k, [])) for k, G in graphs.items()}
         self.budget = int(budget_bytes)
-        self.max_cols = int(max_cols)
+        # columns per batch: one width, or one per graph (a dict)
+        self.max_cols = dict(max_cols) if isinstance(max_cols, dict) else {k: int(max_cols) for k in graphs}
         self.n_b = int(n_b)
         self.clock = clock
         self._gpu = executor is None
@@ -167,9 +168,9 @@ class Server:
 
     # ------------------------------------------------------------ internals
     def _width(self, key):
-        """The worker's n_b and bytes: n_b (or max_cols), lowered in steps of
-        128 while one worker would not fit the budget."""
-        nb = self.n_b or self.max_cols
+        """The worker's n_b and bytes: n_b (or the graph's max_cols), lowered
+        in steps of 128 while one worker would not fit the budget."""
+        nb = self.n_b or self.max_cols[key]
         need = self.sizer(key, nb, max(1, nb // 32))
         while need > self.budget and nb > 128:
             nb = max(128, nb - 128)
