@@ -192,13 +192,24 @@ def serving_bench(pool=SERVE_DEFAULT, n_requests=300, seed=5, loads=(0.5, 0.8, 1
     # distance kernels (weighted grids) pay per distance step whatever the
     # width, so their batches are as wide as a request gets
     max_cols = {k: 4096 if g.w is not None else 1024 for k, g in host.items()}
-    free, _ = torch.cuda.mem_get_info()
-    budget = int(0.6 * free)
+    handles = list(graphs.values()) + [R for rs_ in replicas.values() for R in rs_]
+    budget = 0
+
+    def release():
+        # the plain form's calls leave scratch cached on the handles, the
+        # server's workers their tensors in torch's cache: give both back
+        for G in handles:
+            G.release_scratch()
+        torch.cuda.empty_cache()
 
     def reqs(rate, count=n_requests, lo=64, hi=4096, sd=seed):
         return serve.make_requests(sizes, count, rate, lo=lo, hi=hi, seed=sd, eligible=elig, weights=weights)
 
     def served(rs):
+        nonlocal budget
+        release()
+        free, _ = torch.cuda.mem_get_info()
+        budget = int(0.7 * free)
         srv = serve.Server(graphs, budget_bytes=budget, max_cols=max_cols, replicas=replicas).start()
         try:
             serve.run_served(srv, rs, timeout=3600)
@@ -219,6 +230,7 @@ def serving_bench(pool=SERVE_DEFAULT, n_requests=300, seed=5, loads=(0.5, 0.8, 1
     # warm both forms once (library scratch, torch allocator, module load)
     serve.run_plain(graphs, reqs(0, count=2 * len(pool), hi=256, sd=seed + 1))
     served(reqs(0, count=2 * len(pool), hi=256, sd=seed + 1))
+    release()
     sat_plain_reqs = serve.run_plain(graphs, reqs(0))
     sat_plain = serve.latency_stats(sat_plain_reqs, edges)
     sat_served_reqs = reqs(0)
@@ -227,13 +239,14 @@ def serving_bench(pool=SERVE_DEFAULT, n_requests=300, seed=5, loads=(0.5, 0.8, 1
     cap = n_requests / sat_plain["span_s"]
     rows = []
     for load in loads:
+        release()
         rp = serve.run_plain(graphs, reqs(load * cap))
         rs = reqs(load * cap)
         row = {"offered_load_vs_plain_capacity": load, "rate_per_s": load * cap,
                "plain": serve.latency_stats(rp, edges), "served": served(rs)}
         worst = max(worst, diff(rp, rs))
         rows.append(row)
-    for G in list(graphs.values()) + [R for rs_ in replicas.values() for R in rs_]:
+    for G in handles:
         G.close()
     return {"pool": {k: {"n": host[k].n, "m": int(host[k].m), "weighted": host[k].w is not None} for k in pool},
             "graph_choice": "probability proportional to 1/sqrt(n)", "sources_per_request": "log-uniform [64, 4096]",

@@ -186,6 +186,13 @@ mfbc_status mfbc_graph_create_device(int32_t n, int64_t nnz, const int64_t* rowp
 /* Release the graph and any scratch cached on it.  NULL is ignored. */
 void mfbc_graph_destroy(mfbc_graph* g);
 
+/* Free the device scratch the handle cached for earlier calls (it grows to
+ * the largest call made without opt->workspace); the next such call
+ * allocates again.  The graph stays resident.  Every call has finished its
+ * work when it returns; this one still synchronises the device before it
+ * frees the memory. */
+mfbc_status mfbc_graph_release_scratch(mfbc_graph* g);
+
 /* n, nnz, flags and whether the graph has unit weights (out pointers may be NULL). */
 mfbc_status mfbc_graph_info(const mfbc_graph* g, int32_t* n, int64_t* nnz, uint32_t* flags,
                             int32_t* unit_weights);

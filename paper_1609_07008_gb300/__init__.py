@@ -114,6 +114,7 @@ def load(path: str | None = None):
             "mfbc_sssp_batch": [vp, vp, i32, vp, vp, ctypes.POINTER(Options)],
             "mfbc_sssp_batch_device": [vp, vp, i32, vp, vp, ctypes.POINTER(Options)],
             "mfbc_workspace_size": [vp, i32, i32, ctypes.POINTER(Options), ctypes.POINTER(ctypes.c_uint64)],
+            "mfbc_graph_release_scratch": [vp],
         }
         for name, args in sig.items():
             f = getattr(lib, name)
@@ -224,6 +225,10 @@ class Graph:
     def from_csr(cls, g, stream=None) -> "Graph":
         """From any object with n, rowptr, col, w, directed attributes."""
         return cls(g.rowptr, g.col, g.w, directed=g.directed, stream=stream)
+
+    def release_scratch(self):
+        """Free the device scratch cached on this handle (mfbc_graph_release_scratch)."""
+        _check(load().mfbc_graph_release_scratch(self._h))
 
     def close(self):
         if getattr(self, "_h", None) and self._h.value:

@@ -165,6 +165,23 @@ extern "C" void mfbc_graph_destroy(mfbc_graph* G) {
   delete G;
 }
 
+extern "C" mfbc_status mfbc_graph_release_scratch(mfbc_graph* G) {
+  if (!G) return fail(MFBC_ERR_INVALID, "graph must not be NULL");
+  std::lock_guard<std::mutex> lock(G->mu);
+  if (G->ws) {
+    // calls return once their work is complete, so nothing of this handle
+    // runs here; synchronise anyway before giving the memory back
+    if (cudaDeviceSynchronize() != cudaSuccess || cudaFree(G->ws) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(MFBC_ERR_CUDA, "freeing the cached scratch failed");
+    }
+    G->ws = nullptr;
+    G->ws_bytes = 0;
+  }
+  t_err.clear();
+  return MFBC_OK;
+}
+
 extern "C" mfbc_status mfbc_graph_info(const mfbc_graph* G, int32_t* n, int64_t* nnz, uint32_t* flags,
                                        int32_t* unit) {
   if (!G) return fail(MFBC_ERR_INVALID, "graph must not be NULL");

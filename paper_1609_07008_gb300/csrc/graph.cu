@@ -188,12 +188,19 @@ mfbc_status graph_build(int32_t n, int64_t nnz, const int64_t* h_rowptr, const i
       if (rp[v + 1] > rp[v]) ids.push_back(v);
       g->max_deg = std::max<int64_t>(g->max_deg, rp[v + 1] - rp[v]);
     }
-    const size_t k = std::min<size_t>(ids.size(), (size_t)ORDER_LANDMARKS);
+    // the HOT_ROWS highest degrees also mark the rows the level gathers ask
+    // the L2 to keep (their values are read along most DAG arcs)
+    const size_t k = std::min<size_t>(ids.size(), (size_t)std::max(ORDER_LANDMARKS, HOT_ROWS));
     std::partial_sort(ids.begin(), ids.begin() + k, ids.end(), [&](int32_t a, int32_t b) {
       const int64_t da = rp[a + 1] - rp[a], db = rp[b + 1] - rp[b];
       return da != db ? da > db : a < b;
     });
-    g->landmarks.assign(ids.begin(), ids.begin() + k);
+    g->landmarks.assign(ids.begin(), ids.begin() + std::min<size_t>(k, (size_t)ORDER_LANDMARKS));
+    std::vector<uint32_t> hot(((size_t)n + 31) / 32 + 1, 0u);
+    for (size_t i = 0; i < std::min<size_t>(k, (size_t)HOT_ROWS); i++) hot[(size_t)ids[i] >> 5] |= 1u << (ids[i] & 31);
+    TRY(dev_alloc(g, &g->hot, hot.size(), err));
+    MFBC_CUDA_TRY(cudaMemcpyAsync(g->hot, hot.data(), sizeof(uint32_t) * hot.size(), cudaMemcpyHostToDevice, st), err);
+    MFBC_CUDA_TRY(cudaStreamSynchronize(st), err);
   }
   if (g->directed) {
     // A^T by a stable counting sort on the host: rows of A^T are sorted by

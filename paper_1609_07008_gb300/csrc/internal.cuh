@@ -40,6 +40,7 @@ struct DevGraph {
   bool unit = true;                // every arc weighs 1 (w == NULL or all ones)
   int32_t wmax = 1;
   std::vector<int32_t> landmarks;   // highest out-degree vertices, descending (source ordering)
+  uint32_t* hot = nullptr;         // [n/32] bits: the HOT_ROWS highest out-degree vertices
   int64_t max_deg = 0;             // largest out-degree
   int64_t max_in_deg = 0;          // largest in-degree
   int64_t* rowptr = nullptr;       // CSR of A (out-arcs)
@@ -139,6 +140,7 @@ void general_carve(Carver& c, int32_t n, int nb, GeneralState& s);
 // frontiers kept as per-level bit masks.  See level.cu.
 constexpr int LEVEL_MAX_NB = 1024;   // widest batch of the level kernels
 constexpr int ORDER_LANDMARKS = 128; // distance profile length used to order sources
+constexpr int HOT_ROWS = 4096;       // rows the level gathers load with the L2 evict-last hint
 struct LevelState {
   int nb = 0, W = 0, Lcap = 0;
   double* sv;         // sigma_bar, then zeta + 1/sigma_bar (in place)  [n][nb]

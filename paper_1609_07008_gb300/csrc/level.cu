@@ -234,7 +234,8 @@ __device__ __forceinline__ void fill_dummy_segs(uint4* segs, uint32_t b, uint32_
 // (ascending), as segments.  Returns false (writing nothing) when the
 // buffers are full.
 __device__ __forceinline__ bool emit_quads(const WarpSmem& w, int nm, int32_t v, bool multi, uint32_t quads, int Q,
-                                           uint32_t* prow, uint4* pmask, uint4* segs, uint32_t* work,
+                                           const uint32_t* __restrict__ hot, uint32_t* prow, uint4* pmask,
+                                           uint4* segs, uint32_t* work,
                                            uint32_t pair_cap, uint32_t seg_cap, SlotCursor& cur,
                                            unsigned long long* npairs) {
   const unsigned lane = lane_id();
@@ -262,6 +263,8 @@ __device__ __forceinline__ bool emit_quads(const WarpSmem& w, int nm, int32_t v,
   const uint32_t pb = cur.p, sb = cur.s;
   cur.p += P;
   cur.s += S;
+  // bit 31 of a pair's row index: the row belongs to a high-degree vertex
+  const uint32_t hotbit = ((int)lane < nm && hot && test_bit(hot, w.su[lane])) ? 0x80000000u : 0u;
   if (npairs) *npairs += P + (uint64_t)S * (1ull << 32);   // pairs in the low word, segments in the high
   int r = 0;
   for (uint32_t ql = quads; ql; ql &= ql - 1, r++) {
@@ -271,7 +274,7 @@ __device__ __forceinline__ bool emit_quads(const WarpSmem& w, int nm, int32_t v,
     const uint32_t off = (uint32_t)__shfl_sync(0xffffffffu, excl, d);
     if (nz) {
       const uint32_t at = pb + off + __popc(mk & lt);
-      prow[at] = (uint32_t)w.su[lane] * (uint32_t)Q + (uint32_t)d;
+      prow[at] = ((uint32_t)w.su[lane] * (uint32_t)Q + (uint32_t)d) | hotbit;
       pmask[at] = make_uint4(w.sF[lane][4 * d], w.sF[lane][4 * d + 1], w.sF[lane][4 * d + 2], w.sF[lane][4 * d + 3]);
     }
     if (lane == 0) segs[sb + r] = make_seg(v, pb + off, __popc(mk), d, multi);
@@ -306,8 +309,8 @@ __global__ void __launch_bounds__(LVL_WARPS * 32, MFBC_PAIR_MIN_BLOCKS) k_lvl_fw
     const int32_t* __restrict__ col_t, int W, const uint32_t* __restrict__ full, const uint32_t* __restrict__ V,
     const uint32_t* __restrict__ Fl, const uint32_t* __restrict__ mem_l, uint32_t* Fn, uint32_t* mem_n,
     int32_t* list_n, uint32_t* count_n, int64_t cap_n, uint32_t* flags, uint32_t* next_group, uint32_t* prow,
-    uint4* pmask, uint4* segs, uint32_t* work, uint32_t pair_cap, uint32_t seg_cap, unsigned long long* bytes,
-    unsigned long long* stat) {
+    uint4* pmask, uint4* segs, uint32_t* work, uint32_t pair_cap, uint32_t seg_cap, const uint32_t* __restrict__ hot,
+    unsigned long long* bytes, unsigned long long* stat) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   WarpSmem& sm = reinterpret_cast<WarpSmem*>(smem_raw)[threadIdx.x >> 5];
   const unsigned lane = lane_id();
@@ -396,7 +399,7 @@ __global__ void __launch_bounds__(LVL_WARPS * 32, MFBC_PAIR_MIN_BLOCKS) k_lvl_fw
       if (bytes) nbytes += 4ull * W * (nm + 1);
       const uint32_t cw = __ballot_sync(0xffffffffu, cand != 0u);
       if (!cw) continue;
-      emit_quads(sm, nm, v, multi, quads_of_words(cw, Q), Q, prow, pmask, segs, work, pair_cap, seg_cap, cur,
+      emit_quads(sm, nm, v, multi, quads_of_words(cw, Q), Q, hot, prow, pmask, segs, work, pair_cap, seg_cap, cur,
                  bytes ? &npairs : nullptr);
       if ((int)lane < W && cand) {
         if (multi) atomicOr(&Fn[(size_t)v * W + lane], cand);
@@ -431,8 +434,8 @@ __global__ void __launch_bounds__(LVL_WARPS * 32, MFBC_PAIR_MIN_BLOCKS) k_lvl_bw
     int64_t ib, int64_t ie, const int32_t* __restrict__ item_v, const int64_t* __restrict__ item_meta,
     const int32_t* __restrict__ col, int W, const uint32_t* __restrict__ Fl, const uint32_t* __restrict__ mem_l,
     const uint32_t* __restrict__ Fn, const uint32_t* __restrict__ mem_n, uint32_t* next_group, uint32_t* prow,
-    uint4* pmask, uint4* segs, uint32_t* work, uint32_t pair_cap, uint32_t seg_cap, unsigned long long* bytes,
-    unsigned long long* stat) {
+    uint4* pmask, uint4* segs, uint32_t* work, uint32_t pair_cap, uint32_t seg_cap, const uint32_t* __restrict__ hot,
+    unsigned long long* bytes, unsigned long long* stat) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   WarpSmem& sm = reinterpret_cast<WarpSmem*>(smem_raw)[threadIdx.x >> 5];
   const unsigned lane = lane_id();
@@ -504,7 +507,7 @@ __global__ void __launch_bounds__(LVL_WARPS * 32, MFBC_PAIR_MIN_BLOCKS) k_lvl_bw
       __syncwarp();
       if (bytes) nbytes += 4ull * W * (nm + 1);
       const uint32_t words = __ballot_sync(0xffffffffu, multi ? any != 0u : Fv != 0u);
-      if (words) emit_quads(sm, nm, v, multi, quads_of_words(words, Q), Q, prow, pmask, segs, work, pair_cap,
+      if (words) emit_quads(sm, nm, v, multi, quads_of_words(words, Q), Q, hot, prow, pmask, segs, work, pair_cap,
                             seg_cap, cur, bytes ? &npairs : nullptr);
       __syncwarp();
     }
@@ -582,6 +585,17 @@ __device__ __forceinline__ void stage_chunk(const uint4& myseg, int excl, int in
 #ifndef MFBC_GATHER_NC
 #define MFBC_GATHER_NC 0
 #endif
+// Rows of high-degree vertices (bit 31 of the pair's row index) are loaded
+// with the L2 evict-last priority: most DAG arcs end there, so their sectors
+// are read again and again within a level, while the rows of the many
+// low-degree vertices stream through.  A hint only; results do not depend on it.
+#ifndef MFBC_HOT_HINT
+#define MFBC_HOT_HINT 1
+#endif
+__device__ __forceinline__ void ld4u_keep(const uint64_t* p, uint64_t& a, uint64_t& b, uint64_t& c, uint64_t& d) {
+  asm volatile("ld.global.L1::no_allocate.L2::evict_last.v4.u64 {%0,%1,%2,%3}, [%4];"
+               : "=l"(a), "=l"(b), "=l"(c), "=l"(d) : "l"(p));
+}
 __device__ __forceinline__ void ld4u(const uint64_t* p, uint64_t& a, uint64_t& b, uint64_t& c, uint64_t& d) {
 #if MFBC_GATHER_NC
   asm volatile("ld.global.nc.L1::no_allocate.v4.u64 {%0,%1,%2,%3}, [%4];" : "=l"(a), "=l"(b), "=l"(c), "=l"(d) : "l"(p));
@@ -640,7 +654,10 @@ __device__ __forceinline__ void gather_group(const uint4& myseg, int nin, const 
           const uint32_t mw = reinterpret_cast<const uint32_t*>(&gs.mask[q])[mword];
           sl[r] = (mw >> shift) & 0xfu;
           if (sl[r]) {
-            ld4u(sv + (size_t)gs.row[q] * 128 + 4 * lane, x[r][0], x[r][1], x[r][2], x[r][3]);
+            const uint32_t rr = gs.row[q];
+            const uint64_t* p = sv + (size_t)(rr & 0x7fffffffu) * 128 + 4 * lane;
+            if (rr >> 31) ld4u_keep(p, x[r][0], x[r][1], x[r][2], x[r][3]);
+            else ld4u(p, x[r][0], x[r][1], x[r][2], x[r][3]);
             if (COUNT) nvals += __popc(sl[r]);
           }
         }
@@ -1040,16 +1057,19 @@ static mfbc_status level_round(RunCtx& rc, LevelState& s, bool fwd, int l, int64
   MFBC_CUDA_TRY(cudaMemsetAsync(s.ctr->work, 0, sizeof(uint32_t) * 4, st), rc.err);
   MFBC_CUDA_TRY(cudaMemsetAsync(&s.ctr->list_count[2], 0, sizeof(uint32_t), st), rc.err);
   const unsigned pgrid = grid_for_items(ie - ib, PAIR_GRID);
+  // row indices u * Q + quad need bit 31 free for the hot-row flag
+  const int Qn = std::max(1, W / 4);
+  const uint32_t* hot = MFBC_HOT_HINT && (uint64_t)n * (uint64_t)Qn < (1ull << 31) ? g.hot : nullptr;
   if (fwd)
     PROF(K_LVL_FWD, (k_lvl_fwd_pairs<<<pgrid, LVL_WARPS * 32, LVL_SMEM, st>>>(
                         ib, ie, g.items_in.v, g.items_in.beg, g.col_t, W, s.full, s.V, Fl, Ml, Fn, Mn,
                         s.lists + off_n, &s.ctr->list_count[0], s.list_cap - off_n, &s.ctr->flags,
-                        &s.ctr->list_count[2], s.prow, s.pmask, s.segs, s.ctr->work, s.pair_cap, s.seg_cap,
+                        &s.ctr->list_count[2], s.prow, s.pmask, s.segs, s.ctr->work, s.pair_cap, s.seg_cap, hot,
                         B ? B + K_LVL_FWD : nullptr, s.ctr->stat)));
   else
     PROF(K_LVL_BWD, (k_lvl_bwd_pairs<<<pgrid, LVL_WARPS * 32, LVL_SMEM, st>>>(
                         ib, ie, g.items_out.v, g.items_out.beg, g.col, W, Fl, Ml, Fn, Mn,
-                        &s.ctr->list_count[2], s.prow, s.pmask, s.segs, s.ctr->work, s.pair_cap, s.seg_cap,
+                        &s.ctr->list_count[2], s.prow, s.pmask, s.segs, s.ctr->work, s.pair_cap, s.seg_cap, hot,
                         B ? B + K_LVL_BWD : nullptr, s.ctr->stat)));
   MFBC_CUDA_TRY(cudaMemcpyAsync(rc.h_ctr, s.ctr->list_count, sizeof(uint32_t) * 9, cudaMemcpyDeviceToHost, st), rc.err);
   MFBC_CUDA_TRY(cudaStreamSynchronize(st), rc.err);

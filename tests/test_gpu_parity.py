@@ -420,3 +420,22 @@ def test_autotune_picks_a_candidate_and_results_are_unchanged(weighted):
         assert prof["n_b"] <= t["n_b"]
     assert_lambda_close(lam, oracle.bc(g, srcs))
     G.close()
+
+
+def test_release_scratch_frees_the_cached_workspace():
+    # mfbc_graph_release_scratch gives the handle's cached scratch back; the
+    # next call allocates it again and computes the same result
+    import torch
+    g = gg.rmat(14, 8, seed=12)
+    srcs = gg.sample_sources(g, 512, seed=3)
+    G = mfbc.Graph.from_csr(g)
+    a = G.bc(srcs, n_b=512, path=mfbc.PATH_LEVEL)
+    torch.cuda.synchronize()
+    held = torch.cuda.mem_get_info()[0]
+    G.release_scratch()
+    freed = torch.cuda.mem_get_info()[0] - held
+    assert freed >= G.workspace_size(512, 0, n_b=512, path=mfbc.PATH_LEVEL) // 2
+    G.release_scratch()                           # nothing cached: a no-op
+    assert_lambda_close(G.bc(srcs, n_b=512, path=mfbc.PATH_LEVEL), a, rtol=1e-12)
+    assert_lambda_close(a, oracle.bc(g, srcs))
+    G.close()
