@@ -79,7 +79,8 @@ typedef enum {
 #define MFBC_PATH_GENERAL 1    /* force the general (any integer weight) kernels */
 #define MFBC_PATH_LEVEL   2    /* require the unit-weight level kernels (INVALID if weighted) */
 #define MFBC_PATH_DIST    3    /* distance-ordered kernels for small integer weights
-                                  (INVALID when the largest weight exceeds 4096) */
+                                  (INVALID when the largest weight exceeds 4096); n_b is at
+                                  most 4096 and n * n_b stays below 2^32 */
 #define MFBC_PATH_SMALL   4    /* persistent kernel for small unit-weight graphs: every batch
                                   of the call in one launch (INVALID if weighted or when
                                   n * n_b * 9 bytes per group does not fit; see below) */

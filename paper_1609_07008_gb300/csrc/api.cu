@@ -300,7 +300,14 @@ static mfbc_status make_plan(const mfbc_graph* G, int32_t nsrc, int mode, const 
   else if (path != MFBC_PATH_GENERAL && path != MFBC_PATH_LEVEL && path != MFBC_PATH_DIST &&
            path != MFBC_PATH_SMALL)
     return fail(MFBC_ERR_INVALID, "unknown path");
-  const int maxnb = path == MFBC_PATH_LEVEL ? LEVEL_MAX_NB : (path == MFBC_PATH_SMALL ? 1024 : 4096);
+  int maxnb = path == MFBC_PATH_LEVEL ? LEVEL_MAX_NB : (path == MFBC_PATH_SMALL ? 1024 : 4096);
+  if (path == MFBC_PATH_DIST) {
+    // the distance kernels' settled list holds up to n * n_b (vertex, word)
+    // entries addressed by 32-bit offsets: n * n_b must stay below 2^32
+    const int64_t cap = ((int64_t)0xfffffffe / std::max<int64_t>(g.n, 1)) / 32 * 32;
+    maxnb = (int)std::min<int64_t>(maxnb, cap);
+    if (maxnb < 32) return fail(MFBC_ERR_INVALID, "MFBC_PATH_DIST needs n < 2^27");
+  }
   // the level kernels move 128 columns (four 32-column words) at a time
   const int gran = path == MFBC_PATH_LEVEL ? 128 : 32;
   int req = opt ? opt->n_b : 0;

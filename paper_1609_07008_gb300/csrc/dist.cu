@@ -46,7 +46,9 @@ void dist_carve(Carver& c, int32_t n, int nb, int B, DistState& s) {
   s.dist = c.take<int32_t>(cells);
   s.sig = c.take<double>(cells);
   s.val = c.take<double>(cells);
-  s.mcap = cells + 1;                        // a (vertex, word) settles at most once per column
+  // a (vertex, word) settles at most once per column; offsets into this list
+  // are 32-bit, so the planner keeps n * n_b below 2^32
+  s.mcap = cells + 1;
   s.mlist = c.take<uint32_t>(s.mcap);
   s.bcap = (size_t)n * s.W;                  // (vertex, word) items a bucket can hold
   s.blist = c.take<uint32_t>((size_t)B * s.bcap);

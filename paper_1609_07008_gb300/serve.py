@@ -171,10 +171,16 @@ class Server:
         """The worker's n_b and bytes: n_b (or the graph's max_cols), lowered
         in steps of 128 while one worker would not fit the budget."""
         nb = self.n_b or self.max_cols[key]
-        need = self.sizer(key, nb, max(1, nb // 32))
-        while need > self.budget and nb > 128:
+        while True:
+            try:
+                need = self.sizer(key, nb, max(1, nb // 32))
+            except ValueError:                  # wider than the library takes for this graph
+                need = None
+            if (need is not None and need <= self.budget) or nb <= 128:
+                break
             nb = max(128, nb - 128)
-            need = self.sizer(key, nb, max(1, nb // 32))
+        if need is None:
+            raise ValueError(f"no batch width fits graph {key}")
         return nb, need
 
     def _fill(self, w: _Worker):
@@ -317,8 +323,14 @@ class Server:
         return w.pool[slot].copy()
 
     def _worker_bytes(self, key, nb, slots):
+        from . import MFBCError, MFBC_ERR_INVALID
         G = self.graphs[key]
-        return G.workspace_size(nb, 2, n_b=nb) + 8 * slots * G.n
+        try:
+            return G.workspace_size(nb, 2, n_b=nb) + 8 * slots * G.n
+        except MFBCError as e:
+            if e.status == MFBC_ERR_INVALID:
+                raise ValueError(str(e)) from e
+            raise
 
     def _execute_gpu(self, w: _Worker, parts, rows):
         """One batch: every part's lambda added into its request's pool row."""

@@ -138,3 +138,21 @@ def test_large_path_counts_unweighted_grid_corners(L, path):
         assert np.array_equal(s[0][small], exact[small])
         assert np.max(np.abs(s[0] - exact) / exact) <= 1e-12
     G.close()
+
+
+def test_dist_kernels_width_cap_at_a_million_vertices():
+    # the distance kernels address their settled list (up to n * n_b
+    # entries) with 32-bit offsets, so the planner keeps n * n_b < 2^32: on
+    # the weighted 1024^2 grid (n = 2^20) n_b is at most 4064.  The widest
+    # batch must give the lambda of four 1024-column batches.
+    g = gg.grid2d(1024, weights=(1, 16), seed=1)
+    srcs = gg.sample_sources(g, 4064, seed=2)
+    G = mfbc.Graph.from_csr(g)
+    with pytest.raises(mfbc.MFBCError) as e:
+        G.bc(srcs[:64], n_b=4096, path=mfbc.PATH_DIST)
+    assert e.value.status == mfbc.MFBC_ERR_INVALID and "4064" in str(e.value)
+    wide, prof = G.bc(srcs, path=mfbc.PATH_DIST, profile=True)
+    assert prof["n_b"] == 4064 and prof["batches"] == 1
+    narrow = G.bc(srcs, n_b=1024, path=mfbc.PATH_DIST)
+    assert_lambda_close(wide, narrow, rtol=1e-12)
+    G.close()
