@@ -312,6 +312,11 @@ static mfbc_status make_plan(const mfbc_graph* G, int32_t nsrc, int mode, const 
   const int gran = path == MFBC_PATH_LEVEL ? 128 : 32;
   int req = opt ? opt->n_b : 0;
   if (req < 0) return fail(MFBC_ERR_INVALID, "n_b must be >= 0");
+  if (path == MFBC_PATH_LEVEL && (int64_t)g.n * (LEVEL_MAX_NB / 128) >= (1ll << 31))
+    // pair records name a row as vertex * (n_b / 128) + quad in 31 bits
+    maxnb = (int)std::max<int64_t>(128, (((1ll << 31) - 1) / std::max<int64_t>(g.n, 1)) * 128);
+  if (path == MFBC_PATH_LEVEL && (int64_t)g.n * (maxnb / 128) >= (1ll << 31))
+    return fail(MFBC_ERR_INVALID, "graph too large for the level kernels' 31-bit pair row indices");
   if (req > 0) {
     int nb = (req + gran - 1) / gran * gran;
     if (nb > maxnb) return fail(MFBC_ERR_INVALID, "n_b too large for this path (max " + std::to_string(maxnb) + ")");
