@@ -96,7 +96,7 @@ def make_workload(name, rank=0):
 # records the SHA-1 of the kernel source it was taken on; once that source changes
 # the figure is reported as null.
 TRAFFIC = {
-    ("rmat22", "level_mfbr_gather"): {"per_alg_byte": 62.877 / 39.2486, "sha1": "80479d3112e4d278524903ef97c4d90a0e2674fd",
+    ("rmat22", "level_mfbr_gather"): {"per_alg_byte": 61.801 / 39.2486, "sha1": "9b2940b02a5b6a99df078d159de504b587f1668b",
                                       "source": "paper_1609_07008_gb300/csrc/level.cu"},
 }
 
@@ -422,6 +422,8 @@ def roofline_of(kstats, prof_bytes, peak, peak_kind, workload, step_s):
     roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
             "peak_kind": f"{peak_kind} copy bandwidth", "unit": "GB/s", "frac": achieved / peak,
             "traffic": traffic.get(dom), "bytes_per_launch": per_launch_bytes, "avg_launch_ms": avg_ms,
+            "kernel_bytes_per_launch": {k: v.get("bytes", 0.0) / max(v.get("launches", 1), 1)
+                                        for k, v in prof_bytes["kernels"].items() if v.get("bytes")},
             "whole_step": {"bytes": step_bytes, "achieved": step_bytes / step_s / 1e9,
                            "frac": step_bytes / step_s / 1e9 / peak}}
     if len(traffic) > 1 or (traffic and dom not in traffic):
