@@ -243,7 +243,12 @@ class Server:
                     if self._has_work(w):
                         if w.active:
                             break
-                        nb, need = self._width(w.key)
+                        try:
+                            nb, need = self._width(w.key)
+                        except BaseException as e:     # surface to drain()
+                            self.errors.append(e)
+                            self._cv.notify_all()
+                            return
                         # admission: start when the active workers leave room
                         if not self._held or self._held + need <= self.budget:
                             w.active, w.nb, w.need = True, nb, need

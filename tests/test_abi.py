@@ -87,6 +87,7 @@ def test_host_side_argument_checks(lib):
     st, h = _create(lib, 3, [0, 2, 1, 3], [1, 2, 0], flags=csc)
     assert st == mfbc.MFBC_ERR_INVALID and b"rowptr" in lib.mfbc_last_error()
     assert lib.mfbc_bc(None, None, 0, None, None) == mfbc.MFBC_ERR_INVALID
+    assert lib.mfbc_graph_release_scratch(None) == mfbc.MFBC_ERR_INVALID
     assert lib.mfbc_sssp_batch(None, None, 0, None, None, None) == mfbc.MFBC_ERR_INVALID
     out = ctypes.c_uint64()
     assert lib.mfbc_workspace_size(None, 1, 0, None, ctypes.byref(out)) == mfbc.MFBC_ERR_INVALID

@@ -183,3 +183,16 @@ def test_request_arriving_during_a_batch_joins_the_next_one():
     assert small.done < big.done
     for r in (big, small):
         np.testing.assert_allclose(r.result, oracle.bc(graphs["a"], r.sources), rtol=1e-12, atol=0)
+
+
+def test_a_graph_no_width_fits_is_reported():
+    graphs = _graphs()
+
+    def sizer(k, nb, slots):
+        raise ValueError("wider than the library takes")
+
+    srv = Server(graphs, budget_bytes=1 << 30, executor=lambda *a: None, sizer=sizer)
+    srv.start()
+    with pytest.raises(ValueError, match="no batch width fits"):
+        run_served(srv, [Request(0, "a", np.arange(3, dtype=np.int32), 0.0)], timeout=30)
+    srv.close()
