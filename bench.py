@@ -98,6 +98,8 @@ def make_workload(name, rank=0):
 TRAFFIC = {
     ("rmat22", "level_mfbr_gather"): {"per_alg_byte": 61.801 / 39.2486, "sha1": "9b2940b02a5b6a99df078d159de504b587f1668b",
                                       "source": "paper_1609_07008_gb300/csrc/level.cu"},
+    ("rmat22", "level_mfbf_gather"): {"per_alg_byte": 29.031 / 28.392, "sha1": "9b2940b02a5b6a99df078d159de504b587f1668b",
+                                      "source": "paper_1609_07008_gb300/csrc/level.cu"},
 }
 
 
