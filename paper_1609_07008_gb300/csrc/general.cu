@@ -654,94 +654,30 @@ __device__ __forceinline__ void pull_finish(const PullArgs& a, int32_t v, int wo
   }
 }
 
-// Reduce this lane's column j over the frontier neighbours listed in shared
-// memory (mu: ids, mw: arc weights; nm of them).
-template <bool FWD>
-__device__ __forceinline__ void pull_members(const PullArgs& a, const int32_t* mu, const int32_t* mw, int nm, int word,
-                                             int j, bool act, int32_t dv, PullAcc<FWD>& acc,
-                                             unsigned long long& nbytes) {
-  const unsigned lane = threadIdx.x & 31u;
-  for (int q0 = 0; q0 < nm; q0 += 4) {             // four frontier neighbours in flight
-    int32_t u[4], w[4];
-    uint32_t fw[4];
-#pragma unroll
-    for (int r = 0; r < 4; r++) {
-      const bool in = q0 + r < nm;
-      u[r] = in ? mu[q0 + r] : 0;
-      w[r] = in ? mw[q0 + r] : 0;
-      fw[r] = in ? __ldg(&a.fmask[(size_t)u[r] * a.W + word]) : 0u;
-    }
-    int32_t d[4];
-    bool on[4];
-#pragma unroll
-    for (int r = 0; r < 4; r++) {
-      on[r] = act && ((fw[r] >> lane) & 1u);
-      d[r] = on[r] ? __ldg(&a.dist[(size_t)u[r] * a.nb + j]) : 0;
-    }
-    double x[4];
-#pragma unroll
-    for (int r = 0; r < 4; r++) {
-      if (!FWD) on[r] = on[r] && d[r] == dv + w[r];      // arc v -> u on a shortest path
-      x[r] = on[r] ? __ldg(&a.fval[(size_t)u[r] * a.nb + j]) : 0.0;
-    }
-#pragma unroll
-    for (int r = 0; r < 4; r++) {
-      if (on[r]) {
-        if constexpr (FWD) acc.add(d[r] + w[r], x[r]);
-        else { acc.sum += x[r]; acc.hits++; }
-      }
-      if (a.bytes && q0 + r < nm) nbytes += 4ull * (lane == 0) + 12ull * on[r];
-    }
-  }
-}
-
-// One warp per vertex for rows of at most PULL_ROW_MAX arcs: the row is
-// scanned once, its frontier neighbours (one membership bit each) are listed
-// in shared memory, and every 32-column word is reduced over that list.
+// One warp per (vertex, word) for rows of at most PULL_ROW_MAX arcs.
 template <bool FWD>
 __global__ void __launch_bounds__(256) k_gp_pull_rows(PullArgs a) {
   __shared__ int32_t qbuf[8][40];
-  __shared__ int32_t mem_u[8][PULL_ROW_MAX], mem_w[8][PULL_ROW_MAX];
-  const int wid = (int)(threadIdx.x >> 5);
-  int32_t* q = qbuf[wid];
-  int32_t* mu = mem_u[wid];
-  int32_t* mw = mem_w[wid];
+  int32_t* q = qbuf[threadIdx.x >> 5];
   int qn = 0;
   const unsigned lane = threadIdx.x & 31u;
+  const uint64_t tasks = (uint64_t)a.n * a.W;
   const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
   unsigned long long nbytes = 0;
-  for (uint64_t t = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < (uint64_t)a.n; t += nw) {
-    const int32_t v = (int32_t)t;
+  for (uint64_t t = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < tasks; t += nw) {
+    const int32_t v = (int32_t)(t / a.W);
+    const int word = (int)(t % a.W);
     const int64_t k0 = __ldg(&a.rowptr[v]), k1 = __ldg(&a.rowptr[v + 1]);
     bool mine = false;
     if (k1 > k0 && k1 - k0 <= PULL_ROW_MAX) {
-      int nm = 0;
-      for (int64_t c0 = k0; c0 < k1; c0 += 32) {
-        const int64_t k = c0 + lane;
-        const int32_t u = k < k1 ? __ldg(&a.col[k]) : -1;
-        const bool m = u >= 0 && ((__ldg(&a.fmem[u >> 5]) >> (u & 31)) & 1u);
-        const uint32_t mm = __ballot_sync(0xffffffffu, m);
-        if (m) {
-          const int at = nm + __popc(mm & ((1u << lane) - 1u));
-          mu[at] = u;
-          mw[at] = a.wt ? __ldg(&a.wt[k]) : 1;
-        }
-        nm += __popc(mm);
+      const int j = word * 32 + (int)lane;
+      const int32_t dv = __ldg(&a.dist[(size_t)v * a.nb + j]);
+      const bool act = FWD ? true : (dv != INF && a.cw[(size_t)v * a.nb + j] > 0);
+      if (__any_sync(0xffffffffu, act)) {
+        PullAcc<FWD> acc;
+        pull_span<FWD>(a, k0, k1, word, j, act, dv, acc, nbytes);
+        pull_finish<FWD>(a, v, word, j, dv, acc, mine, nbytes);
       }
-      if (a.bytes && lane == 0) nbytes += 8ull * (uint64_t)(k1 - k0);
-      __syncwarp();
-      if (nm) {
-        for (int word = 0; word < a.W; word++) {
-          const int j = word * 32 + (int)lane;
-          const int32_t dv = __ldg(&a.dist[(size_t)v * a.nb + j]);
-          const bool act = FWD ? true : (dv != INF && a.cw[(size_t)v * a.nb + j] > 0);
-          if (!__any_sync(0xffffffffu, act)) continue;
-          PullAcc<FWD> acc;
-          pull_members<FWD>(a, mu, mw, nm, word, j, act, dv, acc, nbytes);
-          pull_finish<FWD>(a, v, word, j, dv, acc, mine, nbytes);
-        }
-      }
-      __syncwarp();                              // the list is consumed before the next vertex
     }
     wl_push(q, qn, mine, v, a.tlist, a.tcount);
   }
@@ -889,7 +825,7 @@ mfbc_status general_batch(RunCtx& rc, GeneralState& s, const int32_t* d_src_batc
                         s.tmask, s.vflag, nxt, &s.ctr->list_count[1], g.items_in.hubs, g.items_in.nhub,
                         B ? B + K_PULL_FWD : nullptr};
       PROF(K_PULL_FWD, {
-        k_gp_pull_rows<true><<<stride_blocks((uint64_t)n), 256, 0, st>>>(pa);
+        k_gp_pull_rows<true><<<stride_blocks((uint64_t)n * W), 256, 0, st>>>(pa);
         if (g.items_in.nhub) k_gp_pull_hubs<true><<<hub_blocks(g.items_in.nhub, W), 256, 0, st>>>(pa);
       });
     } else {
@@ -935,7 +871,7 @@ mfbc_status general_batch(RunCtx& rc, GeneralState& s, const int32_t* d_src_batc
                         s.tmask, s.vflag, nxt, &s.ctr->list_count[1], g.items_out.hubs, g.items_out.nhub,
                         B ? B + K_PULL_BWD : nullptr};
       PROF(K_PULL_BWD, {
-        k_gp_pull_rows<false><<<stride_blocks((uint64_t)n), 256, 0, st>>>(pb);
+        k_gp_pull_rows<false><<<stride_blocks((uint64_t)n * W), 256, 0, st>>>(pb);
         if (g.items_out.nhub) k_gp_pull_hubs<false><<<hub_blocks(g.items_out.nhub, W), 256, 0, st>>>(pb);
       });
     } else {
