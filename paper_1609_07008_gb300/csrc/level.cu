@@ -140,9 +140,9 @@ __global__ void k_lvl_colmask(const int32_t* __restrict__ src, int W, uint32_t* 
 
 // visited |= F_l for the vertices of level l; mark vertices reached by every
 // column that holds a source (colmask).
-__global__ void k_lvl_visit(const int32_t* __restrict__ list, uint32_t count, int W,
-                            const uint32_t* __restrict__ colmask, const uint32_t* __restrict__ Fl, uint32_t* V,
-                            uint32_t* full) {
+__device__ __forceinline__ void visit_rows(const int32_t* __restrict__ list, uint32_t count, int W,
+                                           const uint32_t* __restrict__ colmask, const uint32_t* __restrict__ Fl,
+                                           uint32_t* V, uint32_t* full) {
   const unsigned lane = lane_id();
   const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
   for (uint64_t i = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < count; i += nw) {
@@ -158,6 +158,24 @@ __global__ void k_lvl_visit(const int32_t* __restrict__ list, uint32_t count, in
     if (__all_sync(0xffffffffu, ok) && lane == 0) atomicOr(&full[v >> 5], 1u << (v & 31));
   }
 }
+__global__ void k_lvl_visit(const int32_t* __restrict__ list, uint32_t count, int W,
+                            const uint32_t* __restrict__ colmask, const uint32_t* __restrict__ Fl, uint32_t* V,
+                            uint32_t* full) {
+  visit_rows(list, count, W, colmask, Fl, V, full);
+}
+
+// The visit of the next level, run by the MFBF gather of the current one
+// after its segments (the gather neither reads V nor full, and the next pair
+// kernel starts after it), which saves a launch per level.
+struct VisitNext {
+  const int32_t* list;       // the next level's vertices
+  uint32_t count;            // 0: no visit here
+  int W;
+  const uint32_t* colmask;
+  const uint32_t* Fn;        // the next level's frontier rows
+  uint32_t* V;
+  uint32_t* full;
+};
 
 // Per-warp shared memory of the pair kernels.
 struct WarpSmem {
@@ -709,7 +727,7 @@ template <bool COUNT>
 __global__ void __launch_bounds__(256, MFBC_GATHER_MIN_BLOCKS) k_lvl_fwd_gather(
     const uint4* __restrict__ segs, const uint32_t* nseg_p, const uint32_t* __restrict__ prow,
     const uint4* __restrict__ pmask, int nb, double* svd, uint32_t* flags, uint32_t* next_group,
-    unsigned long long* bytes, unsigned long long* stat) {
+    unsigned long long* bytes, unsigned long long* stat, VisitNext vn) {
   __shared__ GatherSmem gsm[8];
   GatherSmem& gs = gsm[threadIdx.x >> 5];
   uint64_t* sv = reinterpret_cast<uint64_t*>(svd);
@@ -755,6 +773,7 @@ __global__ void __launch_bounds__(256, MFBC_GATHER_MIN_BLOCKS) k_lvl_fwd_gather(
   }
   if (__any_sync(0xffffffffu, big != 0u) && lane == 0) atomicOr(flags, FLAG_SIGMA_INEXACT);
   if (__any_sync(0xffffffffu, ovf != 0u) && lane == 0) atomicOr(flags, FLAG_COUNT_WRAP);
+  if (vn.count) visit_rows(vn.list, vn.count, vn.W, vn.colmask, vn.Fn, vn.V, vn.full);
   if (COUNT) {
     for (int o = 16; o; o >>= 1) {
       nvals += __shfl_xor_sync(0xffffffffu, nvals, o);
@@ -1044,7 +1063,8 @@ static const unsigned kBwdGatherGrid = 152u * MFBC_BWD_GATHER_MIN_BLOCKS;
 // effects (frontier bits, membership, list appends) are idempotent, so a
 // re-run of a range is harmless.
 static mfbc_status level_round(RunCtx& rc, LevelState& s, bool fwd, int l, int64_t ib, int64_t ie,
-                               int uniform_req, int64_t off_n, double* lambda) {
+                               int uniform_req, int64_t off_n, double* lambda, bool* visited_next = nullptr) {
+  if (visited_next) *visited_next = false;
   const DevGraph& g = *rc.g;
   const int32_t n = g.n;
   const int nb = s.nb, W = s.W;
@@ -1087,17 +1107,25 @@ static mfbc_status level_round(RunCtx& rc, LevelState& s, bool fwd, int l, int64
   }
   const uint32_t nseg = rc.h_ctr[6];
   if (!nseg) return MFBC_OK;
+  // the next level's visit rides on this gather when its list is complete
+  // (one round, no list overflow; the count is clamped to the list's room)
+  VisitNext vn{s.lists + off_n, 0u, W, s.colmask, Fn, s.V, s.full};
+  if (fwd && visited_next && !(rc.h_ctr[4] & FLAG_LEVEL_LIST)) {
+    vn.count = (uint32_t)std::min<int64_t>(rc.h_ctr[0], s.list_cap - off_n);
+    *visited_next = true;
+    rc.prof->k[K_LVL_FWD_G].bytes += 12.0 * W * vn.count;
+  }
   MFBC_CUDA_TRY(cudaMemsetAsync(&s.ctr->work[2], 0, sizeof(uint32_t), st), rc.err);
   const unsigned ggrid = grid_for_items(nseg, fwd ? kGatherGrid : kBwdGatherGrid);
   if (fwd) {
     if (B)
       PROF(K_LVL_FWD_G, (k_lvl_fwd_gather<true><<<ggrid, 256, 0, st>>>(
                             s.segs, &s.ctr->work[1], s.prow, s.pmask, nb, s.sv, &s.ctr->flags, &s.ctr->work[2],
-                            B + K_LVL_FWD_G, s.ctr->stat)));
+                            B + K_LVL_FWD_G, s.ctr->stat, vn)));
     else
       PROF(K_LVL_FWD_G, (k_lvl_fwd_gather<false><<<ggrid, 256, 0, st>>>(
                             s.segs, &s.ctr->work[1], s.prow, s.pmask, nb, s.sv, &s.ctr->flags, &s.ctr->work[2],
-                            nullptr, s.ctr->stat)));
+                            nullptr, s.ctr->stat, vn)));
   } else {
     if (B)
       PROF(K_LVL_BWD_G, (k_lvl_bwd_gather<true><<<ggrid, 256, 0, st>>>(
@@ -1165,15 +1193,18 @@ mfbc_status level_batch(RunCtx& rc, LevelState& s, const int32_t* d_src_batch, i
   auto Ml = [&](int l) { return s.member + (size_t)l * s.mw; };
 
   int L = 0;
+  bool visited = false;                  // level l's visit ran inside the previous gather
   for (int l = 0;; l++) {
     const uint32_t cl = P.cnt[l];
-    PROF(K_LVL_VISIT, (k_lvl_visit<<<grid_for_warps(cl, 152 * 16), LVL_WARPS * 32, 0, st>>>(
-                          s.lists + P.off[l], cl, W, s.colmask, Fl(l), s.V, s.full)));
-    rc.prof->k[K_LVL_VISIT].bytes += 12.0 * W * cl;
+    if (!visited) {
+      PROF(K_LVL_VISIT, (k_lvl_visit<<<grid_for_warps(cl, 152 * 16), LVL_WARPS * 32, 0, st>>>(
+                            s.lists + P.off[l], cl, W, s.colmask, Fl(l), s.V, s.full)));
+      rc.prof->k[K_LVL_VISIT].bytes += 12.0 * W * cl;
+    }
     if (l + 1 >= s.Lcap) { *levels_exceeded = true; level_reset(rc, s, l); return MFBC_ERR_NO_CONVERGENCE; }
     const int64_t off_n = P.off[l] + cl;
     MFBC_CUDA_TRY(cudaMemsetAsync(&s.ctr->list_count[0], 0, sizeof(uint32_t), st), rc.err);
-    mfbc_status e = level_round(rc, s, true, l, 0, g.items_in.count, uniform_req, off_n, nullptr);
+    mfbc_status e = level_round(rc, s, true, l, 0, g.items_in.count, uniform_req, off_n, nullptr, &visited);
     if (e) return e;
     MFBC_CUDA_TRY(cudaMemcpyAsync(rc.h_ctr, s.ctr->list_count, sizeof(uint32_t) * 5, cudaMemcpyDeviceToHost, st), rc.err);
     MFBC_CUDA_TRY(cudaStreamSynchronize(st), rc.err);
