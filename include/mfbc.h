@@ -141,6 +141,10 @@ typedef struct {
                                     form one segment -- the vertex's arcs to the frontier -- and
                                     are reduced in registers by the warp that owns it (a block
                                     for rows of more than 256 arcs); no same-address atomics */
+#define MFBC_ACCUM_HASH      3   /* push, reduced first in shared memory: a block's candidates for
+                                    a high-degree target meet in one slot of the block's hash
+                                    table (key = target vertex and word), and each slot column
+                                    is merged into the batch state with one atomic per block */
 
 /* mfbc_options.flags */
 #define MFBC_OPT_COUNT_BYTES 1u  /* with profile: count algorithmic bytes on the device (slower) */
@@ -260,7 +264,8 @@ typedef struct {
  * it up to 2^13 vertices and 2^18 arcs);
  * n_b in {128, 256, 512, 1024, 2048, 4096} on the general kernels (x the
  * atomic accumulator walking 1 or 8 arcs per step, the segmented accumulator,
- * and the per-product choice) and on the distance kernels; each at most nsrc
+ * the hash accumulator and the per-product choice) and on the distance
+ * kernels; each at most nsrc
  * rounded up;
  * widths that do not fit the device are skipped.  With opt->path == AUTO a
  * weighted graph tries both the general and (weights <= 4096) the distance

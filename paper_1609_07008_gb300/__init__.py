@@ -38,7 +38,7 @@ MFBC_OPT_COUNT_BYTES = 1
 MFBC_OPT_KEEP_ORDER = 2
 MFBC_OPT_TEST_STALL = 4
 MFBC_OPT_ACCUMULATE = 8
-ACCUM_AUTO, ACCUM_ATOMIC, ACCUM_SEGMENTED = 0, 1, 2
+ACCUM_AUTO, ACCUM_ATOMIC, ACCUM_SEGMENTED, ACCUM_HASH = 0, 1, 2, 3
 INF = np.iinfo(np.int32).max
 MAX_KSTATS = 24
 

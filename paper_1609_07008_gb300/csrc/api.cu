@@ -906,7 +906,7 @@ mfbc_status entry(const mfbc_graph* Gc, const int32_t* sources, int32_t nsrc, in
     for (int32_t i = 0; i < nsrc; i++)
       if (sources[i] < 0 || sources[i] >= n) return fail(MFBC_ERR_INVALID, "source id out of range");
   }
-  if (opt && (opt->accumulator < MFBC_ACCUM_AUTO || opt->accumulator > MFBC_ACCUM_SEGMENTED))
+  if (opt && (opt->accumulator < MFBC_ACCUM_AUTO || opt->accumulator > MFBC_ACCUM_HASH))
     return fail(MFBC_ERR_INVALID, "unknown accumulator");
   if (opt && opt->warn_out) *opt->warn_out = 0;
   t_err.clear();
@@ -1037,10 +1037,12 @@ extern "C" mfbc_status mfbc_autotune(mfbc_graph* G, const int32_t* sources, int3
     const int cols = (nsrc + gran - 1) / gran * gran;
     while (widths.size() > 1 && widths.back() > cols) widths.pop_back();
     // general kernels: atomic products walking 1 or 8 arcs per step, the
-    // segmented products, and the per-product choice between them
+    // segmented products, the hash-combined products, and the per-product
+    // choice between atomic and segmented
     struct Var { int arcs, accum; };
     const std::vector<Var> vars = path == MFBC_PATH_GENERAL
-        ? std::vector<Var>{{1, MFBC_ACCUM_ATOMIC}, {8, MFBC_ACCUM_ATOMIC}, {0, MFBC_ACCUM_SEGMENTED}, {0, MFBC_ACCUM_AUTO}}
+        ? std::vector<Var>{{1, MFBC_ACCUM_ATOMIC}, {8, MFBC_ACCUM_ATOMIC}, {0, MFBC_ACCUM_SEGMENTED},
+                           {0, MFBC_ACCUM_HASH}, {0, MFBC_ACCUM_AUTO}}
         : std::vector<Var>{{0, MFBC_ACCUM_AUTO}};
     o.path = path;
     for (int nb : widths)

@@ -139,7 +139,7 @@ __global__ void __launch_bounds__(256, ARCS > 1 ? 4 : 8) k_gp_relax_min(
     const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col, const int32_t* __restrict__ wt,
     const int32_t* __restrict__ flist, uint32_t fcount, int W, int nb,
     const uint32_t* __restrict__ fmask, const int32_t* __restrict__ dist, int32_t* cw, uint32_t* tmask,
-    uint32_t* vflag, int32_t* tlist, uint32_t* tcount, unsigned long long* bytes) {
+    uint32_t* vflag, int32_t* tlist, uint32_t* tcount, unsigned long long* bytes, int64_t min_arcs) {
   __shared__ int32_t qbuf[8][40];
   int32_t* q = qbuf[threadIdx.x >> 5];
   uint64_t gw = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -151,8 +151,9 @@ __global__ void __launch_bounds__(256, ARCS > 1 ? 4 : 8) k_gp_relax_min(
   if (!m) return;
   const int j = word * 32 + lane;
   const bool active = (m >> lane) & 1u;
-  const int32_t du = active ? dist[(size_t)u * nb + j] : 0;
   const int64_t beg = rowptr[u], end = rowptr[u + 1];
+  if (end - beg < min_arcs) return;              // short rows: the hash kernels' share
+  const int32_t du = active ? dist[(size_t)u * nb + j] : 0;
   unsigned long long nb_bytes = 0;
   int qn = 0;
   for (int64_t k0 = beg; k0 < end; k0 += 32) {
@@ -210,7 +211,7 @@ __global__ void __launch_bounds__(256, ARCS > 1 ? 4 : 8) k_gp_relax_tie(
     const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col, const int32_t* __restrict__ wt,
     const int32_t* __restrict__ flist, uint32_t fcount, int W, int nb,
     const uint32_t* __restrict__ fmask, const int32_t* __restrict__ dist, const double* __restrict__ fm,
-    const int32_t* __restrict__ cw, double* cm, unsigned long long* bytes) {
+    const int32_t* __restrict__ cw, double* cm, unsigned long long* bytes, int64_t min_arcs) {
   uint64_t gw = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (gw >= (uint64_t)fcount * W) return;
   const unsigned lane = lane_id();
@@ -220,9 +221,10 @@ __global__ void __launch_bounds__(256, ARCS > 1 ? 4 : 8) k_gp_relax_tie(
   if (!m) return;
   const int j = word * 32 + lane;
   const bool active = (m >> lane) & 1u;
+  const int64_t beg = rowptr[u], end = rowptr[u + 1];
+  if (end - beg < min_arcs) return;
   const int32_t du = active ? dist[(size_t)u * nb + j] : 0;
   const double mu = active ? fm[(size_t)u * nb + j] : 0.0;
-  const int64_t beg = rowptr[u], end = rowptr[u + 1];
   unsigned long long nb_bytes = 0;
   for (int64_t k0 = beg; k0 < end; k0 += 32) {
     const int64_t k = k0 + lane;
@@ -377,7 +379,7 @@ __global__ void __launch_bounds__(256, ARCS > 1 ? 4 : 6) k_gp_propagate(
     const int32_t* __restrict__ wt_t, const int32_t* __restrict__ flist, uint32_t fcount, int W, int nb,
     const uint32_t* __restrict__ fmask, const int32_t* __restrict__ dist, const double* __restrict__ fv,
     double* zp, int32_t* cnt, uint32_t* tmask, uint32_t* vflag, int32_t* tlist, uint32_t* tcount,
-    unsigned long long* bytes) {
+    unsigned long long* bytes, int64_t min_arcs) {
   __shared__ int32_t qbuf[8][40];
   int32_t* q = qbuf[threadIdx.x >> 5];
   int qn = 0;
@@ -390,9 +392,10 @@ __global__ void __launch_bounds__(256, ARCS > 1 ? 4 : 6) k_gp_propagate(
   if (!m) return;
   const int j = word * 32 + lane;
   const bool active = (m >> lane) & 1u;
+  const int64_t beg = rowptr_t[u], end = rowptr_t[u + 1];
+  if (end - beg < min_arcs) return;
   const int32_t du = active ? dist[(size_t)u * nb + j] : 0;
   const double val = active ? fv[(size_t)u * nb + j] : 0.0;
-  const int64_t beg = rowptr_t[u], end = rowptr_t[u + 1];
   unsigned long long nb_bytes = 0;
   for (int64_t k0 = beg; k0 < end; k0 += 32) {
     const int64_t k = k0 + lane;
@@ -509,6 +512,427 @@ __global__ void __launch_bounds__(256) k_gp_lambda(int32_t n, int W, int nb, con
   }
   for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
   if (lane == 0 && cur >= 0) lambda[(size_t)cur * n + v] += acc;
+}
+
+// ---------------------------------------------------------- hash accumulator
+// The push products above, with the reduction at the targets done first in
+// shared memory.  A block takes 8 * HASH_ITEMS (frontier vertex, word) items,
+// ordered word-major, so its warps work on the same 32 columns of different
+// frontier vertices.  Candidates for a hot target (a vertex of high in-degree
+// for MFBF, out-degree for MFBr: where many frontier vertices meet) go to the
+// slot of the key (target, word) in the block's open-addressing table
+// (HASH_PROBES linear probes); each lane reduces its own column there with
+// shared-memory atomics.  Once the block's arcs are walked, every occupied
+// slot is merged into the batch state with one global operation per column,
+// so the global atomics at a hub column fall from one per arc to one per
+// block.  Other targets, and keys that find no free slot, take the atomic
+// path unchanged.  The reductions are the monoid's own (minimum; sums of
+// integer multiplicities, exact in FP64 in any order; sums of MFBr values,
+// whose order only rounds), so the results are those of the atomic path.
+constexpr int HASH_SLOTS = 128;      // keys per block (a power of two)
+constexpr int HASH_PROBES = 8;
+constexpr int HASH_ITEMS = 4;        // (frontier vertex, word) items per warp
+constexpr int HASH_ROW_MAX = 128;    // longer frontier rows go to the atomic kernels: a block
+                                     // waits at its barrier for its longest row
+constexpr unsigned long long HASH_EMPTY = ~0ull;
+
+struct HashSmem {
+  unsigned long long key[HASH_SLOTS];  // (vertex * W + word) or HASH_EMPTY
+  int32_t mn[HASH_SLOTS][32];          // MFBF: the block's minimum candidate; MFBr: its tight-arc count
+  double sum[HASH_SLOTS][32];          // MFBF ties: multiplicity sum (as uint64); MFBr: value sum
+  uint32_t take[HASH_SLOTS];           // MFBF ties: columns whose block minimum is the product's
+  int32_t q[8][40];                    // per-warp list append buffers
+};
+
+__device__ __forceinline__ bool hot_bit(const uint32_t* __restrict__ bits, int32_t v) {
+  return (__ldg(&bits[v >> 5]) >> (v & 31)) & 1u;
+}
+__device__ __forceinline__ uint32_t hash_home(unsigned long long key) {
+  return (uint32_t)((key * 0x9E3779B97F4A7C15ull) >> 57) & (HASH_SLOTS - 1);   // Fibonacci hashing, 7 bits
+}
+// slot of key, inserting it when absent; -1 when its probes find no room
+__device__ __forceinline__ int hash_insert(unsigned long long* keys, unsigned long long key) {
+  const uint32_t h = hash_home(key);
+  for (int p = 0; p < HASH_PROBES; p++) {
+    const int s = (int)((h + (uint32_t)p) & (HASH_SLOTS - 1));
+    unsigned long long k = *((volatile unsigned long long*)&keys[s]);
+    if (k == HASH_EMPTY) k = atomicCAS(&keys[s], HASH_EMPTY, key);
+    if (k == HASH_EMPTY || k == key) return s;
+  }
+  return -1;
+}
+// slot of key in a table no longer written; -1 when absent
+__device__ __forceinline__ int hash_find(const unsigned long long* keys, unsigned long long key) {
+  const uint32_t h = hash_home(key);
+  for (int p = 0; p < HASH_PROBES; p++) {
+    const int s = (int)((h + (uint32_t)p) & (HASH_SLOTS - 1));
+    const unsigned long long k = keys[s];
+    if (k == key) return s;
+    if (k == HASH_EMPTY) return -1;
+  }
+  return -1;
+}
+
+__device__ __forceinline__ void hash_clear(HashSmem& hs, int32_t mn0) {
+  for (int i = threadIdx.x; i < HASH_SLOTS; i += blockDim.x) {
+    hs.key[i] = HASH_EMPTY;
+    hs.take[i] = 0u;
+  }
+  for (int i = threadIdx.x; i < HASH_SLOTS * 32; i += blockDim.x) {
+    (&hs.mn[0][0])[i] = mn0;
+    (&hs.sum[0][0])[i] = 0.0;
+  }
+}
+
+// The item of warp `warp`, step `it` of this block: word-major order.
+__device__ __forceinline__ bool hash_item(uint32_t fcount, int W, int it, uint64_t* i_out) {
+  const uint64_t i = ((uint64_t)blockIdx.x * HASH_ITEMS + (uint64_t)it) * 8 + (threadIdx.x >> 5);
+  *i_out = i;
+  return i < (uint64_t)fcount * W;
+}
+
+// Slots of the arcs t0 .. t0+ARCS-1 of the current 32-arc chunk (lane t holds
+// arc t): the arc's own lane looks its key up when `want` is set for it.
+template <int ARCS>
+__device__ __forceinline__ void hash_slots(HashSmem& hs, bool insert, int t0, int cnt, int32_t myv, int W, int word,
+                                           const uint32_t* __restrict__ hot, uint32_t want, int (&s8)[ARCS]) {
+  const int lane = (int)lane_id();
+  const int r = lane - t0;
+  int slot = -1;
+  if (r >= 0 && r < ARCS && lane < cnt && ((want >> r) & 1u) && hot_bit(hot, myv)) {
+    const unsigned long long key = (unsigned long long)myv * (unsigned)W + (unsigned)word;
+    slot = insert ? hash_insert(hs.key, key) : hash_find(hs.key, key);
+  }
+#pragma unroll
+  for (int k = 0; k < ARCS; k++) s8[k] = __shfl_sync(0xffffffffu, slot, (t0 + k) & 31);
+}
+
+// MFBF product, phase 1 (minimum candidate per (s, v)), hash form.
+template <int ARCS>
+__global__ void __launch_bounds__(256, 4) k_gp_hash_min(
+    const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col, const int32_t* __restrict__ wt,
+    const uint32_t* __restrict__ hot, const int32_t* __restrict__ flist, uint32_t fcount, int W, int nb,
+    const uint32_t* __restrict__ fmask, const int32_t* __restrict__ dist, int32_t* cw, uint32_t* tmask,
+    uint32_t* vflag, int32_t* tlist, uint32_t* tcount, unsigned long long* bytes) {
+  extern __shared__ __align__(16) unsigned char hash_raw[];
+  HashSmem& hs = *reinterpret_cast<HashSmem*>(hash_raw);
+  const unsigned lane = lane_id();
+  int32_t* q = hs.q[threadIdx.x >> 5];
+  int qn = 0;
+  unsigned long long nbytes = 0;
+  hash_clear(hs, INF);
+  __syncthreads();
+  for (int it = 0; it < HASH_ITEMS; it++) {
+    uint64_t i;
+    if (!hash_item(fcount, W, it, &i)) break;
+    const int word = (int)(i / fcount);
+    const int32_t u = flist[i % fcount];
+    const uint32_t m = fmask[(size_t)u * W + word];
+    if (!m) continue;
+    const int j = word * 32 + (int)lane;
+    const bool active = (m >> lane) & 1u;
+    const int32_t du = active ? dist[(size_t)u * nb + j] : 0;
+    const int64_t beg = rowptr[u], end = rowptr[u + 1];
+    if (end - beg > HASH_ROW_MAX) continue;
+    for (int64_t k0 = beg; k0 < end; k0 += 32) {
+      const int64_t k = k0 + lane;
+      const int32_t myv = k < end ? col[k] : 0;
+      const int32_t myw = k < end ? (wt ? wt[k] : 1) : 0;
+      const int cnt = (int)(end - k0 < 32 ? end - k0 : 32);
+      for (int t0 = 0; t0 < cnt; t0 += ARCS) {
+        int32_t v8[ARCS], w8[ARCS], d8[ARCS], c8[ARCS];
+        int s8[ARCS];
+        hash_slots<ARCS>(hs, true, t0, cnt, myv, W, word, hot, 0xffffffffu, s8);
+#pragma unroll
+        for (int r = 0; r < ARCS; r++) {
+          v8[r] = __shfl_sync(0xffffffffu, myv, (t0 + r) & 31);
+          w8[r] = __shfl_sync(0xffffffffu, myw, (t0 + r) & 31);
+        }
+#pragma unroll
+        for (int r = 0; r < ARCS; r++) {
+          d8[r] = 0;
+          c8[r] = 0;
+          if (active && t0 + r < cnt && s8[r] < 0) {
+            const size_t idx = (size_t)v8[r] * nb + j;
+            d8[r] = __ldg(&dist[idx]);
+            c8[r] = cw[idx];
+          }
+        }
+        bool mine = false;
+        int32_t mv = 0;
+#pragma unroll
+        for (int r = 0; r < ARCS; r++) {
+          if (t0 + r < cnt) {
+            const int32_t cand = du + w8[r];
+            if (s8[r] >= 0) {
+              if (active) atomicMin(&hs.mn[s8[r]][lane], cand);
+            } else {
+              const bool touch = active && cand <= d8[r];
+              if (touch && cand < c8[r]) atomicMin(&cw[(size_t)v8[r] * nb + j], cand);
+              const uint32_t tb = __ballot_sync(0xffffffffu, touch);
+              if (tb && (int)lane == r) {
+                atomicOr(&tmask[(size_t)v8[r] * W + word], tb);
+                if (claim_vertex(vflag, v8[r])) { mine = true; mv = v8[r]; }
+              }
+              if (bytes) nbytes += 4ull * __popc(m) + 8ull * __popc(tb);
+            }
+          }
+        }
+        wl_push(q, qn, mine, mv, tlist, tcount);
+      }
+    }
+    if (bytes) nbytes += 8ull * (end - beg) / W + 4ull * __popc(m) + 4ull;
+  }
+  __syncthreads();
+  // merge: one warp per slot, one lane per column
+  for (int sl = (int)(threadIdx.x >> 5); sl < HASH_SLOTS; sl += 8) {
+    const unsigned long long key = hs.key[sl];
+    if (key == HASH_EMPTY) continue;
+    const int32_t v = (int32_t)(key / (unsigned)W);
+    const int word = (int)(key % (unsigned)W);
+    const int32_t mn = hs.mn[sl][lane];
+    bool touch = false;
+    if (mn != INF) {
+      const size_t idx = (size_t)v * nb + word * 32 + lane;
+      touch = mn <= dist[idx];
+      if (touch && mn < cw[idx]) atomicMin(&cw[idx], mn);
+    }
+    const uint32_t tb = __ballot_sync(0xffffffffu, touch);
+    bool mine = false;
+    if (tb && lane == 0) {
+      atomicOr(&tmask[(size_t)v * W + word], tb);
+      mine = claim_vertex(vflag, v);
+    }
+    wl_push(q, qn, mine, v, tlist, tcount);
+    if (bytes) nbytes += 12ull * __popc(__ballot_sync(0xffffffffu, mn != INF));
+  }
+  wl_flush(q, qn, tlist, tcount);
+  if (bytes && lane == 0) atomicAdd(bytes, nbytes);
+}
+
+// MFBF product, phase 2 (sum of the multiplicities that attain the minimum),
+// hash form: the block first finds its own minimum per slot and column
+// (shared memory only), keeps the columns where it equals the product's
+// minimum cw, then sums the frontier multiplicities of the candidates that
+// attain it and adds each slot column to cm once.
+template <int ARCS>
+__global__ void __launch_bounds__(256, 4) k_gp_hash_tie(
+    const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col, const int32_t* __restrict__ wt,
+    const uint32_t* __restrict__ hot, const int32_t* __restrict__ flist, uint32_t fcount, int W, int nb,
+    const uint32_t* __restrict__ fmask, const int32_t* __restrict__ dist, const double* __restrict__ fm,
+    const int32_t* __restrict__ cw, double* cm, unsigned long long* bytes) {
+  extern __shared__ __align__(16) unsigned char hash_raw[];
+  HashSmem& hs = *reinterpret_cast<HashSmem*>(hash_raw);
+  const unsigned lane = lane_id();
+  unsigned long long nbytes = 0;
+  hash_clear(hs, INF);
+  __syncthreads();
+  for (int pass = 0; pass < 2; pass++) {
+    for (int it = 0; it < HASH_ITEMS; it++) {
+      uint64_t i;
+      if (!hash_item(fcount, W, it, &i)) break;
+      const int word = (int)(i / fcount);
+      const int32_t u = flist[i % fcount];
+      const uint32_t m = fmask[(size_t)u * W + word];
+      if (!m) continue;
+      const int j = word * 32 + (int)lane;
+      const bool active = (m >> lane) & 1u;
+      const int32_t du = active ? dist[(size_t)u * nb + j] : 0;
+      const double mu = (pass == 1 && active) ? fm[(size_t)u * nb + j] : 0.0;
+      const int64_t beg = rowptr[u], end = rowptr[u + 1];
+      if (end - beg > HASH_ROW_MAX) continue;
+      for (int64_t k0 = beg; k0 < end; k0 += 32) {
+        const int64_t k = k0 + lane;
+        const int32_t myv = k < end ? col[k] : 0;
+        const int32_t myw = k < end ? (wt ? wt[k] : 1) : 0;
+        const int cnt = (int)(end - k0 < 32 ? end - k0 : 32);
+        for (int t0 = 0; t0 < cnt; t0 += ARCS) {
+          int32_t v8[ARCS], w8[ARCS], c8[ARCS];
+          int s8[ARCS];
+          hash_slots<ARCS>(hs, pass == 0, t0, cnt, myv, W, word, hot, 0xffffffffu, s8);
+#pragma unroll
+          for (int r = 0; r < ARCS; r++) {
+            v8[r] = __shfl_sync(0xffffffffu, myv, (t0 + r) & 31);
+            w8[r] = __shfl_sync(0xffffffffu, myw, (t0 + r) & 31);
+          }
+          if (pass == 0) {
+#pragma unroll
+            for (int r = 0; r < ARCS; r++)
+              if (t0 + r < cnt && s8[r] >= 0 && active) atomicMin(&hs.mn[s8[r]][lane], du + w8[r]);
+            continue;
+          }
+#pragma unroll
+          for (int r = 0; r < ARCS; r++)
+            c8[r] = (active && t0 + r < cnt && s8[r] < 0) ? __ldg(&cw[(size_t)v8[r] * nb + j]) : -1;
+#pragma unroll
+          for (int r = 0; r < ARCS; r++) {
+            if (t0 + r < cnt) {
+              const int32_t cand = du + w8[r];
+              if (s8[r] >= 0) {
+                // integer multiplicities below 2^53 sum exactly as 64-bit
+                // integers (a slot column takes at most one per item);
+                // larger ones, rounded in FP64 anyway, go to cm directly
+                if (active && ((hs.take[s8[r]] >> lane) & 1u) && cand == hs.mn[s8[r]][lane]) {
+                  if (mu < 9007199254740992.0)
+                    atomicAdd(reinterpret_cast<unsigned long long*>(&hs.sum[s8[r]][lane]),
+                              (unsigned long long)mu);
+                  else
+                    atomicAdd(&cm[(size_t)v8[r] * nb + j], mu);
+                }
+              } else {
+                const bool hit = active && cand == c8[r];
+                if (hit) atomicAdd(&cm[(size_t)v8[r] * nb + j], mu);
+                if (bytes) nbytes += 4ull * __popc(m) + 16ull * __popc(__ballot_sync(0xffffffffu, hit));
+              }
+            }
+          }
+        }
+      }
+      if (bytes && pass == 1) nbytes += 8ull * (end - beg) / W + 12ull * __popc(m) + 4ull;
+    }
+    __syncthreads();
+    if (pass == 0) {
+      // columns where the block's minimum is the product's minimum
+      for (int sl = (int)(threadIdx.x >> 5); sl < HASH_SLOTS; sl += 8) {
+        const unsigned long long key = hs.key[sl];
+        if (key == HASH_EMPTY) continue;
+        const int32_t v = (int32_t)(key / (unsigned)W);
+        const int word = (int)(key % (unsigned)W);
+        const int32_t mn = hs.mn[sl][lane];
+        const bool take = mn != INF && mn == cw[(size_t)v * nb + word * 32 + lane];
+        const uint32_t tb = __ballot_sync(0xffffffffu, take);
+        if (lane == 0) hs.take[sl] = tb;
+        if (bytes) nbytes += 4ull * __popc(__ballot_sync(0xffffffffu, mn != INF));
+      }
+      __syncthreads();
+    }
+  }
+  for (int sl = (int)(threadIdx.x >> 5); sl < HASH_SLOTS; sl += 8) {
+    if (hs.key[sl] == HASH_EMPTY) continue;
+    const uint32_t tb = hs.take[sl];
+    if (!tb) continue;
+    const unsigned long long key = hs.key[sl];
+    const int32_t v = (int32_t)(key / (unsigned)W);
+    const int word = (int)(key % (unsigned)W);
+    const unsigned long long sm = reinterpret_cast<const unsigned long long*>(&hs.sum[sl][0])[lane];
+    if (((tb >> lane) & 1u) && sm) atomicAdd(&cm[(size_t)v * nb + word * 32 + lane], (double)sm);
+    if (bytes) nbytes += 8ull * __popc(tb);
+  }
+  if (bytes && lane == 0) atomicAdd(bytes, nbytes);
+}
+
+// MFBr product over A^T (counter decrement, exactly-once enqueue), hash
+// form: per slot column the block sums the values and counts the tight arcs,
+// then adds the sum to Z.p and takes the count off the counter with one
+// atomic each; the lane whose subtraction takes the counter to zero enqueues.
+template <int ARCS>
+__global__ void __launch_bounds__(256, 4) k_gp_hash_prop(
+    const int64_t* __restrict__ rowptr_t, const int32_t* __restrict__ col_t, const int32_t* __restrict__ wt_t,
+    const uint32_t* __restrict__ hot, const int32_t* __restrict__ flist, uint32_t fcount, int W, int nb,
+    const uint32_t* __restrict__ fmask, const int32_t* __restrict__ dist, const double* __restrict__ fv,
+    double* zp, int32_t* cnt, uint32_t* tmask, uint32_t* vflag, int32_t* tlist, uint32_t* tcount,
+    unsigned long long* bytes) {
+  extern __shared__ __align__(16) unsigned char hash_raw[];
+  HashSmem& hs = *reinterpret_cast<HashSmem*>(hash_raw);
+  const unsigned lane = lane_id();
+  int32_t* q = hs.q[threadIdx.x >> 5];
+  int qn = 0;
+  unsigned long long nbytes = 0;
+  hash_clear(hs, 0);
+  __syncthreads();
+  for (int it = 0; it < HASH_ITEMS; it++) {
+    uint64_t i;
+    if (!hash_item(fcount, W, it, &i)) break;
+    const int word = (int)(i / fcount);
+    const int32_t u = flist[i % fcount];
+    const uint32_t m = fmask[(size_t)u * W + word];
+    if (!m) continue;
+    const int j = word * 32 + (int)lane;
+    const bool active = (m >> lane) & 1u;
+    const int32_t du = active ? dist[(size_t)u * nb + j] : 0;
+    const double val = active ? fv[(size_t)u * nb + j] : 0.0;
+    const int64_t beg = rowptr_t[u], end = rowptr_t[u + 1];
+    if (end - beg > HASH_ROW_MAX) continue;
+    for (int64_t k0 = beg; k0 < end; k0 += 32) {
+      const int64_t k = k0 + lane;
+      const int32_t myv = k < end ? col_t[k] : 0;
+      const int32_t myw = k < end ? (wt_t ? wt_t[k] : 1) : 0;
+      const int cntk = (int)(end - k0 < 32 ? end - k0 : 32);
+      for (int t0 = 0; t0 < cntk; t0 += ARCS) {
+        int32_t v8[ARCS], w8[ARCS], d8[ARCS], o8[ARCS];
+        int s8[ARCS];
+#pragma unroll
+        for (int r = 0; r < ARCS; r++) {
+          v8[r] = __shfl_sync(0xffffffffu, myv, (t0 + r) & 31);
+          w8[r] = __shfl_sync(0xffffffffu, myw, (t0 + r) & 31);
+        }
+#pragma unroll
+        for (int r = 0; r < ARCS; r++)
+          d8[r] = (active && t0 + r < cntk) ? __ldg(&dist[(size_t)v8[r] * nb + j]) : INT32_MIN;
+        // only arcs that are tight in some column take a slot
+        uint32_t want = 0u;
+#pragma unroll
+        for (int r = 0; r < ARCS; r++)
+          want |= (__ballot_sync(0xffffffffu, t0 + r < cntk && d8[r] == du - w8[r]) ? 1u : 0u) << r;
+        hash_slots<ARCS>(hs, true, t0, cntk, myv, W, word, hot, want, s8);
+#pragma unroll
+        for (int r = 0; r < ARCS; r++) {
+          o8[r] = 0;
+          if (t0 + r < cntk && d8[r] == du - w8[r]) {
+            if (s8[r] >= 0) {
+              atomicAdd(&hs.sum[s8[r]][lane], val);
+              atomicAdd(&hs.mn[s8[r]][lane], 1);
+            } else {
+              const size_t idx = (size_t)v8[r] * nb + j;
+              atomicAdd(&zp[idx], val);
+              o8[r] = atomicSub(&cnt[idx], 1);
+            }
+          }
+        }
+        bool mine = false;
+        int32_t mv = 0;
+#pragma unroll
+        for (int r = 0; r < ARCS; r++) {
+          if (t0 + r < cntk) {
+            const uint32_t rb = __ballot_sync(0xffffffffu, o8[r] == 1);
+            if (rb && (int)lane == r) {
+              atomicOr(&tmask[(size_t)v8[r] * W + word], rb);
+              if (claim_vertex(vflag, v8[r])) { mine = true; mv = v8[r]; }
+            }
+            if (bytes)
+              nbytes += 4ull * __popc(m) +
+                        (s8[r] < 0 ? 24ull * __popc(__ballot_sync(0xffffffffu, d8[r] == du - w8[r])) : 0ull);
+          }
+        }
+        wl_push(q, qn, mine, mv, tlist, tcount);
+      }
+    }
+    if (bytes) nbytes += 8ull * (end - beg) / W + 16ull * __popc(m) + 4ull;
+  }
+  __syncthreads();
+  for (int sl = (int)(threadIdx.x >> 5); sl < HASH_SLOTS; sl += 8) {
+    const unsigned long long key = hs.key[sl];
+    if (key == HASH_EMPTY) continue;
+    const int32_t v = (int32_t)(key / (unsigned)W);
+    const int word = (int)(key % (unsigned)W);
+    const int32_t c = hs.mn[sl][lane];
+    bool zero = false;
+    if (c > 0) {
+      const size_t idx = (size_t)v * nb + word * 32 + lane;
+      atomicAdd(&zp[idx], hs.sum[sl][lane]);
+      zero = atomicSub(&cnt[idx], c) == c;
+    }
+    const uint32_t rb = __ballot_sync(0xffffffffu, zero);
+    bool mine = false;
+    if (rb && lane == 0) {
+      atomicOr(&tmask[(size_t)v * W + word], rb);
+      mine = claim_vertex(vflag, v);
+    }
+    wl_push(q, qn, mine, v, tlist, tcount);
+    if (bytes) nbytes += 16ull * __popc(__ballot_sync(0xffffffffu, c > 0));
+  }
+  wl_flush(q, qn, tlist, tcount);
+  if (bytes && lane == 0) atomicAdd(bytes, nbytes);
 }
 
 // ------------------------------------------------------ segmented (pull) products
@@ -746,7 +1170,7 @@ static inline unsigned hub_blocks(int32_t nhub, int W) {
 // the frontier's arcs, but meet in atomics at hub columns).
 static inline bool use_pull(const RunCtx& rc, uint32_t fcount, int32_t n) {
   if (rc.accum == MFBC_ACCUM_SEGMENTED) return true;
-  if (rc.accum == MFBC_ACCUM_ATOMIC) return false;
+  if (rc.accum == MFBC_ACCUM_ATOMIC || rc.accum == MFBC_ACCUM_HASH) return false;
   return (uint64_t)fcount * 64 >= (uint64_t)n;
 }
 
@@ -763,6 +1187,30 @@ static mfbc_status read_counts(RunCtx& rc, Counters* ctr) {
   do {                                                                    \
     if (wide) kern<8><<<grid, 256, 0, st>>>(__VA_ARGS__);                 \
     else kern<1><<<grid, 256, 0, st>>>(__VA_ARGS__);                      \
+  } while (0)
+
+// hash accumulator kernels: one block per 8 * HASH_ITEMS items, the table
+// in dynamic shared memory
+static inline unsigned hash_blocks(uint64_t items) {
+  const uint64_t b = (items + 8 * HASH_ITEMS - 1) / (8 * HASH_ITEMS);
+  return (unsigned)(b < 1 ? 1 : b);
+}
+static void hash_smem_attrs() {
+  static bool done = false;
+  if (done) return;
+  const int sz = (int)sizeof(HashSmem);
+  cudaFuncSetAttribute(k_gp_hash_min<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sz);
+  cudaFuncSetAttribute(k_gp_hash_min<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, sz);
+  cudaFuncSetAttribute(k_gp_hash_tie<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sz);
+  cudaFuncSetAttribute(k_gp_hash_tie<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, sz);
+  cudaFuncSetAttribute(k_gp_hash_prop<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sz);
+  cudaFuncSetAttribute(k_gp_hash_prop<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, sz);
+  done = true;
+}
+#define GP_HASH(kern, grid, ...)                                                   \
+  do {                                                                             \
+    if (wide) kern<8><<<grid, 256, sizeof(HashSmem), st>>>(__VA_ARGS__);           \
+    else kern<1><<<grid, 256, sizeof(HashSmem), st>>>(__VA_ARGS__);                \
   } while (0)
 
 #define PROF(id, ...)             \
@@ -828,13 +1276,33 @@ mfbc_status general_batch(RunCtx& rc, GeneralState& s, const int32_t* d_src_batc
         k_gp_pull_rows<true><<<stride_blocks((uint64_t)n * W), 256, 0, st>>>(pa);
         if (g.items_in.nhub) k_gp_pull_hubs<true><<<hub_blocks(g.items_in.nhub, W), 256, 0, st>>>(pa);
       });
+    } else if (rc.accum == MFBC_ACCUM_HASH) {
+      hash_smem_attrs();
+      // rows of at most HASH_ROW_MAX arcs in the hash kernels, longer ones
+      // on the atomic kernels; both minimum passes precede both tie passes
+      const bool longrows = g.max_deg > HASH_ROW_MAX;
+      PROF(K_HASH_MIN, {
+        GP_HASH(k_gp_hash_min, hash_blocks(wp), g.rowptr, g.col, g.w, g.hot_in, cur, fcount, W, nb, s.fmask,
+                s.dist, s.cw, s.tmask, s.vflag, nxt, &s.ctr->list_count[1], B ? B + K_HASH_MIN : nullptr);
+        if (longrows)
+          GP_LAUNCH(k_gp_relax_min, warp_blocks(wp), g.rowptr, g.col, g.w, cur, fcount, W, nb, s.fmask, s.dist,
+                    s.cw, s.tmask, s.vflag, nxt, &s.ctr->list_count[1], B ? B + K_HASH_MIN : nullptr,
+                    (int64_t)HASH_ROW_MAX + 1);
+      });
+      PROF(K_HASH_TIE, {
+        GP_HASH(k_gp_hash_tie, hash_blocks(wp), g.rowptr, g.col, g.w, g.hot_in, cur, fcount, W, nb, s.fmask,
+                s.dist, s.fm, s.cw, s.cm, B ? B + K_HASH_TIE : nullptr);
+        if (longrows)
+          GP_LAUNCH(k_gp_relax_tie, warp_blocks(wp), g.rowptr, g.col, g.w, cur, fcount, W, nb, s.fmask, s.dist,
+                    s.fm, s.cw, s.cm, B ? B + K_HASH_TIE : nullptr, (int64_t)HASH_ROW_MAX + 1);
+      });
     } else {
       PROF(K_RELAX_MIN, GP_LAUNCH(k_gp_relax_min, warp_blocks(wp),
                             g.rowptr, g.col, g.w, cur, fcount, W, nb, s.fmask, s.dist, s.cw, s.tmask,
-                            s.vflag, nxt, &s.ctr->list_count[1], B ? B + K_RELAX_MIN : nullptr));
+                            s.vflag, nxt, &s.ctr->list_count[1], B ? B + K_RELAX_MIN : nullptr, (int64_t)0));
       PROF(K_RELAX_TIE, GP_LAUNCH(k_gp_relax_tie, warp_blocks(wp),
                             g.rowptr, g.col, g.w, cur, fcount, W, nb, s.fmask, s.dist, s.fm, s.cw, s.cm,
-                            B ? B + K_RELAX_TIE : nullptr));
+                            B ? B + K_RELAX_TIE : nullptr, (int64_t)0));
     }
     PROF(K_CLEAR, (k_clear_mask_rows<<<(unsigned)((wp + 255) / 256), 256, 0, st>>>(cur, fcount, W,
                                                                                    s.fmask, s.fmem)));
@@ -874,11 +1342,22 @@ mfbc_status general_batch(RunCtx& rc, GeneralState& s, const int32_t* d_src_batc
         k_gp_pull_rows<false><<<stride_blocks((uint64_t)n * W), 256, 0, st>>>(pb);
         if (g.items_out.nhub) k_gp_pull_hubs<false><<<hub_blocks(g.items_out.nhub, W), 256, 0, st>>>(pb);
       });
+    } else if (rc.accum == MFBC_ACCUM_HASH) {
+      hash_smem_attrs();
+      PROF(K_HASH_PROP, {
+        GP_HASH(k_gp_hash_prop, hash_blocks(wp), g.rowptr_t, g.col_t, g.w_t, g.hot_out, cur, fcount, W, nb,
+                s.fmask, s.dist, s.fm, s.cm, s.cw, s.tmask, s.vflag, nxt, &s.ctr->list_count[1],
+                B ? B + K_HASH_PROP : nullptr);
+        if (g.max_in_deg > HASH_ROW_MAX)
+          GP_LAUNCH(k_gp_propagate, warp_blocks(wp), g.rowptr_t, g.col_t, g.w_t, cur, fcount, W, nb, s.fmask,
+                    s.dist, s.fm, s.cm, s.cw, s.tmask, s.vflag, nxt, &s.ctr->list_count[1],
+                    B ? B + K_HASH_PROP : nullptr, (int64_t)HASH_ROW_MAX + 1);
+      });
     } else {
       PROF(K_PROPAGATE, GP_LAUNCH(k_gp_propagate, warp_blocks(wp),
                             g.rowptr_t, g.col_t, g.w_t, cur, fcount, W, nb, s.fmask, s.dist, s.fm, s.cm,
                             s.cw, s.tmask, s.vflag, nxt, &s.ctr->list_count[1],
-                            B ? B + K_PROPAGATE : nullptr));
+                            B ? B + K_PROPAGATE : nullptr, (int64_t)0));
     }
     PROF(K_CLEAR, (k_clear_mask_rows<<<(unsigned)((wp + 255) / 256), 256, 0, st>>>(cur, fcount, W,
                                                                                    s.fmask, s.fmem)));

@@ -137,6 +137,24 @@ static mfbc_status build_items(DevGraph* g, const std::vector<int64_t>& rp, Item
   return MFBC_OK;
 }
 
+// Targets where the push products' candidates meet often enough for the
+// hash accumulator to combine them in shared memory: vertices whose row in
+// rp (in-arcs for MFBF targets, out-arcs for MFBr targets) holds at least
+// max(16, 2 x the average degree) arcs.  One bit per vertex.
+static mfbc_status upload_hot_targets(DevGraph* g, const std::vector<int64_t>& rp, uint32_t** out, cudaStream_t st,
+                                      std::string* err) {
+  const int32_t n = g->n;
+  const int64_t avg2 = n ? 2 * g->nnz / n : 0;
+  const int64_t thr = std::max<int64_t>(16, avg2);
+  std::vector<uint32_t> bits(((size_t)n + 31) / 32 + 1, 0u);
+  for (int32_t v = 0; v < n; v++)
+    if (rp[(size_t)v + 1] - rp[v] >= thr) bits[(size_t)v >> 5] |= 1u << (v & 31);
+  TRY(dev_alloc(g, out, bits.size(), err));
+  MFBC_CUDA_TRY(cudaMemcpyAsync(*out, bits.data(), sizeof(uint32_t) * bits.size(), cudaMemcpyHostToDevice, st), err);
+  MFBC_CUDA_TRY(cudaStreamSynchronize(st), err);
+  return MFBC_OK;
+}
+
 mfbc_status graph_build(int32_t n, int64_t nnz, const int64_t* h_rowptr, const int32_t* h_col,
                         const int32_t* h_w, uint32_t flags, cudaStream_t st, DevGraph* g,
                         std::string* err) {
@@ -228,6 +246,8 @@ mfbc_status graph_build(int32_t n, int64_t nnz, const int64_t* h_rowptr, const i
     MFBC_CUDA_TRY(cudaStreamSynchronize(st), err);
     TRY(build_items(g, rpt, &g->items_in, false, st, err));
     TRY(build_items(g, rp, &g->items_out, true, st, err));
+    TRY(upload_hot_targets(g, rpt, &g->hot_in, st, err));
+    TRY(upload_hot_targets(g, rp, &g->hot_out, st, err));
   } else {
     g->max_in_deg = g->max_deg;
     g->rowptr_t = g->rowptr;
@@ -235,6 +255,8 @@ mfbc_status graph_build(int32_t n, int64_t nnz, const int64_t* h_rowptr, const i
     g->w_t = g->w;
     TRY(build_items(g, rp, &g->items_in, false, st, err));
     g->items_out = g->items_in;
+    TRY(upload_hot_targets(g, rp, &g->hot_in, st, err));
+    g->hot_out = g->hot_in;
   }
   return MFBC_OK;
 }

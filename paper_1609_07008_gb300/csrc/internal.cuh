@@ -41,6 +41,8 @@ struct DevGraph {
   int32_t wmax = 1;
   std::vector<int32_t> landmarks;   // highest out-degree vertices, descending (source ordering)
   uint32_t* hot = nullptr;         // [n/32] bits: the HOT_ROWS highest out-degree vertices
+  uint32_t* hot_in = nullptr;      // [n/32] bits: in-degree >= max(16, 2 x average) (hash accumulator)
+  uint32_t* hot_out = nullptr;     // [n/32] bits: the same for out-degree (aliases hot_in when undirected)
   int64_t max_deg = 0;             // largest out-degree
   int64_t max_in_deg = 0;          // largest in-degree
   int64_t* rowptr = nullptr;       // CSR of A (out-arcs)
@@ -65,7 +67,8 @@ struct KStat {
 enum KId {
   K_FILL = 0, K_SEED, K_RELAX_MIN, K_RELAX_TIE, K_ACCUM, K_COUNTERS, K_PROPAGATE, K_FINAL,
   K_LAMBDA, K_CLEAR, K_LVL_FWD, K_LVL_VISIT, K_LVL_BWD, K_LVL_HUB, K_LVL_RESET, K_OUTPUT,
-  K_LVL_FWD_G, K_LVL_BWD_G, K_LVL_SPLIT, K_DP_FWD, K_DP_BWD, K_SMALL, K_PULL_FWD, K_PULL_BWD, K_NUM
+  K_LVL_FWD_G, K_LVL_BWD_G, K_LVL_SPLIT, K_DP_FWD, K_DP_BWD, K_SMALL, K_PULL_FWD, K_PULL_BWD,
+  K_HASH_MIN, K_HASH_TIE, K_HASH_PROP, K_NUM
 };
 
 // Bits of Counters::flags, set by kernels and read by the host drivers.

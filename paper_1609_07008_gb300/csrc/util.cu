@@ -89,7 +89,8 @@ static const char* kNames[K_NUM] = {
   "mfbr_counters_leaves", "mfbr_propagate", "mfbr_next_frontier", "lambda_accumulate",
   "clear_masks", "level_mfbf_pairs", "level_visit", "level_mfbr_pairs", "level_mfbr_hub_final",
   "level_reset", "output_copy", "level_mfbf_gather", "level_mfbr_gather", "level_round_split",
-  "dist_mfbf", "dist_mfbr", "small_persistent", "mfbf_pull", "mfbr_pull"};
+  "dist_mfbf", "dist_mfbr", "small_persistent", "mfbf_pull", "mfbr_pull",
+  "mfbf_hash_min", "mfbf_hash_tie", "mfbr_hash"};
 
 Profiler::Profiler() {
   for (int i = 0; i < K_NUM; i++) k[i].name = kNames[i];

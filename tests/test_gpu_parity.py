@@ -404,11 +404,11 @@ def test_autotune_picks_a_candidate_and_results_are_unchanged(weighted):
     G = mfbc.Graph.from_csr(g)
     t = G.autotune(srcs)
     if weighted:
-        # general kernels (3 widths x {atomic x 2 arc steps, segmented, per product}) and
-        # distance kernels (3 widths)
-        assert t["path"] in (mfbc.PATH_GENERAL, mfbc.PATH_DIST) and t["tried"] == 15
+        # general kernels (3 widths x {atomic x 2 arc steps, segmented, hash, per product})
+        # and distance kernels (3 widths)
+        assert t["path"] in (mfbc.PATH_GENERAL, mfbc.PATH_DIST) and t["tried"] == 18
         assert t["arcs"] in ((0, 1, 8) if t["path"] == mfbc.PATH_GENERAL else (0,))
-        assert t["accumulator"] in ((0, 1, 2) if t["path"] == mfbc.PATH_GENERAL else (0,))
+        assert t["accumulator"] in ((0, 1, 2, 3) if t["path"] == mfbc.PATH_GENERAL else (0,))
     else:
         # level kernels (3 widths) and the persistent small-graph kernel (4 widths)
         assert t["path"] in (mfbc.PATH_LEVEL, mfbc.PATH_SMALL) and t["tried"] == 7 and t["arcs"] == 0
