@@ -308,15 +308,17 @@ __device__ __forceinline__ uint32_t quads_of_words(uint32_t words, int Q) {
   return q;
 }
 
-// Work items are handed out in groups of 32 (hub items cost far more than
-// leaf items); the group counter is zeroed before each launch.  (Handing out
-// 4 to 16 groups per atomic was measured slower: balance matters more than
-// the counter.)
-#define FOR_ITEM_GROUPS(ib, ie, counter)                                                    \
+// Work items are handed out in groups of ig <= 32 (hub items cost far more
+// than leaf items); the group counter is zeroed before each launch.  ig is 32
+// unless the range is too short to give every resident warp several groups
+// (small graphs), where smaller groups spread it over more warps.  (Handing
+// out 4 to 16 groups per atomic was measured slower: balance matters more
+// than the counter.)
+#define FOR_ITEM_GROUPS(ib, ie, counter, ig)                                                \
   for (;;) {                                                                              \
     uint32_t grp_ = 0;                                                                    \
     if (lane == 0) grp_ = atomicAdd(counter, 1u);                                         \
-    const uint64_t base = (uint64_t)(ib) + (uint64_t)__shfl_sync(0xffffffffu, grp_, 0) * 32; \
+    const uint64_t base = (uint64_t)(ib) + (uint64_t)__shfl_sync(0xffffffffu, grp_, 0) * (uint64_t)(ig); \
     if (base >= (uint64_t)(ie)) break;
 
 // MFBF pairs of level l (see file comment): for items [ib, ie) of rows not yet
@@ -328,7 +330,7 @@ __global__ void __launch_bounds__(LVL_WARPS * 32, MFBC_PAIR_MIN_BLOCKS) k_lvl_fw
     const uint32_t* __restrict__ Fl, const uint32_t* __restrict__ mem_l, uint32_t* Fn, uint32_t* mem_n,
     int32_t* list_n, uint32_t* count_n, int64_t cap_n, uint32_t* flags, uint32_t* next_group, uint32_t* prow,
     uint4* pmask, uint4* segs, uint32_t* work, uint32_t pair_cap, uint32_t seg_cap, const uint32_t* __restrict__ hot,
-    unsigned long long* bytes, unsigned long long* stat) {
+    unsigned long long* bytes, unsigned long long* stat, int ig) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   WarpSmem& sm = reinterpret_cast<WarpSmem*>(smem_raw)[threadIdx.x >> 5];
   const unsigned lane = lane_id();
@@ -351,13 +353,13 @@ __global__ void __launch_bounds__(LVL_WARPS * 32, MFBC_PAIR_MIN_BLOCKS) k_lvl_fw
     __syncwarp();
     nnew = 0;
   };
-  FOR_ITEM_GROUPS(ib, ie, next_group)
-    // lane-parallel precheck of 32 items: skip rows already reached by every column
+  FOR_ITEM_GROUPS(ib, ie, next_group, ig)
+    // lane-parallel precheck of the group's items: skip rows already reached by every column
     const uint64_t myit = base + lane;
     int32_t myv = 0;
     int64_t mymeta = 0;
     bool act = false;
-    if (myit < (uint64_t)ie) {
+    if ((int)lane < ig && myit < (uint64_t)ie) {
       myv = item_v[myit];
       mymeta = item_meta[myit];
       act = !test_bit(full, myv);
@@ -453,7 +455,7 @@ __global__ void __launch_bounds__(LVL_WARPS * 32, MFBC_PAIR_MIN_BLOCKS) k_lvl_bw
     const int32_t* __restrict__ col, int W, const uint32_t* __restrict__ Fl, const uint32_t* __restrict__ mem_l,
     const uint32_t* __restrict__ Fn, const uint32_t* __restrict__ mem_n, uint32_t* next_group, uint32_t* prow,
     uint4* pmask, uint4* segs, uint32_t* work, uint32_t pair_cap, uint32_t seg_cap, const uint32_t* __restrict__ hot,
-    unsigned long long* bytes, unsigned long long* stat) {
+    unsigned long long* bytes, unsigned long long* stat, int ig) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   WarpSmem& sm = reinterpret_cast<WarpSmem*>(smem_raw)[threadIdx.x >> 5];
   const unsigned lane = lane_id();
@@ -461,13 +463,13 @@ __global__ void __launch_bounds__(LVL_WARPS * 32, MFBC_PAIR_MIN_BLOCKS) k_lvl_bw
   const int Q = W / 4;
   unsigned long long nbytes = 0, npairs = 0;
   SlotCursor cur;
-  FOR_ITEM_GROUPS(ib, ie, next_group)
-    // lane-parallel precheck of 32 items: only rows with a column at level l
+  FOR_ITEM_GROUPS(ib, ie, next_group, ig)
+    // lane-parallel precheck of the group's items: only rows with a column at level l
     const uint64_t myit = base + lane;
     int32_t myv = 0;
     int64_t mymeta = 0;
     bool act = false;
-    if (myit < (uint64_t)ie) {
+    if ((int)lane < ig && myit < (uint64_t)ie) {
       myv = item_v[myit];
       mymeta = item_meta[myit];
       act = test_bit(mem_l, myv);
@@ -710,15 +712,18 @@ __device__ __forceinline__ void gather_group(const uint4& myseg, int nin, const 
   }
 }
 
-#define FOR_SEGMENT_GROUPS(nseg, counter)                                                    \
+// Segments are handed out in groups of gs <= 32 (lane k holds segment k of
+// the group); gs < 32 only when there are too few segments to give every
+// resident warp several groups.
+#define FOR_SEGMENT_GROUPS(nseg, counter, gs)                                                \
   for (;;) {                                                                               \
     uint32_t grp_ = 0;                                                                     \
     if (lane == 0) grp_ = atomicAdd(counter, 1u);                                          \
-    const uint64_t base = (uint64_t)__shfl_sync(0xffffffffu, grp_, 0) * 32;                \
+    const uint64_t base = (uint64_t)__shfl_sync(0xffffffffu, grp_, 0) * (uint64_t)(gs);    \
     if (base >= (uint64_t)(nseg)) break;                                                   \
+    const int nin = (uint64_t)(nseg) - base < (uint64_t)(gs) ? (int)((uint64_t)(nseg) - base) : (gs); \
     uint4 myseg = make_uint4(0u, 0u, 0u, 0u);                                              \
-    if (base + lane < (uint64_t)(nseg)) myseg = segs[base + lane];                         \
-    const int nin = (uint64_t)(nseg) - base < 32 ? (int)((uint64_t)(nseg) - base) : 32;
+    if ((int)lane < nin) myseg = segs[base + lane];
 
 // MFBF gather of level l: sigma_bar(s,v) = sum over the segment's pairs
 // (exact 64-bit integers).  flags: bit 1 some sigma_bar >= 2^53, bit 3 a sum
@@ -727,7 +732,7 @@ template <bool COUNT>
 __global__ void __launch_bounds__(256, MFBC_GATHER_MIN_BLOCKS) k_lvl_fwd_gather(
     const uint4* __restrict__ segs, const uint32_t* nseg_p, const uint32_t* __restrict__ prow,
     const uint4* __restrict__ pmask, int nb, double* svd, uint32_t* flags, uint32_t* next_group,
-    unsigned long long* bytes, unsigned long long* stat, VisitNext vn) {
+    unsigned long long* bytes, unsigned long long* stat, VisitNext vn, int seg_group) {
   __shared__ GatherSmem gsm[8];
   GatherSmem& gs = gsm[threadIdx.x >> 5];
   uint64_t* sv = reinterpret_cast<uint64_t*>(svd);
@@ -735,7 +740,7 @@ __global__ void __launch_bounds__(256, MFBC_GATHER_MIN_BLOCKS) k_lvl_fwd_gather(
   const uint32_t nseg = *nseg_p;
   unsigned long long nvals = 0, nw = 0, nrec = 0;
   uint32_t ovf = 0, big = 0;
-  FOR_SEGMENT_GROUPS(nseg, next_group)
+  FOR_SEGMENT_GROUPS(nseg, next_group, seg_group)
     gather_group<COUNT, true>(myseg, nin, prow, pmask, gs, sv, nvals, nrec, ovf,
         [&](int k, uint64_t a0, uint64_t a1, uint64_t a2, uint64_t a3, float, float, float, float, float, float,
             float, float, uint32_t cs) {
@@ -832,7 +837,7 @@ __global__ void __launch_bounds__(256, MFBC_BWD_GATHER_MIN_BLOCKS) k_lvl_bwd_gat
     const uint4* __restrict__ pmask, int nb, int W, const uint32_t* __restrict__ Fl,
     const int32_t* __restrict__ hub_of, double* svd, double* zacc, double* lambda, int32_t n, int uniform_req,
     const int32_t* __restrict__ quad_req, const int32_t* __restrict__ word_req, uint32_t* next_group,
-    unsigned long long* bytes, unsigned long long* stat) {
+    unsigned long long* bytes, unsigned long long* stat, int seg_group) {
   __shared__ GatherSmem gsm[8];
   __shared__ FinishSmem fsm[8];
   GatherSmem& gs = gsm[threadIdx.x >> 5];
@@ -844,7 +849,7 @@ __global__ void __launch_bounds__(256, MFBC_BWD_GATHER_MIN_BLOCKS) k_lvl_bwd_gat
   const int shift = 4 * (int)(lane & 7u);
   unsigned long long nvals = 0, nw = 0, nrec = 0;
   uint32_t ovf = 0;
-  FOR_SEGMENT_GROUPS(nseg, next_group)
+  FOR_SEGMENT_GROUPS(nseg, next_group, seg_group)
     auto finish = [&](int k, uint64_t, uint64_t, uint64_t, uint64_t, float s0, float s1, float s2, float s3, float c0,
                       float c1, float c2, float c3, uint32_t) {
       const int32_t v = (int32_t)__shfl_sync(0xffffffffu, myseg.x, k);
@@ -919,18 +924,19 @@ __global__ void __launch_bounds__(256, MFBC_BWD_GATHER_MIN_BLOCKS) k_lvl_bwd_gat
 __global__ void __launch_bounds__(LVL_WARPS * 32) k_lvl_hub_final(
     const int32_t* __restrict__ hubs, int32_t nhub, int W, int nb, const uint32_t* __restrict__ Fl,
     const uint32_t* __restrict__ mem_l, double* svd, double* zacc, double* lambda, int32_t n, int uniform_req,
-    const int32_t* __restrict__ word_req, unsigned long long* bytes) {
+    const int32_t* __restrict__ word_req, unsigned long long* bytes, int hc) {
   __shared__ uint16_t cols_all[LVL_WARPS][LEVEL_MAX_NB];
   uint16_t* cols = cols_all[threadIdx.x >> 5];
   const unsigned lane = lane_id();
   const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
   uint64_t* sv = reinterpret_cast<uint64_t*>(svd);
   unsigned long long nbytes = 0;
-  for (uint64_t base = (((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; base < (uint64_t)nhub;
-       base += nw * 32) {
+  // hc <= 32 hubs per warp and round (fewer when there are few hubs)
+  for (uint64_t base = (((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * hc; base < (uint64_t)nhub;
+       base += nw * hc) {
     const uint64_t myh = base + lane;
-    const int32_t myv = myh < (uint64_t)nhub ? hubs[myh] : 0;
-    uint32_t am = __ballot_sync(0xffffffffu, myh < (uint64_t)nhub && test_bit(mem_l, myv));
+    const int32_t myv = (int)lane < hc && myh < (uint64_t)nhub ? hubs[myh] : 0;
+    uint32_t am = __ballot_sync(0xffffffffu, (int)lane < hc && myh < (uint64_t)nhub && test_bit(mem_l, myv));
     while (am) {
       const int t = __ffs(am) - 1;
       am &= am - 1;
@@ -1042,6 +1048,21 @@ static void set_smem_attrs() {
   done = true;
 }
 
+// Units per group (<= 32, a power of two) so that a launch of `warps`
+// resident warps gets at least four groups per warp where the work allows,
+// and the blocks that launch with such groups (at most cap).
+static inline int group_size(uint64_t units, uint64_t warps) {
+  int g = 32;
+  while (g > 1 && units < (uint64_t)g * warps * 4) g >>= 1;
+  return g;
+}
+static inline unsigned grid_for_groups(uint64_t units, int g, unsigned cap) {
+  const uint64_t warps = (units + (uint64_t)g - 1) / (uint64_t)g;
+  uint64_t b = (warps + LVL_WARPS - 1) / LVL_WARPS;
+  if (b < 1) b = 1;
+  return (unsigned)(b > cap ? cap : b);
+}
+
 static inline unsigned grid_for_warps(uint64_t warps, unsigned cap) {
   uint64_t b = (warps + LVL_WARPS - 1) / LVL_WARPS;
   if (b < 1) b = 1;
@@ -1076,7 +1097,8 @@ static mfbc_status level_round(RunCtx& rc, LevelState& s, bool fwd, int l, int64
   uint32_t* Mn = s.member + (size_t)(l + 1) * s.mw;
   MFBC_CUDA_TRY(cudaMemsetAsync(s.ctr->work, 0, sizeof(uint32_t) * 4, st), rc.err);
   MFBC_CUDA_TRY(cudaMemsetAsync(&s.ctr->list_count[2], 0, sizeof(uint32_t), st), rc.err);
-  const unsigned pgrid = grid_for_items(ie - ib, PAIR_GRID);
+  const int ig = group_size((uint64_t)(ie - ib), (uint64_t)PAIR_GRID * LVL_WARPS);
+  const unsigned pgrid = grid_for_groups((uint64_t)(ie - ib), ig, PAIR_GRID);
   // row indices u * Q + quad need bit 31 free for the hot-row flag
   const int Qn = std::max(1, W / 4);
   const uint32_t* hot = MFBC_HOT_HINT && (uint64_t)n * (uint64_t)Qn < (1ull << 31) ? g.hot : nullptr;
@@ -1085,12 +1107,12 @@ static mfbc_status level_round(RunCtx& rc, LevelState& s, bool fwd, int l, int64
                         ib, ie, g.items_in.v, g.items_in.beg, g.col_t, W, s.full, s.V, Fl, Ml, Fn, Mn,
                         s.lists + off_n, &s.ctr->list_count[0], s.list_cap - off_n, &s.ctr->flags,
                         &s.ctr->list_count[2], s.prow, s.pmask, s.segs, s.ctr->work, s.pair_cap, s.seg_cap, hot,
-                        B ? B + K_LVL_FWD : nullptr, s.ctr->stat)));
+                        B ? B + K_LVL_FWD : nullptr, s.ctr->stat, ig)));
   else
     PROF(K_LVL_BWD, (k_lvl_bwd_pairs<<<pgrid, LVL_WARPS * 32, LVL_SMEM, st>>>(
                         ib, ie, g.items_out.v, g.items_out.beg, g.col, W, Fl, Ml, Fn, Mn,
                         &s.ctr->list_count[2], s.prow, s.pmask, s.segs, s.ctr->work, s.pair_cap, s.seg_cap, hot,
-                        B ? B + K_LVL_BWD : nullptr, s.ctr->stat)));
+                        B ? B + K_LVL_BWD : nullptr, s.ctr->stat, ig)));
   MFBC_CUDA_TRY(cudaMemcpyAsync(rc.h_ctr, s.ctr->list_count, sizeof(uint32_t) * 9, cudaMemcpyDeviceToHost, st), rc.err);
   MFBC_CUDA_TRY(cudaStreamSynchronize(st), rc.err);
   rc.prof->drain();
@@ -1116,27 +1138,29 @@ static mfbc_status level_round(RunCtx& rc, LevelState& s, bool fwd, int l, int64
     rc.prof->k[K_LVL_FWD_G].bytes += 12.0 * W * vn.count;
   }
   MFBC_CUDA_TRY(cudaMemsetAsync(&s.ctr->work[2], 0, sizeof(uint32_t), st), rc.err);
-  const unsigned ggrid = grid_for_items(nseg, fwd ? kGatherGrid : kBwdGatherGrid);
+  const unsigned gcap = fwd ? kGatherGrid : kBwdGatherGrid;
+  const int gs = group_size(nseg, (uint64_t)gcap * 8);
+  const unsigned ggrid = grid_for_groups(nseg, gs, gcap);
   if (fwd) {
     if (B)
       PROF(K_LVL_FWD_G, (k_lvl_fwd_gather<true><<<ggrid, 256, 0, st>>>(
                             s.segs, &s.ctr->work[1], s.prow, s.pmask, nb, s.sv, &s.ctr->flags, &s.ctr->work[2],
-                            B + K_LVL_FWD_G, s.ctr->stat, vn)));
+                            B + K_LVL_FWD_G, s.ctr->stat, vn, gs)));
     else
       PROF(K_LVL_FWD_G, (k_lvl_fwd_gather<false><<<ggrid, 256, 0, st>>>(
                             s.segs, &s.ctr->work[1], s.prow, s.pmask, nb, s.sv, &s.ctr->flags, &s.ctr->work[2],
-                            nullptr, s.ctr->stat, vn)));
+                            nullptr, s.ctr->stat, vn, gs)));
   } else {
     if (B)
       PROF(K_LVL_BWD_G, (k_lvl_bwd_gather<true><<<ggrid, 256, 0, st>>>(
                             s.segs, &s.ctr->work[1], s.prow, s.pmask, nb, W, Fl, g.items_out.hub_of, s.sv, s.zacc,
                             lambda, n, uniform_req, s.quad_req, s.word_req, &s.ctr->work[2], B + K_LVL_BWD_G,
-                            s.ctr->stat)));
+                            s.ctr->stat, gs)));
     else
       PROF(K_LVL_BWD_G, (k_lvl_bwd_gather<false><<<ggrid, 256, 0, st>>>(
                             s.segs, &s.ctr->work[1], s.prow, s.pmask, nb, W, Fl, g.items_out.hub_of, s.sv, s.zacc,
                             lambda, n, uniform_req, s.quad_req, s.word_req, &s.ctr->work[2], nullptr,
-                            s.ctr->stat)));
+                            s.ctr->stat, gs)));
   }
   return MFBC_OK;
 }
@@ -1230,10 +1254,12 @@ mfbc_status level_batch(RunCtx& rc, LevelState& s, const int32_t* d_src_batch, i
   for (int l = L; l >= 1; l--) {
     mfbc_status e = level_round(rc, s, false, l, 0, g.items_out.count, uniform_req, 0, lambda);
     if (e) return e;
-    if (g.items_out.nhub)
-      PROF(K_LVL_HUB, (k_lvl_hub_final<<<grid_for_items(g.items_out.nhub, 152 * 8), LVL_WARPS * 32, 0, st>>>(
+    if (g.items_out.nhub) {
+      const int hc = group_size((uint64_t)g.items_out.nhub, 152ull * 8 * LVL_WARPS);
+      PROF(K_LVL_HUB, (k_lvl_hub_final<<<grid_for_groups(g.items_out.nhub, hc, 152 * 8), LVL_WARPS * 32, 0, st>>>(
                           g.items_out.hubs, g.items_out.nhub, W, nb, Fl(l), Ml(l), s.sv, s.zacc, lambda, n,
-                          uniform_req, s.word_req, B ? B + K_LVL_HUB : nullptr)));
+                          uniform_req, s.word_req, B ? B + K_LVL_HUB : nullptr, hc)));
+    }
     if (bwd_iters) (*bwd_iters)++;
   }
   return MFBC_OK;
