@@ -157,6 +157,10 @@ typedef struct {
                                     for one arrival more than the group has, so each wait runs
                                     out of its (shortened, 20 ms) budget and the call returns
                                     MFBC_ERR_TIMEOUT; nothing faults and the context stays usable */
+#define MFBC_OPT_TEST_SMALL_ROUNDS 16u  /* test hook, level kernels: product rounds get pair and
+                                    segment buffers of 2^16 slots, so their rounds overflow and
+                                    are redone over halves of the work items (the path a graph
+                                    beyond 2^31 pairs per round takes); results are unchanged */
 
 /* Build a device-resident graph from HOST compressed-row arrays (Sec. 2.1:
  * A(i,j) = w(i,j) for (i,j) in E; the paper's Tensor::write of the input,

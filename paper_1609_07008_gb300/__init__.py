@@ -37,6 +37,7 @@ PATH_AUTO, PATH_GENERAL, PATH_LEVEL, PATH_DIST, PATH_SMALL = 0, 1, 2, 3, 4
 MFBC_OPT_COUNT_BYTES = 1
 MFBC_OPT_KEEP_ORDER = 2
 MFBC_OPT_TEST_STALL = 4
+MFBC_OPT_TEST_SMALL_ROUNDS = 16
 MFBC_OPT_ACCUMULATE = 8
 ACCUM_AUTO, ACCUM_ATOMIC, ACCUM_SEGMENTED, ACCUM_HASH = 0, 1, 2, 3
 INF = np.iinfo(np.int32).max
@@ -171,11 +172,11 @@ def _stream_handle(stream) -> ctypes.c_void_p | None:
 
 
 def _options(n_b, path, stream, workspace, warn, profile, count_bytes=False, keep_order=False,
-             test_stall=False, accumulator=ACCUM_AUTO) -> Options:
+             test_stall=False, accumulator=ACCUM_AUTO, test_small_rounds=False) -> Options:
     o = Options()
     o.accumulator = int(accumulator)
     o.flags = (MFBC_OPT_COUNT_BYTES if count_bytes else 0) | (MFBC_OPT_KEEP_ORDER if keep_order else 0) | \
-        (MFBC_OPT_TEST_STALL if test_stall else 0)
+        (MFBC_OPT_TEST_STALL if test_stall else 0) | (MFBC_OPT_TEST_SMALL_ROUNDS if test_small_rounds else 0)
     o.n_b = int(n_b)
     o.path = int(path)
     o.stream = _stream_handle(stream)
@@ -250,16 +251,19 @@ class Graph:
     # ----------------------------------------------------------- entry points
     def bc(self, sources, *, n_b: int = 0, path: int = PATH_AUTO, out=None, stream=None, workspace=None,
            profile: bool = False, count_bytes: bool = False, keep_order: bool = False,
-           return_warn: bool = False, test_stall: bool = False, accumulator: int = ACCUM_AUTO):
+           return_warn: bool = False, test_stall: bool = False, accumulator: int = ACCUM_AUTO,
+           test_small_rounds: bool = False):
         """Betweenness centrality summed over `sources` (Algorithm 3).
 
         Host (numpy) sources -> numpy lambda via mfbc_bc; torch CUDA sources
         -> torch CUDA lambda via mfbc_bc_device (into `out` when given).
-        test_stall sets the MFBC_OPT_TEST_STALL test hook."""
+        test_stall and test_small_rounds set the MFBC_OPT_TEST_STALL and
+        MFBC_OPT_TEST_SMALL_ROUNDS test hooks."""
         lib = load()
         warn = ctypes.c_uint32(0)
         prof = Profile() if (profile or count_bytes) else None
-        opt = _options(n_b, path, stream, workspace, warn, prof, count_bytes, keep_order, test_stall, accumulator)
+        opt = _options(n_b, path, stream, workspace, warn, prof, count_bytes, keep_order, test_stall, accumulator,
+                       test_small_rounds)
         if _is_torch(sources):
             import torch
             src = sources.to(dtype=torch.int32).contiguous()
@@ -278,7 +282,8 @@ class Graph:
         return res[0] if len(res) == 1 else tuple(res)
 
     def bc_multi(self, source_lists, *, n_b: int = 0, path: int = PATH_AUTO, out=None, stream=None,
-                 workspace=None, profile: bool = False, rows=None, accumulate: bool = False):
+                 workspace=None, profile: bool = False, rows=None, accumulate: bool = False,
+                 test_small_rounds: bool = False):
         """One lambda row per request: `source_lists` is a sequence of torch
         CUDA int tensors (or one concatenated tensor with a host `offsets`
         pair: (sources, offsets)).  Returns a [nreq, n] float64 CUDA tensor
@@ -301,7 +306,7 @@ class Graph:
         nreq = len(off) - 1
         lam = out if out is not None else torch.empty((nreq, self.n), dtype=torch.float64, device=src.device)
         prof = Profile() if profile else None
-        opt = _options(n_b, path, stream, workspace, None, prof)
+        opt = _options(n_b, path, stream, workspace, None, prof, test_small_rounds=test_small_rounds)
         rws = None
         if rows is not None:
             rws = np.ascontiguousarray(rows, dtype=np.int32)
@@ -327,12 +332,14 @@ class Graph:
                 "accumulator": t.accumulator}
 
     def sssp(self, sources, *, n_b: int = 0, path: int = PATH_AUTO, with_sigma: bool = True, stream=None,
-             workspace=None, profile: bool = False, return_warn: bool = False, accumulator: int = ACCUM_AUTO):
+             workspace=None, profile: bool = False, return_warn: bool = False, accumulator: int = ACCUM_AUTO,
+             test_small_rounds: bool = False):
         """MFBF alone (Algorithm 1): (dist [nsrc, n] int32, sigma [nsrc, n] f64 or None)."""
         lib = load()
         warn = ctypes.c_uint32(0)
         prof = Profile() if profile else None
-        opt = _options(n_b, path, stream, workspace, warn, prof, accumulator=accumulator)
+        opt = _options(n_b, path, stream, workspace, warn, prof, accumulator=accumulator,
+                       test_small_rounds=test_small_rounds)
         if _is_torch(sources):
             import torch
             src = sources.to(dtype=torch.int32).contiguous()

@@ -680,6 +680,7 @@ mfbc_status run(mfbc_graph* G, const int32_t* d_src, int32_t nsrc, int mode, dou
   RunCtx rc{&g, R.st, &R.prof, G->h_ctr, &R.err};
   rc.arcs = G->force_arcs ? G->force_arcs : G->tuned_arcs;
   rc.accum = R.opt && R.opt->accumulator ? R.opt->accumulator : G->tuned_accum;
+  rc.small_rounds = R.opt && (R.opt->flags & MFBC_OPT_TEST_SMALL_ROUNDS);
   Carver c(R.ws, R.ws_bytes);
   GeneralState gs;
   LevelState ls;

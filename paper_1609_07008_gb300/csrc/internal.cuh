@@ -77,6 +77,8 @@ constexpr uint32_t FLAG_SIGMA_INEXACT = 2u;  // some sigma_bar >= 2^53 (FP64 out
 constexpr uint32_t FLAG_BAD_SOURCE = 4u;     // mfbc_bc_static: a source id outside [0, n)
 constexpr uint32_t FLAG_COUNT_WRAP = 8u;     // level kernels: a path count reached 2^58 (batch redone)
 constexpr uint32_t FLAG_TIMEOUT = 16u;       // a bounded device-side wait ran out (MFBC_ERR_TIMEOUT)
+constexpr uint32_t FLAG_ROUND_ABORT = 32u;   // level kernels: a round's pair buffers overflowed; the
+                                             // launches queued after it return at once until cleared
 
 // Device-side counters of algorithmic bytes, one slot per kernel id.
 struct Counters {
@@ -85,6 +87,7 @@ struct Counters {
   uint32_t list_count[4];          // frontier / touched list sizes
   uint32_t flags;                  // FLAG_* bits
   uint32_t work[4];                // level kernels: pairs, segments, gather group counter, overflow
+  uint32_t abort_level;            // level kernels: highest MFBr level whose round overflowed
 };
 
 class Profiler {
@@ -246,6 +249,8 @@ struct RunCtx {
   int arcs = 0;
   // general kernels: how a product reduces its candidates (MFBC_ACCUM_*)
   int accum = 0;
+  // level kernels: test hook MFBC_OPT_TEST_SMALL_ROUNDS (small pair buffers)
+  bool small_rounds = false;
 };
 
 // Request of the batch as a whole: r >= 0 when every used word belongs to

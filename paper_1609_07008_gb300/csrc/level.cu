@@ -50,8 +50,8 @@ constexpr int LVL_WARPS = 8;                 // warps per block
 #define MFBC_PAIR_MIN_BLOCKS 4
 #endif
 constexpr unsigned PAIR_GRID = 152u * MFBC_PAIR_MIN_BLOCKS;   // resident blocks of the pair kernels
-constexpr uint32_t PAIR_CHUNK = 1024;        // pair slots a warp reserves at a time
-constexpr uint32_t SEG_CHUNK = 64;           // segment slots a warp reserves at a time
+constexpr uint32_t PAIR_CHUNK = 2048;        // pair slots a warp reserves at a time (> 32 Q = 256)
+constexpr uint32_t SEG_CHUNK = 64;           // segment slots a warp reserves at a time (at most)
 constexpr uint32_t SEG_DUMMY = 0xffffffffu;  // vertex field of a filler segment
 
 size_t level_bytes(const DevGraph& g, int nb, int Lcap, int64_t list_cap) {
@@ -75,18 +75,24 @@ void level_carve(Carver& c, const DevGraph& g, int nb, int Lcap, int64_t list_ca
   s.list_cap = list_cap;
   s.lists = c.take<int32_t>((size_t)list_cap);
   s.zacc = c.take<double>((size_t)(g.items_out.nhub > 0 ? g.items_out.nhub : 1) * nb);
-  // pair / segment buffers of one product round; a round that overflows them
-  // is split over halves of the item range
-  // (each arc gives at most Q pairs and each item at most Q segments per
-  // round, so these caps only bind for graphs beyond 2^31 of either)
+  // pair / segment buffers of one product round, sized so that no round
+  // overflows them unless the 2^31 clamp binds (a round that overflows is
+  // redone over halves of the item range).  A round uses at most Q pairs per
+  // arc and Q segments per item.  Warps reserve slots in chunks, and an
+  // item whose P pairs (at most 32 Q) do not fit the rest of its warp's
+  // chunk leaves that rest unused: each reservation but a warp's first
+  // fills at least C - 32 Q + 1 slots before it wastes at most 32 Q - 1, and
+  // a warp's last chunk may stay almost empty.  Likewise for segments, whose
+  // chunks hold at least 2 Q.
   const int64_t items = std::max(g.items_in.count, g.items_out.count);
   const int64_t Q = std::max(1, s.W / 4);
-  // (warps reserve slots in chunks: the slack covers one partly used chunk
-  // per resident warp of the pair kernels; a round whose abandoned chunk
-  // tails still overflow is split like any other)
   const int64_t warps = (int64_t)PAIR_GRID * LVL_WARPS;
-  s.pair_cap = (uint32_t)std::min<int64_t>(0x7fffffff, std::max<int64_t>(1 << 16, g.nnz * Q) + warps * PAIR_CHUNK);
-  s.seg_cap = (uint32_t)std::min<int64_t>(0x7fffffff, std::max<int64_t>(1 << 16, items * Q) + warps * SEG_CHUNK);
+  const int64_t pmax = 32 * Q, pairs = std::max<int64_t>(1 << 16, g.nnz * Q);
+  const int64_t pair_need = pairs + (pmax - 1) * (warps + pairs / (PAIR_CHUNK - pmax + 1)) + warps * PAIR_CHUNK;
+  const int64_t segs = std::max<int64_t>(1 << 16, items * Q);
+  const int64_t seg_need = segs + (Q - 1) * (warps + segs / (Q + 1)) + warps * (SEG_CHUNK + Q);
+  s.pair_cap = (uint32_t)std::min<int64_t>(0x7fffffff, pair_need);
+  s.seg_cap = (uint32_t)std::min<int64_t>(0x7fffffff, seg_need);
   s.prow = c.take<uint32_t>((size_t)s.pair_cap);
   s.pmask = c.take<uint4>((size_t)s.pair_cap);
   s.segs = c.take<uint4>((size_t)s.seg_cap);
@@ -169,13 +175,41 @@ __global__ void k_lvl_visit(const int32_t* __restrict__ list, uint32_t count, in
 // kernel starts after it), which saves a launch per level.
 struct VisitNext {
   const int32_t* list;       // the next level's vertices
-  uint32_t count;            // 0: no visit here
+  const uint32_t* count;     // their number (device, written by the pair kernel); nullptr: no visit here
+  int64_t cap;               // room of the list (a longer count is clamped; the batch is then redone)
   int W;
   const uint32_t* colmask;
   const uint32_t* Fn;        // the next level's frontier rows
   uint32_t* V;
   uint32_t* full;
 };
+
+// Segments per group when the host left it open (0): the host's rule (see
+// group_size), from the count the pair kernel left on the device.
+__device__ __forceinline__ int seg_group_of(uint32_t nseg, int given) {
+  if (given > 0) return given;
+  int g = 32;
+  const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
+  while (g > 1 && (uint64_t)nseg < (uint64_t)g * warps * 4) g >>= 1;
+  return g;
+}
+
+// An MFBr gather returns at once when its round's pair buffers overflowed
+// (the host redoes the round over halves of the items) or an earlier round
+// of the same sweep did (flags bit FLAG_ROUND_ABORT, kept until the host
+// clears it); the first such gather records its level.  Its round then wrote
+// no value, so the redo starts from a clean state.  (The MFBF gather takes no
+// segment of an overflowed round; the host reads its counters after every
+// level.)
+__device__ __forceinline__ bool round_aborted(const uint32_t* ovf, uint32_t* flags, uint32_t* abort_level,
+                                              int level) {
+  const uint32_t o = *((volatile const uint32_t*)ovf);
+  if (o && blockIdx.x == 0 && threadIdx.x == 0) {
+    atomicOr(flags, FLAG_ROUND_ABORT);
+    atomicMax(abort_level, (uint32_t)level);
+  }
+  return o || (*((volatile const uint32_t*)flags) & FLAG_ROUND_ABORT);
+}
 
 // Per-warp shared memory of the pair kernels.
 struct WarpSmem {
@@ -255,7 +289,7 @@ __device__ __forceinline__ bool emit_quads(const WarpSmem& w, int nm, int32_t v,
                                            const uint32_t* __restrict__ hot, uint32_t* prow, uint4* pmask,
                                            uint4* segs, uint32_t* work,
                                            uint32_t pair_cap, uint32_t seg_cap, SlotCursor& cur,
-                                           unsigned long long* npairs) {
+                                           unsigned long long* npairs, uint32_t seg_chunk) {
   const unsigned lane = lane_id();
   const uint32_t lt = (1u << lane) - 1u;
   int mycnt = 0;
@@ -276,7 +310,7 @@ __device__ __forceinline__ bool emit_quads(const WarpSmem& w, int nm, int32_t v,
     return false;
   if (cur.s + S > cur.se) {
     fill_dummy_segs(segs, cur.s, cur.se);
-    if (!reserve_slots(&work[1], S, SEG_CHUNK, seg_cap, &work[3], cur.s, cur.se)) return false;
+    if (!reserve_slots(&work[1], S, seg_chunk, seg_cap, &work[3], cur.s, cur.se)) return false;
   }
   const uint32_t pb = cur.p, sb = cur.s;
   cur.p += P;
@@ -330,7 +364,7 @@ __global__ void __launch_bounds__(LVL_WARPS * 32, MFBC_PAIR_MIN_BLOCKS) k_lvl_fw
     const uint32_t* __restrict__ Fl, const uint32_t* __restrict__ mem_l, uint32_t* Fn, uint32_t* mem_n,
     int32_t* list_n, uint32_t* count_n, int64_t cap_n, uint32_t* flags, uint32_t* next_group, uint32_t* prow,
     uint4* pmask, uint4* segs, uint32_t* work, uint32_t pair_cap, uint32_t seg_cap, const uint32_t* __restrict__ hot,
-    unsigned long long* bytes, unsigned long long* stat, int ig) {
+    unsigned long long* bytes, unsigned long long* stat, int ig, uint32_t seg_chunk) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   WarpSmem& sm = reinterpret_cast<WarpSmem*>(smem_raw)[threadIdx.x >> 5];
   const unsigned lane = lane_id();
@@ -339,6 +373,7 @@ __global__ void __launch_bounds__(LVL_WARPS * 32, MFBC_PAIR_MIN_BLOCKS) k_lvl_fw
   unsigned long long nbytes = 0, npairs = 0;
   SlotCursor cur;
   int nnew = 0;                                    // entries of sm.newv
+  if (*((volatile const uint32_t*)flags) & FLAG_ROUND_ABORT) return;
   // append sm.newv to the level-(l+1) list with one atomic
   auto flush_new = [&]() {
     uint32_t b = 0;
@@ -420,7 +455,7 @@ __global__ void __launch_bounds__(LVL_WARPS * 32, MFBC_PAIR_MIN_BLOCKS) k_lvl_fw
       const uint32_t cw = __ballot_sync(0xffffffffu, cand != 0u);
       if (!cw) continue;
       emit_quads(sm, nm, v, multi, quads_of_words(cw, Q), Q, hot, prow, pmask, segs, work, pair_cap, seg_cap, cur,
-                 bytes ? &npairs : nullptr);
+                 bytes ? &npairs : nullptr, seg_chunk);
       if ((int)lane < W && cand) {
         if (multi) atomicOr(&Fn[(size_t)v * W + lane], cand);
         else Fn[(size_t)v * W + lane] = cand;
@@ -455,7 +490,7 @@ __global__ void __launch_bounds__(LVL_WARPS * 32, MFBC_PAIR_MIN_BLOCKS) k_lvl_bw
     const int32_t* __restrict__ col, int W, const uint32_t* __restrict__ Fl, const uint32_t* __restrict__ mem_l,
     const uint32_t* __restrict__ Fn, const uint32_t* __restrict__ mem_n, uint32_t* next_group, uint32_t* prow,
     uint4* pmask, uint4* segs, uint32_t* work, uint32_t pair_cap, uint32_t seg_cap, const uint32_t* __restrict__ hot,
-    unsigned long long* bytes, unsigned long long* stat, int ig) {
+    unsigned long long* bytes, unsigned long long* stat, int ig, const uint32_t* flags, uint32_t seg_chunk) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   WarpSmem& sm = reinterpret_cast<WarpSmem*>(smem_raw)[threadIdx.x >> 5];
   const unsigned lane = lane_id();
@@ -463,6 +498,7 @@ __global__ void __launch_bounds__(LVL_WARPS * 32, MFBC_PAIR_MIN_BLOCKS) k_lvl_bw
   const int Q = W / 4;
   unsigned long long nbytes = 0, npairs = 0;
   SlotCursor cur;
+  if (*((volatile const uint32_t*)flags) & FLAG_ROUND_ABORT) return;
   FOR_ITEM_GROUPS(ib, ie, next_group, ig)
     // lane-parallel precheck of the group's items: only rows with a column at level l
     const uint64_t myit = base + lane;
@@ -528,7 +564,7 @@ __global__ void __launch_bounds__(LVL_WARPS * 32, MFBC_PAIR_MIN_BLOCKS) k_lvl_bw
       if (bytes) nbytes += 4ull * W * (nm + 1);
       const uint32_t words = __ballot_sync(0xffffffffu, multi ? any != 0u : Fv != 0u);
       if (words) emit_quads(sm, nm, v, multi, quads_of_words(words, Q), Q, hot, prow, pmask, segs, work, pair_cap,
-                            seg_cap, cur, bytes ? &npairs : nullptr);
+                            seg_cap, cur, bytes ? &npairs : nullptr, seg_chunk);
       __syncwarp();
     }
   }
@@ -732,12 +768,14 @@ template <bool COUNT>
 __global__ void __launch_bounds__(256, MFBC_GATHER_MIN_BLOCKS) k_lvl_fwd_gather(
     const uint4* __restrict__ segs, const uint32_t* nseg_p, const uint32_t* __restrict__ prow,
     const uint4* __restrict__ pmask, int nb, double* svd, uint32_t* flags, uint32_t* next_group,
-    unsigned long long* bytes, unsigned long long* stat, VisitNext vn, int seg_group) {
+    unsigned long long* bytes, unsigned long long* stat, VisitNext vn, int seg_group, const uint32_t* round_ovf) {
   __shared__ GatherSmem gsm[8];
   GatherSmem& gs = gsm[threadIdx.x >> 5];
   uint64_t* sv = reinterpret_cast<uint64_t*>(svd);
   const unsigned lane = lane_id();
-  const uint32_t nseg = *nseg_p;
+  // pair buffers overflowed: no segment is valid (the host redoes the round)
+  const uint32_t nseg = *((volatile const uint32_t*)round_ovf) ? 0u : *nseg_p;
+  seg_group = seg_group_of(nseg, seg_group);
   unsigned long long nvals = 0, nw = 0, nrec = 0;
   uint32_t ovf = 0, big = 0;
   FOR_SEGMENT_GROUPS(nseg, next_group, seg_group)
@@ -778,7 +816,11 @@ __global__ void __launch_bounds__(256, MFBC_GATHER_MIN_BLOCKS) k_lvl_fwd_gather(
   }
   if (__any_sync(0xffffffffu, big != 0u) && lane == 0) atomicOr(flags, FLAG_SIGMA_INEXACT);
   if (__any_sync(0xffffffffu, ovf != 0u) && lane == 0) atomicOr(flags, FLAG_COUNT_WRAP);
-  if (vn.count) visit_rows(vn.list, vn.count, vn.W, vn.colmask, vn.Fn, vn.V, vn.full);
+  // (not after an overflow: the redo's pair kernel must see the old visited rows)
+  if (vn.count && !*((volatile const uint32_t*)round_ovf)) {
+    const uint32_t c = *((volatile const uint32_t*)vn.count);
+    visit_rows(vn.list, (int64_t)c < vn.cap ? c : (uint32_t)vn.cap, vn.W, vn.colmask, vn.Fn, vn.V, vn.full);
+  }
   if (COUNT) {
     for (int o = 16; o; o >>= 1) {
       nvals += __shfl_xor_sync(0xffffffffu, nvals, o);
@@ -837,7 +879,8 @@ __global__ void __launch_bounds__(256, MFBC_BWD_GATHER_MIN_BLOCKS) k_lvl_bwd_gat
     const uint4* __restrict__ pmask, int nb, int W, const uint32_t* __restrict__ Fl,
     const int32_t* __restrict__ hub_of, double* svd, double* zacc, double* lambda, int32_t n, int uniform_req,
     const int32_t* __restrict__ quad_req, const int32_t* __restrict__ word_req, uint32_t* next_group,
-    unsigned long long* bytes, unsigned long long* stat, int seg_group) {
+    unsigned long long* bytes, unsigned long long* stat, int seg_group, const uint32_t* round_ovf, uint32_t* flags,
+    uint32_t* abort_level, int level) {
   __shared__ GatherSmem gsm[8];
   __shared__ FinishSmem fsm[8];
   GatherSmem& gs = gsm[threadIdx.x >> 5];
@@ -845,7 +888,9 @@ __global__ void __launch_bounds__(256, MFBC_BWD_GATHER_MIN_BLOCKS) k_lvl_bwd_gat
   uint64_t* sv = reinterpret_cast<uint64_t*>(svd);
   const unsigned lane = lane_id();
   const uint32_t lt = (1u << lane) - 1u;
+  if (round_aborted(round_ovf, flags, abort_level, level)) return;
   const uint32_t nseg = *nseg_p;
+  seg_group = seg_group_of(nseg, seg_group);
   const int shift = 4 * (int)(lane & 7u);
   unsigned long long nvals = 0, nw = 0, nrec = 0;
   uint32_t ovf = 0;
@@ -924,10 +969,11 @@ __global__ void __launch_bounds__(256, MFBC_BWD_GATHER_MIN_BLOCKS) k_lvl_bwd_gat
 __global__ void __launch_bounds__(LVL_WARPS * 32) k_lvl_hub_final(
     const int32_t* __restrict__ hubs, int32_t nhub, int W, int nb, const uint32_t* __restrict__ Fl,
     const uint32_t* __restrict__ mem_l, double* svd, double* zacc, double* lambda, int32_t n, int uniform_req,
-    const int32_t* __restrict__ word_req, unsigned long long* bytes, int hc) {
+    const int32_t* __restrict__ word_req, unsigned long long* bytes, int hc, const uint32_t* flags) {
   __shared__ uint16_t cols_all[LVL_WARPS][LEVEL_MAX_NB];
   uint16_t* cols = cols_all[threadIdx.x >> 5];
   const unsigned lane = lane_id();
+  if (*((volatile const uint32_t*)flags) & FLAG_ROUND_ABORT) return;   // the level's gather did not run
   const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
   uint64_t* sv = reinterpret_cast<uint64_t*>(svd);
   unsigned long long nbytes = 0;
@@ -1078,13 +1124,25 @@ static thread_local LevelPlan tl_plan;
 static const unsigned kGatherGrid = 152u * MFBC_GATHER_MIN_BLOCKS;   // resident blocks of the gather kernels
 static const unsigned kBwdGatherGrid = 152u * MFBC_BWD_GATHER_MIN_BLOCKS;
 
+static mfbc_status level_round_halves(RunCtx& rc, LevelState& s, bool fwd, int l, int64_t ib, int64_t ie,
+                                      int uniform_req, int64_t off_n, double* lambda);
+
 // One MFBF (fwd) or MFBr product of level l over the items [ib, ie): the pair
-// kernel, a check of the pair buffers, then the gather kernel.  When the
-// buffers overflow the range is split in halves; the pair kernels' side
+// kernel, then the gather kernel.
+//
+// checked = false: both are queued without waiting.  The gather reads the
+// segment count the pair kernel left on the device and does nothing when the
+// pair buffers overflowed (an MFBr gather also sets FLAG_ROUND_ABORT, so the
+// launches queued after it return at once); the host finds out at its next
+// read of the counters and redoes the round checked.
+// checked = true: the host reads the pair kernel's counters first; when the
+// buffers overflowed the range is split in halves.  The pair kernels' side
 // effects (frontier bits, membership, list appends) are idempotent, so a
 // re-run of a range is harmless.
+// visited_next (MFBF): the gather also runs the next level's visit.
 static mfbc_status level_round(RunCtx& rc, LevelState& s, bool fwd, int l, int64_t ib, int64_t ie,
-                               int uniform_req, int64_t off_n, double* lambda, bool* visited_next = nullptr) {
+                               int uniform_req, int64_t off_n, double* lambda, bool checked,
+                               bool* visited_next = nullptr) {
   if (visited_next) *visited_next = false;
   const DevGraph& g = *rc.g;
   const int32_t n = g.n;
@@ -1095,72 +1153,122 @@ static mfbc_status level_round(RunCtx& rc, LevelState& s, bool fwd, int l, int64
   const uint32_t* Ml = s.member + (size_t)l * s.mw;
   uint32_t* Fn = s.F + (size_t)(l + 1) * n * W;
   uint32_t* Mn = s.member + (size_t)(l + 1) * s.mw;
+  // test hook: buffers of 2^16 slots make rounds overflow and split
+  const uint32_t pair_cap = rc.small_rounds ? std::min<uint32_t>(s.pair_cap, 1u << 16) : s.pair_cap;
+  const uint32_t seg_cap = rc.small_rounds ? std::min<uint32_t>(s.seg_cap, 1u << 16) : s.seg_cap;
   MFBC_CUDA_TRY(cudaMemsetAsync(s.ctr->work, 0, sizeof(uint32_t) * 4, st), rc.err);
   MFBC_CUDA_TRY(cudaMemsetAsync(&s.ctr->list_count[2], 0, sizeof(uint32_t), st), rc.err);
   const int ig = group_size((uint64_t)(ie - ib), (uint64_t)PAIR_GRID * LVL_WARPS);
   const unsigned pgrid = grid_for_groups((uint64_t)(ie - ib), ig, PAIR_GRID);
   // row indices u * Q + quad need bit 31 free for the hot-row flag
   const int Qn = std::max(1, W / 4);
+  // segment slots per reservation: with small item groups a warp emits few
+  // segments, and the unused rest of its chunk only adds filler segments that
+  // the gather walks past
+  const uint32_t seg_chunk =
+      ig == 32 ? SEG_CHUNK : std::max<uint32_t>(2u * Qn, std::min<uint32_t>(SEG_CHUNK, 2u * ig * Qn));
   const uint32_t* hot = MFBC_HOT_HINT && (uint64_t)n * (uint64_t)Qn < (1ull << 31) ? g.hot : nullptr;
   if (fwd)
     PROF(K_LVL_FWD, (k_lvl_fwd_pairs<<<pgrid, LVL_WARPS * 32, LVL_SMEM, st>>>(
                         ib, ie, g.items_in.v, g.items_in.beg, g.col_t, W, s.full, s.V, Fl, Ml, Fn, Mn,
                         s.lists + off_n, &s.ctr->list_count[0], s.list_cap - off_n, &s.ctr->flags,
-                        &s.ctr->list_count[2], s.prow, s.pmask, s.segs, s.ctr->work, s.pair_cap, s.seg_cap, hot,
-                        B ? B + K_LVL_FWD : nullptr, s.ctr->stat, ig)));
+                        &s.ctr->list_count[2], s.prow, s.pmask, s.segs, s.ctr->work, pair_cap, seg_cap, hot,
+                        B ? B + K_LVL_FWD : nullptr, s.ctr->stat, ig, seg_chunk)));
   else
     PROF(K_LVL_BWD, (k_lvl_bwd_pairs<<<pgrid, LVL_WARPS * 32, LVL_SMEM, st>>>(
                         ib, ie, g.items_out.v, g.items_out.beg, g.col, W, Fl, Ml, Fn, Mn,
-                        &s.ctr->list_count[2], s.prow, s.pmask, s.segs, s.ctr->work, s.pair_cap, s.seg_cap, hot,
-                        B ? B + K_LVL_BWD : nullptr, s.ctr->stat, ig)));
-  MFBC_CUDA_TRY(cudaMemcpyAsync(rc.h_ctr, s.ctr->list_count, sizeof(uint32_t) * 9, cudaMemcpyDeviceToHost, st), rc.err);
-  MFBC_CUDA_TRY(cudaStreamSynchronize(st), rc.err);
-  rc.prof->drain();
-  if (rc.h_ctr[8]) {
-    rc.prof->k[K_LVL_SPLIT].launches++;          // reported as "level_round_split"
-    if (ie - ib <= 32) {
-      if (rc.err) *rc.err = "level pair buffers cannot hold one group of 32 work items";
-      return MFBC_ERR_OOM;
-    }
-    const int64_t mid = ib + ((ie - ib) / 2 + 31) / 32 * 32;
-    mfbc_status e = level_round(rc, s, fwd, l, ib, mid, uniform_req, off_n, lambda);
-    if (e) return e;
-    return level_round(rc, s, fwd, l, mid, ie, uniform_req, off_n, lambda);
-  }
-  const uint32_t nseg = rc.h_ctr[6];
-  if (!nseg) return MFBC_OK;
-  // the next level's visit rides on this gather when its list is complete
-  // (one round, no list overflow; the count is clamped to the list's room)
-  VisitNext vn{s.lists + off_n, 0u, W, s.colmask, Fn, s.V, s.full};
-  if (fwd && visited_next && !(rc.h_ctr[4] & FLAG_LEVEL_LIST)) {
-    vn.count = (uint32_t)std::min<int64_t>(rc.h_ctr[0], s.list_cap - off_n);
-    *visited_next = true;
-    rc.prof->k[K_LVL_FWD_G].bytes += 12.0 * W * vn.count;
-  }
-  MFBC_CUDA_TRY(cudaMemsetAsync(&s.ctr->work[2], 0, sizeof(uint32_t), st), rc.err);
+                        &s.ctr->list_count[2], s.prow, s.pmask, s.segs, s.ctr->work, pair_cap, seg_cap, hot,
+                        B ? B + K_LVL_BWD : nullptr, s.ctr->stat, ig, &s.ctr->flags, seg_chunk)));
+  // segments per gather group: from the count, which unchecked rounds leave
+  // to the gather (0), checked ones read first
   const unsigned gcap = fwd ? kGatherGrid : kBwdGatherGrid;
-  const int gs = group_size(nseg, (uint64_t)gcap * 8);
-  const unsigned ggrid = grid_for_groups(nseg, gs, gcap);
+  int gs = 0;
+  unsigned ggrid = gcap;
+  if (checked) {
+    MFBC_CUDA_TRY(cudaMemcpyAsync(rc.h_ctr, s.ctr->list_count, sizeof(uint32_t) * 9, cudaMemcpyDeviceToHost, st),
+                  rc.err);
+    MFBC_CUDA_TRY(cudaStreamSynchronize(st), rc.err);
+    rc.prof->drain();
+    if (rc.h_ctr[8]) return level_round_halves(rc, s, fwd, l, ib, ie, uniform_req, off_n, lambda);
+    const uint32_t nseg = rc.h_ctr[6];
+    if (!nseg) return MFBC_OK;
+    gs = group_size(nseg, (uint64_t)gcap * 8);
+    ggrid = grid_for_groups(nseg, gs, gcap);
+  }
+  // the next level's visit rides on this gather (the count is the device's,
+  // clamped to the list's room)
+  VisitNext vn{s.lists + off_n, nullptr, s.list_cap - off_n, W, s.colmask, Fn, s.V, s.full};
+  if (fwd && visited_next) {
+    vn.count = &s.ctr->list_count[0];
+    *visited_next = true;
+  }
+  const uint32_t* ovf = &s.ctr->work[3];
   if (fwd) {
     if (B)
       PROF(K_LVL_FWD_G, (k_lvl_fwd_gather<true><<<ggrid, 256, 0, st>>>(
                             s.segs, &s.ctr->work[1], s.prow, s.pmask, nb, s.sv, &s.ctr->flags, &s.ctr->work[2],
-                            B + K_LVL_FWD_G, s.ctr->stat, vn, gs)));
+                            B + K_LVL_FWD_G, s.ctr->stat, vn, gs, ovf)));
     else
       PROF(K_LVL_FWD_G, (k_lvl_fwd_gather<false><<<ggrid, 256, 0, st>>>(
                             s.segs, &s.ctr->work[1], s.prow, s.pmask, nb, s.sv, &s.ctr->flags, &s.ctr->work[2],
-                            nullptr, s.ctr->stat, vn, gs)));
+                            nullptr, s.ctr->stat, vn, gs, ovf)));
   } else {
     if (B)
       PROF(K_LVL_BWD_G, (k_lvl_bwd_gather<true><<<ggrid, 256, 0, st>>>(
                             s.segs, &s.ctr->work[1], s.prow, s.pmask, nb, W, Fl, g.items_out.hub_of, s.sv, s.zacc,
                             lambda, n, uniform_req, s.quad_req, s.word_req, &s.ctr->work[2], B + K_LVL_BWD_G,
-                            s.ctr->stat, gs)));
+                            s.ctr->stat, gs, ovf, &s.ctr->flags, &s.ctr->abort_level, l)));
     else
       PROF(K_LVL_BWD_G, (k_lvl_bwd_gather<false><<<ggrid, 256, 0, st>>>(
                             s.segs, &s.ctr->work[1], s.prow, s.pmask, nb, W, Fl, g.items_out.hub_of, s.sv, s.zacc,
                             lambda, n, uniform_req, s.quad_req, s.word_req, &s.ctr->work[2], nullptr,
-                            s.ctr->stat, gs)));
+                            s.ctr->stat, gs, ovf, &s.ctr->flags, &s.ctr->abort_level, l)));
+  }
+  return MFBC_OK;
+}
+
+// A round known to overflow its buffers over [ib, ie), redone as checked
+// rounds over the two halves.
+static mfbc_status level_round_halves(RunCtx& rc, LevelState& s, bool fwd, int l, int64_t ib, int64_t ie,
+                                      int uniform_req, int64_t off_n, double* lambda) {
+  rc.prof->k[K_LVL_SPLIT].launches++;          // reported as "level_round_split"
+  if (ie - ib <= 32) {
+    if (rc.err) *rc.err = "level pair buffers cannot hold one group of 32 work items";
+    return MFBC_ERR_OOM;
+  }
+  const int64_t mid = ib + ((ie - ib) / 2 + 31) / 32 * 32;
+  mfbc_status e = level_round(rc, s, fwd, l, ib, mid, uniform_req, off_n, lambda, true);
+  if (e) return e;
+  return level_round(rc, s, fwd, l, mid, ie, uniform_req, off_n, lambda, true);
+}
+
+// Clear every level mask of the state (after a batch stopped at a list that
+// overflowed: rows of vertices missing from the list may hold bits).
+static mfbc_status level_clear_all(RunCtx& rc, LevelState& s) {
+  const size_t n = (size_t)rc.g->n;
+  cudaStream_t st = rc.stream;
+  MFBC_CUDA_TRY(cudaMemsetAsync(s.V, 0, sizeof(uint32_t) * n * s.W, st), rc.err);
+  MFBC_CUDA_TRY(cudaMemsetAsync(s.F, 0, sizeof(uint32_t) * (size_t)s.Lcap * n * s.W, st), rc.err);
+  MFBC_CUDA_TRY(cudaMemsetAsync(s.member, 0, sizeof(uint32_t) * (size_t)s.Lcap * s.mw, st), rc.err);
+  return MFBC_OK;
+}
+
+// One MFBr level: its round (halves: one known to overflow, redone over
+// halves), then the finalisation of its multi-item rows.
+static mfbc_status level_bwd(RunCtx& rc, LevelState& s, int l, int uniform_req, double* lambda, bool checked,
+                             bool halves = false) {
+  const DevGraph& g = *rc.g;
+  unsigned long long* B = rc.prof->count_bytes ? s.ctr->bytes : nullptr;
+  mfbc_status e = halves ? level_round_halves(rc, s, false, l, 0, g.items_out.count, uniform_req, 0, lambda)
+                         : level_round(rc, s, false, l, 0, g.items_out.count, uniform_req, 0, lambda, checked);
+  if (e) return e;
+  if (g.items_out.nhub) {
+    const int hc = group_size((uint64_t)g.items_out.nhub, 152ull * 8 * LVL_WARPS);
+    PROF(K_LVL_HUB, (k_lvl_hub_final<<<grid_for_groups(g.items_out.nhub, hc, 152 * 8), LVL_WARPS * 32, 0,
+                                       rc.stream>>>(
+                        g.items_out.hubs, g.items_out.nhub, s.W, s.nb, s.F + (size_t)l * g.n * s.W,
+                        s.member + (size_t)l * s.mw, s.sv, s.zacc, lambda, g.n, uniform_req, s.word_req,
+                        B ? B + K_LVL_HUB : nullptr, hc, &s.ctr->flags)));
   }
   return MFBC_OK;
 }
@@ -1172,7 +1280,6 @@ mfbc_status level_batch(RunCtx& rc, LevelState& s, const int32_t* d_src_batch, i
   const int32_t n = g.n;
   const int nb = s.nb, W = s.W;
   cudaStream_t st = rc.stream;
-  unsigned long long* B = rc.prof->count_bytes ? s.ctr->bytes : nullptr;
   *levels_exceeded = false;
   *levels_out = -1;
   if (n == 0) return MFBC_OK;
@@ -1202,6 +1309,7 @@ mfbc_status level_batch(RunCtx& rc, LevelState& s, const int32_t* d_src_batch, i
     }
   }
   MFBC_CUDA_TRY(cudaMemsetAsync(s.ctr->list_count, 0, sizeof(uint32_t) * 4, st), rc.err);
+  MFBC_CUDA_TRY(cudaMemsetAsync(&s.ctr->abort_level, 0, sizeof(uint32_t), st), rc.err);
   MFBC_CUDA_TRY(cudaMemsetAsync(s.full, 0, sizeof(uint32_t) * s.mw, st), rc.err);
   if (g.items_in.nhub)
     PROF(K_FILL, (k_lvl_zero_hubs<<<152 * 4, 256, 0, st>>>(g.items_in.hubs, g.items_in.nhub, nb, s.sv)));
@@ -1214,8 +1322,9 @@ mfbc_status level_batch(RunCtx& rc, LevelState& s, const int32_t* d_src_batch, i
   P.off.assign(1, 0);
   P.cnt.assign(1, rc.h_ctr[0]);
   auto Fl = [&](int l) { return s.F + (size_t)l * n * W; };
-  auto Ml = [&](int l) { return s.member + (size_t)l * s.mw; };
 
+  // MFBF: one host read of the counters per level (the next level's size,
+  // which ends the loop when it is 0, and the flags)
   int L = 0;
   bool visited = false;                  // level l's visit ran inside the previous gather
   for (int l = 0;; l++) {
@@ -1228,20 +1337,35 @@ mfbc_status level_batch(RunCtx& rc, LevelState& s, const int32_t* d_src_batch, i
     if (l + 1 >= s.Lcap) { *levels_exceeded = true; level_reset(rc, s, l); return MFBC_ERR_NO_CONVERGENCE; }
     const int64_t off_n = P.off[l] + cl;
     MFBC_CUDA_TRY(cudaMemsetAsync(&s.ctr->list_count[0], 0, sizeof(uint32_t), st), rc.err);
-    mfbc_status e = level_round(rc, s, true, l, 0, g.items_in.count, uniform_req, off_n, nullptr, &visited);
+    mfbc_status e = level_round(rc, s, true, l, 0, g.items_in.count, uniform_req, off_n, nullptr, false, &visited);
     if (e) return e;
-    MFBC_CUDA_TRY(cudaMemcpyAsync(rc.h_ctr, s.ctr->list_count, sizeof(uint32_t) * 5, cudaMemcpyDeviceToHost, st), rc.err);
+    MFBC_CUDA_TRY(cudaMemcpyAsync(rc.h_ctr, s.ctr->list_count, sizeof(uint32_t) * 9, cudaMemcpyDeviceToHost, st), rc.err);
     MFBC_CUDA_TRY(cudaStreamSynchronize(st), rc.err);
     rc.prof->drain();
+    if (rc.h_ctr[8]) {
+      // the pair buffers overflowed: neither the gather nor the visit ran;
+      // redo the round checked (split over halves of the items)
+      k_clear_flag_bits<<<1, 1, 0, st>>>(&s.ctr->flags, FLAG_ROUND_ABORT);
+      e = level_round_halves(rc, s, true, l, 0, g.items_in.count, uniform_req, off_n, nullptr);
+      if (e) return e;
+      visited = false;
+      MFBC_CUDA_TRY(cudaMemcpyAsync(rc.h_ctr, s.ctr->list_count, sizeof(uint32_t) * 5, cudaMemcpyDeviceToHost, st),
+                    rc.err);
+      MFBC_CUDA_TRY(cudaStreamSynchronize(st), rc.err);
+      rc.prof->drain();
+    }
     if (rc.h_ctr[4] & (FLAG_LEVEL_LIST | FLAG_COUNT_WRAP)) {
       // list capacity exceeded (bit 0) or a path count passed 2^64 (bit 3):
-      // the general kernels redo this batch
+      // the general kernels redo this batch; rows of vertices missing from
+      // the overflowed list may hold bits, so every mask is cleared
       k_clear_flag_bits<<<1, 1, 0, st>>>(&s.ctr->flags, FLAG_LEVEL_LIST | FLAG_COUNT_WRAP);
       *levels_exceeded = true;
-      level_reset(rc, s, l + 1);
+      e = level_clear_all(rc, s);
+      if (e) return e;
       return MFBC_ERR_NO_CONVERGENCE;
     }
     const uint32_t cn = rc.h_ctr[0];
+    if (visited) rc.prof->k[K_LVL_FWD_G].bytes += 12.0 * W * cn;
     P.off.push_back(off_n);
     P.cnt.push_back(cn);
     if (fwd_iters) (*fwd_iters)++;
@@ -1250,17 +1374,27 @@ mfbc_status level_batch(RunCtx& rc, LevelState& s, const int32_t* d_src_batch, i
   *levels_out = L;
   if (!backward) return MFBC_OK;
 
-  // MFBr over levels L .. 1 (level L+1 is empty and all-zero)
+  // MFBr over levels L .. 1 (level L+1 is empty and all-zero), queued
+  // without waiting; one read of the flags at the end.  If a round's pair
+  // buffers overflowed, the sweep stopped there (every later launch returned
+  // at once) and resumes from that level with checked rounds.
   for (int l = L; l >= 1; l--) {
-    mfbc_status e = level_round(rc, s, false, l, 0, g.items_out.count, uniform_req, 0, lambda);
+    mfbc_status e = level_bwd(rc, s, l, uniform_req, lambda, false);
     if (e) return e;
-    if (g.items_out.nhub) {
-      const int hc = group_size((uint64_t)g.items_out.nhub, 152ull * 8 * LVL_WARPS);
-      PROF(K_LVL_HUB, (k_lvl_hub_final<<<grid_for_groups(g.items_out.nhub, hc, 152 * 8), LVL_WARPS * 32, 0, st>>>(
-                          g.items_out.hubs, g.items_out.nhub, W, nb, Fl(l), Ml(l), s.sv, s.zacc, lambda, n,
-                          uniform_req, s.word_req, B ? B + K_LVL_HUB : nullptr, hc)));
-    }
     if (bwd_iters) (*bwd_iters)++;
+  }
+  MFBC_CUDA_TRY(cudaMemcpyAsync(rc.h_ctr, &s.ctr->flags, sizeof(uint32_t), cudaMemcpyDeviceToHost, st), rc.err);
+  MFBC_CUDA_TRY(cudaMemcpyAsync(rc.h_ctr + 1, &s.ctr->abort_level, sizeof(uint32_t), cudaMemcpyDeviceToHost, st),
+                rc.err);
+  MFBC_CUDA_TRY(cudaStreamSynchronize(st), rc.err);
+  rc.prof->drain();
+  if (rc.h_ctr[0] & FLAG_ROUND_ABORT) {
+    const int l0 = (int)rc.h_ctr[1];
+    k_clear_flag_bits<<<1, 1, 0, st>>>(&s.ctr->flags, FLAG_ROUND_ABORT);
+    for (int l = l0; l >= 1; l--) {
+      mfbc_status e = level_bwd(rc, s, l, uniform_req, lambda, true, l == l0);
+      if (e) return e;
+    }
   }
   return MFBC_OK;
 }

@@ -35,6 +35,23 @@ def test_header_declares_the_boundary():
         assert required in names
 
 
+def test_binding_constants_match_the_header():
+    # every MFBC_* constant the binding names has the header's value
+    text = open(HEADER).read()
+    defs = {k: int(v.rstrip("uU"), 0) for k, v in re.findall(r"#define\s+(MFBC_\w+)\s+(0x[0-9a-fA-F]+u?|\d+u?)\b", text)}
+    aliases = {"PATH_": "MFBC_PATH_", "ACCUM_": "MFBC_ACCUM_"}
+    checked = 0
+    for name in dir(mfbc):
+        hname = name
+        for short, full in aliases.items():
+            if name.startswith(short):
+                hname = full + name[len(short):]
+        if hname in defs:
+            assert getattr(mfbc, name) == defs[hname], f"{name} = {getattr(mfbc, name)}, header {defs[hname]}"
+            checked += 1
+    assert checked >= 15
+
+
 def test_every_declared_symbol_is_exported(lib):
     raw = ctypes.CDLL(mbuild.LIB)
     for name in declared_functions():
