@@ -179,6 +179,41 @@ mfbc_status graph_build(int32_t n, int64_t nnz, const int64_t* h_rowptr, const i
     unsigned blocks = (unsigned)std::min<int64_t>(((int64_t)n + 7) / 8, 152 * 32);
     k_check_arcs<<<blocks, 256, 0, st>>>(n, g->rowptr, g->col, g->w, !g->directed, d_f);
   }
+  // While the GPU checks the arcs, the host prepares what depends on the
+  // (already checked) row pointers alone; the result is read further down.
+  // host copy of the row pointers for the work-item lists
+  std::vector<int64_t> rp(h_rowptr, h_rowptr + (size_t)n + 1);
+  std::vector<uint32_t> hot(((size_t)n + 31) / 32 + 1, 0u);
+  {
+    // landmarks for source ordering: the highest out-degree vertices
+    // (degree descending, then id), isolated vertices excluded
+    std::vector<int32_t> ids;
+    ids.reserve((size_t)n);
+    for (int32_t v = 0; v < n; v++) {
+      if (rp[v + 1] > rp[v]) ids.push_back(v);
+      g->max_deg = std::max<int64_t>(g->max_deg, rp[v + 1] - rp[v]);
+    }
+    // the HOT_ROWS highest degrees also mark the rows the level gathers ask
+    // the L2 to keep (their values are read along most DAG arcs)
+    const size_t k = std::min<size_t>(ids.size(), (size_t)std::max(ORDER_LANDMARKS, HOT_ROWS));
+    auto higher = [&](int32_t a, int32_t b) {
+      const int64_t da = rp[a + 1] - rp[a], db = rp[b + 1] - rp[b];
+      return da != db ? da > db : a < b;
+    };
+    std::nth_element(ids.begin(), ids.begin() + k, ids.end(), higher);
+    std::sort(ids.begin(), ids.begin() + k, higher);
+    g->landmarks.assign(ids.begin(), ids.begin() + std::min<size_t>(k, (size_t)ORDER_LANDMARKS));
+    for (size_t i = 0; i < std::min<size_t>(k, (size_t)HOT_ROWS); i++) hot[(size_t)ids[i] >> 5] |= 1u << (ids[i] & 31);
+    TRY(dev_alloc(g, &g->hot, hot.size(), err));
+    MFBC_CUDA_TRY(cudaMemcpyAsync(g->hot, hot.data(), sizeof(uint32_t) * hot.size(), cudaMemcpyHostToDevice, st), err);
+  }
+  if (!g->directed) {
+    g->max_in_deg = g->max_deg;
+    TRY(build_items(g, rp, &g->items_in, false, st, err));      // (waits for the stream)
+    g->items_out = g->items_in;
+    TRY(upload_hot_targets(g, rp, &g->hot_in, st, err));
+    g->hot_out = g->hot_in;
+  }
   MFBC_CUDA_TRY(cudaMemcpyAsync(&f, d_f, sizeof(f), cudaMemcpyDeviceToHost, st), err);
   MFBC_CUDA_TRY(cudaStreamSynchronize(st), err);
   MFBC_CUDA_TRY(cudaGetLastError(), err);
@@ -194,32 +229,6 @@ mfbc_status graph_build(int32_t n, int64_t nnz, const int64_t* h_rowptr, const i
   }
   g->unit = !f.non_unit;
   if (g->unit && g->w) { g->w = nullptr; }   // all ones: treat as unweighted (array still owned)
-
-  // host copy of the row pointers for the work-item lists
-  std::vector<int64_t> rp(h_rowptr, h_rowptr + (size_t)n + 1);
-  {
-    // landmarks for source ordering: the highest out-degree vertices
-    // (degree descending, then id), isolated vertices excluded
-    std::vector<int32_t> ids;
-    ids.reserve((size_t)n);
-    for (int32_t v = 0; v < n; v++) {
-      if (rp[v + 1] > rp[v]) ids.push_back(v);
-      g->max_deg = std::max<int64_t>(g->max_deg, rp[v + 1] - rp[v]);
-    }
-    // the HOT_ROWS highest degrees also mark the rows the level gathers ask
-    // the L2 to keep (their values are read along most DAG arcs)
-    const size_t k = std::min<size_t>(ids.size(), (size_t)std::max(ORDER_LANDMARKS, HOT_ROWS));
-    std::partial_sort(ids.begin(), ids.begin() + k, ids.end(), [&](int32_t a, int32_t b) {
-      const int64_t da = rp[a + 1] - rp[a], db = rp[b + 1] - rp[b];
-      return da != db ? da > db : a < b;
-    });
-    g->landmarks.assign(ids.begin(), ids.begin() + std::min<size_t>(k, (size_t)ORDER_LANDMARKS));
-    std::vector<uint32_t> hot(((size_t)n + 31) / 32 + 1, 0u);
-    for (size_t i = 0; i < std::min<size_t>(k, (size_t)HOT_ROWS); i++) hot[(size_t)ids[i] >> 5] |= 1u << (ids[i] & 31);
-    TRY(dev_alloc(g, &g->hot, hot.size(), err));
-    MFBC_CUDA_TRY(cudaMemcpyAsync(g->hot, hot.data(), sizeof(uint32_t) * hot.size(), cudaMemcpyHostToDevice, st), err);
-    MFBC_CUDA_TRY(cudaStreamSynchronize(st), err);
-  }
   if (g->directed) {
     // A^T by a stable counting sort on the host: rows of A^T are sorted by
     // source vertex, so the transposed graph is deterministic.
@@ -249,14 +258,9 @@ mfbc_status graph_build(int32_t n, int64_t nnz, const int64_t* h_rowptr, const i
     TRY(upload_hot_targets(g, rpt, &g->hot_in, st, err));
     TRY(upload_hot_targets(g, rp, &g->hot_out, st, err));
   } else {
-    g->max_in_deg = g->max_deg;
     g->rowptr_t = g->rowptr;
     g->col_t = g->col;
     g->w_t = g->w;
-    TRY(build_items(g, rp, &g->items_in, false, st, err));
-    g->items_out = g->items_in;
-    TRY(upload_hot_targets(g, rp, &g->hot_in, st, err));
-    g->hot_out = g->hot_in;
   }
   return MFBC_OK;
 }
