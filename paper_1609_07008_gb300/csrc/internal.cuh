@@ -88,6 +88,7 @@ struct Counters {
   uint32_t flags;                  // FLAG_* bits
   uint32_t work[4];                // level kernels: pairs, segments, gather group counter, overflow
   uint32_t abort_level;            // level kernels: highest MFBr level whose round overflowed
+  uint32_t visit_count;            // level kernels: vertices of the next level's visit (0 after an overflow)
 };
 
 class Profiler {

@@ -194,21 +194,23 @@ __device__ __forceinline__ int seg_group_of(uint32_t nseg, int given) {
   return g;
 }
 
-// An MFBr gather returns at once when its round's pair buffers overflowed
-// (the host redoes the round over halves of the items) or an earlier round
-// of the same sweep did (flags bit FLAG_ROUND_ABORT, kept until the host
-// clears it); the first such gather records its level.  Its round then wrote
-// no value, so the redo starts from a clean state.  (The MFBF gather takes no
-// segment of an overflowed round; the host reads its counters after every
-// level.)
-__device__ __forceinline__ bool round_aborted(const uint32_t* ovf, uint32_t* flags, uint32_t* abort_level,
-                                              int level) {
-  const uint32_t o = *((volatile const uint32_t*)ovf);
-  if (o && blockIdx.x == 0 && threadIdx.x == 0) {
+// Between the pair kernel and the gather of a round queued without a host
+// read (one thread): when the pair buffers overflowed (work[3]), or an earlier
+// round of the same MFBr sweep did (flags bit FLAG_ROUND_ABORT, kept until the
+// host clears it), the gather is given no segment and the MFBF gather no
+// visit; an MFBr overflow sets the flag and records its level.  The host
+// finds the overflow at its next read of the counters and redoes the round
+// over halves of the items; the skipped round wrote nothing.
+__global__ void k_lvl_round_gate(uint32_t* work, const uint32_t* list_count, uint32_t* flags, uint32_t* abort_level,
+                                 uint32_t* visit_count, int level, int bwd) {
+  const bool ovf = work[3] != 0u;
+  if (ovf && bwd) {
     atomicOr(flags, FLAG_ROUND_ABORT);
     atomicMax(abort_level, (uint32_t)level);
   }
-  return o || (*((volatile const uint32_t*)flags) & FLAG_ROUND_ABORT);
+  const bool skip = ovf || (*flags & FLAG_ROUND_ABORT);
+  if (skip) work[1] = 0u;
+  *visit_count = skip ? 0u : *list_count;
 }
 
 // Per-warp shared memory of the pair kernels.
@@ -764,21 +766,20 @@ __device__ __forceinline__ void gather_group(const uint4& myseg, int nin, const 
 // MFBF gather of level l: sigma_bar(s,v) = sum over the segment's pairs
 // (exact 64-bit integers).  flags: bit 1 some sigma_bar >= 2^53, bit 3 a sum
 // passed 2^64 (the batch is then recomputed by the general kernels).
-template <bool COUNT>
+template <bool COUNT, bool G32>
 __global__ void __launch_bounds__(256, MFBC_GATHER_MIN_BLOCKS) k_lvl_fwd_gather(
     const uint4* __restrict__ segs, const uint32_t* nseg_p, const uint32_t* __restrict__ prow,
     const uint4* __restrict__ pmask, int nb, double* svd, uint32_t* flags, uint32_t* next_group,
-    unsigned long long* bytes, unsigned long long* stat, VisitNext vn, int seg_group, const uint32_t* round_ovf) {
+    unsigned long long* bytes, unsigned long long* stat, VisitNext vn, int seg_group) {
   __shared__ GatherSmem gsm[8];
   GatherSmem& gs = gsm[threadIdx.x >> 5];
   uint64_t* sv = reinterpret_cast<uint64_t*>(svd);
   const unsigned lane = lane_id();
-  // pair buffers overflowed: no segment is valid (the host redoes the round)
-  const uint32_t nseg = *((volatile const uint32_t*)round_ovf) ? 0u : *nseg_p;
-  seg_group = seg_group_of(nseg, seg_group);
+  const uint32_t nseg = *nseg_p;
+  if (!G32) seg_group = seg_group_of(nseg, seg_group);
   unsigned long long nvals = 0, nw = 0, nrec = 0;
   uint32_t ovf = 0, big = 0;
-  FOR_SEGMENT_GROUPS(nseg, next_group, seg_group)
+  FOR_SEGMENT_GROUPS(nseg, next_group, G32 ? 32 : seg_group)
     gather_group<COUNT, true>(myseg, nin, prow, pmask, gs, sv, nvals, nrec, ovf,
         [&](int k, uint64_t a0, uint64_t a1, uint64_t a2, uint64_t a3, float, float, float, float, float, float,
             float, float, uint32_t cs) {
@@ -816,8 +817,8 @@ __global__ void __launch_bounds__(256, MFBC_GATHER_MIN_BLOCKS) k_lvl_fwd_gather(
   }
   if (__any_sync(0xffffffffu, big != 0u) && lane == 0) atomicOr(flags, FLAG_SIGMA_INEXACT);
   if (__any_sync(0xffffffffu, ovf != 0u) && lane == 0) atomicOr(flags, FLAG_COUNT_WRAP);
-  // (not after an overflow: the redo's pair kernel must see the old visited rows)
-  if (vn.count && !*((volatile const uint32_t*)round_ovf)) {
+  // (the gate's count: 0 after an overflow, whose redo must see the old visited rows)
+  if (vn.count) {
     const uint32_t c = *((volatile const uint32_t*)vn.count);
     visit_rows(vn.list, (int64_t)c < vn.cap ? c : (uint32_t)vn.cap, vn.W, vn.colmask, vn.Fn, vn.V, vn.full);
   }
@@ -873,14 +874,13 @@ __device__ __noinline__ int finish_mixed(const FinishSmem& fm, int total, uint64
 // the row's FP64 accumulator.  Only the columns of v's level-l frontier are
 // finalised (about one in six of the quad on R-MAT inputs), so they are
 // first compacted through shared memory and then finalised one per lane.
-template <bool COUNT>
+template <bool COUNT, bool G32>
 __global__ void __launch_bounds__(256, MFBC_BWD_GATHER_MIN_BLOCKS) k_lvl_bwd_gather(
     const uint4* __restrict__ segs, const uint32_t* nseg_p, const uint32_t* __restrict__ prow,
     const uint4* __restrict__ pmask, int nb, int W, const uint32_t* __restrict__ Fl,
     const int32_t* __restrict__ hub_of, double* svd, double* zacc, double* lambda, int32_t n, int uniform_req,
     const int32_t* __restrict__ quad_req, const int32_t* __restrict__ word_req, uint32_t* next_group,
-    unsigned long long* bytes, unsigned long long* stat, int seg_group, const uint32_t* round_ovf, uint32_t* flags,
-    uint32_t* abort_level, int level) {
+    unsigned long long* bytes, unsigned long long* stat, int seg_group) {
   __shared__ GatherSmem gsm[8];
   __shared__ FinishSmem fsm[8];
   GatherSmem& gs = gsm[threadIdx.x >> 5];
@@ -888,13 +888,12 @@ __global__ void __launch_bounds__(256, MFBC_BWD_GATHER_MIN_BLOCKS) k_lvl_bwd_gat
   uint64_t* sv = reinterpret_cast<uint64_t*>(svd);
   const unsigned lane = lane_id();
   const uint32_t lt = (1u << lane) - 1u;
-  if (round_aborted(round_ovf, flags, abort_level, level)) return;
   const uint32_t nseg = *nseg_p;
-  seg_group = seg_group_of(nseg, seg_group);
+  if (!G32) seg_group = seg_group_of(nseg, seg_group);
   const int shift = 4 * (int)(lane & 7u);
   unsigned long long nvals = 0, nw = 0, nrec = 0;
   uint32_t ovf = 0;
-  FOR_SEGMENT_GROUPS(nseg, next_group, seg_group)
+  FOR_SEGMENT_GROUPS(nseg, next_group, G32 ? 32 : seg_group)
     auto finish = [&](int k, uint64_t, uint64_t, uint64_t, uint64_t, float s0, float s1, float s2, float s3, float c0,
                       float c1, float c2, float c3, uint32_t) {
       const int32_t v = (int32_t)__shfl_sync(0xffffffffu, myseg.x, k);
@@ -1130,11 +1129,12 @@ static mfbc_status level_round_halves(RunCtx& rc, LevelState& s, bool fwd, int l
 // One MFBF (fwd) or MFBr product of level l over the items [ib, ie): the pair
 // kernel, then the gather kernel.
 //
-// checked = false: both are queued without waiting.  The gather reads the
-// segment count the pair kernel left on the device and does nothing when the
-// pair buffers overflowed (an MFBr gather also sets FLAG_ROUND_ABORT, so the
-// launches queued after it return at once); the host finds out at its next
-// read of the counters and redoes the round checked.
+// checked = false: both are queued without waiting, with a one-thread gate
+// between them.  The gather reads the segment count the pair kernel left on
+// the device, which the gate sets to 0 when the pair buffers overflowed (an
+// MFBr overflow also sets FLAG_ROUND_ABORT, so the launches queued after it
+// in the sweep do nothing); the host finds out at its next read of the
+// counters and redoes the round over halves.
 // checked = true: the host reads the pair kernel's counters first; when the
 // buffers overflowed the range is split in halves.  The pair kernels' side
 // effects (frontier bits, membership, list appends) are idempotent, so a
@@ -1195,35 +1195,45 @@ static mfbc_status level_round(RunCtx& rc, LevelState& s, bool fwd, int l, int64
     gs = group_size(nseg, (uint64_t)gcap * 8);
     ggrid = grid_for_groups(nseg, gs, gcap);
   }
-  // the next level's visit rides on this gather (the count is the device's,
+  if (!checked)
+    k_lvl_round_gate<<<1, 1, 0, st>>>(s.ctr->work, &s.ctr->list_count[0], &s.ctr->flags, &s.ctr->abort_level,
+                                      &s.ctr->visit_count, l, fwd ? 0 : 1);
+  // the next level's visit rides on this gather (the count is the gate's,
   // clamped to the list's room)
   VisitNext vn{s.lists + off_n, nullptr, s.list_cap - off_n, W, s.colmask, Fn, s.V, s.full};
-  if (fwd && visited_next) {
-    vn.count = &s.ctr->list_count[0];
+  if (fwd && visited_next && !checked) {
+    vn.count = &s.ctr->visit_count;
     *visited_next = true;
   }
-  const uint32_t* ovf = &s.ctr->work[3];
+  // groups of 32 segments compile to constants (G32): taken when the round
+  // has that many segments (checked) or the graph is large enough that its
+  // wide levels do (unchecked: a quad per item and quad is at least 8x the
+  // segments that 32 per group need)
+  const int64_t items = fwd ? g.items_in.count : g.items_out.count;
+  const bool g32 = checked ? gs == 32 : (uint64_t)items * (uint64_t)Qn >= 8ull * 32 * 4 * gcap * 8;
+#define GATHER_LAUNCH(kern, C, ...)                                                   \
+  do {                                                                                \
+    if (g32) kern<C, true><<<ggrid, 256, 0, st>>>(__VA_ARGS__);                       \
+    else kern<C, false><<<ggrid, 256, 0, st>>>(__VA_ARGS__);                          \
+  } while (0)
   if (fwd) {
     if (B)
-      PROF(K_LVL_FWD_G, (k_lvl_fwd_gather<true><<<ggrid, 256, 0, st>>>(
-                            s.segs, &s.ctr->work[1], s.prow, s.pmask, nb, s.sv, &s.ctr->flags, &s.ctr->work[2],
-                            B + K_LVL_FWD_G, s.ctr->stat, vn, gs, ovf)));
+      PROF(K_LVL_FWD_G, GATHER_LAUNCH(k_lvl_fwd_gather, true, s.segs, &s.ctr->work[1], s.prow, s.pmask, nb, s.sv,
+                                      &s.ctr->flags, &s.ctr->work[2], B + K_LVL_FWD_G, s.ctr->stat, vn, gs));
     else
-      PROF(K_LVL_FWD_G, (k_lvl_fwd_gather<false><<<ggrid, 256, 0, st>>>(
-                            s.segs, &s.ctr->work[1], s.prow, s.pmask, nb, s.sv, &s.ctr->flags, &s.ctr->work[2],
-                            nullptr, s.ctr->stat, vn, gs, ovf)));
+      PROF(K_LVL_FWD_G, GATHER_LAUNCH(k_lvl_fwd_gather, false, s.segs, &s.ctr->work[1], s.prow, s.pmask, nb, s.sv,
+                                      &s.ctr->flags, &s.ctr->work[2], nullptr, s.ctr->stat, vn, gs));
   } else {
     if (B)
-      PROF(K_LVL_BWD_G, (k_lvl_bwd_gather<true><<<ggrid, 256, 0, st>>>(
-                            s.segs, &s.ctr->work[1], s.prow, s.pmask, nb, W, Fl, g.items_out.hub_of, s.sv, s.zacc,
-                            lambda, n, uniform_req, s.quad_req, s.word_req, &s.ctr->work[2], B + K_LVL_BWD_G,
-                            s.ctr->stat, gs, ovf, &s.ctr->flags, &s.ctr->abort_level, l)));
+      PROF(K_LVL_BWD_G, GATHER_LAUNCH(k_lvl_bwd_gather, true, s.segs, &s.ctr->work[1], s.prow, s.pmask, nb, W, Fl,
+                                      g.items_out.hub_of, s.sv, s.zacc, lambda, n, uniform_req, s.quad_req,
+                                      s.word_req, &s.ctr->work[2], B + K_LVL_BWD_G, s.ctr->stat, gs));
     else
-      PROF(K_LVL_BWD_G, (k_lvl_bwd_gather<false><<<ggrid, 256, 0, st>>>(
-                            s.segs, &s.ctr->work[1], s.prow, s.pmask, nb, W, Fl, g.items_out.hub_of, s.sv, s.zacc,
-                            lambda, n, uniform_req, s.quad_req, s.word_req, &s.ctr->work[2], nullptr,
-                            s.ctr->stat, gs, ovf, &s.ctr->flags, &s.ctr->abort_level, l)));
+      PROF(K_LVL_BWD_G, GATHER_LAUNCH(k_lvl_bwd_gather, false, s.segs, &s.ctr->work[1], s.prow, s.pmask, nb, W, Fl,
+                                      g.items_out.hub_of, s.sv, s.zacc, lambda, n, uniform_req, s.quad_req,
+                                      s.word_req, &s.ctr->work[2], nullptr, s.ctr->stat, gs));
   }
+#undef GATHER_LAUNCH
   return MFBC_OK;
 }
 
