@@ -114,8 +114,8 @@ def traffic_per_launch(workload, kernel, alg_bytes):
     return t["per_alg_byte"] * alg_bytes
 
 
-def survey_model(g, srcs, prof_bytes, step_s, peak_gbs):
-    """The survey's per-TEP byte model for MFBF + counters + MFBr + lambda
+def product_byte_model(g, srcs, prof_bytes, step_s, peak_gbs):
+    """A per-TEP byte model of the paper's products for MFBF + counters + MFBr + lambda
     (unweighted graphs, 4-byte arcs).  It is an algorithmic-byte model of the
     paper's products with stored distances and counters, not a ceiling of the
     level kernels: those replace the 4-byte distance check per arc visit by
@@ -649,7 +649,7 @@ def main():
                     "d2h_bytes_per_step": int(hl.nbytes)},
             "gpu_launches": int(launches),
             "roofline": roofline_of(kstats, prof_bytes, peak, peak_kind, args.workload, t / args.steps),
-            "survey_model": survey_model(g, srcs, prof_bytes, t / args.steps, peak),
+            "product_byte_model": product_byte_model(g, srcs, prof_bytes, t / args.steps, peak),
             "gather_stats": {k: prof_bytes.get(k) for k in ("pairs_fwd", "pairs_bwd", "values_fwd", "values_bwd",
                                                             "fwd_iters", "bwd_iters", "batches")},
             "kernels_ms_share": {k: round(v["ms"] / sum(x["ms"] for x in kstats.values()), 4)

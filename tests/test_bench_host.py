@@ -32,12 +32,12 @@ def test_committed_traffic_entries_name_existing_sources():
         assert t["per_alg_byte"] >= 1.0                 # DRAM traffic cannot undercut the compulsory bytes
 
 
-def test_survey_model_terms_on_a_small_graph():
+def test_product_byte_model_terms_on_a_small_graph():
     # two components: a path 0-1-2-3 and an edge 4-5
     g = gg.from_edges(6, [(0, 1), (1, 2), (2, 3), (4, 5)], directed=False)
     srcs = np.array([0, 4], np.int32)
     prof = {"values_bwd": 7}
-    m = bench.survey_model(g, srcs, prof, step_s=1.0, peak_gbs=1.0)
+    m = bench.product_byte_model(g, srcs, prof, step_s=1.0, peak_gbs=1.0)
     R = 4 + 2                                            # reachable pairs, sources included
     F = 6 + 2                                            # arcs in each source's component
     D = 7
@@ -49,7 +49,7 @@ def test_survey_model_terms_on_a_small_graph():
     assert m["bytes_per_tep"] == pytest.approx(total / (len(srcs) * g.m))
     assert m["measured_over_model"] == pytest.approx(total / 1e9)
     w = gg.from_edges(3, [(0, 1), (1, 2)], directed=False, weights=[1, 2])
-    assert bench.survey_model(w, srcs[:1], prof, 1.0, 1.0) is None
+    assert bench.product_byte_model(w, srcs[:1], prof, 1.0, 1.0) is None
 
 
 def test_l2_note_follows_the_state_size():
