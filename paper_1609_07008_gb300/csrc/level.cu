@@ -29,15 +29,22 @@
 // and overwrites sv(s,v) with the frontier value zeta + 1/sigma_bar that its
 // predecessors gather one level later.
 //
-// Work decomposition: the adjacency rows are cut into items of at most
-// CHUNK = 32 arcs; one warp takes one item.  Lane k reads arc k, so a row's
-// neighbour ids arrive in one 128-byte load, membership is one bit test per
-// lane, and the frontier masks of the member neighbours are read as whole
-// 4*W-byte rows (lane = 32-column word).  The gather then walks the columns
-// word by word with lane = column, so each member's multiplicities are read
-// as one contiguous 256-byte segment per word.  Rows longer than one item
-// ("hubs") combine their items with atomics (sv for MFBF, a per-hub
-// accumulator for MFBr followed by a finalisation pass).
+// Work decomposition: the adjacency rows are cut into work items of at most
+// CHUNK = 32 arcs, and a product round is two kernels.  The pair kernel gives
+// a warp a group of items; lane k reads arc k of an item, membership of the
+// neighbour in the level is one bit test per lane, and the member
+// neighbours' frontier rows are read whole (lane = 32-column word).  For
+// every 128-column quad with a candidate it writes a segment header and one
+// pair record (neighbour row, 128-bit column mask) per member neighbour whose
+// mask is non-zero there.  The gather kernel takes segments in groups; per
+// pair, each lane owns four columns of the quad and issues one 32-byte load
+// (one DRAM sector) when its 4-bit slice of the mask is set, summing exact
+// 64-bit path counts (MFBF) or compensated double-float values (MFBr).  Rows
+// longer than one item ("hubs") combine their items with atomics (sv for
+// MFBF, a per-hub FP64 accumulator for MFBr finalised by k_lvl_hub_final).
+// Rounds are queued without host reads; a one-thread gate between the two
+// kernels turns a round whose pair buffers overflowed into a no-op for the
+// host to redo over halves of its items.
 #include <algorithm>
 
 #include "dfloat.cuh"
