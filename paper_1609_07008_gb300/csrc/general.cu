@@ -1,7 +1,12 @@
 // General path: MFBF (Algorithm 1) and MFBr (Algorithm 2) for any integer
-// weights >= 1, as sparse-frontier "push" products over the vertex-major
-// batch state.
+// weights >= 1 over the vertex-major batch state.  A product reduces the
+// candidates that meet at one (vertex, column) in one of three ways
+// (MFBC_ACCUM_*): pushed from the frontier with atomics at the targets (the
+// kernels right below), pulled per target row and reduced in registers
+// (segmented, further down), or pushed and first combined in a per-block
+// shared-memory hash table (hash, further down).
 //
+// Push form:
 // One warp owns one (frontier vertex u, 32-column word) pair; lane l is batch
 // column 32*word + l.  The warp walks u's arc list once, broadcasting 32 arcs
 // at a time by shuffle, and every lane whose column is in the frontier
